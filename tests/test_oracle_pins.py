@@ -1,0 +1,542 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each test fixes one part of the oracle with a closed form, an invariant, a
+library routine or a brute-force recomputation, chosen so that a dropped term,
+a wrong sign or index, or a transposed operand in that part fails it.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle
+import synth
+from tests import scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Eq. 1: projection of a 3D Gaussian
+# --------------------------------------------------------------------------
+
+def test_projection_matches_pinhole_derivative():
+    """Sigma_2D = J W Sigma_3D W^T J^T with J W the derivative of the pinhole map."""
+    base = S.base_cameras()
+    rng = np.random.default_rng(3)
+    cams = oracle.cameras(base)
+    for _ in range(20):
+        X = rng.uniform(-0.4, 0.4, 3)
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        s = np.exp(rng.normal(-3.5, 0.6, 3))
+        v = int(rng.integers(base.num_views))
+        mo = np.array([*X, 0.5], np.float32)
+        qf = q.astype(np.float32)
+        sf = np.array([*s, 0], np.float32)
+        m2, c2, conic = oracle.project(mo, qf, sf, cams[v])
+        Xf = mo[:3].astype(np.float64)
+        mu, C2 = S.projected(base, v, Xf, S.cov3d(qf, sf[:3].astype(np.float64)))
+        np.testing.assert_allclose(m2, mu, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(c2, [C2[0, 0], C2[0, 1], C2[1, 1]], rtol=1e-10,
+                                   atol=1e-12 * np.abs(C2).max())
+        # conic is the inverse of the dilated covariance
+        Cd = C2 + 0.3 * np.eye(2)
+        Ci = np.linalg.inv(Cd)
+        np.testing.assert_allclose(conic, [Ci[0, 0], Ci[0, 1], Ci[1, 1]], rtol=1e-9)
+
+
+def test_isotropic_gaussian_on_axis_closed_form():
+    """On the optical axis an isotropic Gaussian projects to (f s / z)^2 I."""
+    base = S.base_cameras()
+    v = 0
+    R = base.R[v].astype(np.float64)
+    C = -R.T @ base.t[v].astype(np.float64)
+    z = 2.7
+    X = C + z * R[2]
+    sc = 0.05
+    cams = oracle.cameras(base)
+    mo = np.array([*X, 0.8], np.float32)
+    m2, c2, _ = oracle.project(mo, np.array([1, 0, 0, 0], np.float32),
+                               np.array([sc, sc, sc, 0], np.float32), cams[v])
+    pz = R[2] @ (mo[:3].astype(np.float64) - C)
+    px = R[0] @ (mo[:3].astype(np.float64) - C)
+    expect = (128.0 * sc / pz) ** 2
+    assert abs(c2[1]) < 1e-6 * expect and abs(px) < 1e-6
+    np.testing.assert_allclose([c2[0], c2[2]], [expect, expect], rtol=1e-5)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.1 blending: closed forms and brute force (pin P1)
+# --------------------------------------------------------------------------
+
+def _on_axis_scene(depths, scales, opac, rgbs):
+    base = S.base_cameras()
+    R = base.R[0].astype(np.float64)
+    C = -R.T @ base.t[0].astype(np.float64)
+    means = [C + z * R[2] for z in depths]
+    n = len(depths)
+    quats = np.tile([1.0, 0, 0, 0], (n, 1))
+    sc = np.array([[s, s, s] for s in scales])
+    return S.with_gaussians(base.subset_views([0]), means, quats, sc, opac, rgbs)
+
+
+def test_single_gaussian_render_closed_form():
+    sc, z, o = 0.04, 2.8, 0.8
+    rgb = [0.2, 0.6, 0.9]
+    scene = _on_axis_scene([z], [sc], [o], [rgb])
+    col, T, _ = oracle.render(scene)
+    mo = scene.means_opacity[0]
+    R = scene.R[0].astype(np.float64)
+    pz = R[2] @ (mo[:3].astype(np.float64) + R.T @ scene.t[0].astype(np.float64))
+    var = (128.0 * float(scene.scales[0, 0]) / pz) ** 2 + 0.3
+    x = S.pixel_centres(scene, 0) - np.array([64.0, 64.0])
+    alpha = float(mo[3]) * np.exp(-0.5 * (x ** 2).sum(-1) / var)
+    alpha = np.minimum(alpha, float(np.float32(0.99)))
+    keep = alpha >= float(np.float32(1 / 255))
+    # radius of the tile rectangle: ceil(3 sqrt(lambda_max)) in pixels
+    r = math.ceil(3 * math.sqrt(var))
+    inrect = np.zeros_like(keep)
+    lo, hi = int((64 - r) // 16), int((64 + r) // 16) + 1
+    inrect[lo * 16:hi * 16, lo * 16:hi * 16] = True
+    a = np.where(keep & inrect, alpha, 0.0)
+    np.testing.assert_allclose(T[0], 1 - a, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(col[0], a[..., None] * np.array(rgb), rtol=0, atol=1e-6)
+
+
+def test_two_gaussians_composite_in_depth_order():
+    """colour = a1 c1 + (1 - a1) a2 c2, T = (1 - a1)(1 - a2); the nearer one first."""
+    scene = _on_axis_scene([3.1, 2.6], [0.05, 0.03], [0.7, 0.6], [[1, 0, 0], [0, 0, 1]])
+    col, T, _ = oracle.render(scene)
+    c = np.array([[64.0, 64.0]])
+    pix = (64, 64)   # pixel centre (64.5, 64.5)
+    d2 = ((np.array([64.5, 64.5]) - c) ** 2).sum()
+    R = scene.R[0].astype(np.float64)
+    Cc = -R.T @ scene.t[0].astype(np.float64)
+    alphas = []
+    for g in range(2):
+        mo = scene.means_opacity[g]
+        pz = R[2] @ (mo[:3].astype(np.float64) - Cc)
+        var = (128.0 * float(scene.scales[g, 0]) / pz) ** 2 + 0.3
+        alphas.append(float(mo[3]) * math.exp(-0.5 * d2 / var))
+    a_far, a_near = alphas           # Gaussian 1 is nearer (depth 2.6)
+    expect_T = (1 - a_near) * (1 - a_far)
+    expect_c = a_near * np.array([0, 0, 1.0]) + (1 - a_near) * a_far * np.array([1.0, 0, 0])
+    assert abs(T[0][pix] - expect_T) < 1e-7
+    np.testing.assert_allclose(col[0][pix], expect_c, atol=1e-6)
+
+
+def test_tiled_render_equals_bruteforce_with_rect():
+    s = synth.make_scene("tiny", seed=5)
+    rgb, T, _ = oracle.render(s)
+    for v in range(s.num_views):
+        bc, bT = oracle.render_bruteforce(s, v, use_rect=True)
+        assert np.array_equal(bc, rgb[v]) and np.array_equal(bT, T[v])
+
+
+def test_tiled_render_equals_bruteforce_without_rect_when_tails_vanish():
+    """With opacity < 0.353 every pixel outside a Gaussian's 3-sigma tile
+    rectangle has alpha < 1/255, so dropping the rectangle changes nothing."""
+    s = synth.make_scene("tiny", seed=6)
+    s.means_opacity[:, 3] *= 0.35
+    rgb, T, _ = oracle.render(s)
+    for v in range(s.num_views):
+        bc, bT = oracle.render_bruteforce(s, v, use_rect=False)
+        assert np.array_equal(bc, rgb[v]) and np.array_equal(bT, T[v])
+
+
+def test_colour_basis_is_orthonormal():
+    """The 16 colour basis functions are orthonormal on the unit sphere."""
+    n = 64
+    th = (np.arange(n) + 0.5) * np.pi / n
+    ph = (np.arange(2 * n) + 0.5) * np.pi / n
+    G = np.zeros((16, 16))
+    for t in th:
+        for p in ph:
+            d = [math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)]
+            Y = oracle.sh_basis(d)
+            G += np.outer(Y, Y) * math.sin(t) * (np.pi / n) ** 2
+    np.testing.assert_allclose(G, np.eye(16), atol=2e-3)
+
+
+# --------------------------------------------------------------------------
+# Key path and binning (pin P10)
+# --------------------------------------------------------------------------
+
+def test_keypath_agrees_with_fp64_geometry():
+    s = synth.make_scene("tiny", seed=2, tracks=False)
+    k = oracle.keys(s)
+    cams = oracle.cameras(s)
+    for v in range(s.num_views):
+        R = s.R[v].astype(np.float64)
+        p = s.means_opacity[:, :3].astype(np.float64) @ R.T + s.t[v].astype(np.float64)
+        vis = k["visible"][v] == 1
+        assert vis.mean() > 0.9
+        depth = k["depth_bits"][v][vis].view(np.float32).astype(np.float64)
+        np.testing.assert_allclose(depth, p[vis, 2], rtol=1e-6)
+        for g in np.nonzero(vis)[0][:200]:
+            m2, c2, _ = oracle.project(s.means_opacity[g], s.quats[g], s.scales[g], cams[v])
+            Cd = np.array([[c2[0], c2[1]], [c2[1], c2[2]]]) + 0.3 * np.eye(2)
+            lam = np.linalg.eigvalsh(Cd).max()
+            r = math.ceil(3 * math.sqrt(lam))
+            x0, y0, x1, y1 = k["rect"][v, g]
+            ex0 = max(0, math.floor((m2[0] - r) / 16))
+            ex1 = min(8, math.floor((m2[0] + r) / 16) + 1)
+            ey0 = max(0, math.floor((m2[1] - r) / 16))
+            ey1 = min(8, math.floor((m2[1] + r) / 16) + 1)
+            assert abs(x0 - ex0) <= 1 and abs(x1 - ex1) <= 1 and abs(y0 - ey0) <= 1 and abs(y1 - ey1) <= 1
+            assert k["tiles_touched"][v, g] == (x1 - x0) * (y1 - y0)
+
+
+def test_tile_lists_match_lexsort():
+    """Per-tile lists equal a numpy lexsort of (tile, depth bits, index)."""
+    s = synth.make_scene("tiny", seed=3, tracks=False)
+    k = oracle.keys(s)
+    offsets, entries = oracle.bin_lists(s)
+    tiles, depths, ids = [], [], []
+    for v in range(s.num_views):
+        for g in np.nonzero(k["visible"][v])[0]:
+            x0, y0, x1, y1 = k["rect"][v, g]
+            for ty in range(y0, y1):
+                for tx in range(x0, x1):
+                    tiles.append(v * 64 + ty * 8 + tx)
+                    depths.append(int(k["depth_bits"][v, g]))
+                    ids.append(int(g))
+    tiles, depths, ids = map(np.array, (tiles, depths, ids))
+    order = np.lexsort((ids, depths, tiles))
+    expect = (depths[order].astype(np.uint64) << np.uint64(32)) | ids[order].astype(np.uint64)
+    assert np.array_equal(entries, expect)
+    counts = np.bincount(tiles, minlength=4 * 64)
+    assert np.array_equal(np.diff(offsets), counts)
+
+
+# --------------------------------------------------------------------------
+# Eq. 3 == Eq. 4 (pin P2), view-solve thresholds (pin P11)
+# --------------------------------------------------------------------------
+
+def test_weighted_incremental_ls_equals_naive_ls():
+    """The render's moment-based solve equals Eq. 3 built from explicit X, Y.
+
+    One opaque-colour Gaussian alone in view 0: its rendered colour is alpha,
+    which is the per-pixel weight w = alpha T with T = 1."""
+    base = S.base_cameras()
+    scene = S.with_gaussians(base, [[0.05, -0.02, 0.03]], [[0.9, 0.2, -0.3, 0.1]],
+                             [[0.06, 0.03, 0.045]], [0.9], [[1.0, 1.0, 1.0]])
+    rng = np.random.default_rng(0)
+    for v in range(scene.num_views):
+        scene.disp[v] = rng.normal(0, 2.0, scene.disp[v].shape).astype(np.float32)
+        scene.vis[v] = (rng.uniform(size=scene.vis[v].shape) > 0.2).astype(np.uint8)
+    col, _, _ = oracle.render(scene)
+    res = oracle.fit_motion(scene)
+    for v in range(scene.num_views):
+        w = col[v][..., 0].astype(np.float64)
+        m = (w > 0) & (scene.vis[v] == 1)
+        x = S.pixel_centres(scene, v)[m]
+        xp = x + scene.disp[v][m].astype(np.float64)
+        # colour is stored as FP32; recompute the exact weights from the moments' sum
+        A, b = oracle.naive_ls(x, xp, w[m])
+        aff = res["view_affine"][0 if False else v, 0]
+        assert res["view_flags"][v, 0] == oracle.OV_OK
+        np.testing.assert_allclose(aff[:4], A.ravel(), rtol=0, atol=1e-6)
+        np.testing.assert_allclose(aff[4:], b, rtol=0, atol=1e-4)
+        assert res["moments"][v, 0, 13] == m.sum()
+
+
+def test_naive_ls_recovers_exact_affine_and_matches_moment_solve():
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        n = int(rng.integers(3, 200))
+        x = rng.uniform(0, 100, (n, 2))
+        A = np.eye(2) + rng.normal(0, 0.1, (2, 2))
+        b = rng.normal(0, 5, 2)
+        w = rng.uniform(0.01, 1, n)
+        xp = x @ A.T + b + rng.normal(0, 0.5, (n, 2))
+        An, bn = oracle.naive_ls(x, xp, w)
+        # same problem through the moment record and the per-view solve
+        mu = rng.uniform(0, 100, 2)
+        xt = x - mu
+        xpt = xp - mu
+        M = np.zeros(16)
+        M[0] = (w * xt[:, 0] ** 2).sum(); M[1] = (w * xt[:, 0] * xt[:, 1]).sum()
+        M[2] = (w * xt[:, 0]).sum(); M[3] = (w * xt[:, 1] ** 2).sum()
+        M[4] = (w * xt[:, 1]).sum(); M[5] = w.sum()
+        M[6] = (w * xt[:, 0] * xpt[:, 0]).sum(); M[7] = (w * xt[:, 0] * xpt[:, 1]).sum()
+        M[8] = (w * xt[:, 1] * xpt[:, 0]).sum(); M[9] = (w * xt[:, 1] * xpt[:, 1]).sum()
+        M[10] = (w * xpt[:, 0]).sum(); M[11] = (w * xpt[:, 1]).sum(); M[13] = n
+        fl, aff, mn, _ = oracle.view_solve(M, mu, [1.0, 0.0, 1.0])
+        assert fl == oracle.OV_OK
+        np.testing.assert_allclose(aff[:4], An.ravel(), rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(aff[4:], bn, rtol=1e-9, atol=1e-9)
+        # weighted least squares via numpy's lstsq on sqrt(w)-scaled rows
+        X = np.c_[x, np.ones(n)] * np.sqrt(w)[:, None]
+        Z = np.linalg.lstsq(X, xp * np.sqrt(w)[:, None], rcond=None)[0]
+        np.testing.assert_allclose(An, Z[:2].T, rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(bn, Z[2], rtol=1e-9, atol=1e-9)
+        # mu_2D' = A mu + b and Sigma_2D' = A Sigma A^T (Eq. 2)
+        np.testing.assert_allclose(mn, An @ mu + bn, rtol=1e-9, atol=1e-8)
+
+
+def _moments_from_pixels(px, w, mu=(0.0, 0.0), d=None):
+    px = np.asarray(px, np.float64) - mu
+    w = np.asarray(w, np.float64)
+    d = np.zeros_like(px) if d is None else np.asarray(d, np.float64)
+    xp = px + d
+    M = np.zeros(16)
+    M[0] = (w * px[:, 0] ** 2).sum(); M[1] = (w * px[:, 0] * px[:, 1]).sum(); M[2] = (w * px[:, 0]).sum()
+    M[3] = (w * px[:, 1] ** 2).sum(); M[4] = (w * px[:, 1]).sum(); M[5] = w.sum()
+    M[6] = (w * px[:, 0] * xp[:, 0]).sum(); M[7] = (w * px[:, 0] * xp[:, 1]).sum()
+    M[8] = (w * px[:, 1] * xp[:, 0]).sum(); M[9] = (w * px[:, 1] * xp[:, 1]).sum()
+    M[10] = (w * xp[:, 0]).sum(); M[11] = (w * xp[:, 1]).sum(); M[13] = len(w)
+    return M
+
+
+def test_view_thresholds_by_construction():
+    """Sec. 5.1: < 2 px, accumulated alpha < 1e-3, det V1 < 1e-12 are unsolvable."""
+    C = [1.0, 0.0, 1.0]
+    one = _moments_from_pixels([[0.5, 0.5]], [0.5])
+    assert oracle.view_solve(one, [0, 0], C)[0] & oracle.OV_FEW_PX
+    two = _moments_from_pixels([[0.5, 0.5], [1.5, 0.5]], [0.5, 0.5])
+    assert oracle.view_solve(two, [0, 0], C)[0] == oracle.OV_SINGULAR
+    line = _moments_from_pixels([[0.5, 0.5], [1.5, 0.5], [2.5, 0.5]], [0.5, 0.4, 0.3])
+    assert oracle.view_solve(line, [0, 0], C)[0] == oracle.OV_SINGULAR
+    ell = _moments_from_pixels([[0.5, 0.5], [1.5, 0.5], [0.5, 1.5]], [0.5, 0.5, 0.5])
+    assert oracle.view_solve(ell, [0, 0], C)[0] == oracle.OV_OK
+    faint = _moments_from_pixels([[0.5, 0.5], [1.5, 0.5], [0.5, 1.5]], [3e-4, 3e-4, 3e-4])
+    assert oracle.view_solve(faint, [0, 0], C)[0] == oracle.OV_LOW_ALPHA
+    # det V1 = (sum w)^3 det(scatter) = (3w)^3 / 27 for this L-shape: the det
+    # threshold alone decides once the accumulated-alpha test is switched off.
+    lo = oracle.default_options()
+    lo.sumw_min_view = 0.0
+    for w, expect in [(5e-5, oracle.OV_SINGULAR), (2e-4, oracle.OV_OK)]:
+        M = _moments_from_pixels([[0.5, 0.5], [1.5, 0.5], [0.5, 1.5]], [w] * 3)
+        det = np.linalg.det(np.array([[M[0], M[1], M[2]], [M[1], M[3], M[4]], [M[2], M[4], M[5]]]))
+        assert (det < 1e-12) == (expect == oracle.OV_SINGULAR)
+        assert oracle.view_solve(M, [0, 0], C, lo)[0] == expect
+
+
+def test_multiview_thresholds_by_construction():
+    """Sec. 5.1: < 2 views, accumulated alpha < 1e-3, < 3 px over views fail."""
+    base = S.base_cameras()
+    X = np.array([0.02, -0.03, 0.01])
+    q = np.array([0.8, 0.1, 0.5, -0.3])
+    q /= np.linalg.norm(q)
+    s = [0.05, 0.03, 0.04]
+    scene = S.with_gaussians(base, [X], [q], [s], [0.9])
+    Sg = S.cov3d(scene.quats[0], scene.scales[0, :3].astype(np.float64))
+    Xf = scene.means_opacity[0, :3].astype(np.float64)
+    mn, cn = [], []
+    for v in range(4):
+        mu, C2 = S.projected(scene, v, Xf, Sg)
+        mn.append(mu)
+        cn.append([C2[0, 0], C2[0, 1], C2[1, 1]])
+    mn, cn = np.array(mn), np.array(cn)
+    ok = [oracle.OV_OK] * 4
+    r = oracle.multiview(scene, 0, ok, [0.5] * 4, [10] * 4, mn, cn)
+    assert r["status"] & oracle.OS_POS_OK and r["status"] & oracle.OS_COV_OK
+    assert (r["status"] >> 16) == 4
+    np.testing.assert_allclose(r["mean"], Xf, atol=1e-10)
+    r = oracle.multiview(scene, 0, [1, 8, 8, 8], [0.5] * 4, [10] * 4, mn, cn)
+    assert r["status"] & oracle.OS_FEW_VIEWS and not r["status"] & oracle.OS_POS_OK
+    r = oracle.multiview(scene, 0, ok, [2e-4] * 4, [10] * 4, mn, cn)
+    assert r["status"] & oracle.OS_LOW_ALPHA and not r["status"] & oracle.OS_POS_OK
+    r = oracle.multiview(scene, 0, [1, 1, 8, 8], [0.5] * 4, [1, 1, 10, 10], mn, cn)
+    assert r["status"] & oracle.OS_FEW_PX and not r["status"] & oracle.OS_POS_OK
+    np.testing.assert_allclose(r["mean"], Xf)           # unsolvable keeps its input
+
+
+def test_paper_thresholds_golden():
+    with open(os.path.join(GOLDEN, "paper_thresholds.json")) as f:
+        g = json.load(f)
+    o = oracle.default_options()
+    assert o.det_min == g["view"]["det_V1_min"]["value"]
+    assert o.sumw_min_view == g["view"]["accumulated_alpha_min"]["value"]
+    assert o.min_px_view == g["view"]["pixels_min"]["value"]
+    assert o.min_views == g["multiview"]["views_min"]["value"]
+    assert o.sumw_min_total == g["multiview"]["accumulated_alpha_min"]["value"]
+    assert o.min_px_total == g["multiview"]["pixels_min"]["value"]
+
+
+# --------------------------------------------------------------------------
+# Library routines (pins P8, P9)
+# --------------------------------------------------------------------------
+
+def test_lstsq_matches_numpy():
+    rng = np.random.default_rng(4)
+    for m, n in [(4, 3), (12, 3), (36, 6), (9, 6)]:
+        A = rng.normal(size=(m, n)) * np.exp(rng.normal(0, 1, n))
+        b = rng.normal(size=m)
+        x, rc = oracle.lstsq(A, b)
+        xn = np.linalg.lstsq(A, b, rcond=None)[0]
+        sv = np.linalg.svd(A, compute_uv=False)
+        np.testing.assert_allclose(x, xn, rtol=1e-10, atol=1e-12)
+        assert abs(rc - sv.min() / sv.max()) < 1e-10 * max(1.0, rc)
+
+
+def test_eig3_matches_numpy():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        Q = Rotation.random(random_state=rng).as_matrix()
+        lam = np.exp(rng.normal(-8, 2, 3))
+        Sm = Q @ np.diag(lam) @ Q.T
+        l, E = oracle.eig3(Sm)
+        ln = np.linalg.eigvalsh(Sm)
+        np.testing.assert_allclose(np.sort(l), ln, rtol=1e-10, atol=1e-14 * lam.max())
+        np.testing.assert_allclose(E @ np.diag(l) @ E.T, Sm, atol=1e-12 * lam.max())
+        np.testing.assert_allclose(E.T @ E, np.eye(3), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Whole-chain closed forms (pins P3, P4, P6, P7) and invariance (P5)
+# --------------------------------------------------------------------------
+
+def _angle(Ra, Rb):
+    c = (np.trace(Ra.T @ Rb) - 1) / 2
+    return math.acos(max(-1.0, min(1.0, c)))
+
+
+def _exact_tracks(scene, g_motion, radius_pad=1.0):
+    """Paint, per view, each Gaussian's exact Eq. 2 affine inside its footprint."""
+    n = scene.n
+    for v in range(scene.num_views):
+        scene.disp[v][:] = 0
+        owner = np.full(scene.disp[v].shape[:2], -1)
+        for g in range(n):
+            X = scene.means_opacity[g, :3].astype(np.float64)
+            Sg = S.cov3d(scene.quats[g], scene.scales[g, :3].astype(np.float64))
+            Rm, tm = g_motion
+            X2 = Rm @ X + tm
+            S2 = Rm @ Sg @ Rm.T
+            mu, C = S.projected(scene, v, X, Sg)
+            mu2, C2 = S.projected(scene, v, X2, S2)
+            A, b = S.affine_between(mu, C, mu2, C2)
+            r = S.footprint_radius(C, float(scene.means_opacity[g, 3])) + radius_pad
+            d2 = ((S.pixel_centres(scene, v) - mu) ** 2).sum(-1)
+            m = d2 <= r * r
+            assert not (owner[m] >= 0).any(), "footprints overlap"
+            owner[m] = g
+            S.paint_affine(scene, v, A, b, m)
+    return scene
+
+
+def test_single_gaussian_translation_is_recovered_exactly():
+    base = S.base_cameras()
+    q = np.array([0.7, 0.3, -0.4, 0.5])
+    q /= np.linalg.norm(q)
+    scene = S.with_gaussians(base, [[0.05, -0.03, 0.02]], [q], [[0.06, 0.04, 0.03]], [0.99])
+    tm = np.array([0.02, -0.01, 0.015])
+    _exact_tracks(scene, (np.eye(3), tm))
+    r = oracle.fit_motion(scene)
+    st = int(r["out_status"][0])
+    assert st & oracle.OS_POS_OK and st & oracle.OS_COV_OK, hex(st)
+    X = scene.means_opacity[0, :3].astype(np.float64)
+    # Tracks are stored in FP32 (relative rounding ~6e-8 of a few pixels), which
+    # bounds how exactly the affine, and everything after it, can be recovered.
+    np.testing.assert_allclose(r["out_mean"][0], X + tm, atol=1e-8)
+    Sg = S.cov3d(scene.quats[0], scene.scales[0, :3].astype(np.float64))
+    c = r["out_cov3d"][0]
+    Sf = np.array([[c[0], c[1], c[2]], [c[1], c[3], c[4]], [c[2], c[4], c[5]]])
+    np.testing.assert_allclose(Sf, Sg, rtol=0, atol=1e-7 * np.abs(Sg).max())
+    np.testing.assert_allclose(r["out_scale"][0], scene.scales[0, :3], rtol=1e-7)
+    assert _angle(S.rotmat(r["out_quat"][0]), S.rotmat(scene.quats[0])) < 1e-6
+
+
+def test_separated_gaussians_rigid_motion_is_recovered_exactly():
+    base = S.base_cameras()
+    rng = np.random.default_rng(11)
+    # footprints at least 4.6 px apart in every view (checked by _exact_tracks)
+    means = np.array([[0.292, -0.143, -0.234], [-0.191, -0.444, 0.173], [0.09, 0.256, -0.249],
+                      [-0.139, -0.421, -0.267], [0.308, 0.009, 0.285]])
+    n = len(means)
+    quats = Rotation.random(n, random_state=rng).as_quat()[:, [3, 0, 1, 2]]
+    scales = np.exp(rng.normal(-4.0, 0.25, (n, 3)))
+    scene = S.with_gaussians(base, means, quats, scales, np.full(n, 0.95))
+    Rm = Rotation.from_rotvec(np.radians(15) * np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])).as_matrix()
+    tm = np.array([0.03, 0.02, -0.04])
+    _exact_tracks(scene, (Rm, tm))
+    r = oracle.fit_motion(scene)
+    for g in range(n):
+        st = int(r["out_status"][g])
+        assert st & oracle.OS_POS_OK and st & oracle.OS_COV_OK, (g, hex(st))
+        X = scene.means_opacity[g, :3].astype(np.float64)
+        np.testing.assert_allclose(r["out_mean"][g], Rm @ X + tm, atol=1e-8)
+        np.testing.assert_allclose(r["out_scale"][g], scene.scales[g, :3], rtol=1e-6)
+        Rexp = Rm @ S.rotmat(scene.quats[g])
+        assert _angle(S.rotmat(r["out_quat"][g]), Rexp) < 1e-6
+
+
+def test_zero_tracks_leave_gaussians_unchanged():
+    s = synth.make_scene("tiny", seed=4)
+    for v in range(s.num_views):
+        s.disp[v][:] = 0
+        s.vis[v][:] = 1
+    r = oracle.fit_motion(s)
+    st = r["out_status"]
+    ok = (st & oracle.OS_POS_OK) > 0
+    assert ok.mean() > 0.9
+    X = s.means_opacity[:, :3].astype(np.float64)
+    np.testing.assert_allclose(r["out_mean"][ok], X[ok], atol=1e-9)
+    vf = r["view_flags"] == oracle.OV_OK
+    aff = r["view_affine"][vf]
+    np.testing.assert_allclose(aff[:, :4], np.tile([1, 0, 0, 1.0], (aff.shape[0], 1)), atol=1e-9)
+    np.testing.assert_allclose(aff[:, 4:], 0, atol=1e-7)
+    cov = (st & oracle.OS_COV_OK) > 0
+    assert cov.mean() > 0.9
+    np.testing.assert_allclose(r["out_scale"][cov], s.scales[cov, :3], rtol=1e-6)
+    for g in np.nonzero(cov)[0][:300]:
+        assert _angle(S.rotmat(r["out_quat"][g]), S.rotmat(s.quats[g])) < 1e-6
+        q = s.quats[g].astype(np.float64)
+        assert np.dot(r["out_quat"][g], q / np.linalg.norm(q)) > 0
+
+
+def test_constant_displacement_gives_identity_and_offset():
+    s = synth.make_scene("tiny", seed=7)
+    c = np.array([1.5, -0.7], np.float32)
+    for v in range(s.num_views):
+        s.disp[v][:] = c
+        s.vis[v][:] = 1
+    r = oracle.fit_motion(s)
+    vf = r["view_flags"] == oracle.OV_OK
+    aff = r["view_affine"][vf]
+    np.testing.assert_allclose(aff[:, :4], np.tile([1, 0, 0, 1.0], (aff.shape[0], 1)), atol=1e-9)
+    np.testing.assert_allclose(aff[:, 4:], np.tile(c, (aff.shape[0], 1)), atol=1e-7)
+    np.testing.assert_allclose(r["view_mean2d"][vf], r["mean2d"][vf] + c, atol=1e-7)
+
+
+def test_rigid_invariance():
+    """Moving Gaussians and cameras by one rigid transform (tracks kept) moves the
+    fitted Gaussians by that transform."""
+    s = synth.make_scene("tiny", seed=8)
+    Rg = Rotation.from_rotvec([0.3, -0.2, 0.5]).as_matrix()
+    tg = np.array([0.2, -0.1, 0.05])
+    s2 = S.rigid_apply(s, Rg, tg)
+    k1, k2 = oracle.keys(s), oracle.keys(s2)
+    same_keys = (k1["rect"] == k2["rect"]).all(-1) & (k1["visible"] == k2["visible"])
+    assert same_keys.mean() > 0.999
+    r1, r2 = oracle.fit_motion(s), oracle.fit_motion(s2)
+    both = ((r1["out_status"] & 3) == 3) & ((r2["out_status"] & 3) == 3)
+    assert both.mean() > 0.9
+    assert (r1["out_status"] == r2["out_status"]).mean() > 0.99
+    m1 = r1["out_mean"][both] @ Rg.T + tg
+    err = np.linalg.norm(m1 - r2["out_mean"][both], axis=1)
+    assert np.median(err) < 1e-6 and np.quantile(err, 0.99) < 1e-4
+    rel = np.abs(r1["out_scale"][both] / r2["out_scale"][both] - 1)
+    assert np.median(rel) < 1e-5
+    ang = [_angle(Rg @ S.rotmat(a), S.rotmat(b)) for a, b in
+           zip(r1["out_quat"][both][:300], r2["out_quat"][both][:300])]
+    assert np.median(ang) < 1e-5
+
+
+def test_ground_truth_accuracy_report():
+    """Quality, not parity: with tracker-like tracks the fit moves Gaussians
+    toward their ground-truth positions (dense scenes mix motions, so this is
+    a loose bound)."""
+    s = synth.make_scene("tiny", seed=1)
+    r = oracle.fit_motion(s)
+    ok = (r["out_status"] & 1) > 0
+    gt = s.gt_means()
+    e_fit = np.linalg.norm(r["out_mean"][ok] - gt[ok], axis=1)
+    e_still = np.linalg.norm(s.means_opacity[ok, :3] - gt[ok], axis=1)
+    assert np.median(e_fit) < np.median(e_still)
