@@ -1,0 +1,220 @@
+/*
+ * tsplat.h -- C ABI of libtsplat.so: the TrackerSplat motion-compensation hot path
+ * (arXiv 2604.02586, Sec. 4.2-4.4) on one NVIDIA B300 (sm_103a).
+ *
+ * Problem statement (Sec. 4.1, 4.3.1, 4.4): frame-0 3D Gaussians, calibrated
+ * cameras and, per view, a dense track x -> x' for every pixel go in; every
+ * Gaussian comes out relocated, rotated and rescaled, with a status word.
+ *
+ * Conventions shared by every entry point
+ *   - Camera: world -> camera p = R X + t (R row-major), +z forward; pixel (i, j)
+ *     (column i, row j) has centre (i + 0.5, j + 0.5); u = fx p_x / p_z + cx.
+ *   - Gaussian: mean, opacity in (0,1), quaternion (w, x, y, z) (need not be unit),
+ *     linear scales > 0; Sigma_3D = R(q) diag(s^2) R(q)^T (Sec. 3.1).
+ *   - Images are row-major [H][W]; tracks are x' - x in pixels (FP32 pairs).
+ *   - "device" pointers are CUDA device (or managed) memory on the context's device,
+ *     "host" pointers are ordinary CPU memory.  The caller owns every buffer passed
+ *     in; the context owns its workspace (per-view records, tile lists, moments).
+ *   - Every call returns a tsp_status and never throws.  Argument errors are
+ *     reported synchronously, before any work is enqueued.  Work is enqueued on
+ *     the caller's stream (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream); device-side conditions (pair-buffer overflow) are latched in a
+ *     device status word that tsp_sync() reports.
+ *   - A context is not thread-safe: use one context per host thread.  Two calls
+ *     on one context must not overlap on the GPU (the workspace is shared); the
+ *     library does not order them for you if they use different streams.
+ */
+#ifndef TSPLAT_H
+#define TSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSP_VERSION 1
+#define TSP_MAX_VIEWS 32
+#define TSP_MAX_IMAGE 8192
+
+typedef enum {
+    TSP_OK = 0,
+    TSP_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or option     */
+    TSP_ERR_OOM = 2,           /* workspace allocation failed                */
+    TSP_ERR_CUDA = 3,          /* a CUDA runtime call failed (see last error) */
+    TSP_ERR_TIMEOUT = 4,       /* tsp_sync gave up before the work finished  */
+    TSP_ERR_BUDGET = 5,        /* workspace would exceed the context budget  */
+    TSP_ERR_OVERFLOW = 6       /* more (tile, Gaussian) pairs than capacity  */
+} tsp_status;
+
+/* Per-view flags (tsp_result.view_flags) -- Sec. 4.3.5 and Sec. 5.1. */
+#define TSP_VIEW_OK 1u          /* affine solved in this view                      */
+#define TSP_VIEW_FEW_PX 2u      /* fewer than min_px_view pixels added moments     */
+#define TSP_VIEW_LOW_ALPHA 4u   /* accumulated alpha (sum of w) < sumw_min_view    */
+#define TSP_VIEW_SINGULAR 8u    /* det V1 < det_min or pixel scatter too thin      */
+#define TSP_VIEW_CULLED 16u     /* behind the near plane, off-frustum or no tile   */
+
+/* Per-Gaussian status bits (tsp_result.status) -- Sec. 4.4 and Sec. 5.1.
+ * Bits 16..23 hold the number of views whose affine was solved. */
+#define TSP_POS_OK 1u           /* mu_3D' triangulated                             */
+#define TSP_COV_OK 2u           /* Sigma_3D' fitted, rotation and scale updated    */
+#define TSP_NEG_EIG 4u          /* Sigma_3D' had an eigenvalue <= 0 (Sec. 4.4.3)   */
+#define TSP_FEW_VIEWS 8u        /* fewer than min_views solved views               */
+#define TSP_LOW_ALPHA 16u       /* accumulated alpha over views < sumw_min_total   */
+#define TSP_FEW_PX 32u          /* fewer than min_px_total pixels over views       */
+#define TSP_COV_SINGULAR 64u    /* covariance system rank-deficient                */
+#define TSP_TRI_SINGULAR 128u   /* triangulation system rank-deficient             */
+
+typedef struct tsp_camera {
+    int32_t width, height;      /* pixels, 1..TSP_MAX_IMAGE                        */
+    float fx, fy, cx, cy;       /* pinhole intrinsics in pixels, fx, fy > 0        */
+    float R[9];                 /* world -> camera rotation, row-major             */
+    float t[3];                 /* world -> camera translation                     */
+} tsp_camera;
+
+typedef struct tsp_gaussians {
+    int32_t n;                  /* number of Gaussians, 0 <= n < 2^31              */
+    const float* means_opacity; /* [n][4] (x, y, z, opacity); 16-byte aligned      */
+    const float* quats;         /* [n][4] (w, x, y, z); 16-byte aligned            */
+    const float* scales;        /* [n][4] (sx, sy, sz, unused), linear; 16-byte al. */
+} tsp_gaussians;
+
+typedef struct tsp_view_tracks {
+    const float* disp;          /* [H][W][2] tracked x' - x in pixels; 8-byte al.  */
+    const uint8_t* vis;         /* [H][W] non-zero = the track is valid            */
+} tsp_view_tracks;
+
+typedef struct tsp_result {
+    float* means;               /* [n][4] new (x, y, z, opacity unchanged)         */
+    float* quats;               /* [n][4] new (w, x, y, z), unit                   */
+    float* scales;              /* [n][4] new (sx, sy, sz, 0)                      */
+    uint32_t* status;           /* [n] TSP_* bits                                  */
+    float* view_affine;         /* optional [V][n][6]: A00 A01 A10 A11 b0 b1 (Eq. 2) */
+    float* view_moments;        /* optional [V][n][16] PWI-LS moments, see below    */
+    uint32_t* view_flags;       /* optional [V][n] TSP_VIEW_* bits                 */
+} tsp_result;
+/* view_moments layout, coordinates are pixel centre minus mu_2D (x~, y~) and the
+ * tracked displacement d = x' - x, w = alpha T (Eq. 4):
+ *   0 sum w            1 sum w x~         2 sum w y~        3 sum w x~^2
+ *   4 sum w x~ y~      5 sum w y~^2       6 sum w dx        7 sum w dy
+ *   8 sum w x~ dx      9 sum w x~ dy     10 sum w y~ dx    11 sum w y~ dy
+ *  12 sum w over static pixels (|d| < 1)  13 pixels added    14 static pixels  15 0
+ * Eq. 4's V1 and V2 follow: V1 = [[3,4,1],[4,5,2],[1,2,0]] and
+ * V2 = V1[:, 0:2] + [[8,9],[10,11],[6,7]] in this (x~, y~, 1) basis. */
+
+typedef struct tsp_options {
+    int32_t tile_w, tile_h;     /* raster tile; 16 x 16 is the only supported value */
+    float det_min;              /* Sec. 5.1: 1e-12                                 */
+    float sumw_min_view;        /* Sec. 5.1: 1e-3                                  */
+    int32_t min_px_view;        /* Sec. 5.1: 2                                     */
+    float lam_min_px2;          /* thin-pixel-set guard: 1e-4 px^2                 */
+    int32_t min_views;          /* Sec. 5.1: 2                                     */
+    float sumw_min_total;       /* Sec. 5.1: 1e-3                                  */
+    int32_t min_px_total;       /* Sec. 5.1: 3                                     */
+    float cov_rcond_min;        /* covariance system conditioning floor: 1e-10     */
+    int32_t async_pairs;        /* 0: tsp_fit_motion waits for the pair count and  */
+                                /*    grows the pair buffer before sorting;        */
+                                /* 1: never waits; overflow -> TSP_ERR_OVERFLOW at  */
+                                /*    tsp_sync, capacity grows for the next call   */
+    int32_t stage_timing;       /* 1: record CUDA events between the steps of each  */
+                                /*    call; read them with tsp_stage_times          */
+    int32_t collect_stats;      /* 1: the raster step also counts its work (slower; */
+                                /*    for measurement only), see TSP_I_STATS        */
+    int32_t reserved;
+    int64_t pair_capacity;      /* initial (tile, Gaussian) pair capacity, 0 = auto */
+    int64_t budget_bytes;       /* workspace ceiling, 0 = unlimited                */
+} tsp_options;
+
+typedef struct tsp_context tsp_context;
+
+/* Fill *out with the defaults above.  Errors: INVALID_ARG if out is NULL. */
+tsp_status tsp_default_options(tsp_options* out);
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * Errors: INVALID_ARG (bad option), CUDA (device unusable).  *out is set to NULL
+ * on failure. */
+tsp_status tsp_create(int device, const tsp_options* opt, tsp_context** out);
+
+/* Free the workspace and the context (synchronizes the device). NULL is a no-op. */
+tsp_status tsp_destroy(tsp_context* ctx);
+
+/* The motion-compensation step (Sec. 4.2-4.4), enqueued on `stream`:
+ *   a1 project every (view, Gaussian) (Eq. 1), cull, key = (tile, depth);
+ *   a2 count and emit (tile, Gaussian) pairs; a3 sort each tile's list by depth;
+ *   a5 blend front to back per pixel and add w = alpha T weighted track moments
+ *      per Gaussian (Eq. 4, Sec. 4.3.5);
+ *   a6 per (view, Gaussian): discard tests (Sec. 5.1), [A|b] = V1^-1 V2 (Eq. 4),
+ *      mu_2D' and Sigma_2D' (Eq. 2);
+ *   a7 triangulate mu_3D' (Sec. 4.4.1); a8 fit Sigma_3D' (Sec. 4.4.2);
+ *   a9 eigen-decompose, reorder, update rotation and scale (Sec. 4.4.3).
+ * g: device arrays; cams: host [num_views]; tracks: host [num_views] of device
+ * pointers sized by each camera; out: host struct of device pointers (optional
+ * members may be NULL).  Unsolvable Gaussians keep their input values.
+ * Unless options.async_pairs is set, the call waits once (after a2's count) so
+ * that it can size the pair buffer.  Errors: INVALID_ARG, OOM, BUDGET, CUDA. */
+tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams,
+                          int num_views, const tsp_view_tracks* tracks, const tsp_result* out,
+                          void* stream);
+
+/* Same step for callers that hold everything in host memory: g, tracks and out
+ * point to host arrays (pinned memory gives full copy speed).  Inputs are copied
+ * to context-owned device buffers, the step runs, results are copied back and the
+ * call returns after the stream has finished.  Errors as tsp_fit_motion, plus
+ * OVERFLOW if the pair buffer overflowed. */
+tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams,
+                               int num_views, const tsp_view_tracks* tracks,
+                               const tsp_result* out, void* stream);
+
+/* Render colour and final transmittance (Sec. 3.1 blending, same tiles and order
+ * as tsp_fit_motion).  sh: device [n][(sh_degree+1)^2][3] real spherical-harmonic
+ * colour coefficients (degree 0..3, colour = sum c_k Y_k(view dir) + 0.5, clamped
+ * at 0); rgb, final_T: host arrays [num_views] of device pointers to [H][W][3] and
+ * [H][W] FP32.  Errors: INVALID_ARG, OOM, BUDGET, CUDA. */
+tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
+                      const tsp_camera* cams, int num_views, float* const* rgb,
+                      float* const* final_T, void* stream);
+
+/* Wait up to timeout_ms (< 0: forever) for `stream`, then read and clear the
+ * device status word.  Returns OK, TIMEOUT (work still running; call again),
+ * OVERFLOW (the last step ran out of pair capacity; its results are invalid and
+ * the capacity has been raised for the next call) or CUDA. */
+tsp_status tsp_sync(tsp_context* ctx, void* stream, int timeout_ms);
+
+/* Intermediates of the last tsp_fit_motion / tsp_render, for inspection and tests.
+ * Call after tsp_sync.  Copies min(bytes, size) bytes to host memory dst and sets
+ * *size_out (nullable) to the full size in bytes.  dst may be NULL to query size. */
+typedef enum {
+    TSP_I_COUNTS = 0,        /* int64[4]: K pairs, NT tiles, pair capacity, overflow */
+    TSP_I_RECT = 1,          /* int16[V][n][4]: tile rect x0 y0 x1 y1 (all 0 = culled) */
+    TSP_I_DEPTH = 2,         /* uint32[V][n]: bits of the FP32 camera depth          */
+    TSP_I_TILES_TOUCHED = 3, /* uint32[V][n]                                         */
+    TSP_I_TILE_OFFSETS = 4,  /* uint32[NT+1]: tile t owns pairs [off[t], off[t+1])   */
+    TSP_I_PAIRS = 5,         /* uint64[K]: depth_bits << 32 | Gaussian, sorted per tile */
+    TSP_I_MOMENTS = 6,       /* float[V][n][16], layout as view_moments              */
+    TSP_I_STATS = 7          /* uint64[4] raster work of the last call when           */
+                             /* collect_stats = 1: (pixel, Gaussian) evaluations,     */
+                             /* blended contributions, moment additions, list entries */
+} tsp_intermediate;
+tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, size_t* size_out);
+
+/* Device time in milliseconds of the steps of the last call made with
+ * stage_timing = 1: [0] a1 projection (with the buffer clears), [1] a2 scan,
+ * [2] a2 emit, [3] a3 tile sort, [4] a5 raster-accumulate (or render),
+ * [5] a6 per-view solve, [6] a7-a9 multi-view update.  Waits for the call's
+ * events.  Writes min(max_n, 7) values; *count (nullable) = 7.
+ * Errors: INVALID_ARG (no timed call yet), CUDA. */
+tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count);
+
+/* Bytes of device workspace the context currently holds. */
+tsp_status tsp_workspace_bytes(const tsp_context* ctx, size_t* bytes);
+
+/* Static strings; never NULL. */
+const char* tsp_status_string(tsp_status s);
+const char* tsp_last_error(const tsp_context* ctx);
+int tsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSPLAT_H */

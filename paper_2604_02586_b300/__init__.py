@@ -1,0 +1,336 @@
+"""Python binding of libtsplat.so, the B300 motion-compensation path of TrackerSplat.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  The
+C functions are exported under their C names (``tsp_create``, ``tsp_fit_motion``,
+``tsp_fit_motion_host``, ``tsp_render``, ``tsp_sync``, ``tsp_inspect`` ...) and
+wrapped by :class:`Context`, whose methods take torch CUDA tensors (device path)
+or numpy arrays (host path).  Loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["Context", "Camera", "Options", "TSP", "lib", "LIB_PATH", "cameras_from"]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtsplat.so")
+
+
+class TSP:
+    """Status codes and flag bits of include/tsplat.h."""
+    OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_OVERFLOW = range(7)
+    VIEW_OK, VIEW_FEW_PX, VIEW_LOW_ALPHA, VIEW_SINGULAR, VIEW_CULLED = 1, 2, 4, 8, 16
+    POS_OK, COV_OK, NEG_EIG, FEW_VIEWS, LOW_ALPHA, FEW_PX, COV_SINGULAR, TRI_SINGULAR = \
+        1, 2, 4, 8, 16, 32, 64, 128
+    I_COUNTS, I_RECT, I_DEPTH, I_TILES_TOUCHED, I_TILE_OFFSETS, I_PAIRS, I_MOMENTS, I_STATS = range(8)
+    STAGES = ("project", "scan", "emit", "tile_sort", "raster", "view_solve", "multiview")
+    MAX_VIEWS = 32
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("R", C.c_float * 9), ("t", C.c_float * 3)]
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("n", C.c_int32), ("means_opacity", C.c_void_p), ("quats", C.c_void_p),
+                ("scales", C.c_void_p)]
+
+
+class ViewTracks(C.Structure):
+    _fields_ = [("disp", C.c_void_p), ("vis", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("quats", C.c_void_p), ("scales", C.c_void_p),
+                ("status", C.c_void_p), ("view_affine", C.c_void_p), ("view_moments", C.c_void_p),
+                ("view_flags", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("det_min", C.c_float),
+                ("sumw_min_view", C.c_float), ("min_px_view", C.c_int32), ("lam_min_px2", C.c_float),
+                ("min_views", C.c_int32), ("sumw_min_total", C.c_float), ("min_px_total", C.c_int32),
+                ("cov_rcond_min", C.c_float), ("async_pairs", C.c_int32), ("stage_timing", C.c_int32),
+                ("collect_stats", C.c_int32), ("reserved", C.c_int32),
+                ("pair_capacity", C.c_int64), ("budget_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if libtsplat.so has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2604_02586_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, I = C.c_void_p, C.c_int
+        L.tsp_default_options.argtypes = [P]
+        L.tsp_create.argtypes = [I, P, P]
+        L.tsp_destroy.argtypes = [P]
+        L.tsp_fit_motion.argtypes = [P, P, P, I, P, P, P]
+        L.tsp_fit_motion_host.argtypes = [P, P, P, I, P, P, P]
+        L.tsp_render.argtypes = [P, P, P, I, P, I, P, P, P]
+        L.tsp_sync.argtypes = [P, P, I]
+        L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
+        L.tsp_workspace_bytes.argtypes = [P, P]
+        L.tsp_stage_times.argtypes = [P, P, I, P]
+        L.tsp_status_string.argtypes = [I]
+        L.tsp_status_string.restype = C.c_char_p
+        L.tsp_last_error.argtypes = [P]
+        L.tsp_last_error.restype = C.c_char_p
+        L.tsp_version.restype = I
+        for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
+                     "tsp_fit_motion_host", "tsp_render", "tsp_sync", "tsp_inspect",
+                     "tsp_workspace_bytes", "tsp_stage_times"):
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def __getattr__(name):
+    if name.startswith("tsp_"):
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+class TspError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def cameras_from(width, height, fx, fy, cx, cy, R, t):
+    """ctypes array of tsp_camera from per-view arrays."""
+    V = len(width)
+    arr = (Camera * max(V, 1))()
+    for v in range(V):
+        c = arr[v]
+        c.width, c.height = int(width[v]), int(height[v])
+        c.fx, c.fy, c.cx, c.cy = float(fx[v]), float(fy[v]), float(cx[v]), float(cy[v])
+        c.R[:] = [float(x) for x in np.asarray(R[v], np.float32).ravel()]
+        c.t[:] = [float(x) for x in np.asarray(t[v], np.float32).ravel()]
+    return arr, V
+
+
+def _cams(cams):
+    if isinstance(cams, tuple):
+        return cams
+    return cameras_from(cams.width, cams.height, cams.fx, cams.fy, cams.cx, cams.cy, cams.R, cams.t)
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _need(t, shape, dtype, device=None, name="tensor"):
+    """Check a torch tensor's shape, dtype, contiguity and device before its
+    pointer is handed to the library (the kernels trust these sizes)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+
+
+def _need_np(a, shape, name):
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(a.shape)}, expected {tuple(shape)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    """A libtsplat context on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0, **options):
+        self.opt = Options()
+        lib().tsp_default_options(C.byref(self.opt))
+        for k, v in options.items():
+            setattr(self.opt, k, v)
+        self.device = device
+        self._h = C.c_void_p()
+        self._check(lib().tsp_create(device, C.byref(self.opt), C.byref(self._h)), "tsp_create")
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, status, what):
+        if status != TSP.OK:
+            msg = lib().tsp_last_error(self._h).decode() if self._h else ""
+            raise TspError(status, f"{what}: {lib().tsp_status_string(status).decode()}: {msg}")
+
+    def close(self):
+        if self._h:
+            lib().tsp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the motion fit --------------------------------------------------------
+    def fit_motion(self, means_opacity, quats, scales, cams, disp, vis, *, out=None,
+                   view_affine=False, view_moments=False, view_flags=False, stream=None,
+                   sync=False):
+        """Device path.  Tensors are CUDA tensors on the context's device:
+        means_opacity/quats/scales [n,4] f32, disp [V] x [H,W,2] f32, vis [V] x [H,W] u8.
+        Returns a dict of output tensors (allocated here unless ``out`` is given)."""
+        import torch
+        n = int(means_opacity.shape[0])
+        carr, V = _cams(cams)
+        dev = means_opacity.device
+        if out is None:
+            out = dict(means=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                       quats=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                       scales=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                       status=torch.empty((n,), dtype=torch.int32, device=dev))
+            if view_affine:
+                out["view_affine"] = torch.empty((V, n, 6), dtype=torch.float32, device=dev)
+            if view_moments:
+                out["view_moments"] = torch.empty((V, n, 16), dtype=torch.float32, device=dev)
+            if view_flags:
+                out["view_flags"] = torch.empty((V, n), dtype=torch.int32, device=dev)
+        f32 = torch.float32
+        for name, t in (("means_opacity", means_opacity), ("quats", quats), ("scales", scales)):
+            _need(t, (n, 4), f32, dev, name)
+        if len(disp) < V or len(vis) < V:
+            raise ValueError("need one disp and one vis tensor per camera")
+        for v in range(V):
+            H, W = carr[v].height, carr[v].width
+            _need(disp[v], (H, W, 2), f32, dev, f"disp[{v}]")
+            _need(vis[v], (H, W), torch.uint8, dev, f"vis[{v}]")
+        shapes = dict(means=((n, 4), f32), quats=((n, 4), f32), scales=((n, 4), f32),
+                      status=((n,), torch.int32), view_affine=((V, n, 6), f32),
+                      view_moments=((V, n, 16), f32), view_flags=((V, n), torch.int32))
+        for k, t in out.items():
+            _need(t, shapes[k][0], shapes[k][1], dev, f"out[{k}]")
+        g = Gaussians(n, means_opacity.data_ptr(), quats.data_ptr(), scales.data_ptr())
+        tr = (ViewTracks * max(V, 1))()
+        for v in range(V):
+            tr[v].disp, tr[v].vis = disp[v].data_ptr(), vis[v].data_ptr()
+        r = Result(*[(out[k].data_ptr() if k in out else None) for k in
+                     ("means", "quats", "scales", "status", "view_affine", "view_moments", "view_flags")])
+        self._check(lib().tsp_fit_motion(self._h, C.byref(g), carr, V, tr, C.byref(r),
+                                         _stream_handle(stream)), "tsp_fit_motion")
+        if sync:
+            self.sync(stream)
+        return out
+
+    def fit_motion_host(self, means_opacity, quats, scales, cams, disp, vis, out=None, stream=None):
+        """Host path: numpy inputs and outputs; copies happen inside the library."""
+        n = int(means_opacity.shape[0])
+        carr, V = _cams(cams)
+        mo = np.ascontiguousarray(means_opacity, np.float32)
+        q = np.ascontiguousarray(quats, np.float32)
+        s = np.ascontiguousarray(scales, np.float32)
+        if out is None:
+            out = dict(means=np.empty((n, 4), np.float32), quats=np.empty((n, 4), np.float32),
+                       scales=np.empty((n, 4), np.float32), status=np.empty(n, np.uint32))
+        for name, a in (("means_opacity", mo), ("quats", q), ("scales", s)):
+            _need_np(a, (n, 4), name)
+        for k, shp in (("means", (n, 4)), ("quats", (n, 4)), ("scales", (n, 4)), ("status", (n,))):
+            _need_np(out[k], shp, f"out[{k}]")
+            if not out[k].flags.c_contiguous:
+                raise ValueError(f"out[{k}] must be contiguous")
+        if len(disp) < V or len(vis) < V:
+            raise ValueError("need one disp and one vis array per camera")
+        g = Gaussians(n, mo.ctypes.data, q.ctypes.data, s.ctypes.data)
+        tr = (ViewTracks * max(V, 1))()
+        keep = []
+        for v in range(V):
+            d = np.ascontiguousarray(disp[v], np.float32)
+            m = np.ascontiguousarray(vis[v], np.uint8)
+            _need_np(d, (carr[v].height, carr[v].width, 2), f"disp[{v}]")
+            _need_np(m, (carr[v].height, carr[v].width), f"vis[{v}]")
+            keep += [d, m]
+            tr[v].disp, tr[v].vis = d.ctypes.data, m.ctypes.data
+        r = Result(out["means"].ctypes.data, out["quats"].ctypes.data, out["scales"].ctypes.data,
+                   out["status"].ctypes.data, None, None, None)
+        st = C.c_void_p(0) if stream is None else _stream_handle(stream)
+        self._check(lib().tsp_fit_motion_host(self._h, C.byref(g), carr, V, tr, C.byref(r), st),
+                    "tsp_fit_motion_host")
+        return out
+
+    def render(self, means_opacity, quats, scales, sh, sh_degree, cams, stream=None, sync=False):
+        """Colour [V] x [H,W,3] and final transmittance [V] x [H,W] (CUDA tensors)."""
+        import torch
+        n = int(means_opacity.shape[0])
+        carr, V = _cams(cams)
+        dev = means_opacity.device
+        rgb = [torch.empty((carr[v].height, carr[v].width, 3), dtype=torch.float32, device=dev)
+               for v in range(V)]
+        T = [torch.empty((carr[v].height, carr[v].width), dtype=torch.float32, device=dev)
+             for v in range(V)]
+        for name, t in (("means_opacity", means_opacity), ("quats", quats), ("scales", scales)):
+            _need(t, (n, 4), torch.float32, dev, name)
+        _need(sh, (n, (int(sh_degree) + 1) ** 2, 3), torch.float32, dev, "sh")
+        g = Gaussians(n, means_opacity.data_ptr(), quats.data_ptr(), scales.data_ptr())
+        pr = (C.c_void_p * max(V, 1))(*[x.data_ptr() for x in rgb])
+        pt = (C.c_void_p * max(V, 1))(*[x.data_ptr() for x in T])
+        self._check(lib().tsp_render(self._h, C.byref(g), C.c_void_p(sh.data_ptr()), int(sh_degree),
+                                     carr, V, pr, pt, _stream_handle(stream)), "tsp_render")
+        if sync:
+            self.sync(stream)
+        return rgb, T
+
+    def sync(self, stream=None, timeout_ms: int = -1):
+        st = C.c_void_p(0) if stream is None and not _torch_cuda() else _stream_handle(stream)
+        self._check(lib().tsp_sync(self._h, st, int(timeout_ms)), "tsp_sync")
+
+    def inspect(self, which: int) -> np.ndarray:
+        """Copy an intermediate of the last call to host memory (after sync)."""
+        size = C.c_size_t()
+        self._check(lib().tsp_inspect(self._h, which, None, 0, C.byref(size)), "tsp_inspect")
+        dtype = {TSP.I_COUNTS: np.int64, TSP.I_RECT: np.int16, TSP.I_DEPTH: np.uint32,
+                 TSP.I_TILES_TOUCHED: np.uint32, TSP.I_TILE_OFFSETS: np.uint32,
+                 TSP.I_PAIRS: np.uint64, TSP.I_MOMENTS: np.float32, TSP.I_STATS: np.uint64}[which]
+        a = np.empty(size.value // np.dtype(dtype).itemsize, dtype)
+        self._check(lib().tsp_inspect(self._h, which, _hptr(a), size.value, None), "tsp_inspect")
+        return a
+
+    def stage_times(self) -> dict:
+        """Per-step device milliseconds of the last call (needs stage_timing=1)."""
+        ms = (C.c_float * 7)()
+        self._check(lib().tsp_stage_times(self._h, ms, 7, None), "tsp_stage_times")
+        return dict(zip(TSP.STAGES, [float(x) for x in ms]))
+
+    def workspace_bytes(self) -> int:
+        b = C.c_size_t()
+        self._check(lib().tsp_workspace_bytes(self._h, C.byref(b)), "tsp_workspace_bytes")
+        return int(b.value)
+
+
+def _torch_cuda() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

@@ -1,0 +1,661 @@
+// api.cu -- the C ABI of libtsplat.so (include/tsplat.h): argument checks,
+// workspace management and the order of the pipeline steps.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "launch.h"
+
+using namespace tsp;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tsp_context {
+    int device = 0;
+    tsp_options opt{};
+    std::string err;
+    size_t held = 0;
+    // per (view, Gaussian)
+    Buf rect, depth, touched, geom0, geom1, color, moments, vres0, vres1, vres2;
+    // per tile
+    Buf tiles, tile_off;
+    // pairs
+    Buf pairs, pairs_tmp;
+    uint64_t want_pairs = 0;
+    Buf dstatus, stats;
+    uint32_t* h_status = nullptr;   // pinned, 4 words
+    cudaEvent_t ev[8] = {};         // stage boundaries (stage_timing)
+    bool timed = false;             // the last call recorded ev[]
+    // staging for tsp_fit_motion_host
+    Buf st_in, st_out, st_tracks;
+    // last call
+    int last_V = 0, last_n = 0;
+    uint32_t last_NT = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+tsp_status fail(tsp_context* c, tsp_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+tsp_status cuda_fail(tsp_context* c, cudaError_t e, const char* what)
+{
+    return fail(c, TSP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TSP_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&old_);
+        if (old_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(old_); }
+
+private:
+    int old_ = 0;
+};
+
+tsp_status ensure(tsp_context* ctx, Buf& b, size_t need)
+{
+    if (need <= b.bytes) return TSP_OK;
+    size_t nb = align_up(need > b.bytes + b.bytes / 4 ? need : b.bytes + b.bytes / 4);
+    const size_t after = ctx->held - b.bytes + nb;
+    if (ctx->opt.budget_bytes > 0 && after > (size_t)ctx->opt.budget_bytes) {
+        nb = align_up(need);
+        if (ctx->held - b.bytes + nb > (size_t)ctx->opt.budget_bytes)
+            return fail(ctx, TSP_ERR_BUDGET, "workspace of " + std::to_string(ctx->held - b.bytes + nb) +
+                                                 " bytes exceeds the budget");
+    }
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
+        ctx->held -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(ctx, TSP_ERR_OOM, "cudaMalloc of " + std::to_string(nb) + " bytes failed");
+    }
+    b.bytes = nb;
+    ctx->held += nb;
+    return TSP_OK;
+}
+
+void release(tsp_context* ctx, Buf& b)
+{
+    if (b.p) cudaFree(b.p);
+    ctx->held -= b.bytes;
+    b = Buf{};
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+bool device_accessible(const void* p, int dev)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+tsp_status check_options(tsp_context* ctx, const tsp_options& o)
+{
+    if (o.tile_w != kTile || o.tile_h != kTile)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "only 16x16 tiles are supported");
+    if (!(o.det_min >= 0.f) || !(o.sumw_min_view >= 0.f) || !(o.lam_min_px2 >= 0.f) ||
+        !(o.sumw_min_total >= 0.f) || !(o.cov_rcond_min >= 0.f) || !std::isfinite(o.det_min) ||
+        !std::isfinite(o.sumw_min_view) || !std::isfinite(o.lam_min_px2) ||
+        !std::isfinite(o.sumw_min_total) || !std::isfinite(o.cov_rcond_min))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "thresholds must be finite and >= 0");
+    if (o.min_px_view < 0 || o.min_views < 0 || o.min_px_total < 0)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "counts must be >= 0");
+    if (o.pair_capacity < 0 || o.pair_capacity > INT32_MAX || o.budget_bytes < 0)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "bad pair_capacity or budget_bytes");
+    return TSP_OK;
+}
+
+FitParams fit_params(const tsp_options& o)
+{
+    FitParams f;
+    f.det_min = o.det_min;
+    f.sumw_min_view = o.sumw_min_view;
+    f.lam_min_px2 = o.lam_min_px2;
+    f.sumw_min_total = o.sumw_min_total;
+    f.cov_rcond_min = o.cov_rcond_min;
+    f.min_px_view = o.min_px_view;
+    f.min_views = o.min_views;
+    f.min_px_total = o.min_px_total;
+    return f;
+}
+
+// Validate cameras and build the per-call view description.
+tsp_status make_viewset(tsp_context* ctx, const tsp_camera* cams, int V, int n, ViewSet& vs, uint32_t& NT)
+{
+    if (V < 0 || V > TSP_MAX_VIEWS) return fail(ctx, TSP_ERR_INVALID_ARG, "num_views must be in [0, 32]");
+    if (V > 0 && !cams) return fail(ctx, TSP_ERR_INVALID_ARG, "cams is NULL");
+    std::memset(&vs, 0, sizeof(vs));
+    vs.V = V;
+    vs.n = n;
+    uint64_t off = 0;
+    for (int v = 0; v < V; ++v) {
+        const tsp_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > TSP_MAX_IMAGE || c.height > TSP_MAX_IMAGE)
+            return fail(ctx, TSP_ERR_INVALID_ARG, "camera " + std::to_string(v) + ": size out of range");
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.fx) || !std::isfinite(c.fy) ||
+            !std::isfinite(c.cx) || !std::isfinite(c.cy))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "camera " + std::to_string(v) + ": bad intrinsics");
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(c.R[k])) return fail(ctx, TSP_ERR_INVALID_ARG, "camera R not finite");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(c.t[k])) return fail(ctx, TSP_ERR_INVALID_ARG, "camera t not finite");
+        DevCam& d = vs.cam[v];
+        d.W = c.width; d.H = c.height;
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        std::memcpy(d.R, c.R, sizeof(d.R));
+        std::memcpy(d.t, c.t, sizeof(d.t));
+        vs.tiles_x[v] = (c.width + kTile - 1) / kTile;
+        vs.tiles_y[v] = (c.height + kTile - 1) / kTile;
+        vs.toff[v] = (uint32_t)off;
+        off += (uint64_t)vs.tiles_x[v] * vs.tiles_y[v];
+    }
+    vs.toff[V] = (uint32_t)off;
+    NT = (uint32_t)off;
+    return TSP_OK;
+}
+
+tsp_status check_gaussians(tsp_context* ctx, const tsp_gaussians* g, bool device)
+{
+    if (!g) return fail(ctx, TSP_ERR_INVALID_ARG, "g is NULL");
+    if (g->n < 0) return fail(ctx, TSP_ERR_INVALID_ARG, "n < 0");
+    if (g->n == 0) return TSP_OK;
+    const void* ps[3] = {g->means_opacity, g->quats, g->scales};
+    for (const void* p : ps) {
+        if (!p) return fail(ctx, TSP_ERR_INVALID_ARG, "Gaussian array is NULL");
+        if (!aligned(p, 16)) return fail(ctx, TSP_ERR_INVALID_ARG, "Gaussian arrays must be 16-byte aligned");
+        if (device && !device_accessible(p, ctx->device))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "Gaussian array is not device memory of the context's device");
+    }
+    return TSP_OK;
+}
+
+tsp_status check_result(tsp_context* ctx, const tsp_result* out, int n, bool device)
+{
+    if (!out) return fail(ctx, TSP_ERR_INVALID_ARG, "out is NULL");
+    if (n == 0) return TSP_OK;
+    const void* ps[4] = {out->means, out->quats, out->scales, out->status};
+    for (int k = 0; k < 4; ++k) {
+        if (!ps[k]) return fail(ctx, TSP_ERR_INVALID_ARG, "result array is NULL");
+        if (!aligned(ps[k], k < 3 ? 16 : 4)) return fail(ctx, TSP_ERR_INVALID_ARG, "result array misaligned");
+        if (device && !device_accessible(ps[k], ctx->device))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "result array is not device memory of the context's device");
+    }
+    const void* opt[3] = {out->view_affine, out->view_moments, out->view_flags};
+    for (const void* p : opt) {
+        if (!p) continue;
+        if (!device) return fail(ctx, TSP_ERR_INVALID_ARG, "optional outputs are not supported by the host call");
+        if (!aligned(p, 16) && p == out->view_moments)
+            return fail(ctx, TSP_ERR_INVALID_ARG, "view_moments must be 16-byte aligned");
+        if (!aligned(p, 4)) return fail(ctx, TSP_ERR_INVALID_ARG, "optional output misaligned");
+        if (!device_accessible(p, ctx->device))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "optional output is not device memory");
+    }
+    return TSP_OK;
+}
+
+tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render, Work& w)
+{
+    const size_t vn = (size_t)V * (size_t)n;
+    const size_t vn1 = vn > 0 ? vn : 1;
+    tsp_status s;
+    if ((s = ensure(ctx, ctx->rect, vn1 * sizeof(short4)))) return s;
+    if ((s = ensure(ctx, ctx->depth, vn1 * 4))) return s;
+    if ((s = ensure(ctx, ctx->touched, vn1 * 4))) return s;
+    if ((s = ensure(ctx, ctx->geom0, vn1 * 16))) return s;
+    if ((s = ensure(ctx, ctx->geom1, vn1 * 8))) return s;
+    if (render) {
+        if ((s = ensure(ctx, ctx->color, vn1 * 16))) return s;
+    } else {
+        if ((s = ensure(ctx, ctx->moments, vn1 * 64))) return s;
+        if ((s = ensure(ctx, ctx->vres0, vn1 * 16))) return s;
+        if ((s = ensure(ctx, ctx->vres1, vn1 * 16))) return s;
+        if ((s = ensure(ctx, ctx->vres2, vn1 * 8))) return s;
+    }
+    if ((s = ensure(ctx, ctx->tiles, (size_t)2 * (NT + 1) * 4))) return s;
+    if ((s = ensure(ctx, ctx->tile_off, (size_t)(NT + 1) * 4))) return s;
+    uint64_t cap = ctx->want_pairs;
+    if (cap == 0) cap = ctx->opt.pair_capacity > 0 ? (uint64_t)ctx->opt.pair_capacity : (uint64_t)8 * vn;
+    if (cap < (1u << 16)) cap = 1u << 16;
+    if (cap > (uint64_t)INT32_MAX) cap = INT32_MAX;
+    if ((s = ensure(ctx, ctx->pairs, cap * 8))) return s;
+    if ((s = ensure(ctx, ctx->pairs_tmp, cap * 8))) return s;
+    if ((s = ensure(ctx, ctx->dstatus, 16))) return s;
+    if ((s = ensure(ctx, ctx->stats, 32))) return s;
+    w.stats = (unsigned long long*)ctx->stats.p;
+    w.rect = (short4*)ctx->rect.p;
+    w.depth = (uint32_t*)ctx->depth.p;
+    w.touched = (uint32_t*)ctx->touched.p;
+    w.geom0 = (float4*)ctx->geom0.p;
+    w.geom1 = (float2*)ctx->geom1.p;
+    w.color = (float4*)ctx->color.p;
+    w.moments = (float4*)ctx->moments.p;
+    w.vres0 = (float4*)ctx->vres0.p;
+    w.vres1 = (float4*)ctx->vres1.p;
+    w.vres2 = (uint2*)ctx->vres2.p;
+    w.tile_count = (uint32_t*)ctx->tiles.p;
+    w.tile_fill = (uint32_t*)ctx->tiles.p + (NT + 1);
+    w.tile_off = (uint32_t*)ctx->tile_off.p;
+    w.pairs = (uint64_t*)ctx->pairs.p;
+    w.pairs_tmp = (uint64_t*)ctx->pairs_tmp.p;
+    const uint64_t have = ctx->pairs.bytes / 8 < ctx->pairs_tmp.bytes / 8 ? ctx->pairs.bytes / 8 : ctx->pairs_tmp.bytes / 8;
+    w.cap = (uint32_t)(have > (uint64_t)INT32_MAX ? INT32_MAX : have);
+    w.dstatus = (uint32_t*)ctx->dstatus.p;
+    return TSP_OK;
+}
+
+inline cudaError_t mark(tsp_context* ctx, int k, cudaStream_t st)
+{
+    return ctx->opt.stage_timing ? cudaEventRecord(ctx->ev[k], st) : cudaSuccess;
+}
+
+// a1 + a2 (count, scan) and, unless async, the wait that sizes the pair buffer.
+tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const tsp_gaussians* g, const float* sh,
+                     int sh_degree, int mode, uint32_t NT, Work& w, cudaStream_t st)
+{
+    TSP_CUDA(mark(ctx, 0, st));
+    TSP_CUDA(cudaMemsetAsync(ctx->tiles.p, 0, (size_t)2 * (NT + 1) * 4, st));
+    TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 16, st));
+    if (ctx->opt.collect_stats) TSP_CUDA(cudaMemsetAsync(w.stats, 0, 32, st));
+    TSP_CUDA(launch_preprocess(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
+                               (const float4*)g->scales, sh, sh_degree, mode, w, st));
+    TSP_CUDA(mark(ctx, 1, st));
+    TSP_CUDA(launch_scan(w, NT, st));
+    TSP_CUDA(mark(ctx, 2, st));
+    if (!ctx->opt.async_pairs) {
+        TSP_CUDA(cudaMemcpyAsync(ctx->h_status, w.dstatus, 16, cudaMemcpyDeviceToHost, st));
+        TSP_CUDA(cudaStreamSynchronize(st));
+        const uint64_t K = (uint64_t)ctx->h_status[1] | ((uint64_t)ctx->h_status[2] << 32);
+        if (K > w.cap) {
+            if (K > (uint64_t)INT32_MAX)
+                return fail(ctx, TSP_ERR_OVERFLOW, "more than 2^31 - 1 (tile, Gaussian) pairs");
+            ctx->want_pairs = K + K / 8;
+            tsp_status s;
+            if ((s = ensure(ctx, ctx->pairs, ctx->want_pairs * 8))) return s;
+            if ((s = ensure(ctx, ctx->pairs_tmp, ctx->want_pairs * 8))) return s;
+            w.pairs = (uint64_t*)ctx->pairs.p;
+            w.pairs_tmp = (uint64_t*)ctx->pairs_tmp.p;
+            w.cap = (uint32_t)(ctx->want_pairs > (uint64_t)INT32_MAX ? INT32_MAX : ctx->want_pairs);
+            TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 4, st));
+        }
+    }
+    TSP_CUDA(launch_scatter(vs, w, st));
+    TSP_CUDA(mark(ctx, 3, st));
+    TSP_CUDA(launch_tile_sort(w, NT, st));
+    TSP_CUDA(mark(ctx, 4, st));
+    return TSP_OK;
+}
+
+tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams, int V,
+                      const tsp_view_tracks* tracks, const tsp_result* out, cudaStream_t st, bool check_ptrs)
+{
+    tsp_status s;
+    if ((s = check_gaussians(ctx, g, check_ptrs))) return s;
+    const int n = g->n;
+    ViewSet vs;
+    uint32_t NT = 0;
+    if ((s = make_viewset(ctx, cams, V, n, vs, NT))) return s;
+    if ((s = check_result(ctx, out, n, check_ptrs))) return s;
+    if (n > 0 && V > 0) {
+        if (!tracks) return fail(ctx, TSP_ERR_INVALID_ARG, "tracks is NULL");
+        for (int v = 0; v < V; ++v) {
+            if (!tracks[v].disp || !tracks[v].vis)
+                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": track pointer is NULL");
+            if (!aligned(tracks[v].disp, 8))
+                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": disp must be 8-byte aligned");
+            if (check_ptrs && (!device_accessible(tracks[v].disp, ctx->device) ||
+                               !device_accessible(tracks[v].vis, ctx->device)))
+                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": tracks are not device memory");
+            vs.disp[v] = (const float2*)tracks[v].disp;
+            vs.vis[v] = tracks[v].vis;
+        }
+    }
+    Work w{};
+    if ((s = ensure_work(ctx, V, n, NT, false, w))) return s;
+    ctx->last_V = V;
+    ctx->last_n = n;
+    ctx->last_NT = NT;
+    if (n == 0) return TSP_OK;
+    const FitParams fp = fit_params(ctx->opt);
+    ctx->timed = false;
+    if ((s = bin_front(ctx, vs, g, nullptr, 0, 0, NT, w, st))) return s;
+    TSP_CUDA(launch_raster_accumulate(vs, w, NT, ctx->opt.collect_stats != 0, st));
+    TSP_CUDA(mark(ctx, 5, st));
+    TSP_CUDA(launch_view_solve(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
+                               (const float4*)g->scales, fp, w, out->view_affine, out->view_flags, st));
+    TSP_CUDA(mark(ctx, 6, st));
+    TSP_CUDA(launch_multiview(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
+                              (const float4*)g->scales, fp, w, (float4*)out->means, (float4*)out->quats,
+                              (float4*)out->scales, out->status, st));
+    TSP_CUDA(mark(ctx, 7, st));
+    ctx->timed = ctx->opt.stage_timing != 0;
+    if (out->view_moments && V > 0)
+        TSP_CUDA(cudaMemcpyAsync(out->view_moments, w.moments, (size_t)V * n * 64, cudaMemcpyDeviceToDevice, st));
+    return TSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsp_version(void) { return TSP_VERSION; }
+
+const char* tsp_status_string(tsp_status s)
+{
+    switch (s) {
+    case TSP_OK: return "ok";
+    case TSP_ERR_INVALID_ARG: return "invalid argument";
+    case TSP_ERR_OOM: return "out of device memory";
+    case TSP_ERR_CUDA: return "CUDA error";
+    case TSP_ERR_TIMEOUT: return "timed out";
+    case TSP_ERR_BUDGET: return "workspace budget exceeded";
+    case TSP_ERR_OVERFLOW: return "pair buffer overflow";
+    }
+    return "unknown status";
+}
+
+const char* tsp_last_error(const tsp_context* ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+tsp_status tsp_default_options(tsp_options* o)
+{
+    if (!o) return TSP_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->tile_w = kTile;
+    o->tile_h = kTile;
+    o->det_min = 1e-12f;
+    o->sumw_min_view = 1e-3f;
+    o->min_px_view = 2;
+    o->lam_min_px2 = 1e-4f;
+    o->min_views = 2;
+    o->sumw_min_total = 1e-3f;
+    o->min_px_total = 3;
+    o->cov_rcond_min = 1e-10f;
+    return TSP_OK;
+}
+
+tsp_status tsp_create(int device, const tsp_options* opt, tsp_context** out)
+{
+    if (!out) return TSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return device < 0 ? TSP_ERR_INVALID_ARG : TSP_ERR_CUDA;
+    }
+    tsp_context* ctx = new tsp_context();
+    ctx->device = device;
+    if (opt) ctx->opt = *opt;
+    else tsp_default_options(&ctx->opt);
+    tsp_status s = check_options(ctx, ctx->opt);
+    if (s) { delete ctx; return s; }
+    DeviceGuard dg(device);
+    if (cudaMallocHost(&ctx->h_status, 16) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return TSP_ERR_CUDA;
+    }
+    for (cudaEvent_t& e : ctx->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            tsp_destroy(ctx);
+            return TSP_ERR_CUDA;
+        }
+    *out = ctx;
+    return TSP_OK;
+}
+
+tsp_status tsp_destroy(tsp_context* ctx)
+{
+    if (!ctx) return TSP_OK;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->color,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->tiles, &ctx->tile_off,
+                  &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
+                  &ctx->st_tracks};
+    for (Buf* b : all) release(ctx, *b);
+    for (cudaEvent_t e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return TSP_OK;
+}
+
+tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams, int num_views,
+                          const tsp_view_tracks* tracks, const tsp_result* out, void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    return fit_device(ctx, g, cams, num_views, tracks, out, (cudaStream_t)stream, true);
+}
+
+tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams,
+                               int num_views, const tsp_view_tracks* tracks, const tsp_result* out,
+                               void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    tsp_status s;
+    if ((s = check_gaussians(ctx, g, false))) return s;
+    if ((s = check_result(ctx, out, g->n, false))) return s;
+    ViewSet vs;
+    uint32_t NT = 0;
+    const int n = g->n, V = num_views;
+    if ((s = make_viewset(ctx, cams, V, n, vs, NT))) return s;
+    if (n > 0 && V > 0 && !tracks) return fail(ctx, TSP_ERR_INVALID_ARG, "tracks is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t gb = (size_t)n * 16;
+    if ((s = ensure(ctx, ctx->st_in, 3 * align_up(gb) + kAlign))) return s;
+    if ((s = ensure(ctx, ctx->st_out, 3 * align_up(gb) + align_up((size_t)n * 4) + kAlign))) return s;
+    std::vector<size_t> toff(V + 1, 0);
+    for (int v = 0; v < V; ++v) {
+        const size_t px = (size_t)cams[v].width * cams[v].height;
+        toff[v + 1] = toff[v] + align_up(px * 8) + align_up(px);
+    }
+    if ((s = ensure(ctx, ctx->st_tracks, toff[V] + kAlign))) return s;
+    char* in = (char*)ctx->st_in.p;
+    char* ob = (char*)ctx->st_out.p;
+    char* tb = (char*)ctx->st_tracks.p;
+    tsp_gaussians dg_{n, (const float*)in, (const float*)(in + align_up(gb)), (const float*)(in + 2 * align_up(gb))};
+    tsp_result dr{(float*)ob, (float*)(ob + align_up(gb)), (float*)(ob + 2 * align_up(gb)),
+                  (uint32_t*)(ob + 3 * align_up(gb)), nullptr, nullptr, nullptr};
+    std::vector<tsp_view_tracks> dt(V > 0 ? V : 1);
+    if (n > 0) {
+        TSP_CUDA(cudaMemcpyAsync((void*)dg_.means_opacity, g->means_opacity, gb, cudaMemcpyHostToDevice, st));
+        TSP_CUDA(cudaMemcpyAsync((void*)dg_.quats, g->quats, gb, cudaMemcpyHostToDevice, st));
+        TSP_CUDA(cudaMemcpyAsync((void*)dg_.scales, g->scales, gb, cudaMemcpyHostToDevice, st));
+        for (int v = 0; v < V; ++v) {
+            if (!tracks[v].disp || !tracks[v].vis)
+                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": track pointer is NULL");
+            const size_t px = (size_t)cams[v].width * cams[v].height;
+            dt[v].disp = (const float*)(tb + toff[v]);
+            dt[v].vis = (const uint8_t*)(tb + toff[v] + align_up(px * 8));
+            TSP_CUDA(cudaMemcpyAsync((void*)dt[v].disp, tracks[v].disp, px * 8, cudaMemcpyHostToDevice, st));
+            TSP_CUDA(cudaMemcpyAsync((void*)dt[v].vis, tracks[v].vis, px, cudaMemcpyHostToDevice, st));
+        }
+    }
+    if ((s = fit_device(ctx, &dg_, cams, V, dt.data(), &dr, st, false))) return s;
+    if (n > 0) {
+        TSP_CUDA(cudaMemcpyAsync(out->means, dr.means, gb, cudaMemcpyDeviceToHost, st));
+        TSP_CUDA(cudaMemcpyAsync(out->quats, dr.quats, gb, cudaMemcpyDeviceToHost, st));
+        TSP_CUDA(cudaMemcpyAsync(out->scales, dr.scales, gb, cudaMemcpyDeviceToHost, st));
+        TSP_CUDA(cudaMemcpyAsync(out->status, dr.status, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    }
+    return tsp_sync(ctx, stream, -1);
+}
+
+tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
+                      const tsp_camera* cams, int num_views, float* const* rgb, float* const* final_T,
+                      void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    tsp_status s;
+    if ((s = check_gaussians(ctx, g, true))) return s;
+    if (sh_degree < 0 || sh_degree > 3) return fail(ctx, TSP_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    const int n = g->n, V = num_views;
+    if (n > 0 && (!sh || !device_accessible(sh, ctx->device)))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "sh must be device memory");
+    ViewSet vs;
+    uint32_t NT = 0;
+    if ((s = make_viewset(ctx, cams, V, n, vs, NT))) return s;
+    if (V > 0 && (!rgb || !final_T)) return fail(ctx, TSP_ERR_INVALID_ARG, "rgb / final_T is NULL");
+    for (int v = 0; v < V; ++v) {
+        if (!rgb[v] || !final_T[v] || !aligned(rgb[v], 4) || !aligned(final_T[v], 4))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": bad output image");
+        if (!device_accessible(rgb[v], ctx->device) || !device_accessible(final_T[v], ctx->device))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": output is not device memory");
+    }
+    Work w{};
+    if ((s = ensure_work(ctx, V, n, NT, true, w))) return s;
+    ctx->last_V = V;
+    ctx->last_n = n;
+    ctx->last_NT = NT;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->timed = false;
+    if ((s = bin_front(ctx, vs, g, sh, sh_degree, 1, NT, w, st))) return s;
+    TSP_CUDA(launch_raster_render(vs, w, NT, rgb, final_T, st));
+    TSP_CUDA(mark(ctx, 5, st));
+    TSP_CUDA(mark(ctx, 6, st));
+    TSP_CUDA(mark(ctx, 7, st));
+    ctx->timed = ctx->opt.stage_timing != 0;
+    return TSP_OK;
+}
+
+tsp_status tsp_sync(tsp_context* ctx, void* stream, int timeout_ms)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (timeout_ms < 0) {
+        TSP_CUDA(cudaStreamSynchronize(st));
+    } else {
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            const cudaError_t e = cudaStreamQuery(st);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "cudaStreamQuery");
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(ctx, TSP_ERR_TIMEOUT, "stream still busy");
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+    }
+    if (!ctx->dstatus.p) return TSP_OK;
+    TSP_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->dstatus.p, 16, cudaMemcpyDeviceToHost, st));
+    TSP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->h_status[0] & kStatusOverflow) {
+        const uint64_t K = (uint64_t)ctx->h_status[1] | ((uint64_t)ctx->h_status[2] << 32);
+        ctx->want_pairs = K + K / 4;
+        TSP_CUDA(cudaMemsetAsync(ctx->dstatus.p, 0, 4, st));
+        TSP_CUDA(cudaStreamSynchronize(st));
+        return fail(ctx, TSP_ERR_OVERFLOW, "pair buffer overflow: " + std::to_string(K) + " pairs");
+    }
+    return TSP_OK;
+}
+
+tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, size_t* size_out)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    const size_t vn = (size_t)ctx->last_V * ctx->last_n;
+    const void* src = nullptr;
+    size_t size = 0;
+    int64_t counts[4] = {0, 0, 0, 0};
+    if (ctx->dstatus.p) {
+        TSP_CUDA(cudaDeviceSynchronize());
+        uint32_t h[4];
+        TSP_CUDA(cudaMemcpy(h, ctx->dstatus.p, 16, cudaMemcpyDeviceToHost));
+        counts[0] = (int64_t)((uint64_t)h[1] | ((uint64_t)h[2] << 32));
+        counts[3] = h[0] & kStatusOverflow;
+    }
+    counts[1] = ctx->last_NT;
+    counts[2] = (int64_t)(ctx->pairs.bytes / 8 < ctx->pairs_tmp.bytes / 8 ? ctx->pairs.bytes / 8 : ctx->pairs_tmp.bytes / 8);
+    switch (which) {
+    case TSP_I_COUNTS: size = sizeof(counts); break;
+    case TSP_I_RECT: src = ctx->rect.p; size = vn * 8; break;
+    case TSP_I_DEPTH: src = ctx->depth.p; size = vn * 4; break;
+    case TSP_I_TILES_TOUCHED: src = ctx->touched.p; size = vn * 4; break;
+    case TSP_I_TILE_OFFSETS: src = ctx->tile_off.p; size = ((size_t)ctx->last_NT + 1) * 4; break;
+    case TSP_I_PAIRS: {
+        const int64_t K = counts[0] < counts[2] ? counts[0] : counts[2];
+        src = ctx->pairs.p; size = (size_t)K * 8; break;
+    }
+    case TSP_I_MOMENTS: src = ctx->moments.p; size = vn * 64; break;
+    case TSP_I_STATS: src = ctx->stats.p; size = ctx->stats.p ? 32 : 0; break;
+    default: return fail(ctx, TSP_ERR_INVALID_ARG, "unknown intermediate");
+    }
+    if (size_out) *size_out = size;
+    if (!dst) return TSP_OK;
+    const size_t nb = bytes < size ? bytes : size;
+    if (which == TSP_I_COUNTS) {
+        std::memcpy(dst, counts, nb);
+        return TSP_OK;
+    }
+    if (nb > 0 && !src) return fail(ctx, TSP_ERR_INVALID_ARG, "intermediate not available");
+    if (nb > 0) TSP_CUDA(cudaMemcpy(dst, src, nb, cudaMemcpyDeviceToHost));
+    return TSP_OK;
+}
+
+tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count)
+{
+    if (!ctx || (!ms && max_n > 0)) return TSP_ERR_INVALID_ARG;
+    if (count) *count = 7;
+    if (!ctx->timed) return fail(ctx, TSP_ERR_INVALID_ARG, "no call with stage_timing = 1 yet");
+    DeviceGuard dg(ctx->device);
+    TSP_CUDA(cudaEventSynchronize(ctx->ev[7]));
+    for (int k = 0; k < 7 && k < max_n; ++k) TSP_CUDA(cudaEventElapsedTime(&ms[k], ctx->ev[k], ctx->ev[k + 1]));
+    return TSP_OK;
+}
+
+tsp_status tsp_workspace_bytes(const tsp_context* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return TSP_ERR_INVALID_ARG;
+    *bytes = ctx->held;
+    return TSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// binning.cu -- a1 projection, a2 count/scan/emit, a3 per-tile depth sort.
+//
+// Eq. 1 (Sec. 3.1) projects each 3D Gaussian; the blend visits Gaussians in depth
+// order per pixel (Sec. 3.1).  Work is binned by 16x16 tile: each (view, Gaussian)
+// lists itself in every tile its 3-sigma rectangle touches, and each tile's list
+// is sorted by (FP32 depth bits, Gaussian index).
+//
+// Design: a counting sort by tile (one atomic per pair to count, a scan, one atomic
+// per pair to place) followed by a per-tile sort in shared memory.  Each pair is
+// written once and read once by the sort, instead of the 6-8 read/write passes of
+// a global radix sort over (view, tile, depth) keys.
+#include "launch.h"
+
+namespace tsp {
+
+namespace {
+
+__device__ __forceinline__ void sh_colour(const float* sh, int deg, float x, float y, float z, float* rgb)
+{
+    // Real spherical harmonics (Condon-Shortley phase) up to degree 3:
+    // k0 = 1/(2 sqrt(pi)), k1 = sqrt(3/(4 pi)), k2a = sqrt(15/pi)/2, k2b = sqrt(5/pi)/4,
+    // k2c = sqrt(15/pi)/4, k3a = sqrt(35/(2 pi))/4, k3b = sqrt(105/pi)/2,
+    // k3c = sqrt(21/(2 pi))/4, k3d = sqrt(7/pi)/4, k3e = sqrt(105/pi)/4.
+    const float k0 = 0.28209479177387814f, k1 = 0.4886025119029199f;
+    const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.5462742152960396f;
+    const float k3a = 0.5900435899266435f, k3b = 2.890611442640554f, k3c = 0.4570457994644658f;
+    const float k3d = 0.3731763325901154f, k3e = 1.445305721320277f;
+    float Y[16];
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = k0;
+    Y[1] = -k1 * y; Y[2] = k1 * z; Y[3] = -k1 * x;
+    Y[4] = k2a * x * y; Y[5] = -k2a * y * z; Y[6] = k2b * (2.f * zz - xx - yy);
+    Y[7] = -k2a * x * z; Y[8] = k2c * (xx - yy);
+    Y[9] = -k3a * y * (3.f * xx - yy); Y[10] = k3b * x * y * z;
+    Y[11] = -k3c * y * (4.f * zz - xx - yy); Y[12] = k3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -k3c * x * (4.f * zz - xx - yy); Y[14] = k3e * z * (xx - yy);
+    Y[15] = -k3a * x * (xx - 3.f * yy);
+    const int nb = (deg + 1) * (deg + 1);
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+    for (int k = 0; k < nb; ++k) {
+        r += Y[k] * sh[3 * k];
+        g += Y[k] * sh[3 * k + 1];
+        b += Y[k] * sh[3 * k + 2];
+    }
+    rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(g, 0.f); rgb[2] = fmaxf(b, 0.f);
+}
+
+// grid (ceil(n/256), V): one thread per (view, Gaussian), Gaussian index fastest.
+__global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const float4* __restrict__ mo,
+                                                    const float4* __restrict__ q,
+                                                    const float4* __restrict__ s,
+                                                    const float* __restrict__ sh, int sh_degree,
+                                                    int mode, Work w)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    if (g >= vs.n) return;
+    const size_t i = (size_t)v * vs.n + g;
+    if (mode == 0) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        w.moments[4 * i] = z; w.moments[4 * i + 1] = z; w.moments[4 * i + 2] = z; w.moments[4 * i + 3] = z;
+    }
+    const float4 m = mo[g];
+    KeyProj p;
+    if (!key_project(vs.cam[v], m, q[g], s[g], vs.tiles_x[v], vs.tiles_y[v], p)) {
+        w.rect[i] = make_short4(0, 0, 0, 0);
+        w.touched[i] = 0u;
+        w.depth[i] = 0u;
+        return;
+    }
+    w.rect[i] = make_short4((short)p.x0, (short)p.y0, (short)p.x1, (short)p.y1);
+    w.touched[i] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
+    w.depth[i] = __float_as_uint(p.pz);
+    const float3 f = blend_factor(p);
+    w.geom0[i] = make_float4(p.mx, p.my, f.x, f.y);
+    w.geom1[i] = make_float2(f.z, m.w);
+    if (mode == 1) {
+        const DevCam& c = vs.cam[v];
+        // camera centre C = -R^T t; colour depends on the unit direction C -> mean
+        const float Cx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
+        const float Cy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
+        const float Cz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
+        float dx = m.x - Cx, dy = m.y - Cy, dz = m.z - Cz;
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv; dy *= inv; dz *= inv;
+        float rgb[3];
+        sh_colour(sh + (size_t)g * (sh_degree + 1) * (sh_degree + 1) * 3, sh_degree, dx, dy, dz, rgb);
+        w.color[i] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+    }
+    const uint32_t base = vs.toff[v];
+    const int tx_n = vs.tiles_x[v];
+    for (int ty = p.y0; ty < p.y1; ++ty)
+        for (int tx = p.x0; tx < p.x1; ++tx)
+            atomicAdd(&w.tile_count[base + (uint32_t)(ty * tx_n + tx)], 1u);
+}
+
+// Single CTA exclusive scan of NT counts; writes NT+1 offsets and K.
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ off,
+                                               uint32_t NT, uint32_t cap, uint32_t* dstatus)
+{
+    __shared__ unsigned long long warp_tot[32];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t per = (NT + 1023u) / 1024u;
+    const uint32_t b = min(tid * per, NT), e = min(b + per, NT);
+    unsigned long long sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += cnt[i];
+    // inclusive scan across the block
+    const int lane = tid & 31, wid = tid >> 5;
+    unsigned long long x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long t = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    unsigned long long run = x - sum + (wid > 0 ? warp_tot[wid - 1] : 0ull);
+    for (uint32_t i = b; i < e; ++i) {
+        off[i] = (uint32_t)min(run, 0xffffffffull);
+        run += cnt[i];
+    }
+    if (tid == 1023) {
+        const unsigned long long K = warp_tot[31];
+        off[NT] = (uint32_t)min(K, 0xffffffffull);
+        dstatus[1] = (uint32_t)(K & 0xffffffffull);
+        dstatus[2] = (uint32_t)(K >> 32);
+        if (K > cap) atomicOr(&dstatus[0], kStatusOverflow);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    if (g >= vs.n) return;
+    const size_t i = (size_t)v * vs.n + g;
+    if (w.touched[i] == 0u) return;
+    const short4 r = w.rect[i];
+    const uint64_t e = ((uint64_t)w.depth[i] << 32) | (uint32_t)g;
+    const uint32_t base = vs.toff[v];
+    const int tx_n = vs.tiles_x[v];
+    for (int ty = r.y; ty < r.w; ++ty)
+        for (int tx = r.x; tx < r.z; ++tx) {
+            const uint32_t t = base + (uint32_t)(ty * tx_n + tx);
+            const uint32_t slot = atomicAdd(&w.tile_fill[t], 1u);
+            const uint64_t pos = (uint64_t)w.tile_off[t] + slot;
+            if (pos < w.cap) w.pairs[pos] = e;
+        }
+}
+
+constexpr int kSortCap = 4096;      // entries sorted in shared memory at once
+constexpr int kSortThreads = 256;
+
+// Bitonic sort of n <= kSortCap keys at src (global) in shared memory, written back.
+__device__ void smem_sort(uint64_t* src, uint32_t n, uint64_t* s)
+{
+    uint32_t P = 2;
+    while (P < n) P <<= 1;
+    for (uint32_t i = threadIdx.x; i < P; i += kSortThreads) s[i] = i < n ? src[i] : ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += kSortThreads) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const uint64_t a = s[i], b = s[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { s[i] = b; s[l] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) src[i] = s[i];
+    __syncthreads();
+}
+
+// One CTA per tile.  Lists up to kSortCap sort in shared memory; longer lists sort
+// kSortCap-sized runs there and then merge runs pairwise in global memory (each key
+// finds its output slot by a binary search in the partner run; keys are unique).
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort(const uint32_t* __restrict__ off,
+                                                            uint64_t* pairs, uint64_t* tmp, uint32_t cap)
+{
+    __shared__ uint64_t s[kSortCap];
+    const uint32_t t = blockIdx.x;
+    const uint32_t b = min(off[t], cap), e = min(off[t + 1], cap);
+    if (e <= b + 1) return;
+    const uint32_t n = e - b;
+    if (n <= (uint32_t)kSortCap) {
+        smem_sort(pairs + b, n, s);
+        return;
+    }
+    for (uint32_t c = 0; c < n; c += kSortCap) smem_sort(pairs + b + c, min((uint32_t)kSortCap, n - c), s);
+    uint64_t* src = pairs + b;
+    uint64_t* dst = tmp + b;
+    for (uint32_t L = kSortCap; L < n; L <<= 1) {
+        for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
+            const uint32_t run = i / L, start = run * L, partner = run ^ 1u;
+            const uint64_t key = src[i];
+            const uint64_t ps64 = (uint64_t)partner * L;
+            if (ps64 >= n) { dst[i] = key; continue; }
+            const uint32_t ps = (uint32_t)ps64, pe = min(ps + L, n);
+            uint32_t lo = ps, hi = pe;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (src[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            const uint32_t pair_start = min(run, partner) * L;
+            dst[pair_start + (i - start) + (lo - ps)] = key;
+        }
+        __syncthreads();
+        uint64_t* x = src; src = dst; dst = x;
+    }
+    if (src != pairs + b)
+        for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) pairs[b + i] = src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
+                              const float* sh, int sh_degree, int mode, const Work& w, cudaStream_t st)
+{
+    if (vs.n == 0 || vs.V == 0) return cudaSuccess;
+    dim3 grid((vs.n + 255) / 256, vs.V);
+    k_preprocess<<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, mode, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st)
+{
+    k_scan<<<1, 1024, 0, st>>>(w.tile_count, w.tile_off, NT, w.cap, w.dstatus);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st)
+{
+    if (vs.n == 0 || vs.V == 0) return cudaSuccess;
+    dim3 grid((vs.n + 255) / 256, vs.V);
+    k_scatter<<<grid, 256, 0, st>>>(vs, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
+{
+    if (NT == 0) return cudaSuccess;
+    k_tile_sort<<<NT, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap);
+    return cudaGetLastError();
+}
+
+}  // namespace tsp

@@ -1,0 +1,199 @@
+// common.cuh -- types and device helpers shared by the libtsplat kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tsplat.h"
+
+namespace tsp {
+
+constexpr int kTile = 16;                 // raster tile edge (pixels)
+constexpr int kTilePx = kTile * kTile;    // threads per raster CTA
+constexpr int kMaxViews = TSP_MAX_VIEWS;
+
+struct DevCam {
+    int W, H;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+};
+
+// Everything a kernel needs to know about the views of one call.  Passed by value
+// as a kernel parameter (about 3.3 KB), so no host->device copy is needed.
+struct ViewSet {
+    int V;
+    int n;
+    DevCam cam[kMaxViews];
+    int tiles_x[kMaxViews];
+    int tiles_y[kMaxViews];
+    uint32_t toff[kMaxViews + 1];         // first global tile id of each view
+    const float2* disp[kMaxViews];
+    const uint8_t* vis[kMaxViews];
+};
+
+// Per-view output images of the colour render.
+struct RenderOut {
+    float* rgb[kMaxViews];
+    float* T[kMaxViews];
+};
+
+// Workspace pointers (device), owned by the context.
+struct Work {
+    short4* rect;          // [V*n] tile rect x0 y0 x1 y1
+    uint32_t* depth;       // [V*n] FP32 depth bits
+    uint32_t* touched;     // [V*n]
+    float4* geom0;         // [V*n] mu_x, mu_y, i11, k  (blend factor form)
+    float2* geom1;         // [V*n] i22, opacity
+    float4* color;         // [V*n] render colour
+    float4* moments;       // [V*n*4] 16 floats per (view, Gaussian)
+    float4* vres0;         // [V*n] mu'_x, mu'_y, shift c_x, c_y
+    float4* vres1;         // [V*n] S'xx, S'xy, S'yy, sum w
+    uint2* vres2;          // [V*n] view flags, pixels
+    uint32_t* tile_count;  // [NT]
+    uint32_t* tile_fill;   // [NT]
+    uint32_t* tile_off;    // [NT+1]
+    uint64_t* pairs;       // [cap]
+    uint64_t* pairs_tmp;   // [cap]
+    uint32_t cap;
+    uint32_t* dstatus;     // [4]: 0 flags (bit 0 overflow), 1 K (low 32 bits), 2 K high
+    unsigned long long* stats;  // [4] raster work counters (collect_stats only)
+};
+
+struct FitParams {
+    float det_min, sumw_min_view, lam_min_px2, sumw_min_total, cov_rcond_min;
+    int min_px_view, min_views, min_px_total;
+};
+
+constexpr uint32_t kStatusOverflow = 1u;
+
+// --------------------------------------------------------------------------
+// Key path: culling, depth key and tile rectangle in FP32 with a fixed order of
+// correctly rounded operations (every op spelled with an _rn intrinsic, so the
+// compiler cannot contract or reorder).  The same sequence also yields the 2D
+// covariance factor V = J W R(q) S (Eq. 1) used for blending and for Eq. 2.
+// --------------------------------------------------------------------------
+struct KeyProj {
+    float mx, my;          // mu_2D
+    float pz;              // camera depth
+    float V0[3], V1[3];    // rows of J W R(q) S: Sigma_2D = V V^T (undilated)
+    float a, b, c;         // undilated Sigma_2D entries
+    int x0, y0, x1, y1;    // tile rectangle
+};
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ff(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+
+// Returns false if the Gaussian is culled or touches no tile in this view.
+__device__ __forceinline__ bool key_project(const DevCam& c, float4 m, float4 q, float4 s,
+                                            int tiles_x, int tiles_y, KeyProj& o)
+{
+    const float* R = c.R;
+    const float px = ff(R[0], m.x, ff(R[1], m.y, ff(R[2], m.z, c.t[0])));
+    const float py = ff(R[3], m.x, ff(R[4], m.y, ff(R[5], m.z, c.t[1])));
+    const float pz = ff(R[6], m.x, ff(R[7], m.y, ff(R[8], m.z, c.t[2])));
+    if (!(pz > 0.2f)) return false;
+    const float iz = fd(1.0f, pz);
+    const float un = fm(px, iz), vn = fm(py, iz);
+    const float limx = fm(1.3f, fd(fm(0.5f, __int2float_rn(c.W)), c.fx));
+    const float limy = fm(1.3f, fd(fm(0.5f, __int2float_rn(c.H)), c.fy));
+    if (!(fabsf(un) <= limx) || !(fabsf(vn) <= limy)) return false;
+    o.mx = ff(c.fx, un, c.cx);
+    o.my = ff(c.fy, vn, c.cy);
+    o.pz = pz;
+
+    const float n2 = ff(q.x, q.x, ff(q.y, q.y, ff(q.z, q.z, fm(q.w, q.w))));
+    if (!(n2 > 0.0f)) return false;
+    const float inv = fd(1.0f, __fsqrt_rn(n2));
+    const float w = fm(q.x, inv), x = fm(q.y, inv), y = fm(q.z, inv), z = fm(q.w, inv);
+    const float xx = fm(x, x), yy = fm(y, y), zz = fm(z, z);
+    const float xy = fm(x, y), xz = fm(x, z), yz = fm(y, z);
+    const float wx = fm(w, x), wy = fm(w, y), wz = fm(w, z);
+    float Q[3][3];
+    Q[0][0] = fs(1.0f, fm(2.0f, fa(yy, zz)));
+    Q[0][1] = fm(2.0f, fs(xy, wz));
+    Q[0][2] = fm(2.0f, fa(xz, wy));
+    Q[1][0] = fm(2.0f, fa(xy, wz));
+    Q[1][1] = fs(1.0f, fm(2.0f, fa(xx, zz)));
+    Q[1][2] = fm(2.0f, fs(yz, wx));
+    Q[2][0] = fm(2.0f, fs(xz, wy));
+    Q[2][1] = fm(2.0f, fa(yz, wx));
+    Q[2][2] = fs(1.0f, fm(2.0f, fa(xx, yy)));
+    const float sc[3] = {s.x, s.y, s.z};
+    float M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = fm(Q[i][j], sc[j]);
+
+    const float j00 = fm(c.fx, iz), j02 = -fm(fm(c.fx, un), iz);
+    const float j11 = fm(c.fy, iz), j12 = -fm(fm(c.fy, vn), iz);
+    float T0[3], T1[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T0[j] = ff(j00, R[j], fm(j02, R[6 + j]));
+        T1[j] = ff(j11, R[3 + j], fm(j12, R[6 + j]));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        o.V0[j] = ff(T0[0], M[0][j], ff(T0[1], M[1][j], fm(T0[2], M[2][j])));
+        o.V1[j] = ff(T1[0], M[0][j], ff(T1[1], M[1][j], fm(T1[2], M[2][j])));
+    }
+    o.a = ff(o.V0[0], o.V0[0], ff(o.V0[1], o.V0[1], fm(o.V0[2], o.V0[2])));
+    o.b = ff(o.V0[0], o.V1[0], ff(o.V0[1], o.V1[1], fm(o.V0[2], o.V1[2])));
+    o.c = ff(o.V1[0], o.V1[0], ff(o.V1[1], o.V1[1], fm(o.V1[2], o.V1[2])));
+    const float ad = fa(o.a, 0.3f), cd = fa(o.c, 0.3f);
+    const float det = ff(ad, cd, -fm(o.b, o.b));
+    if (!(det > 0.0f)) return false;
+    const float mid = fm(0.5f, fa(ad, cd));
+    const float disc = fmaxf(0.1f, ff(mid, mid, -det));
+    const float lam = fa(mid, __fsqrt_rn(disc));
+    const float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
+    const float ftw = (float)kTile;
+    const float gx = __int2float_rn(tiles_x), gy = __int2float_rn(tiles_y);
+    const float fx0 = fminf(fmaxf(floorf(fd(fs(o.mx, r), ftw)), 0.0f), gx);
+    const float fx1 = fminf(fmaxf(fa(floorf(fd(fa(o.mx, r), ftw)), 1.0f), 0.0f), gx);
+    const float fy0 = fminf(fmaxf(floorf(fd(fs(o.my, r), ftw)), 0.0f), gy);
+    const float fy1 = fminf(fmaxf(fa(floorf(fd(fa(o.my, r), ftw)), 1.0f), 0.0f), gy);
+    o.x0 = (int)fx0; o.x1 = (int)fx1; o.y0 = (int)fy0; o.y1 = (int)fy1;
+    return o.x1 > o.x0 && o.y1 > o.y0;
+}
+
+// sqrt(log2(e) / 2): with this factor folded into the Cholesky factor, the blend
+// evaluates G = exp(-q/2) as exp2(-(z1^2 + z2^2)).
+constexpr float kHalfLog2eSqrt = 0.84932180028801904f;
+
+// Blend parameters in factor form.  The dilated covariance is the Gram matrix of
+// the columns (V0, sqrt(0.3), 0) and (V1, 0, sqrt(0.3)); a Gram-Schmidt step on
+// them gives its Cholesky factor L = [[l11, 0], [l21, l22]] without forming
+// a c - b^2, which keeps thin Gaussians accurate.  Returns (i11, k, i22) with
+// z1 = dx i11, z2 = (dy - k dx) i22.
+__device__ __forceinline__ float3 blend_factor(const KeyProj& p)
+{
+    const float s3 = 0.54772255750516611f;   // sqrt(0.3)
+    const float ad = p.a + 0.3f;
+    const float l11 = sqrtf(ad);
+    const float l21 = p.b / l11;
+    const float f = l21 / l11;
+    const float r0 = p.V1[0] - f * p.V0[0];
+    const float r1 = p.V1[1] - f * p.V0[1];
+    const float r2 = p.V1[2] - f * p.V0[2];
+    const float r3 = -f * s3;
+    const float l22sq = r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3 + 0.3f;
+    const float l22 = sqrtf(l22sq);
+    return make_float3(kHalfLog2eSqrt / l11, f, kHalfLog2eSqrt / l22);
+}
+
+__device__ __forceinline__ void view_of_tile(const ViewSet& vs, uint32_t tile, int& v, int& tx, int& ty)
+{
+    v = 0;
+    while (v + 1 < vs.V && tile >= vs.toff[v + 1]) ++v;
+    const uint32_t local = tile - vs.toff[v];
+    tx = (int)(local % (uint32_t)vs.tiles_x[v]);
+    ty = (int)(local / (uint32_t)vs.tiles_x[v]);
+}
+
+}  // namespace tsp

@@ -1,0 +1,34 @@
+// launch.h -- host-side launchers of the libtsplat kernels (one per pipeline step).
+#pragma once
+
+#include "common.cuh"
+
+namespace tsp {
+
+// a1: project every (view, Gaussian), zero its moment record, count tiles.
+// mode 0 = motion fit, 1 = render (also evaluates colour from sh).
+cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
+                              const float* sh, int sh_degree, int mode, const Work& w,
+                              cudaStream_t st);
+// a2: exclusive scan of the per-tile counts -> tile offsets and the pair count K.
+cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st);
+// a2: emit (depth << 32 | g) into each touched tile's slice.
+cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st);
+// a3: sort each tile's slice ascending (depth, then Gaussian index).
+cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st);
+// a5: blend and accumulate alpha T weighted track moments per (view, Gaussian).
+cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
+                                     cudaStream_t st);
+// render colour and final transmittance.
+cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
+                                 float* const* final_T, cudaStream_t st);
+// a6: per-view discard tests, affine solve, Eq. 2.
+cudaError_t launch_view_solve(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
+                              const FitParams& fp, const Work& w, float* view_affine,
+                              uint32_t* view_flags, cudaStream_t st);
+// a7-a9: triangulation, covariance fit, eigen decomposition and outputs.
+cudaError_t launch_multiview(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
+                             const FitParams& fp, const Work& w, float4* out_means, float4* out_quats,
+                             float4* out_scales, uint32_t* out_status, cudaStream_t st);
+
+}  // namespace tsp

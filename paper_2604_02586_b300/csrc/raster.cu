@@ -1,0 +1,245 @@
+// raster.cu -- a5 raster-accumulate (Sec. 4.3.5) and the colour render (Sec. 3.1).
+//
+// One CTA per 16x16 tile, one thread per pixel.  The tile's depth-sorted list is
+// walked in batches of kBatch Gaussians whose blend parameters are staged in
+// shared memory.  Each pixel blends front to back: alpha = min(0.99, o G(x)),
+// Gaussians with alpha < 1/255 are skipped, the walk stops before a Gaussian that
+// would bring the transmittance below 1e-4, and w = alpha T (Eq. 4's weight).
+//
+// Moments: every visible pixel adds 16 values per Gaussian.  The 32 lanes of a
+// warp are folded with a transposing butterfly (16 shuffles for 16 values, each
+// step exchanges half of the values still held), warps are summed through
+// shared memory, and one float4 atomic per 4 values goes to global memory, so a
+// (tile, Gaussian) pair costs 4 vector atomics whatever the number of pixels.
+#include "launch.h"
+
+namespace tsp {
+
+namespace {
+
+constexpr int kBatch = 64;
+constexpr int kWarps = kTilePx / 32;
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+// Sum of v[k] over the warp for k = lane >> 1, returned in every lane.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 8];
+        const float keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 4];
+        const float keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 2];
+        const float keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(kFull, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
+// kStats = true is a measurement variant: the same walk, plus exact counts of the
+// work done (evaluations, blended contributions, moment additions, list entries).
+template <bool kStats>
+__global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs, const Work w)
+{
+    __shared__ float4 s_g0[kBatch];
+    __shared__ float2 s_g1[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ __align__(16) float s_part[kBatch][kWarps][16];
+
+    const uint32_t tile = blockIdx.x;
+    const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
+    if (beg >= end) return;
+    int v, tx, ty;
+    view_of_tile(vs, tile, v, tx, ty);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = vs.cam[v].W, H = vs.cam[v].H;
+    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
+    const bool inside = px < W && py < H;
+    float ddx = 0.f, ddy = 0.f;
+    bool vis = false;
+    if (inside) {
+        const size_t pix = (size_t)py * W + px;
+        const float2 d = vs.disp[v][pix];
+        ddx = d.x; ddy = d.y;
+        vis = vs.vis[v][pix] != 0;
+    }
+    // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
+    const bool stat = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
+    const float xc = (float)px + 0.5f, yc = (float)py + 0.5f;
+    float T = 1.0f;
+    bool done = !inside;
+    const size_t vbase = (size_t)v * vs.n;
+    unsigned long long n_eval = 0, n_blend = 0, n_add = 0, n_list = 0;
+
+    for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
+        const int nb = (int)min((uint32_t)kBatch, end - b0);
+        if (kStats && tid == 0) n_list += nb;
+        if (tid < nb) {
+            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+            s_id[tid] = g;
+            s_g0[tid] = w.geom0[vbase + g];
+            s_g1[tid] = w.geom1[vbase + g];
+        }
+        __syncthreads();
+        for (int j = 0; j < nb; ++j) {
+            float val[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) val[k] = 0.f;
+            bool add = false;
+            if (!done) {
+                const float4 g0 = s_g0[j];
+                const float2 g1 = s_g1[j];
+                const float ex = xc - g0.x, ey = yc - g0.y;
+                const float z1 = ex * g0.z;
+                const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
+                const float pw = fmaf(z2, z2, z1 * z1);
+                const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+                if (kStats) ++n_eval;
+                if (alpha >= kAlphaMin) {
+                    const float Tn = T * (1.0f - alpha);
+                    if (Tn < kTMin) {
+                        done = true;
+                    } else {
+                        const float wgt = alpha * T;
+                        T = Tn;
+                        if (kStats) ++n_blend;
+                        if (vis) {
+                            if (kStats) ++n_add;
+                            add = true;
+                            const float wx = wgt * ex, wy = wgt * ey;
+                            val[0] = wgt; val[1] = wx; val[2] = wy;
+                            val[3] = wx * ex; val[4] = wx * ey; val[5] = wy * ey;
+                            val[6] = wgt * ddx; val[7] = wgt * ddy;
+                            val[8] = wx * ddx; val[9] = wx * ddy;
+                            val[10] = wy * ddx; val[11] = wy * ddy;
+                            val[12] = stat ? wgt : 0.f;
+                            val[13] = 1.f;
+                            val[14] = stat ? 1.f : 0.f;
+                        }
+                    }
+                }
+            }
+            float r = 0.f;
+            if (__ballot_sync(kFull, add)) r = warp_transpose_sum16(val, lane);
+            if ((lane & 1) == 0) s_part[j][warp][lane >> 1] = r;
+        }
+        __syncthreads();
+        if (tid < nb * 4) {
+            const int j = tid >> 2, qd = tid & 3;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) {
+                const float4 p = *reinterpret_cast<const float4*>(&s_part[j][k][4 * qd]);
+                acc.x += p.x; acc.y += p.y; acc.z += p.z; acc.w += p.w;
+            }
+            if (acc.x != 0.f || acc.y != 0.f || acc.z != 0.f || acc.w != 0.f)
+                atomicAdd(&w.moments[(vbase + s_id[j]) * 4 + qd], acc);
+        }
+        if (__syncthreads_count(!done) == 0) break;
+    }
+    if (kStats) {
+        atomicAdd(&w.stats[0], n_eval);
+        atomicAdd(&w.stats[1], n_blend);
+        atomicAdd(&w.stats[2], n_add);
+        if (tid == 0) atomicAdd(&w.stats[3], n_list);
+    }
+}
+
+__global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, const Work w,
+                                                           const RenderOut ro)
+{
+    __shared__ float4 s_g0[kBatch];
+    __shared__ float2 s_g1[kBatch];
+    __shared__ float4 s_c[kBatch];
+    const uint32_t tile = blockIdx.x;
+    const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
+    int v, tx, ty;
+    view_of_tile(vs, tile, v, tx, ty);
+    const int tid = threadIdx.x;
+    const int W = vs.cam[v].W, H = vs.cam[v].H;
+    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
+    const bool inside = px < W && py < H;
+    const float xc = (float)px + 0.5f, yc = (float)py + 0.5f;
+    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
+    bool done = !inside;
+    const size_t vbase = (size_t)v * vs.n;
+    for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
+        const int nb = (int)min((uint32_t)kBatch, end - b0);
+        if (tid < nb) {
+            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+            s_g0[tid] = w.geom0[vbase + g];
+            s_g1[tid] = w.geom1[vbase + g];
+            s_c[tid] = w.color[vbase + g];
+        }
+        __syncthreads();
+        for (int j = 0; j < nb && !done; ++j) {
+            const float4 g0 = s_g0[j];
+            const float2 g1 = s_g1[j];
+            const float ex = xc - g0.x, ey = yc - g0.y;
+            const float z1 = ex * g0.z;
+            const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
+            const float pw = fmaf(z2, z2, z1 * z1);
+            const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+            if (alpha < kAlphaMin) continue;
+            const float Tn = T * (1.0f - alpha);
+            if (Tn < kTMin) { done = true; break; }
+            const float wgt = alpha * T;
+            const float4 c = s_c[j];
+            cr = fmaf(wgt, c.x, cr); cg = fmaf(wgt, c.y, cg); cb = fmaf(wgt, c.z, cb);
+            T = Tn;
+        }
+        if (__syncthreads_count(!done) == 0) break;
+    }
+    if (inside) {
+        const size_t pix = (size_t)py * W + px;
+        float* o = ro.rgb[v] + 3 * pix;
+        o[0] = cr; o[1] = cg; o[2] = cb;
+        ro.T[v][pix] = T;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
+                                     cudaStream_t st)
+{
+    if (NT == 0 || vs.n == 0) return cudaSuccess;
+    if (stats)
+        k_raster_accumulate<true><<<NT, kTilePx, 0, st>>>(vs, w);
+    else
+        k_raster_accumulate<false><<<NT, kTilePx, 0, st>>>(vs, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
+                                 float* const* final_T, cudaStream_t st)
+{
+    if (NT == 0) return cudaSuccess;
+    RenderOut ro;
+    for (int v = 0; v < vs.V; ++v) { ro.rgb[v] = rgb[v]; ro.T[v] = final_T[v]; }
+    k_raster_render<<<NT, kTilePx, 0, st>>>(vs, w, ro);
+    return cudaGetLastError();
+}
+
+}  // namespace tsp
