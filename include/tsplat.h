@@ -94,14 +94,17 @@ typedef struct tsp_result {
     float* view_moments;        /* optional [V][n][16] PWI-LS moments, see below    */
     uint32_t* view_flags;       /* optional [V][n] TSP_VIEW_* bits                 */
 } tsp_result;
-/* view_moments layout, coordinates are pixel centre minus mu_2D (x~, y~) and the
- * tracked displacement d = x' - x, w = alpha T (Eq. 4):
+/* view_moments layout, w = alpha T (Eq. 4), d = x' - x the tracked displacement and
+ * (x~, y~) = pixel centre minus the moment origin o, where o is mu_2D clamped to
+ * the image rectangle [0, W] x [0, H] (o = mu_2D whenever the centre is on-image):
  *   0 sum w            1 sum w x~         2 sum w y~        3 sum w x~^2
  *   4 sum w x~ y~      5 sum w y~^2       6 sum w dx        7 sum w dy
  *   8 sum w x~ dx      9 sum w x~ dy     10 sum w y~ dx    11 sum w y~ dy
  *  12 sum w over static pixels (|d| < 1)  13 pixels added    14 static pixels  15 0
+ * In slots 6-11, d is taken relative to a reference displacement r (the track at
+ * the pixel holding o), which leaves [A] unchanged and adds r to the intercept.
  * Eq. 4's V1 and V2 follow: V1 = [[3,4,1],[4,5,2],[1,2,0]] and
- * V2 = V1[:, 0:2] + [[8,9],[10,11],[6,7]] in this (x~, y~, 1) basis. */
+ * V2 = V1[:, 0:2] + [[8,9],[10,11],[6,7]] + V1[:, 2] r^T in this (x~, y~, 1) basis. */
 
 typedef struct tsp_options {
     int32_t tile_w, tile_h;     /* raster tile; 16 x 16 is the only supported value */
@@ -112,7 +115,7 @@ typedef struct tsp_options {
     int32_t min_views;          /* Sec. 5.1: 2                                     */
     float sumw_min_total;       /* Sec. 5.1: 1e-3                                  */
     int32_t min_px_total;       /* Sec. 5.1: 3                                     */
-    float cov_rcond_min;        /* covariance system conditioning floor: 1e-10     */
+    float cov_rcond_min;        /* covariance system sigma_min/sigma_max floor: 1e-6 */
     int32_t async_pairs;        /* 0: tsp_fit_motion waits for the pair count and  */
                                 /*    grows the pair buffer before sorting;        */
                                 /* 1: never waits; overflow -> TSP_ERR_OVERFLOW at  */
@@ -192,9 +195,12 @@ typedef enum {
     TSP_I_TILE_OFFSETS = 4,  /* uint32[NT+1]: tile t owns pairs [off[t], off[t+1])   */
     TSP_I_PAIRS = 5,         /* uint64[K]: depth_bits << 32 | Gaussian, sorted per tile */
     TSP_I_MOMENTS = 6,       /* float[V][n][16], layout as view_moments              */
-    TSP_I_STATS = 7          /* uint64[4] raster work of the last call when           */
+    TSP_I_STATS = 7,         /* uint64[4] raster work of the last call when           */
                              /* collect_stats = 1: (pixel, Gaussian) evaluations,     */
                              /* blended contributions, moment additions, list entries */
+    TSP_I_VIEW_MEANS = 8,    /* float[V][n][4]: mu_2D' (x, y) and its shift from mu_2D */
+    TSP_I_VIEW_COV = 9       /* float[V][n][8]: rows of B with Sigma_2D' = B B^T     */
+                             /* (B00 B01 B02 sum-w, B10 B11 B12 0)                     */
 } tsp_intermediate;
 tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, size_t* size_out);
 

@@ -63,7 +63,7 @@ class Outputs(C.Structure):
 
 def default_options(tile=(16, 16)) -> Options:
     """Sec. 5.1 thresholds plus the two added guards (lambda_min, covariance rcond)."""
-    return Options(tile[0], tile[1], 1e-12, 1e-3, 2, 1e-4, 2, 1e-3, 3, 1e-10)
+    return Options(tile[0], tile[1], 1e-12, 1e-3, 2, 1e-4, 2, 1e-3, 3, 1e-6)
 
 
 _lib = None
@@ -160,7 +160,7 @@ def fit_motion(scene, options: Options | None = None, sample=None, per_view=True
         tr[v].disp, tr[v].vis = d.ctypes.data, m.ctypes.data
     res = {}
     if per_view:
-        res.update(moments=np.zeros((V, n, 16)), mean2d=np.zeros((V, n, 2)),
+        res.update(moments=np.zeros((V, n, 18)), mean2d=np.zeros((V, n, 2)),
                    cov2d=np.zeros((V, n, 3)), view_flags=np.zeros((V, n), np.uint32),
                    view_affine=np.zeros((V, n, 6)), view_mean2d=np.zeros((V, n, 2)),
                    view_cov2d=np.zeros((V, n, 3)))

@@ -80,10 +80,10 @@ enum { OS_POS_OK = 1, OS_COV_OK = 2, OS_NEG_EIG = 4, OS_FEW_VIEWS = 8, OS_LOW_AL
 #define ALPHA_MAX ((double)0.99f)
 #define T_MIN ((double)1e-4f)
 #define DILATION 0.3
-/* Half-widths of the windows in which an FP32 evaluation may decide a blend
- * threshold differently from this FP64 one (used to flag pixels, not to decide). */
-#define ALPHA_WIN 2e-7
-#define T_WIN 1e-8
+/* Relative half-widths of the windows in which an FP32 evaluation may decide a
+ * blend threshold differently from this FP64 one (used to flag, not to decide). */
+#define ALPHA_WIN (2e-4 * ALPHA_MIN)
+#define T_WIN (1e-4 * T_MIN)
 
 /* ------------------------------------------------------------------------- */
 /* Key path (FP32, fixed operation order)                                    */
@@ -560,9 +560,12 @@ int orc_bin(int n, int V, const float* means_opacity, const float* quats, const 
  *  12    sum of w over static pixels (|x' - x| < 1 px)                  (Sec. 4.5.2)
  *  13    number of pixels that added moments
  *  14    number of those pixels that are static
- *  15    sum of w at pixels where an earlier threshold decision was within
- *        the FP32 window (ALPHA_WIN / T_WIN) -- bookkeeping for comparisons */
-#define NMOM 16
+ *  15    sum of w at pixels where this or an earlier blend decision (alpha vs
+ *        1/255, T (1 - alpha) vs 1e-4) lay inside the FP32 window -- bookkeeping
+ *        for comparisons with an FP32 implementation, not part of the method
+ *  16    number of such pixels
+ *  17    unused */
+#define NMOM 18
 
 typedef struct {
     const float* disp;    /* [H][W][2] */
@@ -605,16 +608,26 @@ static void blend_view(int v, const binctx* B, const int64_t* offsets, const uin
                                         + G->conic[2] * dy * dy;
                         double alpha = G->opacity * exp(-0.5 * qf);
                         if (alpha > ALPHA_MAX) alpha = ALPHA_MAX;
-                        if (fabs(alpha - ALPHA_MIN) <= ALPHA_WIN) pert = 1;
+                        if (fabs(alpha - ALPHA_MIN) <= ALPHA_WIN) {
+                            pert = 1;
+                            if (mom && vis && (!want || want[g]) && alpha < ALPHA_MIN) {
+                                mom[(size_t)g * NMOM + 16] += 1.0;   /* the FP32 side may add this pixel */
+                            }
+                        }
                         if (alpha < ALPHA_MIN) continue;
                         const double Tn = T * (1.0 - alpha);
-                        if (fabs(Tn - T_MIN) <= T_WIN) pert = 1;
+                        if (fabs(Tn - T_MIN) <= T_WIN) {
+                            pert = 1;
+                            if (mom && vis && (!want || want[g]) && Tn < T_MIN)
+                                mom[(size_t)g * NMOM + 16] += 1.0;
+                        }
                         if (Tn < T_MIN) break;
                         const double w = alpha * T;
                         if (rgb)
                             for (int ch = 0; ch < 3; ++ch) col[ch] += w * G->color[ch];
                         if (mom && vis && (!want || want[g])) {
                             double* M = mom + (size_t)g * NMOM;
+                            if (pert) { M[15] += w; M[16] += 1.0; }
                             const double xp = dx + ddx, yp = dy + ddy;   /* x' - mu_2D */
                             M[0] += w * dx * dx; M[1] += w * dx * dy; M[2] += w * dx;
                             M[3] += w * dy * dy; M[4] += w * dy;      M[5] += w;
@@ -623,7 +636,6 @@ static void blend_view(int v, const binctx* B, const int64_t* offsets, const uin
                             M[10] += w * xp;     M[11] += w * yp;
                             if (stat) { M[12] += w; M[14] += 1.0; }
                             M[13] += 1.0;
-                            if (pert) M[15] += w;
                         }
                         T = Tn;
                     }

@@ -25,7 +25,8 @@ class TSP:
     VIEW_OK, VIEW_FEW_PX, VIEW_LOW_ALPHA, VIEW_SINGULAR, VIEW_CULLED = 1, 2, 4, 8, 16
     POS_OK, COV_OK, NEG_EIG, FEW_VIEWS, LOW_ALPHA, FEW_PX, COV_SINGULAR, TRI_SINGULAR = \
         1, 2, 4, 8, 16, 32, 64, 128
-    I_COUNTS, I_RECT, I_DEPTH, I_TILES_TOUCHED, I_TILE_OFFSETS, I_PAIRS, I_MOMENTS, I_STATS = range(8)
+    I_COUNTS, I_RECT, I_DEPTH, I_TILES_TOUCHED, I_TILE_OFFSETS, I_PAIRS, I_MOMENTS, I_STATS, \
+        I_VIEW_MEANS, I_VIEW_COV = range(10)
     STAGES = ("project", "scan", "emit", "tile_sort", "raster", "view_solve", "multiview")
     MAX_VIEWS = 32
 
@@ -311,7 +312,8 @@ class Context:
         self._check(lib().tsp_inspect(self._h, which, None, 0, C.byref(size)), "tsp_inspect")
         dtype = {TSP.I_COUNTS: np.int64, TSP.I_RECT: np.int16, TSP.I_DEPTH: np.uint32,
                  TSP.I_TILES_TOUCHED: np.uint32, TSP.I_TILE_OFFSETS: np.uint32,
-                 TSP.I_PAIRS: np.uint64, TSP.I_MOMENTS: np.float32, TSP.I_STATS: np.uint64}[which]
+                 TSP.I_PAIRS: np.uint64, TSP.I_MOMENTS: np.float32, TSP.I_STATS: np.uint64,
+                 TSP.I_VIEW_MEANS: np.float32, TSP.I_VIEW_COV: np.float32}[which]
         a = np.empty(size.value // np.dtype(dtype).itemsize, dtype)
         self._check(lib().tsp_inspect(self._h, which, _hptr(a), size.value, None), "tsp_inspect")
         return a

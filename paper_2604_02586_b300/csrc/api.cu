@@ -27,7 +27,7 @@ struct tsp_context {
     std::string err;
     size_t held = 0;
     // per (view, Gaussian)
-    Buf rect, depth, touched, geom0, geom1, color, moments, vres0, vres1, vres2;
+    Buf rect, depth, touched, geom0, geom1, dref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
     Buf tiles, tile_off;
     // pairs
@@ -242,7 +242,8 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
     if ((s = ensure(ctx, ctx->depth, vn1 * 4))) return s;
     if ((s = ensure(ctx, ctx->touched, vn1 * 4))) return s;
     if ((s = ensure(ctx, ctx->geom0, vn1 * 16))) return s;
-    if ((s = ensure(ctx, ctx->geom1, vn1 * 8))) return s;
+    if ((s = ensure(ctx, ctx->geom1, vn1 * 16))) return s;
+    if ((s = ensure(ctx, ctx->dref, vn1 * 8))) return s;
     if (render) {
         if ((s = ensure(ctx, ctx->color, vn1 * 16))) return s;
     } else {
@@ -250,6 +251,7 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
         if ((s = ensure(ctx, ctx->vres0, vn1 * 16))) return s;
         if ((s = ensure(ctx, ctx->vres1, vn1 * 16))) return s;
         if ((s = ensure(ctx, ctx->vres2, vn1 * 8))) return s;
+        if ((s = ensure(ctx, ctx->vres3, vn1 * 16))) return s;
     }
     if ((s = ensure(ctx, ctx->tiles, (size_t)2 * (NT + 1) * 4))) return s;
     if ((s = ensure(ctx, ctx->tile_off, (size_t)(NT + 1) * 4))) return s;
@@ -266,12 +268,14 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
     w.depth = (uint32_t*)ctx->depth.p;
     w.touched = (uint32_t*)ctx->touched.p;
     w.geom0 = (float4*)ctx->geom0.p;
-    w.geom1 = (float2*)ctx->geom1.p;
+    w.geom1 = (float4*)ctx->geom1.p;
+    w.dref = (float2*)ctx->dref.p;
     w.color = (float4*)ctx->color.p;
     w.moments = (float4*)ctx->moments.p;
     w.vres0 = (float4*)ctx->vres0.p;
     w.vres1 = (float4*)ctx->vres1.p;
     w.vres2 = (uint2*)ctx->vres2.p;
+    w.vres3 = (float4*)ctx->vres3.p;
     w.tile_count = (uint32_t*)ctx->tiles.p;
     w.tile_fill = (uint32_t*)ctx->tiles.p + (NT + 1);
     w.tile_off = (uint32_t*)ctx->tile_off.p;
@@ -412,7 +416,7 @@ tsp_status tsp_default_options(tsp_options* o)
     o->min_views = 2;
     o->sumw_min_total = 1e-3f;
     o->min_px_total = 3;
-    o->cov_rcond_min = 1e-10f;
+    o->cov_rcond_min = 1e-6f;
     return TSP_OK;
 }
 
@@ -452,8 +456,8 @@ tsp_status tsp_destroy(tsp_context* ctx)
     if (!ctx) return TSP_OK;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->color,
-                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->tiles, &ctx->tile_off,
+    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->color,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off,
                   &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
                   &ctx->st_tracks};
     for (Buf* b : all) release(ctx, *b);
@@ -626,6 +630,22 @@ tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, siz
     }
     case TSP_I_MOMENTS: src = ctx->moments.p; size = vn * 64; break;
     case TSP_I_STATS: src = ctx->stats.p; size = ctx->stats.p ? 32 : 0; break;
+    case TSP_I_VIEW_MEANS: src = ctx->vres0.p; size = vn * 16; break;
+    case TSP_I_VIEW_COV: {
+        // two planes (vres1, vres3) interleaved per (view, Gaussian) on the host
+        size = vn * 32;
+        if (size_out) *size_out = size;
+        if (!dst) return TSP_OK;
+        std::vector<float4> a(vn), b(vn);
+        if (vn) {
+            TSP_CUDA(cudaMemcpy(a.data(), ctx->vres1.p, vn * 16, cudaMemcpyDeviceToHost));
+            TSP_CUDA(cudaMemcpy(b.data(), ctx->vres3.p, vn * 16, cudaMemcpyDeviceToHost));
+        }
+        std::vector<float4> ab(2 * vn);
+        for (size_t i = 0; i < vn; ++i) { ab[2 * i] = a[i]; ab[2 * i + 1] = b[i]; }
+        std::memcpy(dst, ab.data(), bytes < size ? bytes : size);
+        return TSP_OK;
+    }
     default: return fail(ctx, TSP_ERR_INVALID_ARG, "unknown intermediate");
     }
     if (size_out) *size_out = size;

@@ -72,8 +72,21 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
     w.touched[i] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
     w.depth[i] = __float_as_uint(p.pz);
     const float3 f = blend_factor(p);
-    w.geom0[i] = make_float4(p.mx, p.my, f.x, f.y);
-    w.geom1[i] = make_float2(f.z, m.w);
+    // mean relative to the rectangle's corner pixel (x0*16, y0*16), to ~1e-6 px
+    float2 ux, uy;
+    mean2d_df(vs.cam[v], m, ux, uy);
+    const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * kTile)), ux.y);
+    const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * kTile)), uy.y);
+    w.geom0[i] = make_float4(rx, ry, f.x, f.y);
+    const float2 dlt = moment_origin_shift(ux, uy, vs.cam[v].W, vs.cam[v].H);
+    w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);
+    if (mode == 0) {
+        // reference displacement: the track at the pixel holding the moment origin
+        const int W = vs.cam[v].W, H = vs.cam[v].H;
+        const int ox = min(max((int)floorf(ux.x + ux.y + dlt.x), 0), W - 1);
+        const int oy = min(max((int)floorf(uy.x + uy.y + dlt.y), 0), H - 1);
+        w.dref[i] = vs.disp[v][(size_t)oy * W + ox];
+    }
     if (mode == 1) {
         const DevCam& c = vs.cam[v];
         // camera centre C = -R^T t; colour depends on the unit direction C -> mean

@@ -43,12 +43,14 @@ struct Work {
     short4* rect;          // [V*n] tile rect x0 y0 x1 y1
     uint32_t* depth;       // [V*n] FP32 depth bits
     uint32_t* touched;     // [V*n]
-    float4* geom0;         // [V*n] mu_x, mu_y, i11, k  (blend factor form)
-    float2* geom1;         // [V*n] i22, opacity
+    float4* geom0;         // [V*n] mu - rect origin (x, y), i11, k  (blend factor form)
+    float4* geom1;         // [V*n] i22, opacity, moment origin - mu (x, y)
+    float2* dref;          // [V*n] reference displacement (track at the moment origin)
     float4* color;         // [V*n] render colour
     float4* moments;       // [V*n*4] 16 floats per (view, Gaussian)
     float4* vres0;         // [V*n] mu'_x, mu'_y, shift c_x, c_y
-    float4* vres1;         // [V*n] S'xx, S'xy, S'yy, sum w
+    float4* vres1;         // [V*n] B00, B01, B02, sum w   (Sigma_2D' = B B^T, B = A V)
+    float4* vres3;         // [V*n] B10, B11, B12, 0
     uint2* vres2;          // [V*n] view flags, pixels
     uint32_t* tile_count;  // [NT]
     uint32_t* tile_fill;   // [NT]
@@ -160,6 +162,84 @@ __device__ __forceinline__ bool key_project(const DevCam& c, float4 m, float4 q,
     const float fy1 = fminf(fmaxf(fa(floorf(fd(fa(o.my, r), ftw)), 1.0f), 0.0f), gy);
     o.x0 = (int)fx0; o.x1 = (int)fx1; o.y0 = (int)fy0; o.y1 = (int)fy1;
     return o.x1 > o.x0 && o.y1 > o.y0;
+}
+
+// --------------------------------------------------------------------------
+// Double-float arithmetic (Dekker / Knuth error-free transformations: TwoSum,
+// TwoProd via FMA) for the projected mean.  An FP32 pixel coordinate near 1000
+// carries ~6e-5 px of rounding, which moves alpha = o exp(-q/2) by ~1e-3 at the
+// edge of a 0.6 px footprint; a (hi, lo) pair keeps the mean to ~1e-9 px.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// mu_2D of the mean m in camera c as (hi, lo) pairs: u = ux.x + ux.y.
+__device__ __forceinline__ void mean2d_df(const DevCam& c, float4 m, float2& ux, float2& uy)
+{
+    const float* R = c.R;
+    float ph[3], pl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float p0, e0, p1, e1, p2, e2, s, f1, f2, f3;
+        two_prod(R[3 * k], m.x, p0, e0);
+        two_prod(R[3 * k + 1], m.y, p1, e1);
+        two_prod(R[3 * k + 2], m.z, p2, e2);
+        two_sum(p0, p1, s, f1);
+        two_sum(s, p2, s, f2);
+        two_sum(s, c.t[k], s, f3);
+        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, f1)), __fadd_rn(f2, f3));
+        fast_two_sum(s, lo, ph[k], pl[k]);
+    }
+    const float f[2] = {c.fx, c.fy}, cc[2] = {c.cx, c.cy};
+    float2 out[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        // q = p_k / p_z in double-float
+        const float q1 = __fdiv_rn(ph[k], ph[2]);
+        const float r = __fsub_rn(__fadd_rn(__fmaf_rn(-q1, ph[2], ph[k]), pl[k]), __fmul_rn(q1, pl[2]));
+        const float q2 = __fdiv_rn(r, ph[2]);
+        float qh, ql;
+        fast_two_sum(q1, q2, qh, ql);
+        // u = f q + c
+        float a, ae, sm, se;
+        two_prod(f[k], qh, a, ae);
+        ae = __fmaf_rn(f[k], ql, ae);
+        two_sum(a, cc[k], sm, se);
+        float uh, ul;
+        fast_two_sum(sm, __fadd_rn(se, ae), uh, ul);
+        out[k] = make_float2(uh, ul);
+    }
+    ux = out[0];
+    uy = out[1];
+}
+
+// Origin of a (view, Gaussian)'s moment sums: mu_2D clamped to the image
+// rectangle [0, W] x [0, H].  Returns delta = origin - mu_2D.  When the centre
+// lies off-image, only a sliver at the border is visible; sums taken about the
+// far-away centre would lose 2-3 digits to cancellation in FP32.
+__device__ __forceinline__ float2 moment_origin_shift(float2 ux, float2 uy, int W, int H)
+{
+    const float x = ux.x + ux.y, y = uy.x + uy.y;
+    const float fw = (float)W, fh = (float)H;
+    const float dx = x < 0.f ? -x : (x > fw ? fw - x : 0.f);
+    const float dy = y < 0.f ? -y : (y > fh ? fh - y : 0.f);
+    return make_float2(dx, dy);
 }
 
 // sqrt(log2(e) / 2): with this factor folded into the Cholesky factor, the blend

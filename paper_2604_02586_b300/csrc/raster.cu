@@ -1,16 +1,22 @@
 // raster.cu -- a5 raster-accumulate (Sec. 4.3.5) and the colour render (Sec. 3.1).
 //
-// One CTA per 16x16 tile, one thread per pixel.  The tile's depth-sorted list is
-// walked in batches of kBatch Gaussians whose blend parameters are staged in
-// shared memory.  Each pixel blends front to back: alpha = min(0.99, o G(x)),
-// Gaussians with alpha < 1/255 are skipped, the walk stops before a Gaussian that
-// would bring the transmittance below 1e-4, and w = alpha T (Eq. 4's weight).
+// One CTA per 16x16 tile, one thread per pixel; warp w covers the 8x4 pixel
+// block (w & 1, w >> 1).  The tile's depth-sorted list is walked in batches of
+// kBatch Gaussians whose blend parameters are staged in shared memory together
+// with a conservative footprint box.  A warp whose block misses a Gaussian's box
+// skips it (no pixel there can reach alpha = 1/255, so nothing changes).  Each
+// pixel blends front to back: alpha = min(0.99, o G(x)), Gaussians with
+// alpha < 1/255 are skipped, the walk stops before a Gaussian that would bring
+// the transmittance below 1e-4, and w = alpha T (Eq. 4's weight).
 //
 // Moments: every visible pixel adds 16 values per Gaussian.  The 32 lanes of a
 // warp are folded with a transposing butterfly (16 shuffles for 16 values, each
 // step exchanges half of the values still held), warps are summed through
 // shared memory, and one float4 atomic per 4 values goes to global memory, so a
 // (tile, Gaussian) pair costs 4 vector atomics whatever the number of pixels.
+// Sums are taken about a per-(view, Gaussian) origin (mu_2D clamped to the image)
+// and displacement reference (the track at that origin), which keeps FP32 sums
+// free of cancellation; a6 undoes both shifts exactly.
 #include "launch.h"
 
 namespace tsp {
@@ -23,6 +29,39 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
+
+// Blend record with its mean moved from the Gaussian's rectangle corner to this
+// tile's corner (an exact integer shift, so the staged mean keeps its precision).
+__device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty)
+{
+    g0.x += (float)((r.x - tx) * kTile);
+    g0.y += (float)((r.y - ty) * kTile);
+    return g0;
+}
+
+// Tile-local box outside which alpha = min(0.99, o exp2(-p)) < 1/255 for sure:
+// p <= log2(255 o) is the ellipse z1^2 + z2^2 <= pm, whose extents follow from
+// the factor (i11, k, i22); the 0.1 % widening covers FP32 rounding of p.
+// Gaussians that cannot reach 1/255 anywhere get an empty box.
+__device__ __forceinline__ float4 footprint_box(float4 g0, float4 g1)
+{
+    const float pm = log2f(255.0f * g1.y);
+    if (!(pm > 0.0f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
+    const float sp = sqrtf(pm) * 1.001f;
+    const float ix = 1.0f / g0.z, iy = 1.0f / g1.x;
+    const float hx = sp * ix + 1e-3f;
+    const float hy = sp * sqrtf(g0.w * g0.w * ix * ix + iy * iy) + 1e-3f;
+    return make_float4(g0.x - hx, g0.x + hx, g0.y - hy, g0.y + hy);
+}
+
+// Pixel of thread tid inside its 16x16 tile: warp w -> block (w & 1, w >> 1) of
+// 8x4 pixels, lane l -> (l & 7, l >> 3) inside it.
+__device__ __forceinline__ void pixel_of(int tid, int& lx, int& ly)
+{
+    const int warp = tid >> 5, lane = tid & 31;
+    lx = (warp & 1) * 8 + (lane & 7);
+    ly = (warp >> 1) * 4 + (lane >> 3);
+}
 
 // Sum of v[k] over the warp for k = lane >> 1, returned in every lane.
 __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
@@ -63,7 +102,9 @@ template <bool kStats>
 __global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs, const Work w)
 {
     __shared__ float4 s_g0[kBatch];
-    __shared__ float2 s_g1[kBatch];
+    __shared__ float4 s_g1[kBatch];
+    __shared__ float4 s_box[kBatch];
+    __shared__ float2 s_ref[kBatch];
     __shared__ uint32_t s_id[kBatch];
     __shared__ __align__(16) float s_part[kBatch][kWarps][16];
 
@@ -73,8 +114,10 @@ __global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs,
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int lx, ly;
+    pixel_of(tid, lx, ly);
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < W && py < H;
     float ddx = 0.f, ddy = 0.f;
     bool vis = false;
@@ -86,7 +129,10 @@ __global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs,
     }
     // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
     const bool stat = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
-    const float xc = (float)px + 0.5f, yc = (float)py + 0.5f;
+    // pixel centre relative to the tile corner; Gaussian means are staged the same way
+    const float xc = (float)lx + 0.5f, yc = (float)ly + 0.5f;
+    const float bx0 = (float)((warp & 1) * 8) + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)((warp >> 1) * 4) + 0.5f, by1 = by0 + 3.0f;
     float T = 1.0f;
     bool done = !inside;
     const size_t vbase = (size_t)v * vs.n;
@@ -97,51 +143,65 @@ __global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs,
         if (kStats && tid == 0) n_list += nb;
         if (tid < nb) {
             const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g1 = w.geom1[vbase + g];
             s_id[tid] = g;
-            s_g0[tid] = w.geom0[vbase + g];
-            s_g1[tid] = w.geom1[vbase + g];
+            s_g0[tid] = g0;
+            s_g1[tid] = g1;
+            s_box[tid] = footprint_box(g0, g1);
+            s_ref[tid] = w.dref[vbase + g];
         }
         __syncthreads();
+        const bool warp_done = __all_sync(kFull, done);
         for (int j = 0; j < nb; ++j) {
-            float val[16];
+            const float4 bb = s_box[j];
+            float r = 0.f;
+            // warp-uniform: every lane reads the same box and block bounds
+            if (!warp_done && bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0) {
+                float val[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) val[k] = 0.f;
-            bool add = false;
-            if (!done) {
-                const float4 g0 = s_g0[j];
-                const float2 g1 = s_g1[j];
-                const float ex = xc - g0.x, ey = yc - g0.y;
-                const float z1 = ex * g0.z;
-                const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
-                const float pw = fmaf(z2, z2, z1 * z1);
-                const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
-                if (kStats) ++n_eval;
-                if (alpha >= kAlphaMin) {
-                    const float Tn = T * (1.0f - alpha);
-                    if (Tn < kTMin) {
-                        done = true;
-                    } else {
-                        const float wgt = alpha * T;
-                        T = Tn;
-                        if (kStats) ++n_blend;
-                        if (vis) {
-                            if (kStats) ++n_add;
-                            add = true;
-                            const float wx = wgt * ex, wy = wgt * ey;
-                            val[0] = wgt; val[1] = wx; val[2] = wy;
-                            val[3] = wx * ex; val[4] = wx * ey; val[5] = wy * ey;
-                            val[6] = wgt * ddx; val[7] = wgt * ddy;
-                            val[8] = wx * ddx; val[9] = wx * ddy;
-                            val[10] = wy * ddx; val[11] = wy * ddy;
-                            val[12] = stat ? wgt : 0.f;
-                            val[13] = 1.f;
-                            val[14] = stat ? 1.f : 0.f;
+                for (int k = 0; k < 16; ++k) val[k] = 0.f;
+                bool add = false;
+                if (!done) {
+                    const float4 g0 = s_g0[j];
+                    const float4 g1 = s_g1[j];
+                    const float ex = xc - g0.x, ey = yc - g0.y;
+                    const float z1 = ex * g0.z;
+                    const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
+                    const float pw = fmaf(z2, z2, z1 * z1);
+                    const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+                    if (kStats) ++n_eval;
+                    if (alpha >= kAlphaMin) {
+                        const float Tn = T * (1.0f - alpha);
+                        if (Tn < kTMin) {
+                            done = true;
+                        } else {
+                            const float wgt = alpha * T;
+                            T = Tn;
+                            if (kStats) ++n_blend;
+                            if (vis) {
+                                if (kStats) ++n_add;
+                                add = true;
+                                // coordinates about the moment origin, displacement
+                                // about the Gaussian's reference track
+                                const float mx = ex - g1.z, my = ey - g1.w;
+                                const float2 rf = s_ref[j];
+                                const float dx = ddx - rf.x, dy = ddy - rf.y;
+                                const float wx = wgt * mx, wy = wgt * my;
+                                val[0] = wgt; val[1] = wx; val[2] = wy;
+                                val[3] = wx * mx; val[4] = wx * my; val[5] = wy * my;
+                                val[6] = wgt * dx; val[7] = wgt * dy;
+                                val[8] = wx * dx; val[9] = wx * dy;
+                                val[10] = wy * dx; val[11] = wy * dy;
+                                val[12] = stat ? wgt : 0.f;
+                                val[13] = 1.f;
+                                val[14] = stat ? 1.f : 0.f;
+                            }
                         }
                     }
                 }
+                if (__ballot_sync(kFull, add)) r = warp_transpose_sum16(val, lane);
             }
-            float r = 0.f;
-            if (__ballot_sync(kFull, add)) r = warp_transpose_sum16(val, lane);
             if ((lane & 1) == 0) s_part[j][warp][lane >> 1] = r;
         }
         __syncthreads();
@@ -170,17 +230,22 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
                                                            const RenderOut ro)
 {
     __shared__ float4 s_g0[kBatch];
-    __shared__ float2 s_g1[kBatch];
+    __shared__ float4 s_g1[kBatch];
+    __shared__ float4 s_box[kBatch];
     __shared__ float4 s_c[kBatch];
     const uint32_t tile = blockIdx.x;
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    int lx, ly;
+    pixel_of(tid, lx, ly);
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < W && py < H;
-    const float xc = (float)px + 0.5f, yc = (float)py + 0.5f;
+    const float xc = (float)lx + 0.5f, yc = (float)ly + 0.5f;
+    const float bx0 = (float)((warp & 1) * 8) + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)((warp >> 1) * 4) + 0.5f, by1 = by0 + 3.0f;
     float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
     bool done = !inside;
     const size_t vbase = (size_t)v * vs.n;
@@ -188,14 +253,19 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
         const int nb = (int)min((uint32_t)kBatch, end - b0);
         if (tid < nb) {
             const uint32_t g = (uint32_t)w.pairs[b0 + tid];
-            s_g0[tid] = w.geom0[vbase + g];
-            s_g1[tid] = w.geom1[vbase + g];
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g1 = w.geom1[vbase + g];
+            s_g0[tid] = g0;
+            s_g1[tid] = g1;
+            s_box[tid] = footprint_box(g0, g1);
             s_c[tid] = w.color[vbase + g];
         }
         __syncthreads();
         for (int j = 0; j < nb && !done; ++j) {
+            const float4 bb = s_box[j];
+            if (bb.x > bx1 || bb.y < bx0 || bb.z > by1 || bb.w < by0) continue;
             const float4 g0 = s_g0[j];
-            const float2 g1 = s_g1[j];
+            const float4 g1 = s_g1[j];
             const float ex = xc - g0.x, ey = yc - g0.y;
             const float z1 = ex * g0.z;
             const float z2 = fmaf(-g0.w, ex, ey) * g1.x;

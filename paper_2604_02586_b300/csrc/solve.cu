@@ -25,7 +25,8 @@ namespace {
 
 // Per-view records written by a6 and read by a7/a8:
 //   vres0 = (mu'_x, mu'_y, c_x, c_y) with c = mu' - mu_2D the shift of the centre,
-//   vres1 = (Sigma'_xx, Sigma'_xy, Sigma'_yy, sum w), vres2 = (flags, pixels).
+//   vres1 = (B00, B01, B02, sum w), vres3 = (B10, B11, B12, 0) with Sigma_2D' = B B^T,
+//   vres2 = (flags, pixels).
 
 __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const float4* __restrict__ mo,
                                                     const float4* __restrict__ q,
@@ -74,19 +75,33 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const floa
                 const float Ry0 = M[10] - M[2] * M[6] * isw, Ry1 = M[11] - M[2] * M[7] * isw;
                 const float Y00 = (Syy * Rx0 - Sxy * Ry0) * idS, Y01 = (Syy * Rx1 - Sxy * Ry1) * idS;
                 const float Y10 = (Sxx * Ry0 - Sxy * Rx0) * idS, Y11 = (Sxx * Ry1 - Sxy * Rx1) * idS;
-                const float c0 = (M[6] - M[1] * Y00 - M[2] * Y10) * isw;
-                const float c1 = (M[7] - M[1] * Y01 - M[2] * Y11) * isw;
+                // intercept at the moment origin o = mu + delta; the displacement sums
+                // were taken about the reference r, which only shifts the intercept
+                const float2 rf = w.dref[i];
+                const float co0 = (M[6] - M[1] * Y00 - M[2] * Y10) * isw + rf.x;
+                const float co1 = (M[7] - M[1] * Y01 - M[2] * Y11) * isw + rf.y;
                 A00 = 1.0f + Y00; A01 = Y10; A10 = Y01; A11 = 1.0f + Y11;
                 KeyProj p;
                 key_project(vs.cam[v], mo[g], q[g], s[g], vs.tiles_x[v], vs.tiles_y[v], p);
-                const float ux = p.mx + c0, uy = p.my + c1;
-                // Eq. 2 with the undilated Sigma_2D: Sigma' = A Sigma A^T
-                const float t00 = A00 * p.a + A01 * p.b, t01 = A00 * p.b + A01 * p.c;
-                const float t10 = A10 * p.a + A11 * p.b, t11 = A10 * p.b + A11 * p.c;
+                float2 mxd, myd;
+                mean2d_df(vs.cam[v], mo[g], mxd, myd);
+                // shift of the centre: mu' - mu = c_o + (I - A) delta
+                const float2 dl = moment_origin_shift(mxd, myd, vs.cam[v].W, vs.cam[v].H);
+                const float c0 = co0 + dl.x - (A00 * dl.x + A01 * dl.y);
+                const float c1 = co1 + dl.y - (A10 * dl.x + A11 * dl.y);
+                const float ux = mxd.x + (mxd.y + c0), uy = myd.x + (myd.y + c1);
+                // Eq. 2 with the undilated Sigma_2D = V V^T: Sigma' = (A V)(A V)^T.
+                // The factor B = A V is kept (not the entries of Sigma'), so a thin
+                // footprint's small eigenvalue survives the FP32 hand-over to a8.
+                const float B00 = A00 * p.V0[0] + A01 * p.V1[0], B01 = A00 * p.V0[1] + A01 * p.V1[1];
+                const float B02 = A00 * p.V0[2] + A01 * p.V1[2];
+                const float B10 = A10 * p.V0[0] + A11 * p.V1[0], B11 = A10 * p.V0[1] + A11 * p.V1[1];
+                const float B12 = A10 * p.V0[2] + A11 * p.V1[2];
                 r0 = make_float4(ux, uy, c0, c1);
-                r1 = make_float4(t00 * A00 + t01 * A01, t00 * A10 + t01 * A11, t10 * A10 + t11 * A11, sw);
-                b0 = ux - (A00 * p.mx + A01 * p.my);
-                b1 = uy - (A10 * p.mx + A11 * p.my);
+                r1 = make_float4(B00, B01, B02, sw);
+                w.vres3[i] = make_float4(B10, B11, B12, 0.f);
+                b0 = (mxd.x - (A00 * mxd.x + A01 * myd.x)) + (c0 + mxd.y - (A00 * mxd.y + A01 * myd.y));
+                b1 = (myd.x - (A10 * mxd.x + A11 * myd.x)) + (c1 + myd.y - (A10 * mxd.y + A11 * myd.y));
                 flags = TSP_VIEW_OK;
             }
         }
@@ -142,6 +157,56 @@ __device__ bool chol_solve(double (&A)[N][N], double (&b)[N], double rel)
         for (int j = i + 1; j < N; ++j) x -= A[j][i] * b[j];
         b[i] = x / A[i][i];
     }
+    return true;
+}
+
+// Cholesky with diagonal pivoting (largest remaining Schur diagonal first), which
+// reveals rank deficiency: a rank-5 system (two views leave the variance along
+// their common normal free) ends with a pivot at rounding level.  Returns false
+// if a pivot falls below rel * max diagonal; otherwise b holds the solution.
+template <int N>
+__device__ bool chol_solve_pivoted(double (&A)[N][N], double (&b)[N], double rel)
+{
+    int perm[N];
+    double dmax = 0.0;
+    for (int k = 0; k < N; ++k) {
+        perm[k] = k;
+        dmax = fmax(dmax, A[k][k]);
+    }
+    if (!(dmax > 0.0)) return false;
+    for (int k = 0; k < N; ++k) {
+        int p = k;
+        for (int j = k + 1; j < N; ++j)
+            if (A[j][j] > A[p][p]) p = j;
+        if (p != k) {
+            for (int j = 0; j < N; ++j) { const double t = A[k][j]; A[k][j] = A[p][j]; A[p][j] = t; }
+            for (int j = 0; j < N; ++j) { const double t = A[j][k]; A[j][k] = A[j][p]; A[j][p] = t; }
+            const double tb = b[k]; b[k] = b[p]; b[p] = tb;
+            const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+        }
+        const double d = A[k][k];
+        if (!(d > rel * dmax)) return false;
+        const double l = sqrt(d);
+        A[k][k] = l;
+        for (int i = k + 1; i < N; ++i) A[i][k] /= l;
+        for (int i = k + 1; i < N; ++i)
+            for (int j = k + 1; j <= i; ++j) {
+                A[i][j] -= A[i][k] * A[j][k];
+                A[j][i] = A[i][j];
+            }
+    }
+    double y[N];
+    for (int i = 0; i < N; ++i) {
+        double x = b[i];
+        for (int j = 0; j < i; ++j) x -= A[i][j] * y[j];
+        y[i] = x / A[i][i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double x = y[i];
+        for (int j = i + 1; j < N; ++j) x -= A[j][i] * y[j];
+        y[i] = x / A[i][i];
+    }
+    for (int i = 0; i < N; ++i) b[perm[i]] = y[i];
     return true;
 }
 
@@ -294,8 +359,11 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float
             T[0][k] = j00 * c.R[k] + j02 * c.R[6 + k];
             T[1][k] = j11 * c.R[3 + k] + j12 * c.R[6 + k];
         }
-        const float4 sv = w.vres1[i];
-        const double rhs[3] = {sv.x, sv.y, sv.z};
+        const float4 b0v = w.vres1[i], b1v = w.vres3[i];
+        const double B0[3] = {b0v.x, b0v.y, b0v.z}, B1[3] = {b1v.x, b1v.y, b1v.z};
+        const double rhs[3] = {B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2],
+                               B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2],
+                               B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2]};
         const int ii[3] = {0, 0, 1}, jj[3] = {0, 1, 1};
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
@@ -311,12 +379,12 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float
             for (int u = 0; u < 6; ++u) {
                 b6[u] += cf[u] * rhs[e];
 #pragma unroll
-                for (int k = 0; k <= u; ++k) A6[u][k] += cf[u] * cf[k];
+                for (int k = 0; k < 6; ++k) A6[u][k] += cf[u] * cf[k];
             }
         }
     }
     const double rc2 = (double)fp.cov_rcond_min * (double)fp.cov_rcond_min;
-    if (!chol_solve<6>(A6, b6, rc2)) {
+    if (!chol_solve_pivoted<6>(A6, b6, rc2)) {
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_COV_SINGULAR;
         return;
     }
