@@ -212,6 +212,26 @@ tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, siz
  * Errors: INVALID_ARG (no timed call yet), CUDA. */
 tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count);
 
+/* Per-tile depth sort without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * -- code running while a CUDA graph is being captured, memory-capped tenants
+ * of a shared GPU, hosts whose own allocator owns all device memory.
+ * keys: device [num_keys] (depth_bits << 32 | Gaussian), sorted ascending in
+ * place within each tile t's slice [offsets[t], offsets[t+1]); offsets: device
+ * [num_tiles + 1], non-decreasing, offsets[num_tiles] = num_keys (slices are
+ * clamped to num_keys).  Both on the current CUDA device; keys 8-byte aligned.
+ * The merge scratch for long lists lives in a fixed array inside the library
+ * (TSP_NOALLOC_SORT_MAX_KEYS keys, 8 MB), held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (with the device current); make that first call before
+ * any stream capture.  All calls share the array, so calls that overlap on the
+ * GPU race with each other; nothing in it needs clearing between calls.
+ * Errors: INVALID_ARG (num_keys > TSP_NOALLOC_SORT_MAX_KEYS, NULL or misaligned
+ * pointer), CUDA (lookup or launch failed).  Enqueues on `stream`; no wait. */
+#define TSP_NOALLOC_SORT_MAX_KEYS (1u << 20)
+tsp_status tsp_sort_tiles_noalloc(uint64_t* keys, const uint32_t* offsets, uint32_t num_tiles,
+                                  uint32_t num_keys, void* stream);
+
 /* Bytes of device workspace the context currently holds. */
 tsp_status tsp_workspace_bytes(const tsp_context* ctx, size_t* bytes);
 

@@ -82,6 +82,8 @@ def lib():
         L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
         L.tsp_workspace_bytes.argtypes = [P, P]
         L.tsp_stage_times.argtypes = [P, P, I, P]
+        L.tsp_sort_tiles_noalloc.argtypes = [P, P, C.c_uint32, C.c_uint32, P]
+        L.tsp_sort_tiles_noalloc.restype = I
         L.tsp_status_string.argtypes = [I]
         L.tsp_status_string.restype = C.c_char_p
         L.tsp_last_error.argtypes = [P]
