@@ -124,7 +124,8 @@ typedef struct tsp_options {
                                 /*    call; read them with tsp_stage_times          */
     int32_t collect_stats;      /* 1: the raster step also counts its work (slower; */
                                 /*    for measurement only), see TSP_I_STATS        */
-    int32_t reserved;
+    int32_t raster_pixels_per_thread; /* a5 layout: 1 (8x4 warp blocks) or 2 (8x8);  */
+                                /*    0 = default (2)                              */
     int64_t pair_capacity;      /* initial (tile, Gaussian) pair capacity, 0 = auto */
     int64_t budget_bytes;       /* workspace ceiling, 0 = unlimited                */
 } tsp_options;

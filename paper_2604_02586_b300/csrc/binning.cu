@@ -46,12 +46,16 @@ __device__ __forceinline__ void sh_colour(const float* sh, int deg, float x, flo
 }
 
 // grid (ceil(n/256), V): one thread per (view, Gaussian), Gaussian index fastest.
+// kMode 0: motion fit (zero the moment record, reference displacement);
+// kMode 1: render (view-dependent colour).
+template <int kMode>
 __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const float4* __restrict__ mo,
                                                     const float4* __restrict__ q,
                                                     const float4* __restrict__ s,
                                                     const float* __restrict__ sh, int sh_degree,
-                                                    int mode, Work w)
+                                                    Work w)
 {
+    constexpr int mode = kMode;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     if (g >= vs.n) return;
@@ -107,43 +111,56 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
             atomicAdd(&w.tile_count[base + (uint32_t)(ty * tx_n + tx)], 1u);
 }
 
-// Single CTA exclusive scan of NT counts; writes NT+1 offsets and K.
+// Single-CTA exclusive scan of NT counts, in chunks of 4096 (1024 threads x 4
+// consecutive counts, coalesced) carrying the running total; writes NT+1
+// offsets and K.
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ off,
                                                uint32_t NT, uint32_t cap, uint32_t* dstatus)
 {
     __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long carry_s;
     const uint32_t tid = threadIdx.x;
-    const uint32_t per = (NT + 1023u) / 1024u;
-    const uint32_t b = min(tid * per, NT), e = min(b + per, NT);
-    unsigned long long sum = 0;
-    for (uint32_t i = b; i < e; ++i) sum += cnt[i];
-    // inclusive scan across the block
     const int lane = tid & 31, wid = tid >> 5;
-    unsigned long long x = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
+    if (tid == 0) carry_s = 0;
     __syncthreads();
-    if (wid == 0) {
-        unsigned long long t = warp_tot[lane];
+    for (uint32_t base = 0; base < NT; base += 4096) {
+        const uint32_t i0 = base + 4 * tid;
+        uint32_t c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = (i0 + k < NT) ? cnt[i0 + k] : 0u;
+        const unsigned long long sum = (unsigned long long)c[0] + c[1] + c[2] + c[3];
+        unsigned long long x = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, d);
-            if (lane >= d) t += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
         }
-        warp_tot[lane] = t;
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long t = warp_tot[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, d);
+                if (lane >= d) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const unsigned long long carry = carry_s;
+        unsigned long long run = carry + x - sum + (wid > 0 ? warp_tot[wid - 1] : 0ull);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i0 + k < NT) {
+                off[i0 + k] = (uint32_t)min(run, 0xffffffffull);
+                run += c[k];
+            }
+        __syncthreads();
+        if (tid == 0) carry_s = carry + warp_tot[31];
+        __syncthreads();
     }
-    __syncthreads();
-    unsigned long long run = x - sum + (wid > 0 ? warp_tot[wid - 1] : 0ull);
-    for (uint32_t i = b; i < e; ++i) {
-        off[i] = (uint32_t)min(run, 0xffffffffull);
-        run += cnt[i];
-    }
-    if (tid == 1023) {
-        const unsigned long long K = warp_tot[31];
+    if (tid == 0) {
+        const unsigned long long K = carry_s;
         off[NT] = (uint32_t)min(K, 0xffffffffull);
         dstatus[1] = (uint32_t)(K & 0xffffffffull);
         dstatus[2] = (uint32_t)(K >> 32);
@@ -244,7 +261,10 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4*
 {
     if (vs.n == 0 || vs.V == 0) return cudaSuccess;
     dim3 grid((vs.n + 255) / 256, vs.V);
-    k_preprocess<<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, mode, w);
+    if (mode == 0)
+        k_preprocess<0><<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, w);
+    else
+        k_preprocess<1><<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, w);
     return cudaGetLastError();
 }
 

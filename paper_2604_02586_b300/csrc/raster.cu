@@ -1,10 +1,10 @@
 // raster.cu -- a5 raster-accumulate (Sec. 4.3.5) and the colour render (Sec. 3.1).
 //
-// One CTA per 16x16 tile, one thread per pixel; warp w covers the 8x4 pixel
-// block (w & 1, w >> 1).  The tile's depth-sorted list is walked in batches of
+// One CTA per 16x16 tile.  The tile's depth-sorted list is walked in batches of
 // kBatch Gaussians whose blend parameters are staged in shared memory together
-// with a conservative footprint box.  A warp whose block misses a Gaussian's box
-// skips it (no pixel there can reach alpha = 1/255, so nothing changes).  Each
+// with a conservative footprint box.  Each warp owns a block of the tile and
+// skips every Gaussian whose box misses it (no pixel there can reach
+// alpha = 1/255, so nothing changes).  Each
 // pixel blends front to back: alpha = min(0.99, o G(x)), Gaussians with
 // alpha < 1/255 are skipped, the walk stops before a Gaussian that would bring
 // the transmittance below 1e-4, and w = alpha T (Eq. 4's weight).
@@ -98,15 +98,25 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
 
 // kStats = true is a measurement variant: the same walk, plus exact counts of the
 // work done (evaluations, blended contributions, moment additions, list entries).
-template <bool kStats>
-__global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs, const Work w)
+//
+// P pixels per thread: warp w covers the 8 x (4P) block (w & 1, w >> 1) of the
+// tile; lane l owns pixels (l & 7, (l >> 3) + 4k), k < P.  Per batch, two ballots
+// give each warp the 64-bit set of staged Gaussians whose footprint box touches
+// its block; the warp walks only that set, in list order.  A Gaussian's sums over
+// the warp's pixels are folded once per (warp, Gaussian) hit.
+template <int P, bool kStats>
+__global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet vs, const Work w)
 {
+    constexpr int kThreads = kTilePx / P;
+    constexpr int kNW = kThreads / 32;
+    constexpr int BH = 4 * P;
     __shared__ float4 s_g0[kBatch];
     __shared__ float4 s_g1[kBatch];
     __shared__ float4 s_box[kBatch];
     __shared__ float2 s_ref[kBatch];
     __shared__ uint32_t s_id[kBatch];
-    __shared__ __align__(16) float s_part[kBatch][kWarps][16];
+    __shared__ uint32_t s_mask[kNW][2];
+    __shared__ __align__(16) float s_part[kBatch][kNW][16];
 
     const uint32_t tile = blockIdx.x;
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
@@ -114,28 +124,33 @@ __global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs,
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int lx, ly;
-    pixel_of(tid, lx, ly);
+    const int bxo = (warp & 1) * 8, byo = (warp >> 1) * BH;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < W && py < H;
-    float ddx = 0.f, ddy = 0.f;
-    bool vis = false;
-    if (inside) {
-        const size_t pix = (size_t)py * W + px;
-        const float2 d = vs.disp[v][pix];
-        ddx = d.x; ddy = d.y;
-        vis = vs.vis[v][pix] != 0;
-    }
-    // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
-    const bool stat = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
-    // pixel centre relative to the tile corner; Gaussian means are staged the same way
-    const float xc = (float)lx + 0.5f, yc = (float)ly + 0.5f;
-    const float bx0 = (float)((warp & 1) * 8) + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)((warp >> 1) * 4) + 0.5f, by1 = by0 + 3.0f;
-    float T = 1.0f;
-    bool done = !inside;
     const size_t vbase = (size_t)v * vs.n;
+
+    float T[P], ddx[P], ddy[P], yc[P];
+    bool done[P], vis[P], stat[P];
+    const float xc = (float)(bxo + (lane & 7)) + 0.5f;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const int ly = byo + (lane >> 3) + 4 * k;
+        const int px = tx * kTile + bxo + (lane & 7), py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        yc[k] = (float)ly + 0.5f;
+        ddx[k] = 0.f; ddy[k] = 0.f; vis[k] = false;
+        if (inside) {
+            const size_t pix = (size_t)py * W + px;
+            const float2 d = vs.disp[v][pix];
+            ddx[k] = d.x; ddy[k] = d.y;
+            vis[k] = vs.vis[v][pix] != 0;
+        }
+        // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
+        stat[k] = __fmaf_rn(ddx[k], ddx[k], __fmul_rn(ddy[k], ddy[k])) < 1.0f;
+        T[k] = 1.0f;
+        done[k] = !inside;
+    }
+    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)byo + 0.5f, by1 = by0 + (float)(BH - 1);
     unsigned long long n_eval = 0, n_blend = 0, n_add = 0, n_list = 0;
 
     for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
@@ -152,71 +167,108 @@ __global__ void __launch_bounds__(kTilePx) k_raster_accumulate(const ViewSet vs,
             s_ref[tid] = w.dref[vbase + g];
         }
         __syncthreads();
-        const bool warp_done = __all_sync(kFull, done);
-        for (int j = 0; j < nb; ++j) {
-            const float4 bb = s_box[j];
-            float r = 0.f;
-            // warp-uniform: every lane reads the same box and block bounds
-            if (!warp_done && bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0) {
-                float val[16];
+        bool alive = false;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) val[k] = 0.f;
+        for (int k = 0; k < P; ++k) alive |= !done[k];
+        uint32_t mlo = 0, mhi = 0;
+        if (__any_sync(kFull, alive)) {
+            bool h0 = false, h1 = false;
+            if (lane < nb) {
+                const float4 bb = s_box[lane];
+                h0 = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
+            }
+            if (lane + 32 < nb) {
+                const float4 bb = s_box[lane + 32];
+                h1 = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
+            }
+            mlo = __ballot_sync(kFull, h0);
+            mhi = __ballot_sync(kFull, h1);
+        }
+        if (lane == 0) { s_mask[warp][0] = mlo; s_mask[warp][1] = mhi; }
+        unsigned long long m = ((unsigned long long)mhi << 32) | mlo;
+        while (m) {
+            const int j = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const float4 g0 = s_g0[j];
+            const float4 g1 = s_g1[j];
+            const float2 rf = s_ref[j];
+            float val[16];
+            int npix = 0, nstat = 0;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float ex = xc - g0.x, ey = yc[k] - g0.y;
+                float wk = 0.f;
                 bool add = false;
-                if (!done) {
-                    const float4 g0 = s_g0[j];
-                    const float4 g1 = s_g1[j];
-                    const float ex = xc - g0.x, ey = yc - g0.y;
+                if (!done[k]) {
                     const float z1 = ex * g0.z;
                     const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
                     const float pw = fmaf(z2, z2, z1 * z1);
                     const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
                     if (kStats) ++n_eval;
                     if (alpha >= kAlphaMin) {
-                        const float Tn = T * (1.0f - alpha);
+                        const float Tn = T[k] * (1.0f - alpha);
                         if (Tn < kTMin) {
-                            done = true;
+                            done[k] = true;
                         } else {
-                            const float wgt = alpha * T;
-                            T = Tn;
                             if (kStats) ++n_blend;
-                            if (vis) {
-                                if (kStats) ++n_add;
+                            if (vis[k]) {
+                                wk = alpha * T[k];
                                 add = true;
-                                // coordinates about the moment origin, displacement
-                                // about the Gaussian's reference track
-                                const float mx = ex - g1.z, my = ey - g1.w;
-                                const float2 rf = s_ref[j];
-                                const float dx = ddx - rf.x, dy = ddy - rf.y;
-                                const float wx = wgt * mx, wy = wgt * my;
-                                val[0] = wgt; val[1] = wx; val[2] = wy;
-                                val[3] = wx * mx; val[4] = wx * my; val[5] = wy * my;
-                                val[6] = wgt * dx; val[7] = wgt * dy;
-                                val[8] = wx * dx; val[9] = wx * dy;
-                                val[10] = wy * dx; val[11] = wy * dy;
-                                val[12] = stat ? wgt : 0.f;
-                                val[13] = 1.f;
-                                val[14] = stat ? 1.f : 0.f;
+                                if (kStats) ++n_add;
                             }
+                            T[k] = Tn;
                         }
                     }
                 }
-                if (__ballot_sync(kFull, add)) r = warp_transpose_sum16(val, lane);
+                // coordinates about the moment origin, displacement about the
+                // Gaussian's reference track; wk = 0 where nothing is added
+                const float mx = ex - g1.z, my = ey - g1.w;
+                const float dx = ddx[k] - rf.x, dy = ddy[k] - rf.y;
+                const float wx = wk * mx, wy = wk * my;
+                const float ws = stat[k] ? wk : 0.f;
+                if (k == 0) {
+                    val[0] = wk; val[1] = wx; val[2] = wy;
+                    val[3] = wx * mx; val[4] = wx * my; val[5] = wy * my;
+                    val[6] = wk * dx; val[7] = wk * dy;
+                    val[8] = wx * dx; val[9] = wx * dy;
+                    val[10] = wy * dx; val[11] = wy * dy;
+                    val[12] = ws;
+                } else {
+                    val[0] += wk; val[1] += wx; val[2] += wy;
+                    val[3] = fmaf(wx, mx, val[3]); val[4] = fmaf(wx, my, val[4]); val[5] = fmaf(wy, my, val[5]);
+                    val[6] = fmaf(wk, dx, val[6]); val[7] = fmaf(wk, dy, val[7]);
+                    val[8] = fmaf(wx, dx, val[8]); val[9] = fmaf(wx, dy, val[9]);
+                    val[10] = fmaf(wy, dx, val[10]); val[11] = fmaf(wy, dy, val[11]);
+                    val[12] += ws;
+                }
+                npix += __popc(__ballot_sync(kFull, add));
+                nstat += __popc(__ballot_sync(kFull, add && stat[k]));
             }
-            if ((lane & 1) == 0) s_part[j][warp][lane >> 1] = r;
+            val[13] = 0.f; val[14] = 0.f; val[15] = 0.f;
+            float r = 0.f;
+            if (npix) r = warp_transpose_sum16(val, lane);      // warp-uniform branch
+            if ((lane & 1) == 0)
+                s_part[j][warp][lane >> 1] = lane == 26 ? (float)npix : lane == 28 ? (float)nstat : r;
         }
         __syncthreads();
-        if (tid < nb * 4) {
-            const int j = tid >> 2, qd = tid & 3;
+        for (int t = tid; t < nb * 4; t += kThreads) {
+            const int j = t >> 2, qd = t & 3;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < kWarps; ++k) {
-                const float4 p = *reinterpret_cast<const float4*>(&s_part[j][k][4 * qd]);
-                acc.x += p.x; acc.y += p.y; acc.z += p.z; acc.w += p.w;
+            for (int k = 0; k < kNW; ++k) {
+                const uint32_t mk = s_mask[k][j >> 5];
+                if (mk & (1u << (j & 31))) {
+                    const float4 p = *reinterpret_cast<const float4*>(&s_part[j][k][4 * qd]);
+                    acc.x += p.x; acc.y += p.y; acc.z += p.z; acc.w += p.w;
+                }
             }
             if (acc.x != 0.f || acc.y != 0.f || acc.z != 0.f || acc.w != 0.f)
                 atomicAdd(&w.moments[(vbase + s_id[j]) * 4 + qd], acc);
         }
-        if (__syncthreads_count(!done) == 0) break;
+        bool any_alive = false;
+#pragma unroll
+        for (int k = 0; k < P; ++k) any_alive |= !done[k];
+        if (__syncthreads_count(any_alive) == 0) break;
     }
     if (kStats) {
         atomicAdd(&w.stats[0], n_eval);
@@ -292,13 +344,16 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
 }  // namespace
 
 cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
-                                     cudaStream_t st)
+                                     int pixels_per_thread, cudaStream_t st)
 {
     if (NT == 0 || vs.n == 0) return cudaSuccess;
-    if (stats)
-        k_raster_accumulate<true><<<NT, kTilePx, 0, st>>>(vs, w);
-    else
-        k_raster_accumulate<false><<<NT, kTilePx, 0, st>>>(vs, w);
+    if (pixels_per_thread == 1) {
+        if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w);
+        else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w);
+    } else {
+        if (stats) k_raster_accumulate<2, true><<<NT, kTilePx / 2, 0, st>>>(vs, w);
+        else k_raster_accumulate<2, false><<<NT, kTilePx / 2, 0, st>>>(vs, w);
+    }
     return cudaGetLastError();
 }
 
