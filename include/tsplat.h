@@ -115,7 +115,10 @@ typedef struct tsp_options {
     int32_t min_views;          /* Sec. 5.1: 2                                     */
     float sumw_min_total;       /* Sec. 5.1: 1e-3                                  */
     int32_t min_px_total;       /* Sec. 5.1: 3                                     */
-    float cov_rcond_min;        /* covariance system sigma_min/sigma_max floor: 1e-6 */
+    float cov_rcond_min;        /* covariance system sigma_min/sigma_max floor:    */
+                                /*    1e-6, in [1e-12, 1).  Two views always leave */
+                                /*    the system rank 5 (Sec. 4.4.2), so a Gaussian */
+                                /*    solved in exactly two views is COV_SINGULAR   */
     int32_t async_pairs;        /* 0: tsp_fit_motion waits for the pair count and  */
                                 /*    grows the pair buffer before sorting;        */
                                 /* 1: never waits; overflow -> TSP_ERR_OVERFLOW at  */
@@ -124,8 +127,8 @@ typedef struct tsp_options {
                                 /*    call; read them with tsp_stage_times          */
     int32_t collect_stats;      /* 1: the raster step also counts its work (slower; */
                                 /*    for measurement only), see TSP_I_STATS        */
-    int32_t raster_pixels_per_thread; /* a5 layout: 1 (8x4 warp blocks) or 2 (8x8);  */
-                                /*    0 = default (2)                              */
+    int32_t raster_pixels_per_thread; /* a5 layout: 1 (8x4 warp blocks), 2 (8x8) */
+                                /*    or 4 (8x16); 0 = default (2)                 */
     int64_t pair_capacity;      /* initial (tile, Gaussian) pair capacity, 0 = auto */
     int64_t budget_bytes;       /* workspace ceiling, 0 = unlimited                */
 } tsp_options;

@@ -138,10 +138,13 @@ tsp_status check_options(tsp_context* ctx, const tsp_options& o)
         !std::isfinite(o.sumw_min_view) || !std::isfinite(o.lam_min_px2) ||
         !std::isfinite(o.sumw_min_total) || !std::isfinite(o.cov_rcond_min))
         return fail(ctx, TSP_ERR_INVALID_ARG, "thresholds must be finite and >= 0");
+    if (!(o.cov_rcond_min >= 1e-12f && o.cov_rcond_min < 1.f))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "cov_rcond_min must lie in [1e-12, 1)");
     if (o.min_px_view < 0 || o.min_views < 0 || o.min_px_total < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "counts must be >= 0");
-    if (o.raster_pixels_per_thread < 0 || o.raster_pixels_per_thread > 2)
-        return fail(ctx, TSP_ERR_INVALID_ARG, "raster_pixels_per_thread must be 0, 1 or 2");
+    if (o.raster_pixels_per_thread != 0 && o.raster_pixels_per_thread != 1 &&
+        o.raster_pixels_per_thread != 2 && o.raster_pixels_per_thread != 4)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "raster_pixels_per_thread must be 0, 1, 2 or 4");
     if (o.pair_capacity < 0 || o.pair_capacity > INT32_MAX || o.budget_bytes < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "bad pair_capacity or budget_bytes");
     return TSP_OK;
@@ -365,7 +368,7 @@ tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera
     ctx->timed = false;
     if ((s = bin_front(ctx, vs, g, nullptr, 0, 0, NT, w, st))) return s;
     TSP_CUDA(launch_raster_accumulate(vs, w, NT, ctx->opt.collect_stats != 0,
-                                      ctx->opt.raster_pixels_per_thread == 1 ? 1 : 2, st));
+                                      ctx->opt.raster_pixels_per_thread == 0 ? 2 : ctx->opt.raster_pixels_per_thread, st));
     TSP_CUDA(mark(ctx, 5, st));
     TSP_CUDA(launch_view_solve(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
                                (const float4*)g->scales, fp, w, out->view_affine, out->view_flags, st));

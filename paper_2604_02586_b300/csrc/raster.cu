@@ -24,7 +24,6 @@ namespace tsp {
 namespace {
 
 constexpr int kBatch = 64;
-constexpr int kWarps = kTilePx / 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
@@ -350,6 +349,9 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
     if (pixels_per_thread == 1) {
         if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w);
         else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w);
+    } else if (pixels_per_thread == 4) {
+        if (stats) k_raster_accumulate<4, true><<<NT, kTilePx / 4, 0, st>>>(vs, w);
+        else k_raster_accumulate<4, false><<<NT, kTilePx / 4, 0, st>>>(vs, w);
     } else {
         if (stats) k_raster_accumulate<2, true><<<NT, kTilePx / 2, 0, st>>>(vs, w);
         else k_raster_accumulate<2, false><<<NT, kTilePx / 2, 0, st>>>(vs, w);

@@ -12,11 +12,16 @@
 //   (X = mu + delta) so the right-hand side is -z_mu times the per-view shift of
 //   the centre: no cancellation.  FP32 normal equations, FP64 Cholesky.
 // a8 (Sec. 4.4.2): vech(T Sigma T^T) = vech(Sigma_2D') per solved view with
-//   T = J' W at the new mean, 6 unknowns, normal equations and Cholesky in FP64.
-// a9 (Sec. 4.4.3): Jacobi eigen decomposition in FP64; discard if an eigenvalue
-//   is <= 0; new axis k takes the eigenpair whose rank matches the rank of the old
-//   scale s_k; each axis is flipped to agree with the old one; a reflection is
-//   undone on the least-aligned axis; the quaternion sign follows the old one.
+//   T = J' W at the new mean, 6 unknowns.  Two views are always rank 5 (each T
+//   annihilates its viewing ray d, so sym(d1 d2^T) is a null vector) and are
+//   reported singular without a solve.  With 3+ views: FP32 rows, normal
+//   equations accumulated from exact products in double-float, then an FP64
+//   LDL^T with diagonal pivoting whose last pivot ratio decides rank deficiency.
+// a9 (Sec. 4.4.3): cyclic Jacobi in FP32 for the eigenvectors, eigenvalues as
+//   FP64 Rayleigh quotients; discard if an eigenvalue is <= 0; new axis k takes
+//   the eigenpair whose rank matches the rank of the old scale s_k; each axis is
+//   flipped to agree with the old one; a reflection is undone on the
+//   least-aligned axis; the quaternion sign follows the old one.
 #include "launch.h"
 
 namespace tsp {
@@ -160,119 +165,202 @@ __device__ bool chol_solve(double (&A)[N][N], double (&b)[N], double rel)
     return true;
 }
 
-// Cholesky with diagonal pivoting (largest remaining Schur diagonal first), which
-// reveals rank deficiency: a rank-5 system (two views leave the variance along
-// their common normal free) ends with a pivot at rounding level.  Returns false
-// if a pivot falls below rel * max diagonal; otherwise b holds the solution.
-template <int N>
-__device__ bool chol_solve_pivoted(double (&A)[N][N], double (&b)[N], double rel)
+// Packed lower storage of a symmetric N x N matrix: element (i, j) at tri(i, j).
+__host__ __device__ constexpr int tri(int i, int j)
 {
-    int perm[N];
+    return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i;
+}
+
+// hi + lo += a * b with the product taken exactly (TwoProd) and added by TwoSum:
+// the sum keeps ~44 bits, so normal equations formed from FP32 rows lose nothing
+// to the squaring of their condition number.
+__device__ __forceinline__ void df_madd(float& hi, float& lo, float a, float b)
+{
+    float p, e, s, f;
+    two_prod(a, b, p, e);
+    two_sum(hi, p, s, f);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(f, e));
+}
+
+// Swap rows and columns k < j of a packed symmetric matrix, including the
+// already factorised columns (rows of L) left of k.
+template <int N>
+__device__ __forceinline__ void sym_swap(double (&A)[N * (N + 1) / 2], int k, int j)
+{
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        if (m == k || m == j) continue;
+        const double t = A[tri(k, m)];
+        A[tri(k, m)] = A[tri(j, m)];
+        A[tri(j, m)] = t;
+    }
+    const double t = A[tri(k, k)];
+    A[tri(k, k)] = A[tri(j, j)];
+    A[tri(j, j)] = t;
+}
+
+// Solve A x = b for symmetric positive semi-definite A (packed, N x N) by LDL^T
+// with diagonal pivoting: each step takes the largest remaining Schur diagonal,
+// so a rank-deficient system ends with a pivot at rounding level.  Returns false
+// when a pivot is <= rel * (largest diagonal of A); otherwise b holds x.  Every
+// index is a compile-time constant after unrolling, so A stays in registers.
+template <int N>
+__device__ __forceinline__ bool ldl_solve_pivoted(double (&A)[N * (N + 1) / 2], double (&b)[N], double rel)
+{
+    static_assert(N <= 8, "permutation packed as 4-bit fields");
+    uint32_t perm = 0;                       // original index of row i in bits 4i..4i+3
+    double dinv[N];
     double dmax = 0.0;
+#pragma unroll
     for (int k = 0; k < N; ++k) {
-        perm[k] = k;
-        dmax = fmax(dmax, A[k][k]);
+        perm |= (uint32_t)k << (4 * k);
+        dmax = fmax(dmax, A[tri(k, k)]);
     }
     if (!(dmax > 0.0)) return false;
+#pragma unroll
     for (int k = 0; k < N; ++k) {
         int p = k;
+        double best = A[tri(k, k)];
+#pragma unroll
         for (int j = k + 1; j < N; ++j)
-            if (A[j][j] > A[p][p]) p = j;
-        if (p != k) {
-            for (int j = 0; j < N; ++j) { const double t = A[k][j]; A[k][j] = A[p][j]; A[p][j] = t; }
-            for (int j = 0; j < N; ++j) { const double t = A[j][k]; A[j][k] = A[j][p]; A[j][p] = t; }
-            const double tb = b[k]; b[k] = b[p]; b[p] = tb;
-            const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
-        }
-        const double d = A[k][k];
-        if (!(d > rel * dmax)) return false;
-        const double l = sqrt(d);
-        A[k][k] = l;
-        for (int i = k + 1; i < N; ++i) A[i][k] /= l;
-        for (int i = k + 1; i < N; ++i)
-            for (int j = k + 1; j <= i; ++j) {
-                A[i][j] -= A[i][k] * A[j][k];
-                A[j][i] = A[i][j];
+            if (A[tri(j, j)] > best) { best = A[tri(j, j)]; p = j; }
+#pragma unroll
+        for (int j = k + 1; j < N; ++j)
+            if (p == j) {
+                sym_swap<N>(A, k, j);
+                const double tb = b[k]; b[k] = b[j]; b[j] = tb;
+                const uint32_t x = ((perm >> (4 * k)) ^ (perm >> (4 * j))) & 15u;
+                perm ^= (x << (4 * k)) | (x << (4 * j));
             }
+        const double d = A[tri(k, k)];
+        if (!(d > rel * dmax)) return false;
+        const double di = 1.0 / d;
+        dinv[k] = di;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {          // Schur complement of the pivot
+            const double li = A[tri(i, k)] * di;
+#pragma unroll
+            for (int j = k + 1; j <= i; ++j) A[tri(i, j)] -= li * A[tri(j, k)];
+        }
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) A[tri(i, k)] *= di;   // column k of L
     }
-    double y[N];
-    for (int i = 0; i < N; ++i) {
-        double x = b[i];
-        for (int j = 0; j < i; ++j) x -= A[i][j] * y[j];
-        y[i] = x / A[i][i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {                  // L z = P b, then D^-1
+#pragma unroll
+        for (int m = 0; m < i; ++m) b[i] -= A[tri(i, m)] * b[m];
     }
-    for (int i = N - 1; i >= 0; --i) {
-        double x = y[i];
-        for (int j = i + 1; j < N; ++j) x -= A[j][i] * y[j];
-        y[i] = x / A[i][i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) b[i] *= dinv[i];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {             // L^T y = z
+#pragma unroll
+        for (int m = i + 1; m < N; ++m) b[i] -= A[tri(m, i)] * b[m];
     }
-    for (int i = 0; i < N; ++i) b[perm[i]] = y[i];
+    double x[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {                  // x = P^T y
+        x[j] = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (((perm >> (4 * i)) & 15u) == (uint32_t)j) x[j] = b[i];
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) b[j] = x[j];
     return true;
 }
 
-// Classic Jacobi: rotate away the largest off-diagonal element until the matrix
-// is diagonal to rounding.  Eigenvectors are the columns of E.
-__device__ void eig_sym3(double (&S)[3][3], double (&lam)[3], double (&E)[3][3])
+// One Jacobi rotation of the symmetric 3x3 S in the (p, r) plane (q the third
+// index) that zeroes S[p][r]; the diagonal is updated by +-t S[p][r] and the
+// zeroed entry is set exactly, so off-diagonal rounding never feeds back into
+// the diagonal.  E accumulates the rotations in its columns.  Skips the pair
+// once |S[p][r]| <= 2^-24 sqrt|S[p][p] S[r][r]| (relative-accuracy criterion).
+__device__ __forceinline__ bool jacobi_rotate(float (&S)[3][3], float (&E)[3][3], int p, int r, int q)
 {
+    const float apr = S[p][r], app = S[p][p], arr = S[r][r];
+    if (!(fabsf(apr) > 5.9604645e-8f * sqrtf(fabsf(app * arr)))) return false;
+    const float th = __fdiv_rn(__fsub_rn(arr, app), __fmul_rn(2.f, apr));
+    const float ath = fabsf(th);
+    const float t = ath > 1e18f ? __fdiv_rn(0.5f, th)
+                                : copysignf(__fdiv_rn(1.f, __fadd_rn(ath, __fsqrt_rn(__fmaf_rn(th, th, 1.f)))), th);
+    const float c = __frsqrt_rn(__fmaf_rn(t, t, 1.f)), s = __fmul_rn(t, c);
+    const float tau = __fmul_rn(t, apr);
+    S[p][p] = __fsub_rn(app, tau);
+    S[r][r] = __fadd_rn(arr, tau);
+    S[p][r] = S[r][p] = 0.f;
+    const float sqp = S[q][p], sqr = S[q][r];
+    S[q][p] = S[p][q] = c * sqp - s * sqr;
+    S[q][r] = S[r][q] = s * sqp + c * sqr;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float ekp = E[k][p], ekr = E[k][r];
+        E[k][p] = c * ekp - s * ekr;
+        E[k][r] = s * ekp + c * ekr;
+    }
+    return true;
+}
+
+// Cyclic Jacobi on the FP32 copy of S (at most 8 sweeps; quadratic convergence
+// ends it in 2-4), eigenvalues refined as FP64 Rayleigh quotients e^T S e / e^T e.
+// The Rayleigh quotient error is second order in the FP32 eigenvector error, so
+// the small eigenvalues of an elongated Gaussian keep their relative accuracy.
+__device__ __forceinline__ void eig_sym3(const double (&S)[3][3], double (&lam)[3], float (&E)[3][3])
+{
+    float A[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) E[i][j] = i == j ? 1.0 : 0.0;
-    for (int it = 0; it < 64; ++it) {
-        int p = 0, r = 1;
-        double big = fabs(S[0][1]);
-        if (fabs(S[0][2]) > big) { big = fabs(S[0][2]); p = 0; r = 2; }
-        if (fabs(S[1][2]) > big) { big = fabs(S[1][2]); p = 1; r = 2; }
-        const double scale = fabs(S[0][0]) + fabs(S[1][1]) + fabs(S[2][2]);
-        if (big <= 1e-17 * scale || big == 0.0) break;
-        const double app = S[p][p], arr = S[r][r], apr = S[p][r];
-        const double th = 0.5 * (arr - app) / apr;
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
-        // S <- G^T S G with G the rotation in the (p, r) plane
-        for (int k = 0; k < 3; ++k) {
-            const double skp = S[k][p], skr = S[k][r];
-            S[k][p] = c * skp - sn * skr;
-            S[k][r] = sn * skp + c * skr;
+        for (int j = 0; j < 3; ++j) {
+            A[i][j] = (float)S[i][j];
+            E[i][j] = i == j ? 1.f : 0.f;
         }
-        for (int k = 0; k < 3; ++k) {
-            const double spk = S[p][k], srk = S[r][k];
-            S[p][k] = c * spk - sn * srk;
-            S[r][k] = sn * spk + c * srk;
-        }
-        for (int k = 0; k < 3; ++k) {
-            const double ekp = E[k][p], ekr = E[k][r];
-            E[k][p] = c * ekp - sn * ekr;
-            E[k][r] = sn * ekp + c * ekr;
-        }
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        bool any = jacobi_rotate(A, E, 0, 1, 2);
+        any |= jacobi_rotate(A, E, 0, 2, 1);
+        any |= jacobi_rotate(A, E, 1, 2, 0);
+        if (!any) break;
     }
-    lam[0] = S[0][0]; lam[1] = S[1][1]; lam[2] = S[2][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double e0 = E[0][k], e1 = E[1][k], e2 = E[2][k];
+        const double se0 = S[0][0] * e0 + S[0][1] * e1 + S[0][2] * e2;
+        const double se1 = S[1][0] * e0 + S[1][1] * e1 + S[1][2] * e2;
+        const double se2 = S[2][0] * e0 + S[2][1] * e1 + S[2][2] * e2;
+        lam[k] = (e0 * se0 + e1 * se1 + e2 * se2) / (e0 * e0 + e1 * e1 + e2 * e2);
+    }
 }
 
-__device__ __forceinline__ void rank_ascending(const double (&x)[3], int (&o)[3])
+// Rank of each of three values in ascending order, ties by index (a stable sort).
+template <typename T>
+__device__ __forceinline__ void ranks3(const T (&x)[3], int (&rk)[3])
 {
-    // stable: ties keep index order
-    o[0] = 0; o[1] = 1; o[2] = 2;
-    if (x[o[1]] < x[o[0]]) { const int t = o[0]; o[0] = o[1]; o[1] = t; }
-    if (x[o[2]] < x[o[1]]) { const int t = o[1]; o[1] = o[2]; o[2] = t; }
-    if (x[o[1]] < x[o[0]]) { const int t = o[0]; o[0] = o[1]; o[1] = t; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        rk[k] = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (j != k && (x[j] < x[k] || (x[j] == x[k] && j < k))) ++rk[k];
+    }
 }
 
-__device__ void quat_of(const double (&R)[3][3], double (&q)[4])
+// Unit quaternion (w, x, y, z) of a rotation matrix, branch on the largest of
+// the trace and the diagonal (Shepperd) so the divisor is never small.
+__device__ __forceinline__ void quat_of(const float (&R)[3][3], float (&q)[4])
 {
-    const double d0 = R[0][0], d1 = R[1][1], d2 = R[2][2], tr = d0 + d1 + d2;
+    const float d0 = R[0][0], d1 = R[1][1], d2 = R[2][2], tr = d0 + d1 + d2;
     if (tr >= d0 && tr >= d1 && tr >= d2) {
-        const double h = 2.0 * sqrt(1.0 + tr);
-        q[0] = 0.25 * h; q[1] = (R[2][1] - R[1][2]) / h; q[2] = (R[0][2] - R[2][0]) / h; q[3] = (R[1][0] - R[0][1]) / h;
+        const float h = 2.f * sqrtf(1.f + tr), ih = 1.f / h;
+        q[0] = 0.25f * h; q[1] = (R[2][1] - R[1][2]) * ih; q[2] = (R[0][2] - R[2][0]) * ih; q[3] = (R[1][0] - R[0][1]) * ih;
     } else if (d0 >= d1 && d0 >= d2) {
-        const double h = 2.0 * sqrt(1.0 + d0 - d1 - d2);
-        q[0] = (R[2][1] - R[1][2]) / h; q[1] = 0.25 * h; q[2] = (R[0][1] + R[1][0]) / h; q[3] = (R[0][2] + R[2][0]) / h;
+        const float h = 2.f * sqrtf(1.f + d0 - d1 - d2), ih = 1.f / h;
+        q[0] = (R[2][1] - R[1][2]) * ih; q[1] = 0.25f * h; q[2] = (R[0][1] + R[1][0]) * ih; q[3] = (R[0][2] + R[2][0]) * ih;
     } else if (d1 >= d2) {
-        const double h = 2.0 * sqrt(1.0 - d0 + d1 - d2);
-        q[0] = (R[0][2] - R[2][0]) / h; q[1] = (R[0][1] + R[1][0]) / h; q[2] = 0.25 * h; q[3] = (R[1][2] + R[2][1]) / h;
+        const float h = 2.f * sqrtf(1.f - d0 + d1 - d2), ih = 1.f / h;
+        q[0] = (R[0][2] - R[2][0]) * ih; q[1] = (R[0][1] + R[1][0]) * ih; q[2] = 0.25f * h; q[3] = (R[1][2] + R[2][1]) * ih;
     } else {
-        const double h = 2.0 * sqrt(1.0 - d0 - d1 + d2);
-        q[0] = (R[1][0] - R[0][1]) / h; q[1] = (R[0][2] + R[2][0]) / h; q[2] = (R[1][2] + R[2][1]) / h; q[3] = 0.25 * h;
+        const float h = 2.f * sqrtf(1.f - d0 - d1 + d2), ih = 1.f / h;
+        q[0] = (R[1][0] - R[0][1]) * ih; q[1] = (R[0][2] + R[2][0]) * ih; q[2] = (R[1][2] + R[2][1]) * ih; q[3] = 0.25f * h;
     }
 }
 
@@ -330,113 +418,133 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_TRI_SINGULAR;
         return;
     }
-    const double X[3] = {(double)m.x + dl[0], (double)m.y + dl[1], (double)m.z + dl[2]};
+    const float X0 = (float)((double)m.x + dl[0]), X1 = (float)((double)m.y + dl[1]),
+                X2 = (float)((double)m.z + dl[2]);
     st |= TSP_POS_OK;
-    outm = make_float4((float)X[0], (float)X[1], (float)X[2], m.w);
+    outm = make_float4(X0, X1, X2, m.w);
 
-    // ---- a8 covariance: 3 equations per solved view, unknowns (xx, xy, xz, yy, yz, zz)
-    double A6[6][6], b6[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        b6[a] = 0.0;
-#pragma unroll
-        for (int b = 0; b < 6; ++b) A6[a][b] = 0.0;
+    // ---- a8 covariance: 3 equations per solved view, unknowns (xx, xy, xz, yy, yz, zz).
+    // Each view's T = J' W annihilates its viewing ray d, so sym(d1 d2^T) solves the
+    // homogeneous system of any two views: two views are always rank 5.
+    if (nv < 3) {
+        om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_COV_SINGULAR;
+        return;
     }
+    float Ah[21], Al[21], bh[6], bl[6];
+#pragma unroll
+    for (int u = 0; u < 21; ++u) { Ah[u] = 0.f; Al[u] = 0.f; }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) { bh[u] = 0.f; bl[u] = 0.f; }
     for (int v = 0; v < vs.V; ++v) {
         const size_t i = (size_t)v * n + g;
         if (!(w.vres2[i].x & TSP_VIEW_OK)) continue;
         const DevCam& c = vs.cam[v];
-        double p[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            p[k] = (double)c.R[3 * k] * X[0] + (double)c.R[3 * k + 1] * X[1] + (double)c.R[3 * k + 2] * X[2] + (double)c.t[k];
-        const double iz = 1.0 / p[2];
-        const double j00 = c.fx * iz, j02 = -c.fx * p[0] * iz * iz;
-        const double j11 = c.fy * iz, j12 = -c.fy * p[1] * iz * iz;
-        double T[2][3];
+        const float p0 = fmaf(c.R[0], X0, fmaf(c.R[1], X1, fmaf(c.R[2], X2, c.t[0])));
+        const float p1 = fmaf(c.R[3], X0, fmaf(c.R[4], X1, fmaf(c.R[5], X2, c.t[1])));
+        const float p2 = fmaf(c.R[6], X0, fmaf(c.R[7], X1, fmaf(c.R[8], X2, c.t[2])));
+        const float iz = 1.f / p2;
+        const float j00 = c.fx * iz, j02 = -c.fx * p0 * iz * iz;
+        const float j11 = c.fy * iz, j12 = -c.fy * p1 * iz * iz;
+        float T[2][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            T[0][k] = j00 * c.R[k] + j02 * c.R[6 + k];
-            T[1][k] = j11 * c.R[3 + k] + j12 * c.R[6 + k];
+            T[0][k] = fmaf(j00, c.R[k], j02 * c.R[6 + k]);
+            T[1][k] = fmaf(j11, c.R[3 + k], j12 * c.R[6 + k]);
         }
         const float4 b0v = w.vres1[i], b1v = w.vres3[i];
-        const double B0[3] = {b0v.x, b0v.y, b0v.z}, B1[3] = {b1v.x, b1v.y, b1v.z};
-        const double rhs[3] = {B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2],
-                               B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2],
-                               B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2]};
-        const int ii[3] = {0, 0, 1}, jj[3] = {0, 1, 1};
+        const float rhs[3] = {fmaf(b0v.x, b0v.x, fmaf(b0v.y, b0v.y, b0v.z * b0v.z)),
+                              fmaf(b0v.x, b1v.x, fmaf(b0v.y, b1v.y, b0v.z * b1v.z)),
+                              fmaf(b1v.x, b1v.x, fmaf(b1v.y, b1v.y, b1v.z * b1v.z))};
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            const int a = ii[e], b = jj[e];
-            double cf[6];
+            const int a = e == 2 ? 1 : 0, b = e == 0 ? 0 : 1;
+            float cf[6];
             cf[0] = T[a][0] * T[b][0];
-            cf[1] = T[a][0] * T[b][1] + T[a][1] * T[b][0];
-            cf[2] = T[a][0] * T[b][2] + T[a][2] * T[b][0];
+            cf[1] = fmaf(T[a][0], T[b][1], T[a][1] * T[b][0]);
+            cf[2] = fmaf(T[a][0], T[b][2], T[a][2] * T[b][0]);
             cf[3] = T[a][1] * T[b][1];
-            cf[4] = T[a][1] * T[b][2] + T[a][2] * T[b][1];
+            cf[4] = fmaf(T[a][1], T[b][2], T[a][2] * T[b][1]);
             cf[5] = T[a][2] * T[b][2];
 #pragma unroll
             for (int u = 0; u < 6; ++u) {
-                b6[u] += cf[u] * rhs[e];
+                df_madd(bh[u], bl[u], cf[u], rhs[e]);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) A6[u][k] += cf[u] * cf[k];
+                for (int k = 0; k <= u; ++k) df_madd(Ah[tri(u, k)], Al[tri(u, k)], cf[u], cf[k]);
             }
         }
     }
+    double A6[21], b6[6];
+#pragma unroll
+    for (int u = 0; u < 21; ++u) A6[u] = (double)Ah[u] + (double)Al[u];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) b6[u] = (double)bh[u] + (double)bl[u];
     const double rc2 = (double)fp.cov_rcond_min * (double)fp.cov_rcond_min;
-    if (!chol_solve_pivoted<6>(A6, b6, rc2)) {
+    if (!ldl_solve_pivoted<6>(A6, b6, rc2)) {
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_COV_SINGULAR;
         return;
     }
-    double S[3][3] = {{b6[0], b6[1], b6[2]}, {b6[1], b6[3], b6[4]}, {b6[2], b6[4], b6[5]}};
+    const double S[3][3] = {{b6[0], b6[1], b6[2]}, {b6[1], b6[3], b6[4]}, {b6[2], b6[4], b6[5]}};
 
     // ---- a9 eigen decomposition and the reorder / sign rules
-    double lam[3], E[3][3];
+    double lam[3];
+    float E[3][3];
     eig_sym3(S, lam, E);
     if (!(lam[0] > 0.0) || !(lam[1] > 0.0) || !(lam[2] > 0.0)) {
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_NEG_EIG;
         return;
     }
     // old rotation from the normalised input quaternion (w, x, y, z)
-    const double qn = sqrt((double)qi.x * qi.x + (double)qi.y * qi.y + (double)qi.z * qi.z + (double)qi.w * qi.w);
-    const double qw = qi.x / qn, qx = qi.y / qn, qy = qi.z / qn, qz = qi.w / qn;
-    const double Ro[3][3] = {
-        {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
-        {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
-        {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-    const double so[3] = {si.x, si.y, si.z};
+    const float qn = 1.f / sqrtf(qi.x * qi.x + qi.y * qi.y + qi.z * qi.z + qi.w * qi.w);
+    const float qw = qi.x * qn, qx = qi.y * qn, qy = qi.z * qn, qz = qi.w * qn;
+    const float Ro[3][3] = {
+        {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+        {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+        {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+    const float so[3] = {si.x, si.y, si.z};
     int ro[3], rn[3];
-    rank_ascending(so, ro);
-    rank_ascending(lam, rn);
-    double Rn[3][3], ln[3], al[3];
-    for (int r = 0; r < 3; ++r) {
-        const int k = ro[r], e = rn[r];
-        ln[k] = lam[e];
-        for (int i = 0; i < 3; ++i) Rn[i][k] = E[i][e];
-    }
+    ranks3(so, ro);
+    ranks3(lam, rn);
+    float Rn[3][3], al[3];
+    double ln[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)          // old axis k takes the eigenpair of equal rank
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            if (ro[k] == rn[e]) {
+                ln[k] = lam[e];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) Rn[i][k] = E[i][e];
+            }
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double d = Rn[0][k] * Ro[0][k] + Rn[1][k] * Ro[1][k] + Rn[2][k] * Ro[2][k];
-        if (d < 0.0) {
+        float d = Rn[0][k] * Ro[0][k] + Rn[1][k] * Ro[1][k] + Rn[2][k] * Ro[2][k];
+        if (d < 0.f) {
+#pragma unroll
             for (int i = 0; i < 3; ++i) Rn[i][k] = -Rn[i][k];
             d = -d;
         }
         al[k] = d;
     }
-    const double det = Rn[0][0] * (Rn[1][1] * Rn[2][2] - Rn[1][2] * Rn[2][1])
-                     - Rn[0][1] * (Rn[1][0] * Rn[2][2] - Rn[1][2] * Rn[2][0])
-                     + Rn[0][2] * (Rn[1][0] * Rn[2][1] - Rn[1][1] * Rn[2][0]);
-    if (det < 0.0) {
-        int kmin = 0;
-        if (al[1] < al[kmin]) kmin = 1;
-        if (al[2] < al[kmin]) kmin = 2;
-        for (int i = 0; i < 3; ++i) Rn[i][kmin] = -Rn[i][kmin];
+    const float det = Rn[0][0] * (Rn[1][1] * Rn[2][2] - Rn[1][2] * Rn[2][1])
+                    - Rn[0][1] * (Rn[1][0] * Rn[2][2] - Rn[1][2] * Rn[2][0])
+                    + Rn[0][2] * (Rn[1][0] * Rn[2][1] - Rn[1][1] * Rn[2][0]);
+    if (det < 0.f) {
+        int kmin = al[1] < al[0] ? 1 : 0;
+        if (al[2] < fminf(al[0], al[1])) kmin = 2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (k == kmin) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) Rn[i][k] = -Rn[i][k];
+            }
     }
-    double qq[4];
+    float qq[4];
     quat_of(Rn, qq);
-    if (qq[0] * qw + qq[1] * qx + qq[2] * qy + qq[3] * qz < 0.0)
+    if (qq[0] * qw + qq[1] * qx + qq[2] * qy + qq[3] * qz < 0.f)
+#pragma unroll
         for (int k = 0; k < 4; ++k) qq[k] = -qq[k];
-    outq = make_float4((float)qq[0], (float)qq[1], (float)qq[2], (float)qq[3]);
-    outs = make_float4((float)sqrt(ln[0]), (float)sqrt(ln[1]), (float)sqrt(ln[2]), 0.f);
+    outq = make_float4(qq[0], qq[1], qq[2], qq[3]);
+    outs = make_float4(sqrtf((float)ln[0]), sqrtf((float)ln[1]), sqrtf((float)ln[2]), 0.f);
     om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_COV_OK;
 }
 

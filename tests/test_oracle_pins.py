@@ -347,6 +347,58 @@ def test_multiview_thresholds_by_construction():
     np.testing.assert_allclose(r["mean"], Xf)           # unsolvable keeps its input
 
 
+def test_two_views_leave_covariance_rank_deficient():
+    """Sec. 4.4.2: each view constrains T Sigma T^T with T = J' W, and T maps the
+    view's ray d (camera centre to mean) to zero, so sym(d1 d2^T) is invisible to
+    both views of a pair: the 6-unknown system of two views has rank 5 and the
+    oracle reports it singular, while a third view fixes it."""
+    base = S.base_cameras()
+    X = np.array([0.02, -0.03, 0.01])
+    q = np.array([0.8, 0.1, 0.5, -0.3])
+    q /= np.linalg.norm(q)
+    scene = S.with_gaussians(base, [X], [q], [[0.05, 0.03, 0.04]], [0.9])
+    Xf = scene.means_opacity[0, :3].astype(np.float64)
+    Sg = S.cov3d(scene.quats[0], scene.scales[0, :3].astype(np.float64))
+    T, d = [], []
+    for v in range(4):
+        Tv = S.pinhole_jacobian(scene, v, Xf)
+        Rv = scene.R[v].astype(np.float64)          # FP32 rows: R^-1, not R^T
+        dv = np.linalg.solve(Rv, Rv @ Xf + scene.t[v].astype(np.float64))
+        assert np.linalg.norm(Tv @ dv) < 1e-12 * np.linalg.norm(Tv) * np.linalg.norm(dv)
+        T.append(Tv)
+        d.append(dv)
+    N = np.outer(d[0], d[1]) + np.outer(d[1], d[0])
+    for v in (0, 1):
+        assert np.abs(T[v] @ N @ T[v].T).max() < 1e-12 * np.linalg.norm(T[v]) ** 2 * np.linalg.norm(N)
+    assert np.abs(T[2] @ N @ T[2].T).max() > 1e-3 * np.linalg.norm(T[2]) ** 2 * np.linalg.norm(N)
+
+    def rows(Tv):   # vech(T Sigma T^T) in the unknowns (xx, xy, xz, yy, yz, zz)
+        out = []
+        for a, b in ((0, 0), (0, 1), (1, 1)):
+            t, u = Tv[a], Tv[b]
+            out.append([t[0] * u[0], t[0] * u[1] + t[1] * u[0], t[0] * u[2] + t[2] * u[0],
+                        t[1] * u[1], t[1] * u[2] + t[2] * u[1], t[2] * u[2]])
+        return out
+    sv2 = np.linalg.svd(np.array(rows(T[0]) + rows(T[1])), compute_uv=False)
+    sv3 = np.linalg.svd(np.array(rows(T[0]) + rows(T[1]) + rows(T[2])), compute_uv=False)
+    assert sv2[-1] / sv2[0] < 1e-12 and sv3[-1] / sv3[0] > 1e-3
+
+    mn, cn = [], []
+    for v in range(4):
+        mu, C2 = S.projected(scene, v, Xf, Sg)
+        mn.append(mu)
+        cn.append([C2[0, 0], C2[0, 1], C2[1, 1]])
+    mn, cn = np.array(mn), np.array(cn)
+    r = oracle.multiview(scene, 0, [1, 1, 8, 8], [0.5] * 4, [10] * 4, mn, cn)
+    assert r["status"] & oracle.OS_POS_OK and r["status"] & oracle.OS_COV_SINGULAR
+    r = oracle.multiview(scene, 0, [1, 1, 1, 8], [0.5] * 4, [10] * 4, mn, cn)
+    assert r["status"] & oracle.OS_COV_OK
+    Sn = np.array([[r["cov3d"][0], r["cov3d"][1], r["cov3d"][2]],
+                   [r["cov3d"][1], r["cov3d"][3], r["cov3d"][4]],
+                   [r["cov3d"][2], r["cov3d"][4], r["cov3d"][5]]])
+    np.testing.assert_allclose(Sn, Sg, rtol=1e-6, atol=1e-9 * np.abs(Sg).max())
+
+
 def test_paper_thresholds_golden():
     with open(os.path.join(GOLDEN, "paper_thresholds.json")) as f:
         g = json.load(f)
