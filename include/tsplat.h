@@ -127,8 +127,10 @@ typedef struct tsp_options {
                                 /*    call; read them with tsp_stage_times          */
     int32_t collect_stats;      /* 1: the raster step also counts its work (slower; */
                                 /*    for measurement only), see TSP_I_STATS        */
-    int32_t raster_pixels_per_thread; /* a5 layout: 1 (8x4 warp blocks), 2 (8x8) */
-                                /*    or 4 (8x16); 0 = default (2)                 */
+    int32_t raster_variant;     /* a5 kernel: 0 = two-phase (blend, then per-hit */
+                                /*    moment sums; 8x8 warp blocks), the default;  */
+                                /*    1, 2, 4 = warp-shuffle reduction with 1, 2, 4 */
+                                /*    pixels per thread (8x4, 8x8, 8x16 blocks)     */
     int64_t pair_capacity;      /* initial (tile, Gaussian) pair capacity, 0 = auto */
     int64_t budget_bytes;       /* workspace ceiling, 0 = unlimited                */
 } tsp_options;

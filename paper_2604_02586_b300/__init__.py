@@ -56,7 +56,7 @@ class Options(C.Structure):
                 ("sumw_min_view", C.c_float), ("min_px_view", C.c_int32), ("lam_min_px2", C.c_float),
                 ("min_views", C.c_int32), ("sumw_min_total", C.c_float), ("min_px_total", C.c_int32),
                 ("cov_rcond_min", C.c_float), ("async_pairs", C.c_int32), ("stage_timing", C.c_int32),
-                ("collect_stats", C.c_int32), ("raster_pixels_per_thread", C.c_int32),
+                ("collect_stats", C.c_int32), ("raster_variant", C.c_int32),
                 ("pair_capacity", C.c_int64), ("budget_bytes", C.c_int64)]
 
 

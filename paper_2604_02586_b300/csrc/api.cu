@@ -142,9 +142,9 @@ tsp_status check_options(tsp_context* ctx, const tsp_options& o)
         return fail(ctx, TSP_ERR_INVALID_ARG, "cov_rcond_min must lie in [1e-12, 1)");
     if (o.min_px_view < 0 || o.min_views < 0 || o.min_px_total < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "counts must be >= 0");
-    if (o.raster_pixels_per_thread != 0 && o.raster_pixels_per_thread != 1 &&
-        o.raster_pixels_per_thread != 2 && o.raster_pixels_per_thread != 4)
-        return fail(ctx, TSP_ERR_INVALID_ARG, "raster_pixels_per_thread must be 0, 1, 2 or 4");
+    if (o.raster_variant != 0 && o.raster_variant != 1 && o.raster_variant != 2 &&
+        o.raster_variant != 4)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "raster_variant must be 0, 1, 2 or 4");
     if (o.pair_capacity < 0 || o.pair_capacity > INT32_MAX || o.budget_bytes < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "bad pair_capacity or budget_bytes");
     return TSP_OK;
@@ -368,7 +368,7 @@ tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera
     ctx->timed = false;
     if ((s = bin_front(ctx, vs, g, nullptr, 0, 0, NT, w, st))) return s;
     TSP_CUDA(launch_raster_accumulate(vs, w, NT, ctx->opt.collect_stats != 0,
-                                      ctx->opt.raster_pixels_per_thread == 0 ? 2 : ctx->opt.raster_pixels_per_thread, st));
+                                      ctx->opt.raster_variant, st));
     TSP_CUDA(mark(ctx, 5, st));
     TSP_CUDA(launch_view_solve(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
                                (const float4*)g->scales, fp, w, out->view_affine, out->view_flags, st));

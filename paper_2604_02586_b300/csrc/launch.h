@@ -18,7 +18,7 @@ cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st);
 cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st);
 // a5: blend and accumulate alpha T weighted track moments per (view, Gaussian).
 cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
-                                     int pixels_per_thread, cudaStream_t st);
+                                     int variant, cudaStream_t st);
 // render colour and final transmittance.
 cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
                                  float* const* final_T, cudaStream_t st);

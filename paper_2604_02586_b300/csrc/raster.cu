@@ -277,6 +277,249 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
     }
 }
 
+// Smallest value of p = z1^2 + z2^2 (z1 = ex i11, z2 = (ey - k ex) i22) over the
+// pixel-centre rectangle [bx0, bx1] x [by0, by1] of a warp block, for the
+// tile-local mean (g0.x, g0.y) and factor (i11, k, i22) = (g0.z, g0.w, i22).
+// p is convex, so when the mean lies outside the rectangle the minimum sits on
+// an edge facing the mean: along a vertical edge ex = e it is at ey = k e, along
+// a horizontal edge ey = f at ex = k i22^2 f / (i11^2 + k^2 i22^2), each clamped
+// to the edge.  Returns 0 when the mean is inside.
+__device__ __forceinline__ float block_min_power(float4 g0, float i22, float bx0, float bx1,
+                                                 float by0, float by1)
+{
+    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
+    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
+    float pv = 3.0e38f, ph = 3.0e38f;
+    if (outx) {
+        const float e = ex0 > 0.f ? ex0 : ex1;
+        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
+        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
+        pv = fmaf(z1, z1, z2 * z2);
+    }
+    if (outy) {
+        const float f = ey0 > 0.f ? ey0 : ey1;
+        const float i22s = i22 * i22;
+        const float a = fmaf(g0.z, g0.z, g0.w * g0.w * i22s);
+        const float ex = fminf(fmaxf(g0.w * i22s * f / a, ex0), ex1);
+        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
+        ph = fmaf(z1, z1, z2 * z2);
+    }
+    return (outx || outy) ? fminf(pv, ph) : 0.f;
+}
+
+// Two-phase accumulate (the default).  Warp w owns the 8x8 block (w & 1, w >> 1)
+// of the tile, lane l the pixels (l & 7, (l >> 3) + 4h), h = 0, 1.
+//   Phase 1 (blend, pixel-parallel): for each staged Gaussian whose alpha >= 1/255
+//   ellipse meets the block, every lane blends its two pixels and writes the
+//   weight w = alpha T (0 where nothing is added) into a warp-private buffer,
+//   one column per pending hit.
+//   Phase 2 (moments, hit-parallel): once 16 hits are pending, lane l sums the
+//   13 weighted moments of hit l & 15 over pixel half l >> 4 (32 pixels) from
+//   the buffer; the two halves are added with one shuffle per value and lanes
+//   0-15 add the result to global memory with 4 float4 atomics.
+// Buffer layout: weight of hit c at pixel i of half h at h * kWHalf + i * kWRow + c.
+// A row stride of 17 words makes both the phase-1 writes (lanes = pixels) and
+// the phase-2 reads (lanes = hits) conflict-free, and kWHalf = 16 (mod 32)
+// keeps the two halves on different banks.
+constexpr int kChunk = 16;
+constexpr int kWRow = 17;
+constexpr int kWHalf = 32 * kWRow + 16;
+constexpr int kWWords = kWHalf + 32 * kWRow;
+
+template <bool kStats>
+__global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, const Work w)
+{
+    constexpr int kNW = 4;
+    __shared__ float4 s_g0[kBatch];
+    __shared__ float4 s_g1[kBatch];
+    __shared__ float4 s_box[kBatch];
+    __shared__ float2 s_ref[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ float s_pm[kBatch];
+    __shared__ float s_W[kNW][kWWords];
+    __shared__ float4 s_F[kNW][2][33];      // (d_x, d_y, static, 0) per pixel, halves padded
+
+    const uint32_t tile = blockIdx.x;
+    const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
+    if (beg >= end) return;
+    int v, tx, ty;
+    view_of_tile(vs, tile, v, tx, ty);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bxo = (warp & 1) * 8, byo = (warp >> 1) * 8;
+    const int W = vs.cam[v].W, H = vs.cam[v].H;
+    const size_t vbase = (size_t)v * vs.n;
+    float* const Wb = s_W[warp];
+
+    float T[2];
+    bool done[2], vis[2], stat[2];
+    const float xc = (float)(bxo + (lane & 7)) + 0.5f;
+    float yc[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int ly = byo + (lane >> 3) + 4 * k;
+        const int px = tx * kTile + bxo + (lane & 7), py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        float ddx = 0.f, ddy = 0.f;
+        vis[k] = false;
+        if (inside) {
+            const size_t pix = (size_t)py * W + px;
+            const float2 d = vs.disp[v][pix];
+            ddx = d.x; ddy = d.y;
+            vis[k] = vs.vis[v][pix] != 0;
+        }
+        // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
+        stat[k] = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
+        s_F[warp][k][lane] = make_float4(ddx, ddy, stat[k] ? 1.f : 0.f, 0.f);
+        yc[k] = (float)ly + 0.5f;
+        T[k] = 1.0f;
+        done[k] = !inside;
+    }
+    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
+    unsigned long long n_eval = 0, n_blend = 0, n_add = 0, n_list = 0;
+
+    // pending hit c is held by lane c: moment record, origin, reference, counts
+    int pend = 0;
+    uint32_t h_id = 0;
+    float h_ox = 0.f, h_oy = 0.f, h_rx = 0.f, h_ry = 0.f, h_np = 0.f, h_ns = 0.f;
+
+    auto phase2 = [&](int npend) {
+        __syncwarp();
+        const int c = lane & 15, half = lane >> 4;
+        const float ox = __shfl_sync(kFull, h_ox, c), oy = __shfl_sync(kFull, h_oy, c);
+        const float rx = __shfl_sync(kFull, h_rx, c), ry = __shfl_sync(kFull, h_ry, c);
+        float mx[8], my[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mx[i] = ((float)(bxo + i) + 0.5f) - ox;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) my[r] = ((float)(byo + 4 * half + r) + 0.5f) - oy;
+        float s[13];
+#pragma unroll
+        for (int q = 0; q < 13; ++q) s[q] = 0.f;
+        const float* Wh = Wb + half * kWHalf + c;
+        const float4* Fh = s_F[warp][half];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float wv = Wh[i * kWRow];
+            const float4 f = Fh[i];
+            const float X = mx[i & 7], Y = my[i >> 3];
+            const float dx = f.x - rx, dy = f.y - ry;
+            const float wx = wv * X, wy = wv * Y;
+            s[0] += wv; s[1] += wx; s[2] += wy;
+            s[3] = fmaf(wx, X, s[3]); s[4] = fmaf(wx, Y, s[4]); s[5] = fmaf(wy, Y, s[5]);
+            s[6] = fmaf(wv, dx, s[6]); s[7] = fmaf(wv, dy, s[7]);
+            s[8] = fmaf(wx, dx, s[8]); s[9] = fmaf(wx, dy, s[9]);
+            s[10] = fmaf(wy, dx, s[10]); s[11] = fmaf(wy, dy, s[11]);
+            s[12] = fmaf(wv, f.z, s[12]);
+        }
+#pragma unroll
+        for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
+        if (lane < npend && h_np > 0.f) {
+            float4* dst = &w.moments[(vbase + h_id) * 4];
+            atomicAdd(dst + 0, make_float4(s[0], s[1], s[2], s[3]));
+            atomicAdd(dst + 1, make_float4(s[4], s[5], s[6], s[7]));
+            atomicAdd(dst + 2, make_float4(s[8], s[9], s[10], s[11]));
+            atomicAdd(dst + 3, make_float4(s[12], h_np, h_ns, 0.f));
+        }
+        __syncwarp();
+    };
+
+    for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
+        const int nb = (int)min((uint32_t)kBatch, end - b0);
+        if (kStats && tid == 0) n_list += nb;
+        if (tid < nb) {
+            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g1 = w.geom1[vbase + g];
+            s_id[tid] = g;
+            s_g0[tid] = g0;
+            s_g1[tid] = g1;
+            s_box[tid] = footprint_box(g0, g1);
+            s_pm[tid] = log2f(255.0f * g1.y) * 1.002f + 1e-4f;
+            s_ref[tid] = w.dref[vbase + g];
+        }
+        __syncthreads();
+        const bool alive = !done[0] || !done[1];
+        unsigned long long m = 0;
+        if (__any_sync(kFull, alive)) {
+            bool h0 = false, h1 = false;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int j = lane + 32 * hh;
+                bool hit = false;
+                if (j < nb) {
+                    const float4 bb = s_box[j];
+                    hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
+                    if (hit) hit = block_min_power(s_g0[j], s_g1[j].x, bx0, bx1, by0, by1) <= s_pm[j];
+                }
+                if (hh == 0) h0 = hit; else h1 = hit;
+            }
+            m = ((unsigned long long)__ballot_sync(kFull, h1) << 32) | __ballot_sync(kFull, h0);
+        }
+        while (m) {
+            const int j = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const float4 g0 = s_g0[j];
+            const float4 g1 = s_g1[j];
+            bool add[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                float wk = 0.f;
+                add[k] = false;
+                if (!done[k]) {
+                    const float ex = xc - g0.x, ey = yc[k] - g0.y;
+                    const float z1 = ex * g0.z;
+                    const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
+                    const float pw = fmaf(z2, z2, z1 * z1);
+                    const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+                    if (kStats) ++n_eval;
+                    if (alpha >= kAlphaMin) {
+                        const float Tn = T[k] * (1.0f - alpha);
+                        if (Tn < kTMin) {
+                            done[k] = true;
+                        } else {
+                            if (kStats) ++n_blend;
+                            if (vis[k]) {
+                                wk = alpha * T[k];
+                                add[k] = true;
+                                if (kStats) ++n_add;
+                            }
+                            T[k] = Tn;
+                        }
+                    }
+                }
+                Wb[k * kWHalf + lane * kWRow + pend] = wk;
+            }
+            const int np = __popc(__ballot_sync(kFull, add[0])) + __popc(__ballot_sync(kFull, add[1]));
+            const int ns = __popc(__ballot_sync(kFull, add[0] && stat[0])) +
+                           __popc(__ballot_sync(kFull, add[1] && stat[1]));
+            if (lane == pend) {
+                h_id = s_id[j];
+                h_ox = g0.x + g1.z;
+                h_oy = g0.y + g1.w;
+                const float2 rf = s_ref[j];
+                h_rx = rf.x;
+                h_ry = rf.y;
+                h_np = (float)np;
+                h_ns = (float)ns;
+            }
+            if (++pend == kChunk) {
+                phase2(kChunk);
+                pend = 0;
+            }
+        }
+        const bool any_alive = !done[0] || !done[1];
+        if (__syncthreads_count(any_alive) == 0) break;
+    }
+    if (pend) phase2(pend);
+    if (kStats) {
+        atomicAdd(&w.stats[0], n_eval);
+        atomicAdd(&w.stats[1], n_blend);
+        atomicAdd(&w.stats[2], n_add);
+        if (tid == 0) atomicAdd(&w.stats[3], n_list);
+    }
+}
+
 __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, const Work w,
                                                            const RenderOut ro)
 {
@@ -343,13 +586,16 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
 }  // namespace
 
 cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
-                                     int pixels_per_thread, cudaStream_t st)
+                                     int variant, cudaStream_t st)
 {
     if (NT == 0 || vs.n == 0) return cudaSuccess;
-    if (pixels_per_thread == 1) {
+    if (variant == 0) {
+        if (stats) k_raster_accumulate_2p<true><<<NT, 128, 0, st>>>(vs, w);
+        else k_raster_accumulate_2p<false><<<NT, 128, 0, st>>>(vs, w);
+    } else if (variant == 1) {
         if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w);
         else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w);
-    } else if (pixels_per_thread == 4) {
+    } else if (variant == 4) {
         if (stats) k_raster_accumulate<4, true><<<NT, kTilePx / 4, 0, st>>>(vs, w);
         else k_raster_accumulate<4, false><<<NT, kTilePx / 4, 0, st>>>(vs, w);
     } else {

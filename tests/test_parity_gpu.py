@@ -120,13 +120,14 @@ def test_moments(gpu_ready, name):
     check_moments(o, g)
 
 
-@pytest.mark.parametrize("ppt", [1, 4])
+@pytest.mark.parametrize("variant", [1, 2, 4])
 @pytest.mark.parametrize("name", ["tiny", "capture_sub"])
-def test_raster_layouts(gpu_ready, name, ppt):
-    """The 8x4 and 8x16 warp-block layouts of the raster step meet the same bar
-    as the default 8x8 one (the butterfly order differs, the blend does not)."""
+def test_raster_variants(gpu_ready, name, variant):
+    """The warp-shuffle raster kernels (8x4, 8x8 and 8x16 warp blocks) meet the
+    same bar as the default two-phase one: the summation order differs, the
+    blend decisions and pixel counts do not."""
     s, g2, o, sens = case(name)
-    g = P.run_gpu(s, raster_pixels_per_thread=ppt)
+    g = P.run_gpu(s, raster_variant=variant)
     check_moments(o, g)
     assert np.array_equal(g["pairs"], g2["pairs"])
     assert np.array_equal(g["view_moments"][..., 13:15], g2["view_moments"][..., 13:15])
@@ -274,11 +275,11 @@ def test_bad_pointers_are_rejected_before_launch(gpu_ready):
 
 def test_options_are_validated(gpu_ready):
     import paper_2604_02586_b300 as tsp
-    for bad in ({"cov_rcond_min": 0.0}, {"cov_rcond_min": 1.0}, {"raster_pixels_per_thread": 3},
+    for bad in ({"cov_rcond_min": 0.0}, {"cov_rcond_min": 1.0}, {"raster_variant": 3},
                 {"tile_w": 32}, {"det_min": -1.0}, {"min_views": -1}):
         with pytest.raises(tsp.TspError):
             tsp.Context(0, **bad)
-    for ok in ({"cov_rcond_min": 1e-12}, {"raster_pixels_per_thread": 4}):
+    for ok in ({"cov_rcond_min": 1e-12}, {"raster_variant": 4}):
         tsp.Context(0, **ok).close()
 
 
