@@ -308,15 +308,18 @@ __device__ __forceinline__ float block_min_power(float4 g0, float i22, float bx0
 }
 
 // Two-phase accumulate (the default).  Warp w owns the 8x8 block (w & 1, w >> 1)
-// of the tile, lane l the pixels (l & 7, (l >> 3) + 4h), h = 0, 1.
-//   Phase 1 (blend, pixel-parallel): for each staged Gaussian whose alpha >= 1/255
-//   ellipse meets the block, every lane blends its two pixels and writes the
-//   weight w = alpha T (0 where nothing is added) into a warp-private buffer,
-//   one column per pending hit.
+// of the tile, lane l the pixels (l & 7, (l >> 3) + 4h), h = 0, 1, and walks the
+// tile's depth-ordered list on its own (no block-wide barrier): 32 entries at a
+// time, lane l loads entry l, tests whether its alpha >= 1/255 ellipse meets the
+// block, and stages the hits in warp-private shared memory.
+//   Phase 1 (blend, pixel-parallel): for each hit, every lane blends its two
+//   pixels and writes the weight w = alpha T (0 where nothing is added) into a
+//   warp-private buffer, one column per pending hit; hits that add no pixel of
+//   the block are dropped.
 //   Phase 2 (moments, hit-parallel): once 16 hits are pending, lane l sums the
 //   13 weighted moments of hit l & 15 over pixel half l >> 4 (32 pixels) from
-//   the buffer; the two halves are added with one shuffle per value and lanes
-//   0-15 add the result to global memory with 4 float4 atomics.
+//   the buffer; the halves are joined with one shuffle per value and lanes 0-15
+//   add the result to global memory with 4 float4 atomics.
 // Buffer layout: weight of hit c at pixel i of half h at h * kWHalf + i * kWRow + c.
 // A row stride of 17 words makes both the phase-1 writes (lanes = pixels) and
 // the phase-2 reads (lanes = hits) conflict-free, and kWHalf = 16 (mod 32)
@@ -327,15 +330,13 @@ constexpr int kWHalf = 32 * kWRow + 16;
 constexpr int kWWords = kWHalf + 32 * kWRow;
 
 template <bool kStats>
-__global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, const Work w)
+__global__ void __launch_bounds__(128, 6) k_raster_accumulate_2p(const ViewSet vs, const Work w)
 {
     constexpr int kNW = 4;
-    __shared__ float4 s_g0[kBatch];
-    __shared__ float4 s_g1[kBatch];
-    __shared__ float4 s_box[kBatch];
-    __shared__ float2 s_ref[kBatch];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ float s_pm[kBatch];
+    __shared__ float4 s_g0[kNW][32];
+    __shared__ float4 s_g1[kNW][32];
+    __shared__ float4 s_hd[kNW][32];        // (origin x, origin y, reference x, reference y)
+    __shared__ uint32_t s_id[kNW][32];
     __shared__ float s_W[kNW][kWWords];
     __shared__ float4 s_F[kNW][2][33];      // (d_x, d_y, static, 0) per pixel, halves padded
 
@@ -376,23 +377,22 @@ __global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, 
     }
     const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
     const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
-    unsigned long long n_eval = 0, n_blend = 0, n_add = 0, n_list = 0;
+    unsigned long long n_eval = 0, n_blend = 0, n_add = 0;
+    if (kStats && tid == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
-    // pending hit c is held by lane c: moment record, origin, reference, counts
+    // pending hit c is held by lane c: moment record, origin and reference, counts
     int pend = 0;
     uint32_t h_id = 0;
-    float h_ox = 0.f, h_oy = 0.f, h_rx = 0.f, h_ry = 0.f, h_np = 0.f, h_ns = 0.f;
+    float4 h_hd = make_float4(0.f, 0.f, 0.f, 0.f);
+    float h_np = 0.f, h_ns = 0.f;
 
     auto phase2 = [&](int npend) {
         __syncwarp();
         const int c = lane & 15, half = lane >> 4;
-        const float ox = __shfl_sync(kFull, h_ox, c), oy = __shfl_sync(kFull, h_oy, c);
-        const float rx = __shfl_sync(kFull, h_rx, c), ry = __shfl_sync(kFull, h_ry, c);
-        float mx[8], my[4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) mx[i] = ((float)(bxo + i) + 0.5f) - ox;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) my[r] = ((float)(byo + 4 * half + r) + 0.5f) - oy;
+        const float ox = __shfl_sync(kFull, h_hd.x, c), oy = __shfl_sync(kFull, h_hd.y, c);
+        const float rx = __shfl_sync(kFull, h_hd.z, c), ry = __shfl_sync(kFull, h_hd.w, c);
+        const float x0 = ((float)bxo + 0.5f) - ox;
+        const float y0 = ((float)(byo + 4 * half) + 0.5f) - oy;
         float s[13];
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] = 0.f;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, 
         for (int i = 0; i < 32; ++i) {
             const float wv = Wh[i * kWRow];
             const float4 f = Fh[i];
-            const float X = mx[i & 7], Y = my[i >> 3];
+            const float X = x0 + (float)(i & 7), Y = y0 + (float)(i >> 3);
             const float dx = f.x - rx, dy = f.y - ry;
             const float wx = wv * X, wy = wv * Y;
             s[0] += wv; s[1] += wx; s[2] += wy;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, 
         }
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
-        if (lane < npend && h_np > 0.f) {
+        if (lane < npend) {
             float4* dst = &w.moments[(vbase + h_id) * 4];
             atomicAdd(dst + 0, make_float4(s[0], s[1], s[2], s[3]));
             atomicAdd(dst + 1, make_float4(s[4], s[5], s[6], s[7]));
@@ -424,82 +424,58 @@ __global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, 
         __syncwarp();
     };
 
-    for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
-        const int nb = (int)min((uint32_t)kBatch, end - b0);
-        if (kStats && tid == 0) n_list += nb;
-        if (tid < nb) {
-            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+    for (uint32_t b0 = beg; b0 < end; b0 += 32) {
+        if (!__any_sync(kFull, !done[0] || !done[1])) break;
+        bool hit = false;
+        if (b0 + lane < end) {
+            const uint32_t g = (uint32_t)w.pairs[b0 + lane];
             const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
             const float4 g1 = w.geom1[vbase + g];
-            s_id[tid] = g;
-            s_g0[tid] = g0;
-            s_g1[tid] = g1;
-            s_box[tid] = footprint_box(g0, g1);
-            s_pm[tid] = log2f(255.0f * g1.y) * 1.002f + 1e-4f;
-            s_ref[tid] = w.dref[vbase + g];
-        }
-        __syncthreads();
-        const bool alive = !done[0] || !done[1];
-        unsigned long long m = 0;
-        if (__any_sync(kFull, alive)) {
-            bool h0 = false, h1 = false;
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const int j = lane + 32 * hh;
-                bool hit = false;
-                if (j < nb) {
-                    const float4 bb = s_box[j];
-                    hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
-                    if (hit) hit = block_min_power(s_g0[j], s_g1[j].x, bx0, bx1, by0, by1) <= s_pm[j];
-                }
-                if (hh == 0) h0 = hit; else h1 = hit;
+            const float4 bb = footprint_box(g0, g1);
+            hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
+            if (hit)
+                hit = block_min_power(g0, g1.x, bx0, bx1, by0, by1) <=
+                      log2f(255.0f * g1.y) * 1.002f + 1e-4f;
+            if (hit) {
+                const float2 rf = w.dref[vbase + g];
+                s_g0[warp][lane] = g0;
+                s_g1[warp][lane] = g1;
+                s_hd[warp][lane] = make_float4(g0.x + g1.z, g0.y + g1.w, rf.x, rf.y);
+                s_id[warp][lane] = g;
             }
-            m = ((unsigned long long)__ballot_sync(kFull, h1) << 32) | __ballot_sync(kFull, h0);
         }
+        uint32_t m = __ballot_sync(kFull, hit);
+        __syncwarp();
         while (m) {
-            const int j = __ffsll((long long)m) - 1;
+            const int j = __ffs(m) - 1;
             m &= m - 1;
-            const float4 g0 = s_g0[j];
-            const float4 g1 = s_g1[j];
+            const float4 g0 = s_g0[warp][j];
+            const float4 g1 = s_g1[warp][j];
             bool add[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                float wk = 0.f;
-                add[k] = false;
-                if (!done[k]) {
-                    const float ex = xc - g0.x, ey = yc[k] - g0.y;
-                    const float z1 = ex * g0.z;
-                    const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
-                    const float pw = fmaf(z2, z2, z1 * z1);
-                    const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
-                    if (kStats) ++n_eval;
-                    if (alpha >= kAlphaMin) {
-                        const float Tn = T[k] * (1.0f - alpha);
-                        if (Tn < kTMin) {
-                            done[k] = true;
-                        } else {
-                            if (kStats) ++n_blend;
-                            if (vis[k]) {
-                                wk = alpha * T[k];
-                                add[k] = true;
-                                if (kStats) ++n_add;
-                            }
-                            T[k] = Tn;
-                        }
-                    }
-                }
-                Wb[k * kWHalf + lane * kWRow + pend] = wk;
+                const float ex = xc - g0.x, ey = yc[k] - g0.y;
+                const float z1 = ex * g0.z;
+                const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
+                const float pw = fmaf(z2, z2, z1 * z1);
+                const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+                const bool pass = !done[k] && alpha >= kAlphaMin;
+                const float Tn = T[k] * (1.0f - alpha);
+                const bool term = pass && Tn < kTMin;
+                const bool blend = pass && !term;
+                add[k] = blend && vis[k];
+                Wb[k * kWHalf + lane * kWRow + pend] = add[k] ? alpha * T[k] : 0.f;
+                if (kStats) { n_eval += !done[k]; n_blend += blend; n_add += add[k]; }
+                T[k] = blend ? Tn : T[k];
+                done[k] = done[k] || term;
             }
             const int np = __popc(__ballot_sync(kFull, add[0])) + __popc(__ballot_sync(kFull, add[1]));
+            if (np == 0) continue;                     // nothing of this block to add
             const int ns = __popc(__ballot_sync(kFull, add[0] && stat[0])) +
                            __popc(__ballot_sync(kFull, add[1] && stat[1]));
             if (lane == pend) {
-                h_id = s_id[j];
-                h_ox = g0.x + g1.z;
-                h_oy = g0.y + g1.w;
-                const float2 rf = s_ref[j];
-                h_rx = rf.x;
-                h_ry = rf.y;
+                h_id = s_id[warp][j];
+                h_hd = s_hd[warp][j];
                 h_np = (float)np;
                 h_ns = (float)ns;
             }
@@ -508,15 +484,13 @@ __global__ void __launch_bounds__(128) k_raster_accumulate_2p(const ViewSet vs, 
                 pend = 0;
             }
         }
-        const bool any_alive = !done[0] || !done[1];
-        if (__syncthreads_count(any_alive) == 0) break;
+        __syncwarp();                                  // staging is rewritten next
     }
     if (pend) phase2(pend);
     if (kStats) {
         atomicAdd(&w.stats[0], n_eval);
         atomicAdd(&w.stats[1], n_blend);
         atomicAdd(&w.stats[2], n_add);
-        if (tid == 0) atomicAdd(&w.stats[3], n_list);
     }
 }
 
@@ -590,8 +564,11 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
 {
     if (NT == 0 || vs.n == 0) return cudaSuccess;
     if (variant == 0) {
-        if (stats) k_raster_accumulate_2p<true><<<NT, 128, 0, st>>>(vs, w);
-        else k_raster_accumulate_2p<false><<<NT, 128, 0, st>>>(vs, w);
+        // six 28.5 KB CTAs per SM need the largest shared-memory carveout
+        auto kern = stats ? k_raster_accumulate_2p<true> : k_raster_accumulate_2p<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        kern<<<NT, 128, 0, st>>>(vs, w);
     } else if (variant == 1) {
         if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w);
         else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w);
