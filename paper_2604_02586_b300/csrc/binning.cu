@@ -214,44 +214,132 @@ __device__ void smem_sort(uint64_t* src, uint32_t n, uint64_t* s)
     __syncthreads();
 }
 
-// One CTA per tile.  Lists up to kSortCap sort in shared memory; longer lists sort
-// kSortCap-sized runs there and then merge runs pairwise in global memory (each key
-// finds its output slot by a binary search in the partner run; keys are unique).
-__global__ void __launch_bounds__(kSortThreads) k_tile_sort(const uint32_t* __restrict__ off,
-                                                            uint64_t* pairs, uint64_t* tmp, uint32_t cap)
+// One warp per tile list of 2 <= n <= 32 * KPL keys, bitonic-sorted in registers:
+// lane l holds list positions l * KPL + i, i < KPL, padded with ~0 (keys are
+// unique and never ~0).  Exchanges across a stride j < KPL stay inside a lane;
+// strides j >= KPL pair lane l with lane l ^ (j / KPL) through a shuffle.  The
+// direction of a comparator is set by bit k of the position (ascending where it
+// is 0), which is a bit of i for k < KPL and a bit of the lane otherwise.
+constexpr int kWarpSortMax = 1024;
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
 {
-    __shared__ uint64_t s[kSortCap];
-    const uint32_t t = blockIdx.x;
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+template <int KPL>
+__device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint32_t n, int lane)
+{
+    uint64_t x[KPL];
+#pragma unroll
+    for (int i = 0; i < KPL; ++i) {
+        const uint32_t e = (uint32_t)(lane * KPL + i);
+        x[i] = e < n ? keys[e] : ~0ull;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32 * KPL; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= KPL) {
+                const int lj = j / KPL;
+                const bool up = (lane & (k / KPL)) == 0;       // k > j >= KPL
+                const bool take_min = up == ((lane & lj) == 0);
+#pragma unroll
+                for (int i = 0; i < KPL; ++i) {
+                    const uint64_t y = shfl_xor_u64(x[i], lj);
+                    x[i] = take_min ? (y < x[i] ? y : x[i]) : (y > x[i] ? y : x[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < KPL; ++i) {
+                    const int p = i ^ j;
+                    if (p > i) {
+                        const bool up = k >= KPL ? (lane & (k / KPL)) == 0 : (i & k) == 0;
+                        const uint64_t a = x[i], b = x[p];
+                        const bool sw = (a > b) == up;
+                        x[i] = sw ? b : a;
+                        x[p] = sw ? a : b;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < KPL; ++i) {
+        const uint32_t e = (uint32_t)(lane * KPL + i);
+        if (e < n) keys[e] = x[i];
+    }
+}
+
+// Eight tiles per 256-thread CTA, one per warp; tiles whose lists are longer than
+// kWarpSortMax are appended to long_list (count in *long_count) for k_tile_sort.
+__global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restrict__ off,
+                                                        uint64_t* __restrict__ pairs, uint32_t cap,
+                                                        uint32_t NT, uint32_t* __restrict__ long_list,
+                                                        uint32_t* __restrict__ long_count)
+{
+    const uint32_t t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= NT) return;
     const uint32_t b = min(off[t], cap), e = min(off[t + 1], cap);
     if (e <= b + 1) return;
     const uint32_t n = e - b;
-    if (n <= (uint32_t)kSortCap) {
-        smem_sort(pairs + b, n, s);
-        return;
-    }
-    for (uint32_t c = 0; c < n; c += kSortCap) smem_sort(pairs + b + c, min((uint32_t)kSortCap, n - c), s);
-    uint64_t* src = pairs + b;
-    uint64_t* dst = tmp + b;
-    for (uint32_t L = kSortCap; L < n; L <<= 1) {
-        for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
-            const uint32_t run = i / L, start = run * L, partner = run ^ 1u;
-            const uint64_t key = src[i];
-            const uint64_t ps64 = (uint64_t)partner * L;
-            if (ps64 >= n) { dst[i] = key; continue; }
-            const uint32_t ps = (uint32_t)ps64, pe = min(ps + L, n);
-            uint32_t lo = ps, hi = pe;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (src[mid] < key) lo = mid + 1; else hi = mid;
-            }
-            const uint32_t pair_start = min(run, partner) * L;
-            dst[pair_start + (i - start) + (lo - ps)] = key;
+    uint64_t* keys = pairs + b;
+    if (n <= 32) warp_sort_list<1>(keys, n, lane);
+    else if (n <= 64) warp_sort_list<2>(keys, n, lane);
+    else if (n <= 128) warp_sort_list<4>(keys, n, lane);
+    else if (n <= 256) warp_sort_list<8>(keys, n, lane);
+    else if (n <= 512) warp_sort_list<16>(keys, n, lane);
+    else if (n <= (uint32_t)kWarpSortMax) warp_sort_list<32>(keys, n, lane);
+    else if (lane == 0) long_list[atomicAdd(long_count, 1u)] = t;
+}
+
+// Lists longer than kWarpSortMax, one CTA at a time per listed tile.  Up to
+// kSortCap keys sort in shared memory; longer lists sort kSortCap-sized runs there
+// and then merge runs pairwise in global memory (each key finds its output slot
+// by a binary search in the partner run; keys are unique).
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort(const uint32_t* __restrict__ off,
+                                                            uint64_t* pairs, uint64_t* tmp, uint32_t cap,
+                                                            const uint32_t* __restrict__ long_list,
+                                                            const uint32_t* __restrict__ long_count)
+{
+    __shared__ uint64_t s[kSortCap];
+    const uint32_t count = *long_count;
+    for (uint32_t li = blockIdx.x; li < count; li += gridDim.x) {
+        const uint32_t t = long_list[li];
+        const uint32_t b = min(off[t], cap), e = min(off[t + 1], cap);
+        const uint32_t n = e - b;
+        if (n <= (uint32_t)kSortCap) {
+            smem_sort(pairs + b, n, s);
+            continue;
         }
+        for (uint32_t c = 0; c < n; c += kSortCap) smem_sort(pairs + b + c, min((uint32_t)kSortCap, n - c), s);
+        uint64_t* src = pairs + b;
+        uint64_t* dst = tmp + b;
+        for (uint32_t L = kSortCap; L < n; L <<= 1) {
+            for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
+                const uint32_t run = i / L, start = run * L, partner = run ^ 1u;
+                const uint64_t key = src[i];
+                const uint64_t ps64 = (uint64_t)partner * L;
+                if (ps64 >= n) { dst[i] = key; continue; }
+                const uint32_t ps = (uint32_t)ps64, pe = min(ps + L, n);
+                uint32_t lo = ps, hi = pe;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (src[mid] < key) lo = mid + 1; else hi = mid;
+                }
+                const uint32_t pair_start = min(run, partner) * L;
+                dst[pair_start + (i - start) + (lo - ps)] = key;
+            }
+            __syncthreads();
+            uint64_t* x = src; src = dst; dst = x;
+        }
+        if (src != pairs + b)
+            for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) pairs[b + i] = src[i];
         __syncthreads();
-        uint64_t* x = src; src = dst; dst = x;
     }
-    if (src != pairs + b)
-        for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) pairs[b + i] = src[i];
 }
 
 }  // namespace
@@ -285,7 +373,11 @@ cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st)
 cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
 {
     if (NT == 0) return cudaSuccess;
-    k_tile_sort<<<NT, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap);
+    // tile_fill is free once the pairs are scattered: it holds the long-list tiles
+    k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill,
+                                                   &w.dstatus[3]);
+    k_tile_sort<<<256, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
+                                              &w.dstatus[3]);
     return cudaGetLastError();
 }
 

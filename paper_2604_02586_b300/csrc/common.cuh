@@ -58,7 +58,8 @@ struct Work {
     uint64_t* pairs;       // [cap]
     uint64_t* pairs_tmp;   // [cap]
     uint32_t cap;
-    uint32_t* dstatus;     // [4]: 0 flags (bit 0 overflow), 1 K (low 32 bits), 2 K high
+    uint32_t* dstatus;     // [4]: 0 flags (bit 0 overflow), 1 K (low 32 bits), 2 K high,
+                           //      3 number of tiles whose lists need the long-list sort
     unsigned long long* stats;  // [4] raster work counters (collect_stats only)
 };
 

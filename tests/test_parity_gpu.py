@@ -92,6 +92,26 @@ def test_bins_bit_exact(gpu_ready, name):
     assert np.array_equal(g["pairs"], ent)
 
 
+@pytest.mark.parametrize("scale", [1.0, 0.3])
+def test_all_list_lengths_bin_bit_exact(gpu_ready, scale):
+    """Dense 512x512 scenes whose tile lists span every sort path: the one-warp
+    register sorts (2..1024 keys), the shared-memory sort (..4096) and the
+    run merge (longer)."""
+    s = synth.make_scene("tiny", 3, n=20000, views=2, width=512, height=512, focal=512.0)
+    s.means_opacity[:, :3] *= scale
+    g = P.run_gpu(s)
+    off, ent = oracle.bin_lists(s)
+    d = np.diff(off)
+    if scale == 1.0:
+        assert all(((d > a) & (d <= b)).any() for a, b in
+                   ((1, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 1024), (1024, 4096)))
+    else:
+        assert d.max() > 4096
+    assert int(g["counts"][0]) == len(ent) and int(g["counts"][3]) == 0
+    assert np.array_equal(g["tile_off"].astype(np.int64), off)
+    assert np.array_equal(g["pairs"], ent)
+
+
 def check_moments(o, g):
     om = P.oracle_moments_in_library_layout(o["moments"])
     gm = g["view_moments"].astype(np.float64)
