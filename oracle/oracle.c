@@ -564,7 +564,8 @@ int orc_bin(int n, int V, const float* means_opacity, const float* quats, const 
  *        1/255, T (1 - alpha) vs 1e-4) lay inside the FP32 window -- bookkeeping
  *        for comparisons with an FP32 implementation, not part of the method
  *  16    number of such pixels
- *  17    unused */
+ *  17    sum of w |d|^2 (d = the track's displacement) -- bookkeeping: the scale
+ *        of the displacement terms, for modelling FP32 rounding of the sums */
 #define NMOM 18
 
 typedef struct {
@@ -636,6 +637,7 @@ static void blend_view(int v, const binctx* B, const int64_t* offsets, const uin
                             M[10] += w * xp;     M[11] += w * yp;
                             if (stat) { M[12] += w; M[14] += 1.0; }
                             M[13] += 1.0;
+                            M[17] += w * ((double)ddx * ddx + (double)ddy * ddy);
                         }
                         T = Tn;
                     }

@@ -12,9 +12,10 @@ border pixels) that the FP64 oracle itself moves by more than the tolerance unde
 those perturbations.  ``sensitivity`` measures both: (1) the oracle re-run with
 tracks and opacities scaled by (1 + u), u ~ U(-1e-6, 1e-6); (2) the oracle's own
 moments, expressed in the library's layout (origin mu_2D clamped to the image,
-displacement about the track at that origin), perturbed as FP32 sums of a few
-hundred terms (relative 2^-20) and rounded to FP32, re-solved in FP64 and
-carried through the oracle's multi-view update.  A quantity is held to
+displacement about the track at that origin), each moved by 2^-21 of a bound on
+the sum of its terms' magnitudes (the FP32 summation error; three random draws)
+and rounded to FP32, re-solved in FP64 and carried through the oracle's
+multi-view update.  A quantity is held to
 its tolerance only where the oracle moved by less than half of it under both;
 the others are checked for validity only and counted.
 """
@@ -105,12 +106,18 @@ def _response(scene, orc, o2, ids):
                 angle=rot_angle(o2["out_quat"][ids], orc["out_quat"][ids]))
 
 
-def fp32_moment_rounding(scene, orc, ids, rel=2.0 ** -20, seed=7):
+def fp32_moment_rounding(scene, orc, ids, rel=2.0 ** -21, seed=7):
     """Oracle outputs when its per-view moments are FP32 sums in the library's
-    layout (see the module docstring): each sum is scaled by (1 + u),
-    u ~ U(-rel, rel) -- an FP32 sum of ~256 terms carries ~sqrt(256) units in
-    the last place, 2^-20 relative -- and rounded to FP32.  Needs per-view
-    oracle outputs."""
+    layout (see the module docstring).  The library forms each sum from 32-term
+    per-lane partial sums, one shuffle add and one atomic add per 8x8 block hit
+    (some 20), so it is off by about sqrt(52) units in the last place -- 2^-21 --
+    of the sum of the terms' magnitudes, which for sums of mixed sign (first
+    moments about the origin, displacement terms about the reference) is far
+    larger than 2^-21 of the sum itself.  Each sum therefore
+    moves by rel * u * m, u ~ U(-1, 1), with m a Cauchy-Schwarz bound on the
+    magnitude sum built from the second moments (sum w |x~|^2 from the moment
+    record, sum w |d - r|^2 from its bookkeeping slot), and is rounded to FP32.
+    Needs per-view oracle outputs."""
     M = orc["moments"]
     V, n = M.shape[:2]
     mu = orc["mean2d"]
@@ -136,9 +143,17 @@ def fp32_moment_rounding(scene, orc, ids, rel=2.0 ** -20, seed=7):
     S2o = S2 - out(S1, dl) - out(dl, S1) + sw_[..., None] * out(dl, dl)
     D1o = D1 - sw_ * r
     Dxo = Dx - out(dl, D1) - out(S1, r) + sw_[..., None] * out(dl, r)
+    # magnitude bounds: sum w |x~_i| <= sqrt(sw S2_ii), sum w |x~_i (d - r)_j| <= sqrt(S2_ii E2)
+    E2 = np.maximum(M[..., 17] - 2 * (r[..., 0] * (M[..., 10] - M[..., 2]) + r[..., 1] * (M[..., 11] - M[..., 4]))
+                    + sw * (r ** 2).sum(-1), 0.0)
+    s2d = np.maximum(np.stack([S2o[..., 0, 0], S2o[..., 1, 1]], -1), 0.0)
+    m_S1 = np.sqrt(sw_ * s2d)
+    m_S2 = np.sqrt(s2d[..., :, None] * s2d[..., None, :])
+    m_D1 = np.sqrt(sw_ * E2[..., None]) * np.ones(2)
+    m_Dx = np.sqrt(s2d[..., :, None] * E2[..., None, None]) * np.ones((2, 2))
     rng = np.random.default_rng(seed)
-    f = lambda a: (a * (1 + rel * rng.uniform(-1, 1, a.shape))).astype(np.float32).astype(np.float64)
-    sw2, S1o, S2o, D1o, Dxo = f(sw), f(S1o), f(S2o), f(D1o), f(Dxo)
+    f = lambda a, m: (a + rel * m * rng.uniform(-1, 1, a.shape)).astype(np.float32).astype(np.float64)
+    sw2, S1o, S2o, D1o, Dxo = f(sw, sw), f(S1o, m_S1), f(S2o, m_S2), f(D1o, m_D1), f(Dxo, m_Dx)
     sw2_ = sw2[..., None]
     S1b = S1o + sw2_ * dl
     S2b = S2o + out(S1o, dl) + out(dl, S1o) + sw2_[..., None] * out(dl, dl)
@@ -181,16 +196,22 @@ def sensitivity(scene, orc, sample=None, rel=1e-6):
     a = _response(scene, orc, o2, ids)
     if not per_view:
         return a
-    o3 = fp32_moment_rounding(scene, orc, ids)
-    b = _response(scene, orc, o3, ids)
+    # three draws of the rounding model: one random direction can miss a sensitive one
+    o3s = [fp32_moment_rounding(scene, orc, ids, seed=sd) for sd in (7, 8, 9)]
+    bs = [_response(scene, orc, o, ids) for o in o3s]
+    b = dict(status_stable=np.logical_and.reduce([x["status_stable"] for x in bs]),
+             pos=np.max([x["pos"] for x in bs], 0), scale=np.max([x["scale"] for x in bs], 0),
+             angle=np.max([x["angle"] for x in bs], 0))
+    o3 = o3s[0]
     out = dict(status_stable=a["status_stable"] & b["status_stable"],
                pos=np.maximum(a["pos"], b["pos"]), scale=np.maximum(a["scale"], b["scale"]),
                angle=np.maximum(a["angle"], b["angle"]))
     if sample is None:
         m1 = np.linalg.norm(o2["view_mean2d"] - orc["view_mean2d"], axis=-1)
-        m2 = np.linalg.norm(o3["view_mean2d"] - orc["view_mean2d"], axis=-1)
+        m2 = np.max([np.linalg.norm(o["view_mean2d"] - orc["view_mean2d"], axis=-1) for o in o3s], 0)
         out["mu"] = np.maximum(m1, m2)
-        out["view_flags_stable"] = (o2["view_flags"] == orc["view_flags"]) & (o3["view_flags"] == orc["view_flags"])
+        out["view_flags_stable"] = (o2["view_flags"] == orc["view_flags"]) & \
+            np.logical_and.reduce([o["view_flags"] == orc["view_flags"] for o in o3s])
     return out
 
 
@@ -243,7 +264,8 @@ def compare_outputs(scene, gpu, orc, ids=None):
         cov_rel[j] = np.linalg.norm(Cg - Co) / np.linalg.norm(Co)
     return dict(status_equal=float((sg == so).mean()), n=len(ids), status_equal_mask=(sg == so),
                 status_mismatch=ids[sg != so], both_pos=both_pos, both_cov=both_cov,
-                pos_err=pos_err / E, scale_rel=scale_rel, angle=ang, gap=gap, cov_rel=cov_rel)
+                pos_err=pos_err / E, scale_rel=scale_rel, angle=ang, gap=gap, cov_rel=cov_rel,
+                views=(orc["out_status"][ids] >> 16) & 0xFF)
 
 
 def summarize(cmp, sens=None, pos_tol=1e-4, scale_tol=1e-4, rot_tol=1e-3):
@@ -272,4 +294,19 @@ def summarize(cmp, sens=None, pos_tol=1e-4, scale_tol=1e-4, rot_tol=1e-3):
                 scale_fail=int((sr > 1e-4).sum()),
                 angle_max=float(an.max()) if an.size else 0.0, angle_fail=int((an > 1e-3).sum()),
                 cov_rel_max=float(cmp["cov_rel"][bc].max()) if bc.any() else 0.0,
-                n_both_pos=int(cmp["both_pos"].sum()), n_both_cov=int(bc.sum()))
+                n_both_pos=int(cmp["both_pos"].sum()), n_both_cov=int(bc.sum()),
+                worst=_worst(cmp, sens, bc & ok_scale, ok_gap, cmp["both_pos"] & ok_pos))
+
+
+def _worst(cmp, sens, m_scale, m_rot, m_pos, k=3):
+    """The k largest errors of each kind with their oracle sensitivity and the
+    number of views, for failure messages."""
+    out = {}
+    for name, err, m, key in (("scale", cmp["scale_rel"], m_scale, "scale"),
+                              ("angle", cmp["angle"], m_rot, "angle"),
+                              ("pos", cmp["pos_err"], m_pos, "pos")):
+        idx = np.flatnonzero(m)
+        idx = idx[np.argsort(err[idx])[::-1][:k]]
+        out[name] = [(int(i), float(err[i]), float(sens[key][i]) if sens is not None else None,
+                      int(cmp["views"][i])) for i in idx]
+    return out
