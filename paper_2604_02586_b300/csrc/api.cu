@@ -29,7 +29,7 @@ struct tsp_context {
     // per (view, Gaussian)
     Buf rect, depth, touched, geom0, geom1, dref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
-    Buf tiles, tile_off;
+    Buf tiles, tile_off, span_sum;
     // pairs
     Buf pairs, pairs_tmp;
     uint64_t want_pairs = 0;
@@ -258,8 +258,9 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
         if ((s = ensure(ctx, ctx->vres2, vn1 * 8))) return s;
         if ((s = ensure(ctx, ctx->vres3, vn1 * 16))) return s;
     }
-    if ((s = ensure(ctx, ctx->tiles, (size_t)2 * (NT + 1) * 4))) return s;
+    if ((s = ensure(ctx, ctx->tiles, (size_t)2 * (NT + 1) * kCounterStride * 4))) return s;
     if ((s = ensure(ctx, ctx->tile_off, (size_t)(NT + 1) * 4))) return s;
+    if ((s = ensure(ctx, ctx->span_sum, ((size_t)NT / 1024 + 2) * 8))) return s;
     uint64_t cap = ctx->want_pairs;
     if (cap == 0) cap = ctx->opt.pair_capacity > 0 ? (uint64_t)ctx->opt.pair_capacity : (uint64_t)8 * vn;
     if (cap < (1u << 16)) cap = 1u << 16;
@@ -282,8 +283,9 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
     w.vres2 = (uint2*)ctx->vres2.p;
     w.vres3 = (float4*)ctx->vres3.p;
     w.tile_count = (uint32_t*)ctx->tiles.p;
-    w.tile_fill = (uint32_t*)ctx->tiles.p + (NT + 1);
+    w.tile_fill = (uint32_t*)ctx->tiles.p + (size_t)(NT + 1) * kCounterStride;
     w.tile_off = (uint32_t*)ctx->tile_off.p;
+    w.span_sum = (unsigned long long*)ctx->span_sum.p;
     w.pairs = (uint64_t*)ctx->pairs.p;
     w.pairs_tmp = (uint64_t*)ctx->pairs_tmp.p;
     const uint64_t have = ctx->pairs.bytes / 8 < ctx->pairs_tmp.bytes / 8 ? ctx->pairs.bytes / 8 : ctx->pairs_tmp.bytes / 8;
@@ -302,7 +304,7 @@ tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const tsp_gaussians* g
                      int sh_degree, int mode, uint32_t NT, Work& w, cudaStream_t st)
 {
     TSP_CUDA(mark(ctx, 0, st));
-    TSP_CUDA(cudaMemsetAsync(ctx->tiles.p, 0, (size_t)2 * (NT + 1) * 4, st));
+    TSP_CUDA(cudaMemsetAsync(ctx->tiles.p, 0, (size_t)2 * (NT + 1) * kCounterStride * 4, st));
     TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 16, st));
     if (ctx->opt.collect_stats) TSP_CUDA(cudaMemsetAsync(w.stats, 0, 32, st));
     TSP_CUDA(launch_preprocess(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
@@ -463,7 +465,7 @@ tsp_status tsp_destroy(tsp_context* ctx)
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->color,
-                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum,
                   &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
                   &ctx->st_tracks};
     for (Buf* b : all) release(ctx, *b);

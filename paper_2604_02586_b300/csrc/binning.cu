@@ -108,84 +108,137 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
     const int tx_n = vs.tiles_x[v];
     for (int ty = p.y0; ty < p.y1; ++ty)
         for (int tx = p.x0; tx < p.x1; ++tx)
-            atomicAdd(&w.tile_count[base + (uint32_t)(ty * tx_n + tx)], 1u);
+            atomicAdd(&w.tile_count[(size_t)(base + (uint32_t)(ty * tx_n + tx)) * kCounterStride], 1u);
 }
 
-// Single-CTA exclusive scan of NT counts, in chunks of 4096 (1024 threads x 4
-// consecutive counts, coalesced) carrying the running total; writes NT+1
-// offsets and K.
-__global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ off,
-                                               uint32_t NT, uint32_t cap, uint32_t* dstatus)
+// Exclusive scan of the NT strided tile counts in three launches: (1) each CTA
+// sums a span of kScanSpan tiles (4 independent loads per thread), (2) one CTA
+// scans the span sums and writes K and off[NT], (3) each CTA scans its span again
+// and adds the span's prefix.
+constexpr int kScanThreads = 256;
+constexpr int kScanSpan = 4 * kScanThreads;
+
+// Block-wide inclusive scan of one 64-bit value per thread; returns the inclusive
+// prefix and leaves the block total in *total.
+__device__ __forceinline__ unsigned long long block_scan_incl(unsigned long long x,
+                                                              unsigned long long* warp_tot,
+                                                              unsigned long long* total)
 {
-    __shared__ unsigned long long warp_tot[32];
-    __shared__ unsigned long long carry_s;
-    const uint32_t tid = threadIdx.x;
-    const int lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) carry_s = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < NT; base += 4096) {
-        const uint32_t i0 = base + 4 * tid;
-        uint32_t c[4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c[k] = (i0 + k < NT) ? cnt[i0 + k] : 0u;
-        const unsigned long long sum = (unsigned long long)c[0] + c[1] + c[2] + c[3];
-        unsigned long long x = sum;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long q = lane < nw ? warp_tot[lane] : 0ull;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, q, d);
+            if (lane >= d) q += y;
         }
-        if (lane == 31) warp_tot[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            unsigned long long t = warp_tot[lane];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, d);
-                if (lane >= d) t += y;
-            }
-            warp_tot[lane] = t;
-        }
-        __syncthreads();
-        const unsigned long long carry = carry_s;
-        unsigned long long run = carry + x - sum + (wid > 0 ? warp_tot[wid - 1] : 0ull);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (i0 + k < NT) {
-                off[i0 + k] = (uint32_t)min(run, 0xffffffffull);
-                run += c[k];
-            }
-        __syncthreads();
-        if (tid == 0) carry_s = carry + warp_tot[31];
-        __syncthreads();
+        if (lane < nw) warp_tot[lane] = q;
     }
-    if (tid == 0) {
-        const unsigned long long K = carry_s;
-        off[NT] = (uint32_t)min(K, 0xffffffffull);
-        dstatus[1] = (uint32_t)(K & 0xffffffffull);
-        dstatus[2] = (uint32_t)(K >> 32);
-        if (K > cap) atomicOr(&dstatus[0], kStatusOverflow);
+    __syncthreads();
+    const unsigned long long r = x + (wid > 0 ? warp_tot[wid - 1] : 0ull);
+    *total = warp_tot[nw - 1];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void load_counts4(const uint32_t* __restrict__ cnt, uint32_t NT, uint32_t i0,
+                                             uint32_t (&c)[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = (i0 + k < NT) ? cnt[(size_t)(i0 + k) * kCounterStride] : 0u;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t NT,
+                                                              unsigned long long* __restrict__ span_sum)
+{
+    __shared__ unsigned long long warp_tot[32];
+    uint32_t c[4];
+    load_counts4(cnt, NT, blockIdx.x * kScanSpan + 4 * threadIdx.x, c);
+    unsigned long long tot;
+    block_scan_incl((unsigned long long)c[0] + c[1] + c[2] + c[3], warp_tot, &tot);
+    if (threadIdx.x == 0) span_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_spans(unsigned long long* __restrict__ span_sum, uint32_t nspan,
+                                                     uint32_t* __restrict__ off, uint32_t NT, uint32_t cap,
+                                                     uint32_t* dstatus)
+{
+    __shared__ unsigned long long warp_tot[32];
+    unsigned long long carry = 0;
+    for (uint32_t b = 0; b < nspan; b += 1024) {
+        const uint32_t i = b + threadIdx.x;
+        const unsigned long long x = i < nspan ? span_sum[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long incl = block_scan_incl(x, warp_tot, &tot);
+        if (i < nspan) span_sum[i] = carry + incl - x;            // exclusive prefix
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        off[NT] = (uint32_t)min(carry, 0xffffffffull);
+        dstatus[1] = (uint32_t)(carry & 0xffffffffull);
+        dstatus[2] = (uint32_t)(carry >> 32);
+        if (carry > cap) atomicOr(&dstatus[0], kStatusOverflow);
     }
 }
 
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ cnt, uint32_t NT,
+                                                            const unsigned long long* __restrict__ span_pre,
+                                                            uint32_t* __restrict__ off)
+{
+    __shared__ unsigned long long warp_tot[32];
+    const uint32_t i0 = blockIdx.x * kScanSpan + 4 * threadIdx.x;
+    uint32_t c[4];
+    load_counts4(cnt, NT, i0, c);
+    const unsigned long long sum = (unsigned long long)c[0] + c[1] + c[2] + c[3];
+    unsigned long long tot;
+    unsigned long long run = block_scan_incl(sum, warp_tot, &tot) - sum + span_pre[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (i0 + k < NT) {
+            off[i0 + k] = (uint32_t)min(run, 0xffffffffull);
+            run += c[k];
+        }
+}
+
+// Up to 8 tiles of a record are handled per round: their slot atomics are all
+// issued before any result is used, so a record waits about one atomic round
+// trip per 8 tiles rather than one per tile.
 __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
 {
+    constexpr int kIlp = 8;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     if (g >= vs.n) return;
     const size_t i = (size_t)v * vs.n + g;
-    if (w.touched[i] == 0u) return;
+    const uint32_t cnt = w.touched[i];
+    if (cnt == 0u) return;
     const short4 r = w.rect[i];
     const uint64_t e = ((uint64_t)w.depth[i] << 32) | (uint32_t)g;
     const uint32_t base = vs.toff[v];
     const int tx_n = vs.tiles_x[v];
-    for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx = r.x; tx < r.z; ++tx) {
-            const uint32_t t = base + (uint32_t)(ty * tx_n + tx);
-            const uint32_t slot = atomicAdd(&w.tile_fill[t], 1u);
-            const uint64_t pos = (uint64_t)w.tile_off[t] + slot;
-            if (pos < w.cap) w.pairs[pos] = e;
+    int tx = r.x, ty = r.y;
+    for (uint32_t k0 = 0; k0 < cnt; k0 += kIlp) {
+        uint32_t t[kIlp], slot[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            t[u] = base + (uint32_t)(ty * tx_n + tx);
+            if (k0 + u < cnt) slot[u] = atomicAdd(&w.tile_fill[(size_t)t[u] * kCounterStride], 1u);
+            if (++tx == r.z) { tx = r.x; ++ty; }
         }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u)
+            if (k0 + u < cnt) {
+                const uint64_t pos = (uint64_t)w.tile_off[t[u]] + slot[u];
+                if (pos < w.cap) w.pairs[pos] = e;
+            }
+    }
 }
 
 constexpr int kSortCap = 4096;      // entries sorted in shared memory at once
@@ -358,7 +411,10 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4*
 
 cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(w.tile_count, w.tile_off, NT, w.cap, w.dstatus);
+    const uint32_t nspan = (NT + kScanSpan - 1) / kScanSpan;
+    if (nspan > 0) k_scan_reduce<<<nspan, kScanThreads, 0, st>>>(w.tile_count, NT, w.span_sum);
+    k_scan_spans<<<1, 1024, 0, st>>>(w.span_sum, nspan, w.tile_off, NT, w.cap, w.dstatus);
+    if (nspan > 0) k_scan_down<<<nspan, kScanThreads, 0, st>>>(w.tile_count, NT, w.span_sum, w.tile_off);
     return cudaGetLastError();
 }
 

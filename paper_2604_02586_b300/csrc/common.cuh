@@ -10,6 +10,9 @@ namespace tsp {
 
 constexpr int kTile = 16;                 // raster tile edge (pixels)
 constexpr int kTilePx = kTile * kTile;    // threads per raster CTA
+// Per-tile atomic counters sit 128 bytes apart: one L2 line (one slice) each, so
+// the atomics of neighbouring hot tiles do not queue behind one another.
+constexpr int kCounterStride = 32;
 constexpr int kMaxViews = TSP_MAX_VIEWS;
 
 struct DevCam {
@@ -52,8 +55,8 @@ struct Work {
     float4* vres1;         // [V*n] B00, B01, B02, sum w   (Sigma_2D' = B B^T, B = A V)
     float4* vres3;         // [V*n] B10, B11, B12, 0
     uint2* vres2;          // [V*n] view flags, pixels
-    uint32_t* tile_count;  // [NT]
-    uint32_t* tile_fill;   // [NT]
+    uint32_t* tile_count;  // [NT * kCounterStride], tile t at t * kCounterStride
+    uint32_t* tile_fill;   // [NT * kCounterStride] likewise; after the scatter: long-list tiles
     uint32_t* tile_off;    // [NT+1]
     uint64_t* pairs;       // [cap]
     uint64_t* pairs_tmp;   // [cap]
@@ -61,6 +64,7 @@ struct Work {
     uint32_t* dstatus;     // [4]: 0 flags (bit 0 overflow), 1 K (low 32 bits), 2 K high,
                            //      3 number of tiles whose lists need the long-list sort
     unsigned long long* stats;  // [4] raster work counters (collect_stats only)
+    unsigned long long* span_sum; // [ceil(NT / 1024)] tile-count scan scratch
 };
 
 struct FitParams {
