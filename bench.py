@@ -147,9 +147,30 @@ def raster_traffic():
     return t.get("bytes_per_launch_full")
 
 
+def rank_seed(rank):
+    """Each rank solves its own frame pair: a scene drawn from its own seed."""
+    return 2 + 1000 * rank
+
+
 def make_scene(a, rank):
     import synth
-    return synth.make_scene("capture", seed=2 + 1000 * rank, n=a.n, views=a.views)
+    return synth.make_scene("capture", seed=rank_seed(rank), n=a.n, views=a.views)
+
+
+def reduce_max(x, world, device):
+    """The largest of the ranks' values (the job takes as long as its slowest rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, steps, total_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world * steps / (total_ms / 1e3)
 
 
 def cpu_baseline(scene, max_views=8):
@@ -248,12 +269,8 @@ def run_ours(a):
     ctx.sync()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = units * world * a.steps / (total_ms / 1e3)
+    total_ms = reduce_max(float(np.sum(step_ms)), world, dev)
+    value = job_value(units, world, a.steps, total_ms)
 
     # end to end through the host-buffer entry point (pinned inputs and outputs)
     e2e = None
@@ -294,6 +311,13 @@ def run_ours(a):
     achieved = flops / t_r / 1e12
     peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
     stage_mean = {k: float(np.mean([x[k] for x in stages])) for k in stages[0]}
+    # whole step against HBM: the bytes the method must move per frame pair --
+    # tracks and visibility, Gaussians in, results out, each pair written and read
+    b_alg = (sum(int(d.nbytes) + int(v.nbytes) for d, v in zip(scene.disp, scene.vis))
+             + 48 * scene.n + 52 * scene.n + 2 * 12 * K)
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    hbm_step = {"bytes": b_alg, "achieved_gbs": b_alg / (total_ms / a.steps / 1e3) / 1e9,
+                "peak_gbs": hbm, "frac": b_alg / (total_ms / a.steps / 1e3) / 1e9 / hbm}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
@@ -302,11 +326,12 @@ def run_ours(a):
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": raster_traffic(),
-                     "kernel": "k_raster_accumulate",
+                     "kernel": "k_raster_accumulate_2p",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit counts)",
                      "work": {"evaluations": n_eval, "blended": n_blend, "moment_adds": n_add,
                               "list_entries": n_list, "pairs_K": K},
                      "kernel_ms": t_r * 1e3},
+        "hbm_step": hbm_step,
         "stage_ms": stage_mean,
         "gpu_launches": KERNELS_PER_STEP * a.steps,
         "clocks": clk.summary(),
