@@ -29,6 +29,15 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
+// 2^x by the SFU's approximate exponential (flush-to-zero; |rel. error| ~ 2^-22).
+// x <= 0 here, and a result below 2^-126 (alpha < 1/255 by far) flushes to 0.
+__device__ __forceinline__ float sfu_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Blend record with its mean moved from the Gaussian's rectangle corner to this
 // tile's corner (an exact integer shift, so the staged mean keeps its precision).
 __device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty)
@@ -330,7 +339,7 @@ constexpr int kWHalf = 32 * kWRow + 16;
 constexpr int kWWords = kWHalf + 32 * kWRow;
 
 template <bool kStats>
-__global__ void __launch_bounds__(128, 6) k_raster_accumulate_2p(const ViewSet vs, const Work w)
+__global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w)
 {
     constexpr int kNW = 4;
     __shared__ float4 s_g0[kNW][32];
@@ -424,11 +433,13 @@ __global__ void __launch_bounds__(128, 6) k_raster_accumulate_2p(const ViewSet v
         __syncwarp();
     };
 
+    uint32_t g_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
     for (uint32_t b0 = beg; b0 < end; b0 += 32) {
         if (!__any_sync(kFull, !done[0] || !done[1])) break;
         bool hit = false;
+        const uint32_t g = g_next;
+        if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
         if (b0 + lane < end) {
-            const uint32_t g = (uint32_t)w.pairs[b0 + lane];
             const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
             const float4 g1 = w.geom1[vbase + g];
             const float4 bb = footprint_box(g0, g1);
@@ -451,14 +462,18 @@ __global__ void __launch_bounds__(128, 6) k_raster_accumulate_2p(const ViewSet v
             m &= m - 1;
             const float4 g0 = s_g0[warp][j];
             const float4 g1 = s_g1[warp][j];
+            // both pixels of a lane share the column: ex, z1; the second row is 4 below
+            const float ex = xc - g0.x;
+            const float z1 = ex * g0.z;
+            const float z1s = z1 * z1;
+            float z2[2];
+            z2[0] = fmaf(-g0.w, ex, yc[0] - g0.y) * g1.x;
+            z2[1] = fmaf(4.0f, g1.x, z2[0]);
             bool add[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const float ex = xc - g0.x, ey = yc[k] - g0.y;
-                const float z1 = ex * g0.z;
-                const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
-                const float pw = fmaf(z2, z2, z1 * z1);
-                const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+                const float pw = fmaf(z2[k], z2[k], z1s);
+                const float alpha = fminf(kAlphaMax, g1.y * sfu_exp2(-pw));
                 const bool pass = !done[k] && alpha >= kAlphaMin;
                 const float Tn = T[k] * (1.0f - alpha);
                 const bool term = pass && Tn < kTMin;

@@ -147,13 +147,16 @@ def test_moments(gpu_ready, name):
 @pytest.mark.parametrize("name", ["tiny", "capture_sub"])
 def test_raster_variants(gpu_ready, name, variant):
     """The warp-shuffle raster kernels (8x4, 8x8 and 8x16 warp blocks) meet the
-    same bar as the default two-phase one: the summation order differs, the
-    blend decisions and pixel counts do not."""
+    same bar as the default two-phase one.  Their summation order and exponential
+    differ, so pixel counts may differ only by blend decisions that the oracle
+    records as lying inside the FP32 window (each side within that count of it)."""
     s, g2, o, sens = case(name)
     g = P.run_gpu(s, raster_variant=variant)
     check_moments(o, g)
     assert np.array_equal(g["pairs"], g2["pairs"])
-    assert np.array_equal(g["view_moments"][..., 13:15], g2["view_moments"][..., 13:15])
+    pc = o["moments"][..., 16]
+    assert np.all(np.abs(g["view_moments"][..., 13:15].astype(np.float64)
+                         - g2["view_moments"][..., 13:15]) <= 2 * pc[..., None])
     check_fitted(s, g, o, sens)
 
 
