@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian·view track fits/s at 200k Gaussians×18 views; p50/p99 frame latency"
 UNIT = "fits/s"
-KERNELS_PER_STEP = 10         # project, scan (3), emit, tile sort (2), raster, view solve, multi-view
+KERNELS_PER_STEP = 11         # project, scan (3), emit, tile sort (2), reference gather, raster, view solve, multi-view
 RASTER_SRC = os.path.join(ROOT, "paper_2604_02586_b300", "csrc", "raster.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "raster_accumulate_traffic.json")
 

@@ -167,10 +167,13 @@ tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_ca
                           void* stream);
 
 /* Same step for callers that hold everything in host memory: g, tracks and out
- * point to host arrays (pinned memory gives full copy speed).  Inputs are copied
- * to context-owned device buffers, the step runs, results are copied back and the
- * call returns after the stream has finished.  Errors as tsp_fit_motion, plus
- * OVERFLOW if the pair buffer overflowed. */
+ * point to host arrays (pinned memory gives full copy speed and lets the copies
+ * overlap the computation).  The Gaussians are copied on `stream` and projected,
+ * binned and sorted while the tracks are copied on a context-owned stream in
+ * about six view groups; each group's raster starts once its tracks have landed.
+ * Results are copied back and the call returns after both streams have finished
+ * with the caller's buffers.  Errors as tsp_fit_motion, plus OVERFLOW if the pair
+ * buffer overflowed. */
 tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams,
                                int num_views, const tsp_view_tracks* tracks,
                                const tsp_result* out, void* stream);

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libtsplat.so (include/tsplat.h): argument checks,
 // workspace management and the order of the pipeline steps.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -27,7 +28,7 @@ struct tsp_context {
     std::string err;
     size_t held = 0;
     // per (view, Gaussian)
-    Buf rect, depth, touched, geom0, geom1, dref, color, moments, vres0, vres1, vres2, vres3;
+    Buf rect, depth, touched, geom0, geom1, dref, oref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
     Buf tiles, tile_off, span_sum;
     // pairs
@@ -37,8 +38,11 @@ struct tsp_context {
     uint32_t* h_status = nullptr;   // pinned, 4 words
     cudaEvent_t ev[8] = {};         // stage boundaries (stage_timing)
     bool timed = false;             // the last call recorded ev[]
-    // staging for tsp_fit_motion_host
+    // staging for tsp_fit_motion_host: tracks stream in on copy_stream, one event
+    // per view group, while the Gaussians are binned on the caller's stream
     Buf st_in, st_out, st_tracks;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t group_ev[32] = {};
     // last call
     int last_V = 0, last_n = 0;
     uint32_t last_NT = 0;
@@ -249,6 +253,7 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
     if ((s = ensure(ctx, ctx->geom0, vn1 * 16))) return s;
     if ((s = ensure(ctx, ctx->geom1, vn1 * 16))) return s;
     if ((s = ensure(ctx, ctx->dref, vn1 * 8))) return s;
+    if (!render && (s = ensure(ctx, ctx->oref, vn1 * 4))) return s;
     if (render) {
         if ((s = ensure(ctx, ctx->color, vn1 * 16))) return s;
     } else {
@@ -276,6 +281,7 @@ tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render,
     w.geom0 = (float4*)ctx->geom0.p;
     w.geom1 = (float4*)ctx->geom1.p;
     w.dref = (float2*)ctx->dref.p;
+    w.oref = (uint32_t*)ctx->oref.p;
     w.color = (float4*)ctx->color.p;
     w.moments = (float4*)ctx->moments.p;
     w.vres0 = (float4*)ctx->vres0.p;
@@ -336,8 +342,14 @@ tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const tsp_gaussians* g
     return TSP_OK;
 }
 
+// The whole path a1-a9 on device buffers.  With ready != nullptr the tracks of
+// views [k*group, (k+1)*group) are still being copied and ready[k] is recorded on
+// the copy stream once they have landed: the tracks-free steps (projection,
+// binning, sorting) run first, then each view group's reference gather and raster
+// wait for their own copy.
 tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams, int V,
-                      const tsp_view_tracks* tracks, const tsp_result* out, cudaStream_t st, bool check_ptrs)
+                      const tsp_view_tracks* tracks, const tsp_result* out, cudaStream_t st, bool check_ptrs,
+                      int group = 0, const cudaEvent_t* ready = nullptr)
 {
     tsp_status s;
     if ((s = check_gaussians(ctx, g, check_ptrs))) return s;
@@ -369,8 +381,14 @@ tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera
     const FitParams fp = fit_params(ctx->opt);
     ctx->timed = false;
     if ((s = bin_front(ctx, vs, g, nullptr, 0, 0, NT, w, st))) return s;
-    TSP_CUDA(launch_raster_accumulate(vs, w, NT, ctx->opt.collect_stats != 0,
-                                      ctx->opt.raster_variant, st));
+    if (group <= 0) group = V;
+    for (int v0 = 0, k = 0; v0 < V; v0 += group, ++k) {
+        const int v1 = std::min(V, v0 + group);
+        if (ready) TSP_CUDA(cudaStreamWaitEvent(st, ready[k], 0));
+        TSP_CUDA(launch_dref(vs, w, v0, v1, st));
+        TSP_CUDA(launch_raster_accumulate(vs, w, vs.toff[v0], vs.toff[v1] - vs.toff[v0],
+                                          ctx->opt.collect_stats != 0, ctx->opt.raster_variant, st));
+    }
     TSP_CUDA(mark(ctx, 5, st));
     TSP_CUDA(launch_view_solve(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
                                (const float4*)g->scales, fp, w, out->view_affine, out->view_flags, st));
@@ -464,13 +482,16 @@ tsp_status tsp_destroy(tsp_context* ctx)
     if (!ctx) return TSP_OK;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->color,
+    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->oref, &ctx->color,
                   &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum,
                   &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
                   &ctx->st_tracks};
     for (Buf* b : all) release(ctx, *b);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->group_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
     return TSP_OK;
@@ -515,21 +536,47 @@ tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const t
     tsp_result dr{(float*)ob, (float*)(ob + align_up(gb)), (float*)(ob + 2 * align_up(gb)),
                   (uint32_t*)(ob + 3 * align_up(gb)), nullptr, nullptr, nullptr};
     std::vector<tsp_view_tracks> dt(V > 0 ? V : 1);
+    // views per copy group: about six groups, so the first raster starts after
+    // one sixth of the track bytes and the copies hide the binning and rasters
+    const int group = V > 0 ? (V + 5) / 6 : 1;
+    if (n > 0 && V > 0) {
+        if (!ctx->copy_stream &&
+            cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->copy_stream = nullptr;
+            return fail(ctx, TSP_ERR_CUDA, "cannot create the copy stream");
+        }
+        for (int k = 0; k * group < V; ++k)
+            if (!ctx->group_ev[k] && cudaEventCreateWithFlags(&ctx->group_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->group_ev[k] = nullptr;
+                return fail(ctx, TSP_ERR_CUDA, "cannot create a copy event");
+            }
+        for (int v = 0; v < V; ++v)
+            if (!tracks[v].disp || !tracks[v].vis)
+                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": track pointer is NULL");
+    }
     if (n > 0) {
         TSP_CUDA(cudaMemcpyAsync((void*)dg_.means_opacity, g->means_opacity, gb, cudaMemcpyHostToDevice, st));
         TSP_CUDA(cudaMemcpyAsync((void*)dg_.quats, g->quats, gb, cudaMemcpyHostToDevice, st));
         TSP_CUDA(cudaMemcpyAsync((void*)dg_.scales, g->scales, gb, cudaMemcpyHostToDevice, st));
         for (int v = 0; v < V; ++v) {
-            if (!tracks[v].disp || !tracks[v].vis)
-                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": track pointer is NULL");
             const size_t px = (size_t)cams[v].width * cams[v].height;
             dt[v].disp = (const float*)(tb + toff[v]);
             dt[v].vis = (const uint8_t*)(tb + toff[v] + align_up(px * 8));
-            TSP_CUDA(cudaMemcpyAsync((void*)dt[v].disp, tracks[v].disp, px * 8, cudaMemcpyHostToDevice, st));
-            TSP_CUDA(cudaMemcpyAsync((void*)dt[v].vis, tracks[v].vis, px, cudaMemcpyHostToDevice, st));
+            TSP_CUDA(cudaMemcpyAsync((void*)dt[v].disp, tracks[v].disp, px * 8, cudaMemcpyHostToDevice,
+                                     ctx->copy_stream));
+            TSP_CUDA(cudaMemcpyAsync((void*)dt[v].vis, tracks[v].vis, px, cudaMemcpyHostToDevice, ctx->copy_stream));
+            if ((v + 1) % group == 0 || v + 1 == V)
+                TSP_CUDA(cudaEventRecord(ctx->group_ev[v / group], ctx->copy_stream));
         }
     }
-    if ((s = fit_device(ctx, &dg_, cams, V, dt.data(), &dr, st, false))) return s;
+    if ((s = fit_device(ctx, &dg_, cams, V, dt.data(), &dr, st, false, group,
+                        n > 0 && V > 0 ? ctx->group_ev : nullptr))) {
+        // the caller may release its host buffers once we return: finish reading them
+        if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+        return s;
+    }
     if (n > 0) {
         TSP_CUDA(cudaMemcpyAsync(out->means, dr.means, gb, cudaMemcpyDeviceToHost, st));
         TSP_CUDA(cudaMemcpyAsync(out->quats, dr.quats, gb, cudaMemcpyDeviceToHost, st));

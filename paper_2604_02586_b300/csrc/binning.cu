@@ -85,11 +85,11 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
     const float2 dlt = moment_origin_shift(ux, uy, vs.cam[v].W, vs.cam[v].H);
     w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);
     if (mode == 0) {
-        // reference displacement: the track at the pixel holding the moment origin
+        // the pixel holding the moment origin; k_dref reads the track there
         const int W = vs.cam[v].W, H = vs.cam[v].H;
         const int ox = min(max((int)floorf(ux.x + ux.y + dlt.x), 0), W - 1);
         const int oy = min(max((int)floorf(uy.x + uy.y + dlt.y), 0), H - 1);
-        w.dref[i] = vs.disp[v][(size_t)oy * W + ox];
+        w.oref[i] = (uint32_t)oy * (uint32_t)W + (uint32_t)ox;
     }
     if (mode == 1) {
         const DevCam& c = vs.cam[v];
@@ -109,6 +109,19 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
     for (int ty = p.y0; ty < p.y1; ++ty)
         for (int tx = p.x0; tx < p.x1; ++tx)
             atomicAdd(&w.tile_count[(size_t)(base + (uint32_t)(ty * tx_n + tx)) * kCounterStride], 1u);
+}
+
+// Reference displacement of every (view, Gaussian) record of views v0.. (grid.y
+// views): the track at the pixel holding the moment origin.  Separate from the
+// preprocess so that tracks may still be in flight while the tiles are binned.
+__global__ void __launch_bounds__(256) k_dref(const ViewSet vs, Work w, int v0)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = v0 + (int)blockIdx.y;
+    if (g >= vs.n) return;
+    const size_t i = (size_t)v * vs.n + g;
+    if (w.touched[i] == 0u) return;
+    w.dref[i] = vs.disp[v][w.oref[i]];
 }
 
 // Exclusive scan of the NT strided tile counts in three launches: (1) each CTA
@@ -406,6 +419,14 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4*
         k_preprocess<0><<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, w);
     else
         k_preprocess<1><<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dref(const ViewSet& vs, const Work& w, int v0, int v1, cudaStream_t st)
+{
+    if (vs.n == 0 || v1 <= v0) return cudaSuccess;
+    dim3 grid((vs.n + 255) / 256, v1 - v0);
+    k_dref<<<grid, 256, 0, st>>>(vs, w, v0);
     return cudaGetLastError();
 }
 

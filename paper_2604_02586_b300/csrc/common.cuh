@@ -49,6 +49,7 @@ struct Work {
     float4* geom0;         // [V*n] mu - rect origin (x, y), i11, k  (blend factor form)
     float4* geom1;         // [V*n] i22, opacity, moment origin - mu (x, y)
     float2* dref;          // [V*n] reference displacement (track at the moment origin)
+    uint32_t* oref;        // [V*n] pixel index of the moment origin (fit mode)
     float4* color;         // [V*n] render colour
     float4* moments;       // [V*n*4] 16 floats per (view, Gaussian)
     float4* vres0;         // [V*n] mu'_x, mu'_y, shift c_x, c_y

@@ -10,15 +10,19 @@ namespace tsp {
 cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
                               const float* sh, int sh_degree, int mode, const Work& w,
                               cudaStream_t st);
+// a1 (fit mode): reference displacement of views [v0, v1) -- the track at each
+// record's moment origin.  Needs those views' tracks; the other steps of a1-a4 do not.
+cudaError_t launch_dref(const ViewSet& vs, const Work& w, int v0, int v1, cudaStream_t st);
 // a2: exclusive scan of the per-tile counts -> tile offsets and the pair count K.
 cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st);
 // a2: emit (depth << 32 | g) into each touched tile's slice.
 cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st);
 // a3: sort each tile's slice ascending (depth, then Gaussian index).
 cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st);
-// a5: blend and accumulate alpha T weighted track moments per (view, Gaussian).
-cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
-                                     int variant, cudaStream_t st);
+// a5: blend and accumulate alpha T weighted track moments per (view, Gaussian), for
+// the ntiles tiles starting at tile_base (tiles are numbered view by view).
+cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t tile_base, uint32_t ntiles,
+                                     bool stats, int variant, cudaStream_t st);
 // render colour and final transmittance.
 cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
                                  float* const* final_T, cudaStream_t st);

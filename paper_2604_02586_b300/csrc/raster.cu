@@ -113,7 +113,8 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
 // its block; the warp walks only that set, in list order.  A Gaussian's sums over
 // the warp's pixels are folded once per (warp, Gaussian) hit.
 template <int P, bool kStats>
-__global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet vs, const Work w)
+__global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet vs, const Work w,
+                                                                       uint32_t tile_base)
 {
     constexpr int kThreads = kTilePx / P;
     constexpr int kNW = kThreads / 32;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
     __shared__ uint32_t s_mask[kNW][2];
     __shared__ __align__(16) float s_part[kBatch][kNW][16];
 
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = tile_base + blockIdx.x;
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     if (beg >= end) return;
     int v, tx, ty;
@@ -339,7 +340,8 @@ constexpr int kWHalf = 32 * kWRow + 16;
 constexpr int kWWords = kWHalf + 32 * kWRow;
 
 template <bool kStats>
-__global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w)
+__global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w,
+                                                                          uint32_t tile_base)
 {
     constexpr int kNW = 4;
     __shared__ float4 s_g0[kNW][32];
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
     __shared__ float s_W[kNW][kWWords];
     __shared__ float4 s_F[kNW][2][33];      // (d_x, d_y, static, 0) per pixel, halves padded
 
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = tile_base + blockIdx.x;
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     if (beg >= end) return;
     int v, tx, ty;
@@ -574,25 +576,26 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
 
 }  // namespace
 
-cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t NT, bool stats,
-                                     int variant, cudaStream_t st)
+cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t tile_base, uint32_t ntiles,
+                                     bool stats, int variant, cudaStream_t st)
 {
-    if (NT == 0 || vs.n == 0) return cudaSuccess;
+    if (ntiles == 0 || vs.n == 0) return cudaSuccess;
+    const uint32_t NT = ntiles, tb = tile_base;
     if (variant == 0) {
-        // six 28.5 KB CTAs per SM need the largest shared-memory carveout
+        // seven 28.5 KB CTAs per SM need the largest shared-memory carveout
         auto kern = stats ? k_raster_accumulate_2p<true> : k_raster_accumulate_2p<false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        kern<<<NT, 128, 0, st>>>(vs, w);
+        kern<<<NT, 128, 0, st>>>(vs, w, tb);
     } else if (variant == 1) {
-        if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w);
-        else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w);
+        if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w, tb);
+        else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w, tb);
     } else if (variant == 4) {
-        if (stats) k_raster_accumulate<4, true><<<NT, kTilePx / 4, 0, st>>>(vs, w);
-        else k_raster_accumulate<4, false><<<NT, kTilePx / 4, 0, st>>>(vs, w);
+        if (stats) k_raster_accumulate<4, true><<<NT, kTilePx / 4, 0, st>>>(vs, w, tb);
+        else k_raster_accumulate<4, false><<<NT, kTilePx / 4, 0, st>>>(vs, w, tb);
     } else {
-        if (stats) k_raster_accumulate<2, true><<<NT, kTilePx / 2, 0, st>>>(vs, w);
-        else k_raster_accumulate<2, false><<<NT, kTilePx / 2, 0, st>>>(vs, w);
+        if (stats) k_raster_accumulate<2, true><<<NT, kTilePx / 2, 0, st>>>(vs, w, tb);
+        else k_raster_accumulate<2, false><<<NT, kTilePx / 2, 0, st>>>(vs, w, tb);
     }
     return cudaGetLastError();
 }
