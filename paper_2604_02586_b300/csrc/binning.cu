@@ -220,36 +220,66 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
         }
 }
 
-// Up to 8 tiles of a record are handled per round: their slot atomics are all
-// issued before any result is used, so a record waits about one atomic round
-// trip per 8 tiles rather than one per tile.
+// The 32 records of a warp (one view, consecutive Gaussians) are flattened into
+// their (record, tile) items: a warp scan of the tile counts numbers the items,
+// lane l takes items l, l + 32, ..., finds the owning record as the last lane
+// whose exclusive count is <= the item (a 5-step shuffle search), and 8 items per
+// lane have their slot atomics in flight before any result is used.  Lanes stay
+// busy whatever the mix of culled, small and large records.
 __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
 {
     constexpr int kIlp = 8;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
-    if (g >= vs.n) return;
-    const size_t i = (size_t)v * vs.n + g;
-    const uint32_t cnt = w.touched[i];
-    if (cnt == 0u) return;
-    const short4 r = w.rect[i];
-    const uint64_t e = ((uint64_t)w.depth[i] << 32) | (uint32_t)g;
+    const int lane = threadIdx.x & 31;
+    uint32_t cnt = 0u, rxy = 0u, rzw = 0u, klo = 0u, khi = 0u;
+    if (g < vs.n) {
+        const size_t i = (size_t)v * vs.n + g;
+        cnt = w.touched[i];
+        if (cnt) {
+            const short4 r = w.rect[i];
+            rxy = (uint32_t)(uint16_t)r.x | ((uint32_t)(uint16_t)r.y << 16);
+            rzw = (uint32_t)(uint16_t)r.z | ((uint32_t)(uint16_t)r.w << 16);
+            klo = (uint32_t)g;
+            khi = w.depth[i];
+        }
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t exc = inc - cnt;
     const uint32_t base = vs.toff[v];
     const int tx_n = vs.tiles_x[v];
-    int tx = r.x, ty = r.y;
-    for (uint32_t k0 = 0; k0 < cnt; k0 += kIlp) {
-        uint32_t t[kIlp], slot[kIlp];
+    for (uint32_t it0 = 0; it0 < total; it0 += 32 * kIlp) {
+        uint32_t t[kIlp], slot[kIlp], k0[kIlp], k1[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
-            t[u] = base + (uint32_t)(ty * tx_n + tx);
-            if (k0 + u < cnt) slot[u] = atomicAdd(&w.tile_fill[(size_t)t[u] * kCounterStride], 1u);
-            if (++tx == r.z) { tx = r.x; ++ty; }
+            const uint32_t item = it0 + (uint32_t)(u * 32 + lane);
+            int own = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, exc, own + step);
+                if (e <= item) own += step;
+            }
+            const uint32_t off = item - __shfl_sync(0xffffffffu, exc, own);
+            const uint32_t xy = __shfl_sync(0xffffffffu, rxy, own);
+            const uint32_t zw = __shfl_sync(0xffffffffu, rzw, own);
+            k0[u] = __shfl_sync(0xffffffffu, klo, own);
+            k1[u] = __shfl_sync(0xffffffffu, khi, own);
+            const uint32_t x0 = xy & 0xffffu, y0 = xy >> 16, rw = (zw & 0xffffu) - x0;
+            const uint32_t dy = rw ? off / rw : 0u, dx = off - dy * rw;
+            t[u] = base + (y0 + dy) * (uint32_t)tx_n + x0 + dx;
+            if (item < total) slot[u] = atomicAdd(&w.tile_fill[(size_t)t[u] * kCounterStride], 1u);
         }
 #pragma unroll
         for (int u = 0; u < kIlp; ++u)
-            if (k0 + u < cnt) {
+            if (it0 + (uint32_t)(u * 32 + lane) < total) {
                 const uint64_t pos = (uint64_t)w.tile_off[t[u]] + slot[u];
-                if (pos < w.cap) w.pairs[pos] = e;
+                if (pos < w.cap) w.pairs[pos] = ((uint64_t)k1[u] << 32) | k0[u];
             }
     }
 }
@@ -286,7 +316,7 @@ __device__ void smem_sort(uint64_t* src, uint32_t n, uint64_t* s)
 // strides j >= KPL pair lane l with lane l ^ (j / KPL) through a shuffle.  The
 // direction of a comparator is set by bit k of the position (ascending where it
 // is 0), which is a bit of i for k < KPL and a bit of the lane otherwise.
-constexpr int kWarpSortMax = 1024;
+constexpr int kWarpSortMax = 512;
 
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
 {
@@ -357,8 +387,7 @@ __global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restri
     else if (n <= 64) warp_sort_list<2>(keys, n, lane);
     else if (n <= 128) warp_sort_list<4>(keys, n, lane);
     else if (n <= 256) warp_sort_list<8>(keys, n, lane);
-    else if (n <= 512) warp_sort_list<16>(keys, n, lane);
-    else if (n <= (uint32_t)kWarpSortMax) warp_sort_list<32>(keys, n, lane);
+    else if (n <= (uint32_t)kWarpSortMax) warp_sort_list<16>(keys, n, lane);
     else if (lane == 0) long_list[atomicAdd(long_count, 1u)] = t;
 }
 

@@ -98,7 +98,7 @@ def test_bins_bit_exact(gpu_ready, name):
 @pytest.mark.parametrize("scale", [1.0, 0.3])
 def test_all_list_lengths_bin_bit_exact(gpu_ready, scale):
     """Dense 512x512 scenes whose tile lists span every sort path: the one-warp
-    register sorts (2..1024 keys), the shared-memory sort (..4096) and the
+    register sorts (2..512 keys), the shared-memory sort (..4096) and the
     run merge (longer)."""
     s = synth.make_scene("tiny", 3, n=20000, views=2, width=512, height=512, focal=512.0)
     s.means_opacity[:, :3] *= scale
