@@ -37,11 +37,14 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "raster_accumulate_traffic.json")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=200_000)
-    ap.add_argument("--views", type=int, default=18)
+    ap.add_argument("--preset", default="capture", choices=["capture", "tiny"],
+                    help="capture: 200k Gaussians x 18 views at 1352x1014 (the metric's workload); "
+                         "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound)")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -54,10 +57,20 @@ def dist_env():
     return rank, world, local
 
 
-def config(a):
-    return {"workload": "capture frame pair: 200k Gaussians x 18 views @ 1352x1014, tracks + vis",
-            "n_gaussians": a.n, "views": a.views, "width": 1352, "height": 1014, "tile": "16x16",
-            "l2": "flushed between timed steps (256 MB write); inputs 222 MB > L2"}
+def config(a, scene=None):
+    import synth
+    p = synth.PRESETS[a.preset]
+    n = a.n if a.n is not None else p["n"]
+    views = a.views if a.views is not None else p["views"]
+    w, h = (int(scene.width[0]), int(scene.height[0])) if scene is not None else (None, None)
+    name = {"capture": "capture frame pair", "tiny": "tiny frame pair"}[a.preset]
+    c = {"workload": f"{name}: {n} Gaussians x {views} views @ {w}x{h}, tracks + vis",
+         "n_gaussians": n, "views": views, "width": w, "height": h, "tile": "16x16"}
+    if a.preset == "capture":
+        c["l2"] = "flushed between timed steps (256 MB write); inputs 222 MB > L2"
+    else:
+        c["l2"] = "flushed between timed steps (256 MB write); inputs fit in L2 (launch-bound case)"
+    return c
 
 
 def cpu_model():
@@ -85,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -154,7 +167,7 @@ def rank_seed(rank):
 
 def make_scene(a, rank):
     import synth
-    return synth.make_scene("capture", seed=rank_seed(rank), n=a.n, views=a.views)
+    return synth.make_scene(a.preset, seed=rank_seed(rank), n=a.n, views=a.views)
 
 
 def reduce_max(x, world, device):
@@ -204,7 +217,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(a),
+            "data": "synthetic", "config": config(a, scene),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"each step: all {scene.n} Gaussians over {V} of "
                                        f"{scene.num_views} views, FP64 C oracle on {cpu_model()}"},
@@ -322,7 +335,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config(a),
+        "config": config(a, scene),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": raster_traffic(),

@@ -31,7 +31,7 @@ def _worker(rank, world, port, q):
     r, w, _ = bench.dist_env()
     local_ms = 10.0 + 5.0 * r                       # rank 1 is the slow one
     mx = bench.reduce_max(local_ms, w, "cpu")
-    scene = bench.make_scene(types.SimpleNamespace(n=300, views=2), r)
+    scene = bench.make_scene(types.SimpleNamespace(preset="capture", n=300, views=2), r)
     q.put((r, w, mx, bench.job_value(1000, w, 4, mx), bench.rank_seed(r),
            float(scene.means_opacity[:, :3].sum())))
     dist.barrier()
@@ -66,7 +66,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
-        bench.run_reference(types.SimpleNamespace(n=300, views=2, steps=1, warmup=0, gpus=2))
+        bench.run_reference(types.SimpleNamespace(preset="capture", n=300, views=2, steps=1, warmup=0, gpus=2))
     assert buf.getvalue() == ""
 
 
@@ -76,7 +76,7 @@ def test_reference_arm_line_on_rank_zero(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "1")
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
-        bench.run_reference(types.SimpleNamespace(n=300, views=2, steps=1, warmup=0, gpus=1))
+        bench.run_reference(types.SimpleNamespace(preset="capture", n=300, views=2, steps=1, warmup=0, gpus=1))
     line = json.loads(buf.getvalue())
     assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
