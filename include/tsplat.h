@@ -35,7 +35,9 @@ extern "C" {
 #endif
 
 #define TSP_VERSION 1
-#define TSP_MAX_VIEWS 32
+#define TSP_MAX_VIEWS 32          /* views of one frame                                */
+#define TSP_MAX_FRAMES 16         /* frames of one tsp_fit_motion_batch call           */
+#define TSP_MAX_BATCH_VIEWS 128   /* views of all frames of one tsp_fit_motion_batch   */
 #define TSP_MAX_IMAGE 8192
 
 typedef enum {
@@ -106,6 +108,16 @@ typedef struct tsp_result {
  * Eq. 4's V1 and V2 follow: V1 = [[3,4,1],[4,5,2],[1,2,0]] and
  * V2 = V1[:, 0:2] + [[8,9],[10,11],[6,7]] + V1[:, 2] r^T in this (x~, y~, 1) basis. */
 
+/* One frame pair of a batch: its Gaussians, cameras, tracks and outputs, with
+ * the same meaning and memory rules as the arguments of tsp_fit_motion. */
+typedef struct tsp_frame {
+    tsp_gaussians g;
+    const tsp_camera* cams;     /* host [num_views]                                */
+    int32_t num_views;          /* 0..TSP_MAX_VIEWS                                */
+    const tsp_view_tracks* tracks; /* host [num_views] of device pointers          */
+    tsp_result out;
+} tsp_frame;
+
 typedef struct tsp_options {
     int32_t tile_w, tile_h;     /* raster tile; 16 x 16 is the only supported value */
     float det_min;              /* Sec. 5.1: 1e-12                                 */
@@ -165,6 +177,15 @@ tsp_status tsp_destroy(tsp_context* ctx);
 tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams,
                           int num_views, const tsp_view_tracks* tracks, const tsp_result* out,
                           void* stream);
+
+/* Several frame pairs (Sec. 4.6: frame pairs are independent units) in one
+ * launch of each step: up to TSP_MAX_FRAMES frames of uneven Gaussian counts and
+ * view counts, at most TSP_MAX_BATCH_VIEWS views in all.  Each frame's outputs
+ * are those tsp_fit_motion would give it alone (floating-point sums may differ in
+ * the last bits: atomic additions run in another order).  The pair buffer holds
+ * the pairs of all frames; tsp_inspect reports the records of all frames, frame
+ * by frame, view-major within a frame.  Errors as tsp_fit_motion. */
+tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int num_frames, void* stream);
 
 /* Same step for callers that hold everything in host memory: g, tracks and out
  * point to host arrays (pinned memory gives full copy speed and lets the copies

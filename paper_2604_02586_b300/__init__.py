@@ -51,6 +51,11 @@ class Result(C.Structure):
                 ("view_flags", C.c_void_p)]
 
 
+class Frame(C.Structure):
+    _fields_ = [("g", Gaussians), ("cams", C.c_void_p), ("num_views", C.c_int32),
+                ("tracks", C.c_void_p), ("out", Result)]
+
+
 class Options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("det_min", C.c_float),
                 ("sumw_min_view", C.c_float), ("min_px_view", C.c_int32), ("lam_min_px2", C.c_float),
@@ -77,6 +82,7 @@ def lib():
         L.tsp_destroy.argtypes = [P]
         L.tsp_fit_motion.argtypes = [P, P, P, I, P, P, P]
         L.tsp_fit_motion_host.argtypes = [P, P, P, I, P, P, P]
+        L.tsp_fit_motion_batch.argtypes = [P, P, I, P]
         L.tsp_render.argtypes = [P, P, P, I, P, I, P, P, P]
         L.tsp_sync.argtypes = [P, P, I]
         L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
@@ -90,7 +96,7 @@ def lib():
         L.tsp_last_error.restype = C.c_char_p
         L.tsp_version.restype = I
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
-                     "tsp_fit_motion_host", "tsp_render", "tsp_sync", "tsp_inspect",
+                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_render", "tsp_sync", "tsp_inspect",
                      "tsp_workspace_bytes", "tsp_stage_times"):
             getattr(L, name).restype = I
         _lib = L
@@ -200,12 +206,10 @@ class Context:
         self.close()
 
     # -- the motion fit --------------------------------------------------------
-    def fit_motion(self, means_opacity, quats, scales, cams, disp, vis, *, out=None,
-                   view_affine=False, view_moments=False, view_flags=False, stream=None,
-                   sync=False):
-        """Device path.  Tensors are CUDA tensors on the context's device:
-        means_opacity/quats/scales [n,4] f32, disp [V] x [H,W,2] f32, vis [V] x [H,W] u8.
-        Returns a dict of output tensors (allocated here unless ``out`` is given)."""
+    def _frame(self, means_opacity, quats, scales, cams, disp, vis, out=None,
+               view_affine=False, view_moments=False, view_flags=False):
+        """Check one frame's tensors and build its C structures (kept alive by the
+        returned tuple: Gaussians, camera array, view count, tracks, Result, out)."""
         import torch
         n = int(means_opacity.shape[0])
         carr, V = _cams(cams)
@@ -241,11 +245,42 @@ class Context:
             tr[v].disp, tr[v].vis = disp[v].data_ptr(), vis[v].data_ptr()
         r = Result(*[(out[k].data_ptr() if k in out else None) for k in
                      ("means", "quats", "scales", "status", "view_affine", "view_moments", "view_flags")])
+        return g, carr, V, tr, r, out
+
+    def fit_motion(self, means_opacity, quats, scales, cams, disp, vis, *, out=None,
+                   view_affine=False, view_moments=False, view_flags=False, stream=None,
+                   sync=False):
+        """Device path.  Tensors are CUDA tensors on the context's device:
+        means_opacity/quats/scales [n,4] f32, disp [V] x [H,W,2] f32, vis [V] x [H,W] u8.
+        Returns a dict of output tensors (allocated here unless ``out`` is given)."""
+        g, carr, V, tr, r, out = self._frame(means_opacity, quats, scales, cams, disp, vis, out,
+                                             view_affine, view_moments, view_flags)
         self._check(lib().tsp_fit_motion(self._h, C.byref(g), carr, V, tr, C.byref(r),
                                          _stream_handle(stream)), "tsp_fit_motion")
         if sync:
             self.sync(stream)
         return out
+
+    def fit_motion_batch(self, frames, *, stream=None, sync=False):
+        """Several frame pairs in one launch of each step.  ``frames`` is a list of
+        dicts with the arguments of fit_motion (means_opacity, quats, scales, cams,
+        disp, vis and optionally out, view_affine, view_moments, view_flags).
+        Returns the list of per-frame output dicts."""
+        keys = ("means_opacity", "quats", "scales", "cams", "disp", "vis")
+        prep = [self._frame(*[f[k] for k in keys], f.get("out"), f.get("view_affine", False),
+                            f.get("view_moments", False), f.get("view_flags", False)) for f in frames]
+        arr = (Frame * max(len(prep), 1))()
+        for k, (g, carr, V, tr, r, _) in enumerate(prep):
+            arr[k].g = g
+            arr[k].cams = C.cast(carr, C.c_void_p)
+            arr[k].num_views = V
+            arr[k].tracks = C.cast(tr, C.c_void_p)
+            arr[k].out = r
+        self._check(lib().tsp_fit_motion_batch(self._h, arr, len(prep), _stream_handle(stream)),
+                    "tsp_fit_motion_batch")
+        if sync:
+            self.sync(stream)
+        return [p[5] for p in prep]
 
     def fit_motion_host(self, means_opacity, quats, scales, cams, disp, vis, out=None, stream=None):
         """Host path: numpy inputs and outputs; copies happen inside the library."""

@@ -44,7 +44,7 @@ struct tsp_context {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t group_ev[32] = {};
     // last call
-    int last_V = 0, last_n = 0;
+    size_t last_R = 0;              // (view, Gaussian) records of the last call
     uint32_t last_NT = 0;
 };
 
@@ -169,37 +169,65 @@ FitParams fit_params(const tsp_options& o)
 }
 
 // Validate cameras and build the per-call view description.
-tsp_status make_viewset(tsp_context* ctx, const tsp_camera* cams, int V, int n, ViewSet& vs, uint32_t& NT)
+// Fill the kernels' view set for the frames of one launch: cameras (validated),
+// tile offsets, each view's frame, Gaussian count and record base.  g_of(f)
+// gives frame f's Gaussian arrays.  NT = tiles of all views, R = records.
+tsp_status make_viewset(tsp_context* ctx, const tsp_frame* frames, int F, ViewSet& vs, uint32_t& NT,
+                        uint64_t& R)
 {
-    if (V < 0 || V > TSP_MAX_VIEWS) return fail(ctx, TSP_ERR_INVALID_ARG, "num_views must be in [0, 32]");
-    if (V > 0 && !cams) return fail(ctx, TSP_ERR_INVALID_ARG, "cams is NULL");
+    if (F < 0 || F > TSP_MAX_FRAMES) return fail(ctx, TSP_ERR_INVALID_ARG, "num_frames must be in [0, 16]");
+    if (F > 0 && !frames) return fail(ctx, TSP_ERR_INVALID_ARG, "frames is NULL");
     std::memset(&vs, 0, sizeof(vs));
-    vs.V = V;
-    vs.n = n;
-    uint64_t off = 0;
-    for (int v = 0; v < V; ++v) {
-        const tsp_camera& c = cams[v];
-        if (c.width < 1 || c.height < 1 || c.width > TSP_MAX_IMAGE || c.height > TSP_MAX_IMAGE)
-            return fail(ctx, TSP_ERR_INVALID_ARG, "camera " + std::to_string(v) + ": size out of range");
-        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.fx) || !std::isfinite(c.fy) ||
-            !std::isfinite(c.cx) || !std::isfinite(c.cy))
-            return fail(ctx, TSP_ERR_INVALID_ARG, "camera " + std::to_string(v) + ": bad intrinsics");
-        for (int k = 0; k < 9; ++k)
-            if (!std::isfinite(c.R[k])) return fail(ctx, TSP_ERR_INVALID_ARG, "camera R not finite");
-        for (int k = 0; k < 3; ++k)
-            if (!std::isfinite(c.t[k])) return fail(ctx, TSP_ERR_INVALID_ARG, "camera t not finite");
-        DevCam& d = vs.cam[v];
-        d.W = c.width; d.H = c.height;
-        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-        std::memcpy(d.R, c.R, sizeof(d.R));
-        std::memcpy(d.t, c.t, sizeof(d.t));
-        vs.tiles_x[v] = (c.width + kTile - 1) / kTile;
-        vs.tiles_y[v] = (c.height + kTile - 1) / kTile;
-        vs.toff[v] = (uint32_t)off;
-        off += (uint64_t)vs.tiles_x[v] * vs.tiles_y[v];
+    uint64_t off = 0, rec = 0;
+    int V = 0;
+    for (int f = 0; f < F; ++f) {
+        const tsp_frame& fr = frames[f];
+        const int Vf = fr.num_views, n = fr.g.n;
+        if (Vf < 0 || Vf > TSP_MAX_VIEWS) return fail(ctx, TSP_ERR_INVALID_ARG, "num_views must be in [0, 32]");
+        if (V + Vf > TSP_MAX_BATCH_VIEWS)
+            return fail(ctx, TSP_ERR_INVALID_ARG, "more than 128 views in one batch");
+        if (Vf > 0 && !fr.cams) return fail(ctx, TSP_ERR_INVALID_ARG, "cams is NULL");
+        if (n < 0) return fail(ctx, TSP_ERR_INVALID_ARG, "n < 0");
+        vs.fview[f] = V;
+        vs.fn[f] = n;
+        vs.fmo[f] = (const float4*)fr.g.means_opacity;
+        vs.fq[f] = (const float4*)fr.g.quats;
+        vs.fs[f] = (const float4*)fr.g.scales;
+        vs.nmax = std::max(vs.nmax, n);
+        for (int k = 0; k < Vf; ++k, ++V) {
+            const tsp_camera& c = fr.cams[k];
+            const std::string where = "frame " + std::to_string(f) + " camera " + std::to_string(k);
+            if (c.width < 1 || c.height < 1 || c.width > TSP_MAX_IMAGE || c.height > TSP_MAX_IMAGE)
+                return fail(ctx, TSP_ERR_INVALID_ARG, where + ": size out of range");
+            if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.fx) || !std::isfinite(c.fy) ||
+                !std::isfinite(c.cx) || !std::isfinite(c.cy))
+                return fail(ctx, TSP_ERR_INVALID_ARG, where + ": bad intrinsics");
+            for (int j = 0; j < 9; ++j)
+                if (!std::isfinite(c.R[j])) return fail(ctx, TSP_ERR_INVALID_ARG, where + ": R not finite");
+            for (int j = 0; j < 3; ++j)
+                if (!std::isfinite(c.t[j])) return fail(ctx, TSP_ERR_INVALID_ARG, where + ": t not finite");
+            DevCam& d = vs.cam[V];
+            d.W = c.width; d.H = c.height;
+            d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+            std::memcpy(d.R, c.R, sizeof(d.R));
+            std::memcpy(d.t, c.t, sizeof(d.t));
+            vs.tiles_x[V] = (c.width + kTile - 1) / kTile;
+            vs.tiles_y[V] = (c.height + kTile - 1) / kTile;
+            vs.toff[V] = (uint32_t)off;
+            off += (uint64_t)vs.tiles_x[V] * vs.tiles_y[V];
+            vs.vframe[V] = f;
+            vs.vn[V] = n;
+            vs.vrec[V] = rec;
+            rec += (uint64_t)n;
+        }
     }
+    vs.V = V;
+    vs.F = F;
+    vs.fview[F] = V;
     vs.toff[V] = (uint32_t)off;
+    if (off > 0xffffffffull) return fail(ctx, TSP_ERR_INVALID_ARG, "too many tiles");
     NT = (uint32_t)off;
+    R = rec;
     return TSP_OK;
 }
 
@@ -242,9 +270,9 @@ tsp_status check_result(tsp_context* ctx, const tsp_result* out, int n, bool dev
     return TSP_OK;
 }
 
-tsp_status ensure_work(tsp_context* ctx, int V, int n, uint32_t NT, bool render, Work& w)
+tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, Work& w)
 {
-    const size_t vn = (size_t)V * (size_t)n;
+    const size_t vn = (size_t)R;
     const size_t vn1 = vn > 0 ? vn : 1;
     tsp_status s;
     if ((s = ensure(ctx, ctx->rect, vn1 * sizeof(short4)))) return s;
@@ -306,15 +334,14 @@ inline cudaError_t mark(tsp_context* ctx, int k, cudaStream_t st)
 }
 
 // a1 + a2 (count, scan) and, unless async, the wait that sizes the pair buffer.
-tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const tsp_gaussians* g, const float* sh,
-                     int sh_degree, int mode, uint32_t NT, Work& w, cudaStream_t st)
+tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const float* sh, int sh_degree, int mode,
+                     uint32_t NT, Work& w, cudaStream_t st)
 {
     TSP_CUDA(mark(ctx, 0, st));
     TSP_CUDA(cudaMemsetAsync(ctx->tiles.p, 0, (size_t)2 * (NT + 1) * kCounterStride * 4, st));
     TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 16, st));
     if (ctx->opt.collect_stats) TSP_CUDA(cudaMemsetAsync(w.stats, 0, 32, st));
-    TSP_CUDA(launch_preprocess(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
-                               (const float4*)g->scales, sh, sh_degree, mode, w, st));
+    TSP_CUDA(launch_preprocess(vs, sh, sh_degree, mode, w, st));
     TSP_CUDA(mark(ctx, 1, st));
     TSP_CUDA(launch_scan(w, NT, st));
     TSP_CUDA(mark(ctx, 2, st));
@@ -342,45 +369,56 @@ tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const tsp_gaussians* g
     return TSP_OK;
 }
 
-// The whole path a1-a9 on device buffers.  With ready != nullptr the tracks of
-// views [k*group, (k+1)*group) are still being copied and ready[k] is recorded on
+// The whole path a1-a9 for the frames of one launch, on device buffers.  With
+// ready != nullptr the tracks of views [k*group, (k+1)*group) (views of all
+// frames numbered together) are still being copied and ready[k] is recorded on
 // the copy stream once they have landed: the tracks-free steps (projection,
-// binning, sorting) run first, then each view group's reference gather and raster
-// wait for their own copy.
-tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams, int V,
-                      const tsp_view_tracks* tracks, const tsp_result* out, cudaStream_t st, bool check_ptrs,
+// binning, sorting) run first, then each view group's reference gather and
+// raster wait for their own copy.
+tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStream_t st, bool check_ptrs,
                       int group = 0, const cudaEvent_t* ready = nullptr)
 {
     tsp_status s;
-    if ((s = check_gaussians(ctx, g, check_ptrs))) return s;
-    const int n = g->n;
+    if (F > 0 && !frames) return fail(ctx, TSP_ERR_INVALID_ARG, "frames is NULL");
+    for (int f = 0; f < F; ++f) {
+        if ((s = check_gaussians(ctx, &frames[f].g, check_ptrs))) return s;
+        if ((s = check_result(ctx, &frames[f].out, frames[f].g.n, check_ptrs))) return s;
+    }
     ViewSet vs;
     uint32_t NT = 0;
-    if ((s = make_viewset(ctx, cams, V, n, vs, NT))) return s;
-    if ((s = check_result(ctx, out, n, check_ptrs))) return s;
-    if (n > 0 && V > 0) {
-        if (!tracks) return fail(ctx, TSP_ERR_INVALID_ARG, "tracks is NULL");
-        for (int v = 0; v < V; ++v) {
-            if (!tracks[v].disp || !tracks[v].vis)
-                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": track pointer is NULL");
-            if (!aligned(tracks[v].disp, 8))
-                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": disp must be 8-byte aligned");
-            if (check_ptrs && (!device_accessible(tracks[v].disp, ctx->device) ||
-                               !device_accessible(tracks[v].vis, ctx->device)))
-                return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": tracks are not device memory");
-            vs.disp[v] = (const float2*)tracks[v].disp;
-            vs.vis[v] = tracks[v].vis;
+    uint64_t R = 0;
+    if ((s = make_viewset(ctx, frames, F, vs, NT, R))) return s;
+    FrameOut fo{};
+    for (int f = 0; f < F; ++f) {
+        const tsp_frame& fr = frames[f];
+        fo.means[f] = (float4*)fr.out.means;
+        fo.quats[f] = (float4*)fr.out.quats;
+        fo.scales[f] = (float4*)fr.out.scales;
+        fo.status[f] = fr.out.status;
+        fo.view_affine[f] = fr.out.view_affine;
+        fo.view_flags[f] = fr.out.view_flags;
+        if (fr.g.n == 0 || fr.num_views == 0) continue;
+        if (!fr.tracks) return fail(ctx, TSP_ERR_INVALID_ARG, "tracks is NULL");
+        for (int k = 0; k < fr.num_views; ++k) {
+            const std::string where = "frame " + std::to_string(f) + " view " + std::to_string(k);
+            const tsp_view_tracks& tr = fr.tracks[k];
+            if (!tr.disp || !tr.vis) return fail(ctx, TSP_ERR_INVALID_ARG, where + ": track pointer is NULL");
+            if (!aligned(tr.disp, 8)) return fail(ctx, TSP_ERR_INVALID_ARG, where + ": disp must be 8-byte aligned");
+            if (check_ptrs && (!device_accessible(tr.disp, ctx->device) || !device_accessible(tr.vis, ctx->device)))
+                return fail(ctx, TSP_ERR_INVALID_ARG, where + ": tracks are not device memory");
+            vs.disp[vs.fview[f] + k] = (const float2*)tr.disp;
+            vs.vis[vs.fview[f] + k] = tr.vis;
         }
     }
     Work w{};
-    if ((s = ensure_work(ctx, V, n, NT, false, w))) return s;
-    ctx->last_V = V;
-    ctx->last_n = n;
+    if ((s = ensure_work(ctx, R, NT, false, w))) return s;
+    ctx->last_R = (size_t)R;
     ctx->last_NT = NT;
-    if (n == 0) return TSP_OK;
+    if (vs.nmax == 0) return TSP_OK;
     const FitParams fp = fit_params(ctx->opt);
+    const int V = vs.V;
     ctx->timed = false;
-    if ((s = bin_front(ctx, vs, g, nullptr, 0, 0, NT, w, st))) return s;
+    if ((s = bin_front(ctx, vs, nullptr, 0, 0, NT, w, st))) return s;
     if (group <= 0) group = V;
     for (int v0 = 0, k = 0; v0 < V; v0 += group, ++k) {
         const int v1 = std::min(V, v0 + group);
@@ -390,16 +428,32 @@ tsp_status fit_device(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera
                                           ctx->opt.collect_stats != 0, ctx->opt.raster_variant, st));
     }
     TSP_CUDA(mark(ctx, 5, st));
-    TSP_CUDA(launch_view_solve(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
-                               (const float4*)g->scales, fp, w, out->view_affine, out->view_flags, st));
+    TSP_CUDA(launch_view_solve(vs, fp, w, fo, st));
     TSP_CUDA(mark(ctx, 6, st));
-    TSP_CUDA(launch_multiview(vs, (const float4*)g->means_opacity, (const float4*)g->quats,
-                              (const float4*)g->scales, fp, w, (float4*)out->means, (float4*)out->quats,
-                              (float4*)out->scales, out->status, st));
+    TSP_CUDA(launch_multiview(vs, fp, w, fo, st));
     TSP_CUDA(mark(ctx, 7, st));
     ctx->timed = ctx->opt.stage_timing != 0;
-    if (out->view_moments && V > 0)
-        TSP_CUDA(cudaMemcpyAsync(out->view_moments, w.moments, (size_t)V * n * 64, cudaMemcpyDeviceToDevice, st));
+    for (int f = 0; f < F; ++f) {
+        const tsp_frame& fr = frames[f];
+        const size_t recs = (size_t)fr.num_views * (size_t)fr.g.n;
+        if (fr.out.view_moments && recs > 0)
+            TSP_CUDA(cudaMemcpyAsync(fr.out.view_moments, w.moments + 4 * vs.vrec[vs.fview[f]], recs * 64,
+                                     cudaMemcpyDeviceToDevice, st));
+    }
+    return TSP_OK;
+}
+
+// One frame as a batch of one.
+tsp_status single_frame(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams, int V,
+                        const tsp_view_tracks* tracks, const tsp_result* out, tsp_frame& fr)
+{
+    if (!g) return fail(ctx, TSP_ERR_INVALID_ARG, "g is NULL");
+    if (!out) return fail(ctx, TSP_ERR_INVALID_ARG, "out is NULL");
+    fr.g = *g;
+    fr.cams = cams;
+    fr.num_views = V;
+    fr.tracks = tracks;
+    fr.out = *out;
     return TSP_OK;
 }
 
@@ -502,7 +556,17 @@ tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_ca
 {
     if (!ctx) return TSP_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
-    return fit_device(ctx, g, cams, num_views, tracks, out, (cudaStream_t)stream, true);
+    tsp_frame fr;
+    tsp_status s;
+    if ((s = single_frame(ctx, g, cams, num_views, tracks, out, fr))) return s;
+    return fit_device(ctx, &fr, 1, (cudaStream_t)stream, true);
+}
+
+tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int num_frames, void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    return fit_device(ctx, frames, num_frames, (cudaStream_t)stream, true);
 }
 
 tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const tsp_camera* cams,
@@ -514,10 +578,15 @@ tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const t
     tsp_status s;
     if ((s = check_gaussians(ctx, g, false))) return s;
     if ((s = check_result(ctx, out, g->n, false))) return s;
-    ViewSet vs;
-    uint32_t NT = 0;
+    {
+        tsp_frame probe;
+        if ((s = single_frame(ctx, g, cams, num_views, tracks, out, probe))) return s;
+        ViewSet vs;
+        uint32_t NT = 0;
+        uint64_t R = 0;
+        if ((s = make_viewset(ctx, &probe, 1, vs, NT, R))) return s;   // validates the cameras
+    }
     const int n = g->n, V = num_views;
-    if ((s = make_viewset(ctx, cams, V, n, vs, NT))) return s;
     if (n > 0 && V > 0 && !tracks) return fail(ctx, TSP_ERR_INVALID_ARG, "tracks is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t gb = (size_t)n * 16;
@@ -571,8 +640,8 @@ tsp_status tsp_fit_motion_host(tsp_context* ctx, const tsp_gaussians* g, const t
                 TSP_CUDA(cudaEventRecord(ctx->group_ev[v / group], ctx->copy_stream));
         }
     }
-    if ((s = fit_device(ctx, &dg_, cams, V, dt.data(), &dr, st, false, group,
-                        n > 0 && V > 0 ? ctx->group_ev : nullptr))) {
+    tsp_frame dfr{dg_, cams, V, dt.data(), dr};
+    if ((s = fit_device(ctx, &dfr, 1, st, false, group, n > 0 && V > 0 ? ctx->group_ev : nullptr))) {
         // the caller may release its host buffers once we return: finish reading them
         if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
         return s;
@@ -600,7 +669,12 @@ tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh,
         return fail(ctx, TSP_ERR_INVALID_ARG, "sh must be device memory");
     ViewSet vs;
     uint32_t NT = 0;
-    if ((s = make_viewset(ctx, cams, V, n, vs, NT))) return s;
+    uint64_t R = 0;
+    tsp_frame fr{};
+    fr.g = *g;
+    fr.cams = cams;
+    fr.num_views = V;
+    if ((s = make_viewset(ctx, &fr, 1, vs, NT, R))) return s;
     if (V > 0 && (!rgb || !final_T)) return fail(ctx, TSP_ERR_INVALID_ARG, "rgb / final_T is NULL");
     for (int v = 0; v < V; ++v) {
         if (!rgb[v] || !final_T[v] || !aligned(rgb[v], 4) || !aligned(final_T[v], 4))
@@ -609,13 +683,12 @@ tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh,
             return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": output is not device memory");
     }
     Work w{};
-    if ((s = ensure_work(ctx, V, n, NT, true, w))) return s;
-    ctx->last_V = V;
-    ctx->last_n = n;
+    if ((s = ensure_work(ctx, R, NT, true, w))) return s;
+    ctx->last_R = (size_t)R;
     ctx->last_NT = NT;
     cudaStream_t st = (cudaStream_t)stream;
     ctx->timed = false;
-    if ((s = bin_front(ctx, vs, g, sh, sh_degree, 1, NT, w, st))) return s;
+    if ((s = bin_front(ctx, vs, sh, sh_degree, 1, NT, w, st))) return s;
     TSP_CUDA(launch_raster_render(vs, w, NT, rgb, final_T, st));
     TSP_CUDA(mark(ctx, 5, st));
     TSP_CUDA(mark(ctx, 6, st));
@@ -660,7 +733,7 @@ tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, siz
 {
     if (!ctx) return TSP_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
-    const size_t vn = (size_t)ctx->last_V * ctx->last_n;
+    const size_t vn = ctx->last_R;
     const void* src = nullptr;
     size_t size = 0;
     int64_t counts[4] = {0, 0, 0, 0};

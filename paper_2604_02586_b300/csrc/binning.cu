@@ -45,28 +45,26 @@ __device__ __forceinline__ void sh_colour(const float* sh, int deg, float x, flo
     rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(g, 0.f); rgb[2] = fmaxf(b, 0.f);
 }
 
-// grid (ceil(n/256), V): one thread per (view, Gaussian), Gaussian index fastest.
-// kMode 0: motion fit (zero the moment record, reference displacement);
-// kMode 1: render (view-dependent colour).
+// grid (ceil(nmax/256), V): one thread per (view, Gaussian), Gaussian index fastest.
+// kMode 0: motion fit (zero the moment record, note the moment origin's pixel);
+// kMode 1: render (view-dependent colour; one frame).
 template <int kMode>
-__global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const float4* __restrict__ mo,
-                                                    const float4* __restrict__ q,
-                                                    const float4* __restrict__ s,
-                                                    const float* __restrict__ sh, int sh_degree,
-                                                    Work w)
+__global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const float* __restrict__ sh,
+                                                    int sh_degree, Work w)
 {
     constexpr int mode = kMode;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
-    if (g >= vs.n) return;
-    const size_t i = (size_t)v * vs.n + g;
+    if (g >= vs.vn[v]) return;
+    const size_t i = (size_t)vs.vrec[v] + g;
+    const int fr = vs.vframe[v];
     if (mode == 0) {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         w.moments[4 * i] = z; w.moments[4 * i + 1] = z; w.moments[4 * i + 2] = z; w.moments[4 * i + 3] = z;
     }
-    const float4 m = mo[g];
+    const float4 m = vs.fmo[fr][g];
     KeyProj p;
-    if (!key_project(vs.cam[v], m, q[g], s[g], vs.tiles_x[v], vs.tiles_y[v], p)) {
+    if (!key_project(vs.cam[v], m, vs.fq[fr][g], vs.fs[fr][g], vs.tiles_x[v], vs.tiles_y[v], p)) {
         w.rect[i] = make_short4(0, 0, 0, 0);
         w.touched[i] = 0u;
         w.depth[i] = 0u;
@@ -118,8 +116,8 @@ __global__ void __launch_bounds__(256) k_dref(const ViewSet vs, Work w, int v0)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = v0 + (int)blockIdx.y;
-    if (g >= vs.n) return;
-    const size_t i = (size_t)v * vs.n + g;
+    if (g >= vs.vn[v]) return;
+    const size_t i = (size_t)vs.vrec[v] + g;
     if (w.touched[i] == 0u) return;
     w.dref[i] = vs.disp[v][w.oref[i]];
 }
@@ -233,8 +231,8 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
     const int v = blockIdx.y;
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0u, rxy = 0u, rzw = 0u, klo = 0u, khi = 0u;
-    if (g < vs.n) {
-        const size_t i = (size_t)v * vs.n + g;
+    if (g < vs.vn[v]) {
+        const size_t i = (size_t)vs.vrec[v] + g;
         cnt = w.touched[i];
         if (cnt) {
             const short4 r = w.rect[i];
@@ -439,22 +437,22 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(const uint32_t* __re
 
 }  // namespace
 
-cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
-                              const float* sh, int sh_degree, int mode, const Work& w, cudaStream_t st)
+cudaError_t launch_preprocess(const ViewSet& vs, const float* sh, int sh_degree, int mode, const Work& w,
+                              cudaStream_t st)
 {
-    if (vs.n == 0 || vs.V == 0) return cudaSuccess;
-    dim3 grid((vs.n + 255) / 256, vs.V);
+    if (vs.nmax == 0 || vs.V == 0) return cudaSuccess;
+    dim3 grid((vs.nmax + 255) / 256, vs.V);
     if (mode == 0)
-        k_preprocess<0><<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, w);
+        k_preprocess<0><<<grid, 256, 0, st>>>(vs, sh, sh_degree, w);
     else
-        k_preprocess<1><<<grid, 256, 0, st>>>(vs, mo, q, s, sh, sh_degree, w);
+        k_preprocess<1><<<grid, 256, 0, st>>>(vs, sh, sh_degree, w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dref(const ViewSet& vs, const Work& w, int v0, int v1, cudaStream_t st)
 {
-    if (vs.n == 0 || v1 <= v0) return cudaSuccess;
-    dim3 grid((vs.n + 255) / 256, v1 - v0);
+    if (vs.nmax == 0 || v1 <= v0) return cudaSuccess;
+    dim3 grid((vs.nmax + 255) / 256, v1 - v0);
     k_dref<<<grid, 256, 0, st>>>(vs, w, v0);
     return cudaGetLastError();
 }
@@ -470,8 +468,8 @@ cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st)
 
 cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st)
 {
-    if (vs.n == 0 || vs.V == 0) return cudaSuccess;
-    dim3 grid((vs.n + 255) / 256, vs.V);
+    if (vs.nmax == 0 || vs.V == 0) return cudaSuccess;
+    dim3 grid((vs.nmax + 255) / 256, vs.V);
     k_scatter<<<grid, 256, 0, st>>>(vs, w);
     return cudaGetLastError();
 }
@@ -482,7 +480,7 @@ cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
     // tile_fill is free once the pairs are scattered: it holds the long-list tiles
     k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill,
                                                    &w.dstatus[3]);
-    k_tile_sort<<<256, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
+    k_tile_sort<<<64, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
                                               &w.dstatus[3]);
     return cudaGetLastError();
 }

@@ -13,7 +13,8 @@ constexpr int kTilePx = kTile * kTile;    // threads per raster CTA
 // Per-tile atomic counters sit 128 bytes apart: one L2 line (one slice) each, so
 // the atomics of neighbouring hot tiles do not queue behind one another.
 constexpr int kCounterStride = 32;
-constexpr int kMaxViews = TSP_MAX_VIEWS;
+constexpr int kMaxViews = TSP_MAX_BATCH_VIEWS;   // view slots of one launch, all frames
+constexpr int kMaxFrames = TSP_MAX_FRAMES;
 
 struct DevCam {
     int W, H;
@@ -22,17 +23,39 @@ struct DevCam {
     float t[3];
 };
 
-// Everything a kernel needs to know about the views of one call.  Passed by value
-// as a kernel parameter (about 3.3 KB), so no host->device copy is needed.
+// Everything a kernel needs to know about the frames and views of one launch.
+// Passed by value as a kernel parameter (about 16 KB, under the 32 KB limit), so
+// no host->device copy is needed.  Views of all frames are numbered together;
+// view v belongs to frame vframe[v], whose vn[v] Gaussians have their records
+// (view, Gaussian) at vrec[v] + g.
 struct ViewSet {
-    int V;
-    int n;
+    int V;                                // view slots (all frames)
+    int F;                                // frames
+    int nmax;                             // largest Gaussian count of a frame
     DevCam cam[kMaxViews];
     int tiles_x[kMaxViews];
     int tiles_y[kMaxViews];
     uint32_t toff[kMaxViews + 1];         // first global tile id of each view
     const float2* disp[kMaxViews];
     const uint8_t* vis[kMaxViews];
+    int vframe[kMaxViews];
+    int vn[kMaxViews];
+    unsigned long long vrec[kMaxViews];
+    int fview[kMaxFrames + 1];            // first view of each frame
+    int fn[kMaxFrames];                   // Gaussians of each frame
+    const float4* fmo[kMaxFrames];        // means + opacity, quaternions, scales
+    const float4* fq[kMaxFrames];
+    const float4* fs[kMaxFrames];
+};
+
+// Per-frame outputs of the motion fit (optional members may be null).
+struct FrameOut {
+    float4* means[kMaxFrames];
+    float4* quats[kMaxFrames];
+    float4* scales[kMaxFrames];
+    uint32_t* status[kMaxFrames];
+    float* view_affine[kMaxFrames];       // [views of the frame][n][6]
+    uint32_t* view_flags[kMaxFrames];     // [views of the frame][n]
 };
 
 // Per-view output images of the colour render.
@@ -41,21 +64,22 @@ struct RenderOut {
     float* T[kMaxViews];
 };
 
-// Workspace pointers (device), owned by the context.
+// Workspace pointers (device), owned by the context.  Per-record arrays hold one
+// entry per (view, Gaussian) of every frame ([R] below, R = sum of views x n).
 struct Work {
-    short4* rect;          // [V*n] tile rect x0 y0 x1 y1
-    uint32_t* depth;       // [V*n] FP32 depth bits
-    uint32_t* touched;     // [V*n]
-    float4* geom0;         // [V*n] mu - rect origin (x, y), i11, k  (blend factor form)
-    float4* geom1;         // [V*n] i22, opacity, moment origin - mu (x, y)
-    float2* dref;          // [V*n] reference displacement (track at the moment origin)
-    uint32_t* oref;        // [V*n] pixel index of the moment origin (fit mode)
-    float4* color;         // [V*n] render colour
-    float4* moments;       // [V*n*4] 16 floats per (view, Gaussian)
-    float4* vres0;         // [V*n] mu'_x, mu'_y, shift c_x, c_y
-    float4* vres1;         // [V*n] B00, B01, B02, sum w   (Sigma_2D' = B B^T, B = A V)
-    float4* vres3;         // [V*n] B10, B11, B12, 0
-    uint2* vres2;          // [V*n] view flags, pixels
+    short4* rect;          // [R] tile rect x0 y0 x1 y1
+    uint32_t* depth;       // [R] FP32 depth bits
+    uint32_t* touched;     // [R]
+    float4* geom0;         // [R] mu - rect origin (x, y), i11, k  (blend factor form)
+    float4* geom1;         // [R] i22, opacity, moment origin - mu (x, y)
+    float2* dref;          // [R] reference displacement (track at the moment origin)
+    uint32_t* oref;        // [R] pixel index of the moment origin (fit mode)
+    float4* color;         // [R] render colour
+    float4* moments;       // [R*4] 16 floats per (view, Gaussian)
+    float4* vres0;         // [R] mu'_x, mu'_y, shift c_x, c_y
+    float4* vres1;         // [R] B00, B01, B02, sum w   (Sigma_2D' = B B^T, B = A V)
+    float4* vres3;         // [R] B10, B11, B12, 0
+    uint2* vres2;          // [R] view flags, pixels
     uint32_t* tile_count;  // [NT * kCounterStride], tile t at t * kCounterStride
     uint32_t* tile_fill;   // [NT * kCounterStride] likewise; after the scatter: long-list tiles
     uint32_t* tile_off;    // [NT+1]
@@ -275,8 +299,12 @@ __device__ __forceinline__ float3 blend_factor(const KeyProj& p)
 
 __device__ __forceinline__ void view_of_tile(const ViewSet& vs, uint32_t tile, int& v, int& tx, int& ty)
 {
-    v = 0;
-    while (v + 1 < vs.V && tile >= vs.toff[v + 1]) ++v;
+    int lo = 0, hi = vs.V - 1;                 // last view whose first tile is <= tile
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vs.toff[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    v = lo;
     const uint32_t local = tile - vs.toff[v];
     tx = (int)(local % (uint32_t)vs.tiles_x[v]);
     ty = (int)(local / (uint32_t)vs.tiles_x[v]);

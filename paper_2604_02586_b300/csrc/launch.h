@@ -5,10 +5,9 @@
 
 namespace tsp {
 
-// a1: project every (view, Gaussian), zero its moment record, count tiles.
-// mode 0 = motion fit, 1 = render (also evaluates colour from sh).
-cudaError_t launch_preprocess(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
-                              const float* sh, int sh_degree, int mode, const Work& w,
+// a1: project every (view, Gaussian) of every frame, zero its moment record,
+// count tiles.  mode 0 = motion fit, 1 = render (one frame; colour from sh).
+cudaError_t launch_preprocess(const ViewSet& vs, const float* sh, int sh_degree, int mode, const Work& w,
                               cudaStream_t st);
 // a1 (fit mode): reference displacement of views [v0, v1) -- the track at each
 // record's moment origin.  Needs those views' tracks; the other steps of a1-a4 do not.
@@ -27,12 +26,10 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
 cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
                                  float* const* final_T, cudaStream_t st);
 // a6: per-view discard tests, affine solve, Eq. 2.
-cudaError_t launch_view_solve(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
-                              const FitParams& fp, const Work& w, float* view_affine,
-                              uint32_t* view_flags, cudaStream_t st);
-// a7-a9: triangulation, covariance fit, eigen decomposition and outputs.
-cudaError_t launch_multiview(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
-                             const FitParams& fp, const Work& w, float4* out_means, float4* out_quats,
-                             float4* out_scales, uint32_t* out_status, cudaStream_t st);
+cudaError_t launch_view_solve(const ViewSet& vs, const FitParams& fp, const Work& w, const FrameOut& fo,
+                              cudaStream_t st);
+// a7-a9: triangulation, covariance fit, eigen decomposition and outputs, per frame.
+cudaError_t launch_multiview(const ViewSet& vs, const FitParams& fp, const Work& w, const FrameOut& fo,
+                             cudaStream_t st);
 
 }  // namespace tsp

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bxo = (warp & 1) * 8, byo = (warp >> 1) * BH;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const size_t vbase = (size_t)v * vs.n;
+    const size_t vbase = (size_t)vs.vrec[v];
 
     float T[P], ddx[P], ddy[P], yc[P];
     bool done[P], vis[P], stat[P];
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bxo = (warp & 1) * 8, byo = (warp >> 1) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const size_t vbase = (size_t)v * vs.n;
+    const size_t vbase = (size_t)vs.vrec[v];
     float* const Wb = s_W[warp];
 
     float T[2];
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
     const float by0 = (float)((warp >> 1) * 4) + 0.5f, by1 = by0 + 3.0f;
     float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
     bool done = !inside;
-    const size_t vbase = (size_t)v * vs.n;
+    const size_t vbase = (size_t)vs.vrec[v];
     for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
         const int nb = (int)min((uint32_t)kBatch, end - b0);
         if (tid < nb) {
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
 cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t tile_base, uint32_t ntiles,
                                      bool stats, int variant, cudaStream_t st)
 {
-    if (ntiles == 0 || vs.n == 0) return cudaSuccess;
+    if (ntiles == 0 || vs.nmax == 0) return cudaSuccess;
     const uint32_t NT = ntiles, tb = tile_base;
     if (variant == 0) {
         // seven 28.5 KB CTAs per SM need the largest shared-memory carveout

@@ -33,16 +33,18 @@ namespace {
 //   vres1 = (B00, B01, B02, sum w), vres3 = (B10, B11, B12, 0) with Sigma_2D' = B B^T,
 //   vres2 = (flags, pixels).
 
-__global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const float4* __restrict__ mo,
-                                                    const float4* __restrict__ q,
-                                                    const float4* __restrict__ s, const FitParams fp,
-                                                    const Work w, float* __restrict__ view_affine,
-                                                    uint32_t* __restrict__ view_flags)
+__global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const FitParams fp, const Work w,
+                                                    const FrameOut fo)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
-    if (g >= vs.n) return;
-    const size_t i = (size_t)v * vs.n + g;
+    const int n = vs.vn[v];
+    if (g >= n) return;
+    const size_t i = (size_t)vs.vrec[v] + g;
+    const int f = vs.vframe[v];
+    const float4* __restrict__ mo = vs.fmo[f];
+    const float4* __restrict__ q = vs.fq[f];
+    const float4* __restrict__ s = vs.fs[f];
     uint32_t flags = 0;
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(0.f, 0.f, 0.f, 0.f);
     float A00 = 0.f, A01 = 0.f, A10 = 0.f, A11 = 0.f, b0 = 0.f, b1 = 0.f;
@@ -114,9 +116,11 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const floa
     w.vres0[i] = r0;
     w.vres1[i] = r1;
     w.vres2[i] = make_uint2(flags, (uint32_t)npix);
-    if (view_flags) view_flags[i] = flags;
-    if (view_affine) {
-        float* a = view_affine + 6 * i;
+    // per-frame outputs: [views of the frame][n]
+    const size_t fi = (size_t)(v - vs.fview[f]) * n + g;
+    if (fo.view_flags[f]) fo.view_flags[f][fi] = flags;
+    if (fo.view_affine[f]) {
+        float* a = fo.view_affine[f] + 6 * fi;
         a[0] = A00; a[1] = A01; a[2] = A10; a[3] = A11; a[4] = b0; a[5] = b1;
     }
 }
@@ -364,24 +368,27 @@ __device__ __forceinline__ void quat_of(const float (&R)[3][3], float (&q)[4])
     }
 }
 
-__global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float4* __restrict__ mo,
-                                                   const float4* __restrict__ qin,
-                                                   const float4* __restrict__ sin_, const FitParams fp,
-                                                   const Work w, float4* __restrict__ om,
-                                                   float4* __restrict__ oq, float4* __restrict__ os,
-                                                   uint32_t* __restrict__ ost)
+// grid (ceil(nmax/128), F): one thread per Gaussian of frame blockIdx.y, over the
+// frame's views [fview[f], fview[f+1]).
+__global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitParams fp, const Work w,
+                                                   const FrameOut fo)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= vs.n) return;
-    const int n = vs.n;
-    const float4 m = mo[g], qi = qin[g], si = sin_[g];
+    const int f = blockIdx.y;
+    if (g >= vs.fn[f]) return;
+    const int v0 = vs.fview[f], v1 = vs.fview[f + 1];
+    float4* __restrict__ om = fo.means[f];
+    float4* __restrict__ oq = fo.quats[f];
+    float4* __restrict__ os = fo.scales[f];
+    uint32_t* __restrict__ ost = fo.status[f];
+    const float4 m = vs.fmo[f][g], qi = vs.fq[f][g], si = vs.fs[f][g];
     int nv = 0;
     float sw = 0.f, npx = 0.f;
-    for (int v = 0; v < vs.V; ++v) {
-        const uint2 f = w.vres2[(size_t)v * n + g];
+    for (int v = v0; v < v1; ++v) {
+        const uint2 f = w.vres2[(size_t)vs.vrec[v] + g];
         if (f.x & TSP_VIEW_OK) {
             ++nv;
-            sw += w.vres1[(size_t)v * n + g].w;
+            sw += w.vres1[(size_t)vs.vrec[v] + g].w;
             npx += (float)f.y;
         }
     }
@@ -398,8 +405,8 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float
     // ---- a7 triangulation about the old mean
     float N00 = 0.f, N01 = 0.f, N02 = 0.f, N11 = 0.f, N12 = 0.f, N22 = 0.f;
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-    for (int v = 0; v < vs.V; ++v) {
-        const size_t i = (size_t)v * n + g;
+    for (int v = v0; v < v1; ++v) {
+        const size_t i = (size_t)vs.vrec[v] + g;
         if (!(w.vres2[i].x & TSP_VIEW_OK)) continue;
         const DevCam& c = vs.cam[v];
         const float4 a = w.vres0[i];
@@ -435,8 +442,8 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float
     for (int u = 0; u < 21; ++u) { Ah[u] = 0.f; Al[u] = 0.f; }
 #pragma unroll
     for (int u = 0; u < 6; ++u) { bh[u] = 0.f; bl[u] = 0.f; }
-    for (int v = 0; v < vs.V; ++v) {
-        const size_t i = (size_t)v * n + g;
+    for (int v = v0; v < v1; ++v) {
+        const size_t i = (size_t)vs.vrec[v] + g;
         if (!(w.vres2[i].x & TSP_VIEW_OK)) continue;
         const DevCam& c = vs.cam[v];
         const float p0 = fmaf(c.R[0], X0, fmaf(c.R[1], X1, fmaf(c.R[2], X2, c.t[0])));
@@ -550,23 +557,21 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const float
 
 }  // namespace
 
-cudaError_t launch_view_solve(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
-                              const FitParams& fp, const Work& w, float* view_affine,
-                              uint32_t* view_flags, cudaStream_t st)
+cudaError_t launch_view_solve(const ViewSet& vs, const FitParams& fp, const Work& w, const FrameOut& fo,
+                              cudaStream_t st)
 {
-    if (vs.n == 0 || vs.V == 0) return cudaSuccess;
-    dim3 grid((vs.n + 255) / 256, vs.V);
-    k_view_solve<<<grid, 256, 0, st>>>(vs, mo, q, s, fp, w, view_affine, view_flags);
+    if (vs.nmax == 0 || vs.V == 0) return cudaSuccess;
+    dim3 grid((vs.nmax + 255) / 256, vs.V);
+    k_view_solve<<<grid, 256, 0, st>>>(vs, fp, w, fo);
     return cudaGetLastError();
 }
 
-cudaError_t launch_multiview(const ViewSet& vs, const float4* mo, const float4* q, const float4* s,
-                             const FitParams& fp, const Work& w, float4* out_means, float4* out_quats,
-                             float4* out_scales, uint32_t* out_status, cudaStream_t st)
+cudaError_t launch_multiview(const ViewSet& vs, const FitParams& fp, const Work& w, const FrameOut& fo,
+                             cudaStream_t st)
 {
-    if (vs.n == 0) return cudaSuccess;
-    k_multiview<<<(vs.n + 127) / 128, 128, 0, st>>>(vs, mo, q, s, fp, w, out_means, out_quats,
-                                                     out_scales, out_status);
+    if (vs.nmax == 0 || vs.F == 0) return cudaSuccess;
+    dim3 grid((vs.nmax + 127) / 128, vs.F);
+    k_multiview<<<grid, 128, 0, st>>>(vs, fp, w, fo);
     return cudaGetLastError();
 }
 

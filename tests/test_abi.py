@@ -67,10 +67,28 @@ def test_create_without_gpu_fails_cleanly(L):
     assert L.tsp_create(-1, None, C.byref(h)) == tsp.TSP.ERR_INVALID_ARG
 
 
-def test_struct_layouts_match_header():
-    # sizes implied by the header's field lists (no padding surprises)
-    assert C.sizeof(tsp.Camera) == 72
-    assert C.sizeof(tsp.Gaussians) == 32
-    assert C.sizeof(tsp.ViewTracks) == 16
-    assert C.sizeof(tsp.Result) == 56
-    assert C.sizeof(tsp.Options) == 72
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that a C
+    compiler gives the header's structure (gcc, compiled here)."""
+    import subprocess
+    pairs = {"tsp_camera": tsp.Camera, "tsp_gaussians": tsp.Gaussians, "tsp_view_tracks": tsp.ViewTracks,
+             "tsp_result": tsp.Result, "tsp_frame": tsp.Frame, "tsp_options": tsp.Options}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tsplat.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, val = ln.split()
+        got[(cname, field)] = int(val)
+    for cname, py in pairs.items():
+        assert C.sizeof(py) == got[(cname, "size")], cname
+        for fname, _ in py._fields_:
+            assert getattr(py, fname).offset == got[(cname, fname)], (cname, fname)

@@ -1,0 +1,126 @@
+"""tsp_fit_motion_batch: frame pairs of uneven sizes in one launch of each step
+(Sec. 4.6: frame pairs are independent units), through the C ABI (needs a B300).
+
+Each frame of a batch must meet the single-frame bar against the FP64 oracle:
+its tile lists bit-exactly (the batch numbers the tiles of all frames together),
+its fitted Gaussians within the motion-fit tolerances; and it must agree with the
+same frame solved alone (statuses equal, values within the tolerances: only the
+order of the floating-point atomic additions differs).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import parity as P
+from tests.test_parity_gpu import check_fitted, POS_TOL, SCALE_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu_ready():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_02586_b300 import build as tbuild
+    tbuild.build()
+    return True
+
+
+def scenes():
+    return [synth.make_scene("tiny", 11, n=1500),
+            synth.make_scene("capture", 12, n=6000, views=5, width=320, height=240, focal=240.0),
+            synth.make_scene("tiny", 13, n=700, views=3, width=100, height=70, focal=80.0)]
+
+
+def frame_args(s, **kw):
+    d = P.to_device(s)
+    return dict(means_opacity=d["means_opacity"], quats=d["quats"], scales=d["scales"], cams=s,
+                disp=d["disp"], vis=d["vis"], **kw)
+
+
+def host(out):
+    r = {k: v.cpu().numpy() for k, v in out.items()}
+    r["status"] = r["status"].view(np.uint32)
+    if "view_flags" in r:
+        r["view_flags"] = r["view_flags"].view(np.uint32)
+    return r
+
+
+@pytest.fixture(scope="module")
+def batch(gpu_ready):
+    import torch
+    import paper_2604_02586_b300 as tsp
+    ss = scenes()
+    with tsp.Context(0) as ctx:
+        outs = ctx.fit_motion_batch([frame_args(s, view_flags=True) for s in ss], sync=True)
+        torch.cuda.synchronize()
+        T = tsp.TSP
+        inter = dict(tile_off=ctx.inspect(T.I_TILE_OFFSETS), pairs=ctx.inspect(T.I_PAIRS),
+                     counts=ctx.inspect(T.I_COUNTS))
+        alone = []
+        for s in ss:
+            alone.append(host(ctx.fit_motion(**frame_args(s, view_flags=True), sync=True)))
+    return ss, [host(o) for o in outs], alone, inter
+
+
+def test_batch_tile_lists_bit_exact_per_frame(batch):
+    ss, _, _, inter = batch
+    off_all = inter["tile_off"].astype(np.int64)
+    pairs = inter["pairs"]
+    t0, total = 0, 0
+    for s in ss:
+        off, ent = oracle.bin_lists(s)
+        nt = len(off) - 1
+        seg = off_all[t0:t0 + nt + 1]
+        assert np.array_equal(seg - seg[0], off)
+        assert np.array_equal(pairs[seg[0]:seg[-1]], ent)
+        t0 += nt
+        total += len(ent)
+    assert int(inter["counts"][0]) == total and int(inter["counts"][3]) == 0
+
+
+def test_batch_frames_meet_the_oracle_bar(batch):
+    ss, outs, _, _ = batch
+    for s, g in zip(ss, outs):
+        o = oracle.fit_motion(s)
+        check_fitted(s, g, o, P.sensitivity(s, o))
+
+
+def test_batch_frames_equal_frames_alone(batch):
+    ss, outs, alone, _ = batch
+    for s, b, a in zip(ss, outs, alone):
+        assert (b["status"] == a["status"]).mean() > 0.999
+        both = ((b["status"] & 1) > 0) & ((a["status"] & 1) > 0)
+        dp = np.linalg.norm(b["means"][both, :3] - a["means"][both, :3], axis=1) / s.extent
+        assert dp.max() < POS_TOL
+        assert (b["view_flags"] == a["view_flags"]).mean() > 0.999
+
+
+def test_batch_with_empty_and_viewless_frames(gpu_ready):
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s = synth.make_scene("tiny", 14, n=400)
+    viewless = frame_args(s.subset_views([]))
+    empty = frame_args(s)
+    for k in ("means_opacity", "quats", "scales"):
+        empty[k] = empty[k][:0]
+    with tsp.Context(0) as ctx:
+        outs = ctx.fit_motion_batch([empty, frame_args(s), viewless], sync=True)
+        ref = ctx.fit_motion(**frame_args(s), sync=True)
+    assert outs[0]["means"].shape[0] == 0
+    st = outs[2]["status"].cpu().numpy().view(np.uint32)
+    assert np.all(st & oracle.OS_FEW_VIEWS) and not np.any(st & oracle.OS_POS_OK)
+    assert torch.equal(outs[2]["means"], viewless["means_opacity"])
+    assert (outs[1]["status"] == ref["status"]).float().mean().item() > 0.999
+
+
+def test_batch_limits_are_enforced(gpu_ready):
+    import paper_2604_02586_b300 as tsp
+    s = synth.make_scene("tiny", 15, n=50, views=32, width=32, height=32, focal=32.0)
+    with tsp.Context(0) as ctx:
+        with pytest.raises(tsp.TspError):
+            ctx.fit_motion_batch([frame_args(s)] * 5)        # 160 views > 128
+        with pytest.raises(tsp.TspError):
+            ctx.fit_motion_batch([frame_args(synth.make_scene("tiny", 16, n=20))] * 17)   # 17 frames
