@@ -37,7 +37,7 @@ extern "C" {
 #define TSP_VERSION 1
 #define TSP_MAX_VIEWS 32          /* views of one frame                                */
 #define TSP_MAX_FRAMES 16         /* frames of one tsp_fit_motion_batch call           */
-#define TSP_MAX_BATCH_VIEWS 128   /* views of all frames of one tsp_fit_motion_batch   */
+#define TSP_MAX_BATCH_VIEWS 192   /* views of all frames of one tsp_fit_motion_batch   */
 #define TSP_MAX_IMAGE 8192
 
 typedef enum {
@@ -141,6 +141,8 @@ typedef struct tsp_options {
                                 /*    for measurement only), see TSP_I_STATS        */
     int32_t raster_variant;     /* a5 kernel: 0 = two-phase (blend, then per-hit */
                                 /*    moment sums; 8x8 warp blocks), the default;  */
+                                /*    5 = the same, persistent: resident CTAs whose */
+                                /*    warps take (tile, block) items from a queue;  */
                                 /*    1, 2, 4 = warp-shuffle reduction with 1, 2, 4 */
                                 /*    pixels per thread (8x4, 8x8, 8x16 blocks)     */
     int64_t pair_capacity;      /* initial (tile, Gaussian) pair capacity, 0 = auto */

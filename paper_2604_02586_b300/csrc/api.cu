@@ -30,7 +30,8 @@ struct tsp_context {
     // per (view, Gaussian)
     Buf rect, depth, touched, geom0, geom1, dref, oref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
-    Buf tiles, tile_off, span_sum;
+    Buf tiles, tile_off, span_sum, queue;
+    int resident_ctas = 0;          // CTAs of the persistent raster resident at once
     // pairs
     Buf pairs, pairs_tmp;
     uint64_t want_pairs = 0;
@@ -147,8 +148,8 @@ tsp_status check_options(tsp_context* ctx, const tsp_options& o)
     if (o.min_px_view < 0 || o.min_views < 0 || o.min_px_total < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "counts must be >= 0");
     if (o.raster_variant != 0 && o.raster_variant != 1 && o.raster_variant != 2 &&
-        o.raster_variant != 4)
-        return fail(ctx, TSP_ERR_INVALID_ARG, "raster_variant must be 0, 1, 2 or 4");
+        o.raster_variant != 4 && o.raster_variant != 5)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "raster_variant must be 0, 1, 2, 4 or 5");
     if (o.pair_capacity < 0 || o.pair_capacity > INT32_MAX || o.budget_bytes < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "bad pair_capacity or budget_bytes");
     return TSP_OK;
@@ -185,7 +186,7 @@ tsp_status make_viewset(tsp_context* ctx, const tsp_frame* frames, int F, ViewSe
         const int Vf = fr.num_views, n = fr.g.n;
         if (Vf < 0 || Vf > TSP_MAX_VIEWS) return fail(ctx, TSP_ERR_INVALID_ARG, "num_views must be in [0, 32]");
         if (V + Vf > TSP_MAX_BATCH_VIEWS)
-            return fail(ctx, TSP_ERR_INVALID_ARG, "more than 128 views in one batch");
+            return fail(ctx, TSP_ERR_INVALID_ARG, "more than 192 views in one batch");
         if (Vf > 0 && !fr.cams) return fail(ctx, TSP_ERR_INVALID_ARG, "cams is NULL");
         if (n < 0) return fail(ctx, TSP_ERR_INVALID_ARG, "n < 0");
         vs.fview[f] = V;
@@ -294,6 +295,7 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     if ((s = ensure(ctx, ctx->tiles, (size_t)2 * (NT + 1) * kCounterStride * 4))) return s;
     if ((s = ensure(ctx, ctx->tile_off, (size_t)(NT + 1) * 4))) return s;
     if ((s = ensure(ctx, ctx->span_sum, ((size_t)NT / 1024 + 2) * 8))) return s;
+    if ((s = ensure(ctx, ctx->queue, 16))) return s;
     uint64_t cap = ctx->want_pairs;
     if (cap == 0) cap = ctx->opt.pair_capacity > 0 ? (uint64_t)ctx->opt.pair_capacity : (uint64_t)8 * vn;
     if (cap < (1u << 16)) cap = 1u << 16;
@@ -320,6 +322,7 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     w.tile_fill = (uint32_t*)ctx->tiles.p + (size_t)(NT + 1) * kCounterStride;
     w.tile_off = (uint32_t*)ctx->tile_off.p;
     w.span_sum = (unsigned long long*)ctx->span_sum.p;
+    w.queue = (uint32_t*)ctx->queue.p;
     w.pairs = (uint64_t*)ctx->pairs.p;
     w.pairs_tmp = (uint64_t*)ctx->pairs_tmp.p;
     const uint64_t have = ctx->pairs.bytes / 8 < ctx->pairs_tmp.bytes / 8 ? ctx->pairs.bytes / 8 : ctx->pairs_tmp.bytes / 8;
@@ -425,7 +428,8 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
         if (ready) TSP_CUDA(cudaStreamWaitEvent(st, ready[k], 0));
         TSP_CUDA(launch_dref(vs, w, v0, v1, st));
         TSP_CUDA(launch_raster_accumulate(vs, w, vs.toff[v0], vs.toff[v1] - vs.toff[v0],
-                                          ctx->opt.collect_stats != 0, ctx->opt.raster_variant, st));
+                                          ctx->opt.collect_stats != 0, ctx->opt.raster_variant,
+                                          ctx->resident_ctas, st));
     }
     TSP_CUDA(mark(ctx, 5, st));
     TSP_CUDA(launch_view_solve(vs, fp, w, fo, st));
@@ -521,6 +525,12 @@ tsp_status tsp_create(int device, const tsp_options* opt, tsp_context** out)
         delete ctx;
         return TSP_ERR_CUDA;
     }
+    if (raster_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        tsp_destroy(ctx);
+        return TSP_ERR_CUDA;
+    }
+    ctx->resident_ctas = raster_resident_ctas(device);
     for (cudaEvent_t& e : ctx->ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
@@ -537,7 +547,7 @@ tsp_status tsp_destroy(tsp_context* ctx)
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->oref, &ctx->color,
-                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum, &ctx->queue,
                   &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
                   &ctx->st_tracks};
     for (Buf* b : all) release(ctx, *b);

@@ -90,6 +90,7 @@ struct Work {
                            //      3 number of tiles whose lists need the long-list sort
     unsigned long long* stats;  // [4] raster work counters (collect_stats only)
     unsigned long long* span_sum; // [ceil(NT / 1024)] tile-count scan scratch
+    uint32_t* queue;       // [1] work-queue head of the persistent raster
 };
 
 struct FitParams {

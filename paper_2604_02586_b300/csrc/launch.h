@@ -20,8 +20,15 @@ cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st);
 cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st);
 // a5: blend and accumulate alpha T weighted track moments per (view, Gaussian), for
 // the ntiles tiles starting at tile_base (tiles are numbered view by view).
+// variant 0: two-phase, one CTA per tile; 5: two-phase persistent over
+// resident_ctas CTAs fed by a device-side queue (w.queue); 1, 2, 4: warp-shuffle
+// reduction with that many pixels per thread.
 cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t tile_base, uint32_t ntiles,
-                                     bool stats, int variant, cudaStream_t st);
+                                     bool stats, int variant, int resident_ctas, cudaStream_t st);
+// One-time kernel attributes of the raster step (shared-memory carveout).
+cudaError_t raster_prepare();
+// CTAs of the persistent raster that fit on the device at once.
+int raster_resident_ctas(int device);
 // render colour and final transmittance.
 cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
                                  float* const* final_T, cudaStream_t st);

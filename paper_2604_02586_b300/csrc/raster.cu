@@ -17,6 +17,8 @@
 // Sums are taken about a per-(view, Gaussian) origin (mu_2D clamped to the image)
 // and displacement reference (the track at that origin), which keeps FP32 sums
 // free of cancellation; a6 undoes both shifts exactly.
+#include <algorithm>
+
 #include "launch.h"
 
 namespace tsp {
@@ -339,28 +341,31 @@ constexpr int kWRow = 17;
 constexpr int kWHalf = 32 * kWRow + 16;
 constexpr int kWWords = kWHalf + 32 * kWRow;
 
-template <bool kStats>
-__global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w,
-                                                                          uint32_t tile_base)
-{
-    constexpr int kNW = 4;
-    __shared__ float4 s_g0[kNW][32];
-    __shared__ float4 s_g1[kNW][32];
-    __shared__ float4 s_hd[kNW][32];        // (origin x, origin y, reference x, reference y)
-    __shared__ uint32_t s_id[kNW][32];
-    __shared__ float s_W[kNW][kWWords];
-    __shared__ float4 s_F[kNW][2][33];      // (d_x, d_y, static, 0) per pixel, halves padded
+// Warp-private shared memory of the two-phase walk.
+struct WarpSmem {
+    float4 g0[32];
+    float4 g1[32];
+    float4 hd[32];                 // (origin x, origin y, reference x, reference y)
+    uint32_t id[32];
+    float W[kWWords];
+    float4 F[2][33];               // (d_x, d_y, static, 0) per pixel, halves padded
+};
 
-    const uint32_t tile = tile_base + blockIdx.x;
+// One warp, one 8x8 block `blk` of tile `tile`: the two-phase walk above.  Work
+// counts (kStats) accumulate in cnt.
+template <bool kStats>
+__device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& w, uint32_t tile, int blk,
+                                                 WarpSmem& sm, unsigned long long (&cnt)[3])
+{
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     if (beg >= end) return;
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int bxo = (warp & 1) * 8, byo = (warp >> 1) * 8;
+    const int lane = threadIdx.x & 31;
+    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
     const size_t vbase = (size_t)vs.vrec[v];
-    float* const Wb = s_W[warp];
+    float* const Wb = sm.W;
 
     float T[2];
     bool done[2], vis[2], stat[2];
@@ -381,15 +386,14 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
         }
         // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
         stat[k] = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
-        s_F[warp][k][lane] = make_float4(ddx, ddy, stat[k] ? 1.f : 0.f, 0.f);
+        sm.F[k][lane] = make_float4(ddx, ddy, stat[k] ? 1.f : 0.f, 0.f);
         yc[k] = (float)ly + 0.5f;
         T[k] = 1.0f;
         done[k] = !inside;
     }
     const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
     const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
-    unsigned long long n_eval = 0, n_blend = 0, n_add = 0;
-    if (kStats && tid == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
+    if (kStats && blk == 0 && lane == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
     // pending hit c is held by lane c: moment record, origin and reference, counts
     int pend = 0;
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] = 0.f;
         const float* Wh = Wb + half * kWHalf + c;
-        const float4* Fh = s_F[warp][half];
+        const float4* Fh = sm.F[half];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             const float wv = Wh[i * kWRow];
@@ -451,10 +455,10 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
                       log2f(255.0f * g1.y) * 1.002f + 1e-4f;
             if (hit) {
                 const float2 rf = w.dref[vbase + g];
-                s_g0[warp][lane] = g0;
-                s_g1[warp][lane] = g1;
-                s_hd[warp][lane] = make_float4(g0.x + g1.z, g0.y + g1.w, rf.x, rf.y);
-                s_id[warp][lane] = g;
+                sm.g0[lane] = g0;
+                sm.g1[lane] = g1;
+                sm.hd[lane] = make_float4(g0.x + g1.z, g0.y + g1.w, rf.x, rf.y);
+                sm.id[lane] = g;
             }
         }
         uint32_t m = __ballot_sync(kFull, hit);
@@ -462,8 +466,8 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
         while (m) {
             const int j = __ffs(m) - 1;
             m &= m - 1;
-            const float4 g0 = s_g0[warp][j];
-            const float4 g1 = s_g1[warp][j];
+            const float4 g0 = sm.g0[j];
+            const float4 g1 = sm.g1[j];
             // both pixels of a lane share the column: ex, z1; the second row is 4 below
             const float ex = xc - g0.x;
             const float z1 = ex * g0.z;
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
                 const bool blend = pass && !term;
                 add[k] = blend && vis[k];
                 Wb[k * kWHalf + lane * kWRow + pend] = add[k] ? alpha * T[k] : 0.f;
-                if (kStats) { n_eval += !done[k]; n_blend += blend; n_add += add[k]; }
+                if (kStats) { cnt[0] += !done[k]; cnt[1] += blend; cnt[2] += add[k]; }
                 T[k] = blend ? Tn : T[k];
                 done[k] = done[k] || term;
             }
@@ -491,8 +495,8 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
             const int ns = __popc(__ballot_sync(kFull, add[0] && stat[0])) +
                            __popc(__ballot_sync(kFull, add[1] && stat[1]));
             if (lane == pend) {
-                h_id = s_id[warp][j];
-                h_hd = s_hd[warp][j];
+                h_id = sm.id[j];
+                h_hd = sm.hd[j];
                 h_np = (float)np;
                 h_ns = (float)ns;
             }
@@ -504,10 +508,49 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
         __syncwarp();                                  // staging is rewritten next
     }
     if (pend) phase2(pend);
+}
+
+// Grid form: one CTA per tile, warp w takes block w.
+template <bool kStats>
+__global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w,
+                                                                          uint32_t tile_base)
+{
+    __shared__ WarpSmem sm[4];
+    const int warp = threadIdx.x >> 5;
+    unsigned long long cnt[3] = {0ull, 0ull, 0ull};
+    accumulate_block<kStats>(vs, w, tile_base + blockIdx.x, warp, sm[warp], cnt);
     if (kStats) {
-        atomicAdd(&w.stats[0], n_eval);
-        atomicAdd(&w.stats[1], n_blend);
-        atomicAdd(&w.stats[2], n_add);
+        atomicAdd(&w.stats[0], cnt[0]);
+        atomicAdd(&w.stats[1], cnt[1]);
+        atomicAdd(&w.stats[2], cnt[2]);
+    }
+}
+
+// Persistent form: a grid sized to the resident CTAs, each warp taking
+// (tile, block) items from a device-side queue (one atomic per item, ascending
+// tile order) until none are left.  Warps never wait for one another and no
+// CTA is launched per tile.
+template <bool kStats>
+__global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(const ViewSet vs, const Work w,
+                                                                                     uint32_t tile_base,
+                                                                                     uint32_t ntiles,
+                                                                                     uint32_t* queue)
+{
+    __shared__ WarpSmem sm[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long cnt[3] = {0ull, 0ull, 0ull};
+    const uint32_t items = 4u * ntiles;
+    for (;;) {
+        uint32_t item = 0u;
+        if (lane == 0) item = atomicAdd(queue, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= items) break;
+        accumulate_block<kStats>(vs, w, tile_base + (item >> 2), (int)(item & 3u), sm[warp], cnt);
+    }
+    if (kStats) {
+        atomicAdd(&w.stats[0], cnt[0]);
+        atomicAdd(&w.stats[1], cnt[1]);
+        atomicAdd(&w.stats[2], cnt[2]);
     }
 }
 
@@ -576,17 +619,35 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
 
 }  // namespace
 
+cudaError_t raster_prepare()
+{
+    // up to seven 28.5 KB CTAs per SM need the largest shared-memory carveout; set
+    // once per context, outside any stream capture
+    const void* kerns[] = {(const void*)k_raster_accumulate_2p<false>, (const void*)k_raster_accumulate_2p<true>,
+                           (const void*)k_raster_accumulate_2p_persistent<false>,
+                           (const void*)k_raster_accumulate_2p_persistent<true>};
+    for (const void* k : kerns) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                   (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t tile_base, uint32_t ntiles,
-                                     bool stats, int variant, cudaStream_t st)
+                                     bool stats, int variant, int resident_ctas, cudaStream_t st)
 {
     if (ntiles == 0 || vs.nmax == 0) return cudaSuccess;
     const uint32_t NT = ntiles, tb = tile_base;
     if (variant == 0) {
-        // seven 28.5 KB CTAs per SM need the largest shared-memory carveout
-        auto kern = stats ? k_raster_accumulate_2p<true> : k_raster_accumulate_2p<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-        kern<<<NT, 128, 0, st>>>(vs, w, tb);
+        if (stats) k_raster_accumulate_2p<true><<<NT, 128, 0, st>>>(vs, w, tb);
+        else k_raster_accumulate_2p<false><<<NT, 128, 0, st>>>(vs, w, tb);
+    } else if (variant == 5) {
+        const cudaError_t e = cudaMemsetAsync(w.queue, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+        const uint32_t grid = (uint32_t)std::max<long long>(1, std::min<long long>(resident_ctas, (long long)NT));
+        if (stats) k_raster_accumulate_2p_persistent<true><<<grid, 128, 0, st>>>(vs, w, tb, NT, w.queue);
+        else k_raster_accumulate_2p_persistent<false><<<grid, 128, 0, st>>>(vs, w, tb, NT, w.queue);
     } else if (variant == 1) {
         if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w, tb);
         else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w, tb);
@@ -598,6 +659,18 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
         else k_raster_accumulate<2, false><<<NT, kTilePx / 2, 0, st>>>(vs, w, tb);
     }
     return cudaGetLastError();
+}
+
+int raster_resident_ctas(int device)
+{
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_accumulate_2p_persistent<false>, 128, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 148 * 4;
+    }
+    return std::max(1, sms * std::max(1, per_sm));
 }
 
 cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,

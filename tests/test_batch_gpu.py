@@ -121,6 +121,52 @@ def test_batch_limits_are_enforced(gpu_ready):
     s = synth.make_scene("tiny", 15, n=50, views=32, width=32, height=32, focal=32.0)
     with tsp.Context(0) as ctx:
         with pytest.raises(tsp.TspError):
-            ctx.fit_motion_batch([frame_args(s)] * 5)        # 160 views > 128
+            ctx.fit_motion_batch([frame_args(s)] * 7)        # 224 views > 192
         with pytest.raises(tsp.TspError):
             ctx.fit_motion_batch([frame_args(synth.make_scene("tiny", 16, n=20))] * 17)   # 17 frames
+
+
+def test_batch_replays_from_a_cuda_graph(gpu_ready):
+    """The batch call enqueues no host synchronisation and no allocation once its
+    workspace is sized (asynchronous pair counting), so it can be captured in a
+    CUDA graph; a replay after the tracks change in place gives what a direct
+    call on the changed tracks gives."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    ss = scenes()
+    args = [frame_args(s) for s in ss]
+    with tsp.Context(0) as probe:
+        probe.fit_motion_batch(args, sync=True)
+        K = int(probe.inspect(tsp.TSP.I_COUNTS)[0])
+    for variant in (0, 5):
+        with tsp.Context(0, async_pairs=1, pair_capacity=2 * K, raster_variant=variant) as ctx:
+            outs = ctx.fit_motion_batch(args, sync=True)           # sizes the workspace
+            for a, o in zip(args, outs):
+                a["out"] = o
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                ctx.fit_motion_batch(args)                        # warm-up on the capture stream
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                ctx.fit_motion_batch(args)
+            for a in args:                                        # new tracks, same buffers
+                for d in a["disp"]:
+                    d.mul_(0.5)
+            graph.replay()
+            torch.cuda.synchronize()
+            got = [host(o) for o in outs]
+            ctx.sync()
+            direct = [host(o) for o in ctx.fit_motion_batch([{k: v for k, v in a.items() if k != "out"}
+                                                             for a in args], sync=True)]
+            for s, g, d in zip(ss, got, direct):
+                assert (g["status"] == d["status"]).mean() > 0.999
+                both = ((g["status"] & 1) > 0) & ((d["status"] & 1) > 0)
+                dp = np.linalg.norm(g["means"][both, :3] - d["means"][both, :3], axis=1) / s.extent
+                assert dp.max() < POS_TOL
+        for a in args:                                            # restore for the next variant
+            a.pop("out", None)
+            for d in a["disp"]:
+                d.mul_(2.0)

@@ -143,11 +143,11 @@ def test_moments(gpu_ready, name):
     check_moments(o, g)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 4])
+@pytest.mark.parametrize("variant", [1, 2, 4, 5])
 @pytest.mark.parametrize("name", ["tiny", "capture_sub"])
 def test_raster_variants(gpu_ready, name, variant):
-    """The warp-shuffle raster kernels (8x4, 8x8 and 8x16 warp blocks) meet the
-    same bar as the default two-phase one.  Their summation order and exponential
+    """The warp-shuffle raster kernels (8x4, 8x8 and 8x16 warp blocks) and the
+    persistent two-phase kernel meet the same bar as the default two-phase one.  Their summation order and exponential
     differ, so pixel counts may differ only by blend decisions that the oracle
     records as lying inside the FP32 window (each side within that count of it)."""
     s, g2, o, sens = case(name)
