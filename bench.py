@@ -40,9 +40,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--preset", default="capture", choices=["capture", "tiny"],
+    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch"],
                     help="capture: 200k Gaussians x 18 views at 1352x1014 (the metric's workload); "
-                         "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound)")
+                         "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound); "
+                         "batch: 8 uneven frame pairs, batched vs one at a time")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
@@ -358,9 +359,123 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+def batch_scenes(seed=31, frames=8):
+    """Eight frame pairs of uneven size: 50k-300k Gaussians, 12-24 views, each at
+    1352x1014 (f = 1000) or 640x360 (f = 473), one rigid motion per frame."""
+    import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(frames):
+        n = int(rng.integers(50_000, 300_001))
+        V = int(rng.integers(12, 25))
+        W, H, f = (1352, 1014, 1000.0) if rng.random() < 0.5 else (640, 360, 473.0)
+        out.append(synth.make_scene("frame", seed=seed * 100 + k, n=n, views=V, width=W, height=H, focal=f))
+    return out
+
+
+def small_scenes(seed=41, frames=8):
+    """Eight small frame pairs (2k-20k Gaussians, 4-8 views at 320x240): the
+    launch-bound regime where one launch per step for all frames matters."""
+    import synth
+    rng = np.random.default_rng(seed)
+    return [synth.make_scene("frame", seed=seed * 100 + k, n=int(rng.integers(2_000, 20_001)),
+                             views=int(rng.integers(4, 9)), width=320, height=240, focal=240.0)
+            for k in range(frames)]
+
+
+def run_batch(a):
+    """Batched frame pairs against the one-at-a-time path: the same eight frames
+    solved by eight tsp_fit_motion calls, by one tsp_fit_motion_batch call, and
+    by a CUDA-graph replay of that call (raster kernel picked by the autotuner),
+    for the batch configuration and for eight small frames."""
+    import torch
+    from paper_2604_02586_b300 import build as tbuild
+    tbuild.build()
+    torch.cuda.set_device(0)
+    line = measure_batch(a, batch_scenes(), "Gaussian·view track fits/s, 8 uneven frame pairs in one batched graph launch")
+    small = measure_batch(a, small_scenes(), "small")
+    line["small_frames"] = {k: small[k] for k in ("value", "ms_per_step", "one_at_a_time", "batched_no_graph",
+                                                   "speedup_vs_one_at_a_time", "status_agreement_with_one_at_a_time")}
+    line["small_frames"]["workload"] = small["config"]["workload"]
+    print(json.dumps(line), flush=True)
+
+
+def measure_batch(a, scenes, metric):
+    import torch
+    import paper_2604_02586_b300 as tsp
+    dev = torch.device("cuda", 0)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    args = [dict(means_opacity=t(s.means_opacity), quats=t(s.quats), scales=t(s.scales), cams=s,
+                 disp=[t(d) for d in s.disp], vis=[t(v) for v in s.vis]) for s in scenes]
+    units = sum(s.n * s.num_views for s in scenes)
+    with tsp.Context(0) as probe:
+        probe.fit_motion_batch(args, sync=True)
+        K = int(probe.inspect(tsp.TSP.I_COUNTS)[0])
+    ctx = tsp.Context(0, async_pairs=1, pair_capacity=int(K * 1.1) + 1024)
+    variant, tune_ms = ctx.autotune(args, repeats=2)
+    outs = ctx.fit_motion_batch(args, sync=True)
+    for x, o in zip(args, outs):
+        x["out"] = o
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        with ClockSampler(0) as clk:
+            for _ in range(a.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        return ms, clk.summary()
+
+    one_ms, _ = timed(lambda: [ctx.fit_motion(**x) for x in args])
+    one_status = [o["status"].clone() for o in outs]
+    bat_ms, _ = timed(lambda: ctx.fit_motion_batch(args))
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        ctx.fit_motion_batch(args)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ctx.fit_motion_batch(args)
+    gr_ms, clocks = timed(graph.replay)
+    ctx.sync()
+    same = float(np.mean([(o["status"] == s0).float().mean().item() for o, s0 in zip(outs, one_status)]))
+    ctx.close()
+    fps = lambda ms: units / (float(np.mean(ms)) / 1e3)
+    line = {"metric": metric,
+            "value": fps(gr_ms), "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": float(np.mean(gr_ms)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "8 frame pairs: " + ", ".join(f"{s.n}x{s.num_views}@{int(s.width[0])}x{int(s.height[0])}"
+                                                             for s in scenes),
+                       "units_per_step": units, "pairs_K": K,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "p50_ms": float(np.percentile(gr_ms, 50)), "p99_ms": float(np.percentile(gr_ms, 99)),
+            "one_at_a_time": {"value": fps(one_ms), "ms_per_step": float(np.mean(one_ms)),
+                              "p50_ms": float(np.percentile(one_ms, 50)), "p99_ms": float(np.percentile(one_ms, 99))},
+            "batched_no_graph": {"value": fps(bat_ms), "ms_per_step": float(np.mean(bat_ms))},
+            "speedup_vs_one_at_a_time": float(np.mean(one_ms)) / float(np.mean(gr_ms)),
+            "status_agreement_with_one_at_a_time": same,
+            "autotune": {"chosen_raster_variant": variant, "raster_ms": tune_ms},
+            "clocks": clocks}
+    return line
+
+
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.preset == "batch":
+        run_batch(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

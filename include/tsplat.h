@@ -189,6 +189,18 @@ tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_ca
  * by frame, view-major within a frame.  Errors as tsp_fit_motion. */
 tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int num_frames, void* stream);
 
+/* Autotuner: runs the motion fit on the given frames (outputs are written) with
+ * each candidate raster kernel -- two-phase with one CTA per tile (variant 0),
+ * two-phase persistent over a work queue (5), warp-shuffle 8x8 blocks (2) --
+ * `repeats` timed times after one warm-up each, and keeps the one whose median
+ * raster time is lowest as the context's raster_variant.  chosen (nullable)
+ * receives it, raster_ms (nullable, [TSP_TUNE_CANDIDATES]) the medians in that
+ * order.  Synchronises the stream.  Errors as tsp_fit_motion_batch; the options
+ * are left unchanged on error. */
+#define TSP_TUNE_CANDIDATES 3
+tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats, void* stream,
+                        int* chosen, float* raster_ms);
+
 /* Same step for callers that hold everything in host memory: g, tracks and out
  * point to host arrays (pinned memory gives full copy speed and lets the copies
  * overlap the computation).  The Gaussians are copied on `stream` and projected,

@@ -83,6 +83,7 @@ def lib():
         L.tsp_fit_motion.argtypes = [P, P, P, I, P, P, P]
         L.tsp_fit_motion_host.argtypes = [P, P, P, I, P, P, P]
         L.tsp_fit_motion_batch.argtypes = [P, P, I, P]
+        L.tsp_autotune.argtypes = [P, P, I, I, P, P, P]
         L.tsp_render.argtypes = [P, P, P, I, P, I, P, P, P]
         L.tsp_sync.argtypes = [P, P, I]
         L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
@@ -96,7 +97,7 @@ def lib():
         L.tsp_last_error.restype = C.c_char_p
         L.tsp_version.restype = I
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
-                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_render", "tsp_sync", "tsp_inspect",
+                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render", "tsp_sync", "tsp_inspect",
                      "tsp_workspace_bytes", "tsp_stage_times"):
             getattr(L, name).restype = I
         _lib = L
@@ -281,6 +282,24 @@ class Context:
         if sync:
             self.sync(stream)
         return [p[5] for p in prep]
+
+    TUNE_CANDIDATES = (0, 5, 2)
+
+    def autotune(self, frames, repeats=3, stream=None):
+        """Time each candidate raster kernel on ``frames`` (fit_motion_batch
+        arguments) and keep the fastest.  Returns (variant, {variant: median ms})."""
+        keys = ("means_opacity", "quats", "scales", "cams", "disp", "vis")
+        prep = [self._frame(*[f[k] for k in keys], f.get("out")) for f in frames]
+        arr = (Frame * max(len(prep), 1))()
+        for k, (g, carr, V, tr, r, _) in enumerate(prep):
+            arr[k].g, arr[k].cams, arr[k].num_views = g, C.cast(carr, C.c_void_p), V
+            arr[k].tracks, arr[k].out = C.cast(tr, C.c_void_p), r
+        chosen = C.c_int(0)
+        ms = (C.c_float * len(self.TUNE_CANDIDATES))()
+        self._check(lib().tsp_autotune(self._h, arr, len(prep), int(repeats), _stream_handle(stream),
+                                       C.byref(chosen), ms), "tsp_autotune")
+        self.opt.raster_variant = chosen.value
+        return chosen.value, dict(zip(self.TUNE_CANDIDATES, [float(x) for x in ms]))
 
     def fit_motion_host(self, means_opacity, quats, scales, cams, disp, vis, out=None, stream=None):
         """Host path: numpy inputs and outputs; copies happen inside the library."""

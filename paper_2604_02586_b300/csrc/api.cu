@@ -52,6 +52,7 @@ struct tsp_context {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kTuneCandidates = 3;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -806,6 +807,47 @@ tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count)
     DeviceGuard dg(ctx->device);
     TSP_CUDA(cudaEventSynchronize(ctx->ev[7]));
     for (int k = 0; k < 7 && k < max_n; ++k) TSP_CUDA(cudaEventElapsedTime(&ms[k], ctx->ev[k], ctx->ev[k + 1]));
+    return TSP_OK;
+}
+
+tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats, void* stream,
+                        int* chosen, float* raster_ms)
+{
+    if (!ctx || repeats < 1 || repeats > 100) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    static const int kCandidates[kTuneCandidates] = {0, 5, 2};
+    const tsp_options saved = ctx->opt;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->opt.stage_timing = 1;
+    ctx->opt.collect_stats = 0;
+    int best_v = saved.raster_variant;
+    float best = 3.0e38f;
+    tsp_status s = TSP_OK;
+    for (int c = 0; c < kTuneCandidates && s == TSP_OK; ++c) {
+        ctx->opt.raster_variant = kCandidates[c];
+        std::vector<float> t;
+        for (int r = 0; r <= repeats && s == TSP_OK; ++r) {        // the first run is a warm-up
+            if ((s = fit_device(ctx, frames, num_frames, st, true))) break;
+            if ((s = tsp_sync(ctx, stream, -1))) break;
+            if (r == 0 || !ctx->timed) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]) != cudaSuccess) {
+                cudaGetLastError();
+                s = fail(ctx, TSP_ERR_CUDA, "cudaEventElapsedTime");
+                break;
+            }
+            t.push_back(ms);
+        }
+        if (s != TSP_OK || t.empty()) break;
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (raster_ms) raster_ms[c] = med;
+        if (med < best) { best = med; best_v = kCandidates[c]; }
+    }
+    ctx->opt = saved;
+    if (s != TSP_OK) return s;
+    ctx->opt.raster_variant = best_v;
+    if (chosen) *chosen = best_v;
     return TSP_OK;
 }
 

@@ -98,6 +98,11 @@ PRESETS = {
     "capture": dict(n=200_000, box=4.0, logs_mu=-5.0, logs_sd=0.7, opacity="beta22",
                     sh_degree=3, views=18, rig="hemisphere", radius=4.0, W=1352, H=1014,
                     f=1000.0, clusters=8, max_deg=30.0, max_trans=0.6, noise=0.5),
+    # one frame of a batch: the capture scene's Gaussians and rig, the tiny preset's
+    # motion (one rigid transform, <= 20 deg, translation <= 0.1 of the box)
+    "frame": dict(n=200_000, box=4.0, logs_mu=-5.0, logs_sd=0.7, opacity="beta22",
+                  sh_degree=3, views=18, rig="hemisphere", radius=4.0, W=1352, H=1014,
+                  f=1000.0, clusters=1, max_deg=20.0, max_trans=0.4, noise=0.5),
 }
 
 

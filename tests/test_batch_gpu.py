@@ -170,3 +170,17 @@ def test_batch_replays_from_a_cuda_graph(gpu_ready):
             a.pop("out", None)
             for d in a["disp"]:
                 d.mul_(2.0)
+
+
+def test_autotune_picks_a_candidate_and_results_hold(gpu_ready):
+    import paper_2604_02586_b300 as tsp
+    ss = scenes()
+    args = [frame_args(s) for s in ss]
+    with tsp.Context(0) as ctx:
+        ref = [host(o) for o in ctx.fit_motion_batch(args, sync=True)]
+        chosen, times = ctx.autotune(args, repeats=2)
+        assert chosen in tsp.Context.TUNE_CANDIDATES
+        assert all(t > 0 for t in times.values()) and times[chosen] == min(times.values())
+        got = [host(o) for o in ctx.fit_motion_batch(args, sync=True)]
+    for g, r in zip(got, ref):
+        assert (g["status"] == r["status"]).mean() > 0.999
