@@ -1,0 +1,292 @@
+"""Request loop for frame-pair motion solves (continuous batching on one GPU).
+
+Requests arrive for scenes; a scene's consecutive frames chain (the Gaussians a
+solve returns are the next frame's input, Sec. 5.1's per-frame pipeline).  The
+server keeps each active scene resident on the device -- its Gaussians and a
+library context whose workspace (sort buffers, moments) is reused frame after
+frame -- and admits waiting requests as slots and device memory free up:
+
+* a request is admitted when its scene has no frame in flight, fewer than
+  ``max_inflight`` requests are on the device, and the estimated device bytes
+  of everything resident plus its tracks stay within ``budget_bytes``; idle
+  scenes are evicted (least recently used first, state copied to host memory)
+  to make room;
+* each scene owns a CUDA stream, so the work of requests admitted while others
+  run overlaps on the device; a scene's frames are serialised on its stream;
+* completion is polled with CUDA events; latency = completion - arrival.
+
+``one_at_a_time`` replays the same arrivals through a single stream, one request
+after the other, as the plain path to compare against.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import Context, TSP, TspError
+
+
+def _to_device(a, dev):
+    # host numpy arrays or (preferably pinned) CPU tensors; pinned sources copy
+    # asynchronously on the current stream
+    import torch
+    t = a if isinstance(a, torch.Tensor) else torch.from_numpy(a)
+    return t.to(dev, non_blocking=True)
+
+
+@dataclasses.dataclass
+class Request:
+    """One frame pair of a scene: host (pinned) tracks for each of its views."""
+    rid: int
+    scene: str
+    cams: object                 # object with width/height/fx/fy/cx/cy/R/t per view
+    disp: list                   # host float32 [H, W, 2] per view (numpy or pinned tensor)
+    vis: list                    # host uint8 [H, W] per view
+    arrival: float = 0.0         # seconds, relative to the start of the run
+    start: float = 0.0
+    done: float = 0.0
+    inputs: dict | None = None   # device Gaussians the solve started from (keep_inputs)
+    result: dict | None = None   # device outputs
+
+    @property
+    def latency(self):
+        return self.done - self.arrival
+
+    def track_bytes(self):
+        nb = lambda a: int(a.nbytes) if hasattr(a, "nbytes") else a.numel() * a.element_size()
+        return sum(nb(d) + nb(v) for d, v in zip(self.disp, self.vis))
+
+
+class _Scene:
+    def __init__(self, sid, mo, q, s):
+        self.sid = sid
+        self.host = (mo, q, s)           # host copy while not resident
+        self.dev = None                  # (means_opacity, quats, scales) on the device
+        self.ctx = None
+        self.stream = None
+        self.busy = False
+        self.last_used = 0.0
+        self.ws_bytes = 0
+        self.views = 1
+
+    @property
+    def n(self):
+        return int((self.dev or self.host)[0].shape[0])
+
+    def resident_bytes(self, views=0):
+        # Gaussians (state + outputs) and the library workspace: ~190 B per
+        # (view, Gaussian) record plus ~16 B per expected (tile, Gaussian) pair
+        rec = self.n * max(views, self.views, 1)
+        est = 2 * 48 * self.n + 190 * rec + 16 * 8 * rec
+        return max(est, self.ws_bytes + 2 * 48 * self.n)
+
+
+class MotionServer:
+    def __init__(self, device=0, budget_bytes=120 << 30, max_inflight=8, keep_inputs=False, **options):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        self.budget = int(budget_bytes)
+        self.max_inflight = int(max_inflight)
+        self.keep_inputs = keep_inputs
+        self.options = dict(async_pairs=1)
+        self.options.update(options)
+        self.scenes: dict[str, _Scene] = {}
+        self.waiting: collections.deque[Request] = collections.deque()
+        self.inflight: list[tuple[Request, _Scene, object, tuple]] = []
+        self.retries = 0
+        self.finished: list[Request] = []
+        self.t0 = time.perf_counter()
+        self.evictions = 0
+        self.peak_bytes = 0
+
+    # ---------------------------------------------------------------- scenes
+    def add_scene(self, sid, means_opacity, quats, scales):
+        """Register a scene by its first frame's Gaussians (host float32 [n, 4])."""
+        self.scenes[sid] = _Scene(sid, np.ascontiguousarray(means_opacity, np.float32),
+                                  np.ascontiguousarray(quats, np.float32),
+                                  np.ascontiguousarray(scales, np.float32))
+
+    def scene_state(self, sid):
+        """The scene's current Gaussians as host arrays."""
+        sc = self.scenes[sid]
+        if sc.dev is None:
+            return sc.host
+        sc.stream.synchronize()
+        return tuple(t.cpu().numpy() for t in sc.dev)
+
+    def _used_bytes(self, extra_views=None):
+        used = 0
+        for sc in self.scenes.values():
+            if sc.dev is not None:
+                used += sc.resident_bytes()
+        for req, sc, _, _ in self.inflight:
+            used += req.track_bytes()
+        return used
+
+    def _make_resident(self, sc, req):
+        torch = self.torch
+        if sc.stream is None:
+            sc.stream = torch.cuda.Stream(device=self.dev)
+        with torch.cuda.stream(sc.stream):
+            sc.dev = tuple(torch.from_numpy(a).pin_memory().to(self.dev, non_blocking=True) for a in sc.host)
+        sc.host = None
+        if sc.ctx is None:
+            sc.ctx = Context(self.device, **self.options)
+
+    def _evict(self, sc):
+        sc.stream.synchronize()
+        sc.host = tuple(t.cpu().numpy() for t in sc.dev)
+        sc.dev = None
+        sc.ws_bytes = sc.ctx.workspace_bytes()
+        sc.ctx.close()
+        sc.ctx = None
+        self.evictions += 1
+
+    # -------------------------------------------------------------- requests
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def submit(self, req: Request):
+        self.waiting.append(req)
+
+    def _admit(self):
+        """Launch every waiting request that fits (FIFO; a request whose scene is
+        busy waits without blocking the ones behind it)."""
+        keep = collections.deque()
+        while self.waiting:
+            req = self.waiting.popleft()
+            sc = self.scenes[req.scene]
+            if sc.busy or len(self.inflight) >= self.max_inflight:
+                keep.append(req)
+                continue
+            need = req.track_bytes() + (0 if sc.dev is not None else sc.resident_bytes(len(req.disp)))
+            used = self._used_bytes()
+            if used + need > self.budget:
+                idle = sorted((s for s in self.scenes.values() if s.dev is not None and not s.busy and s is not sc),
+                              key=lambda s: s.last_used)
+                while idle and used + need > self.budget:
+                    self._evict(idle.pop(0))
+                    used = self._used_bytes()
+                if used + need > self.budget:
+                    keep.append(req)
+                    continue
+            self._launch(req, sc)
+            self.peak_bytes = max(self.peak_bytes, self._used_bytes())
+        self.waiting = keep
+
+    def _launch(self, req, sc):
+        torch = self.torch
+        if sc.dev is None:
+            self._make_resident(sc, req)
+        sc.busy = True
+        sc.views = max(sc.views, len(req.disp))
+        req.start = self.now()
+        with torch.cuda.stream(sc.stream):
+            disp = [_to_device(d, self.dev) for d in req.disp]
+            vis = [_to_device(v, self.dev) for v in req.vis]
+            mo, q, s = sc.dev
+            if self.keep_inputs:
+                req.inputs = dict(means_opacity=mo.clone(), quats=q.clone(), scales=s.clone())
+            out = sc.ctx.fit_motion(mo, q, s, req.cams, disp, vis, stream=sc.stream)
+            # the solved Gaussians are the next frame's input
+            new_mo = out["means"]
+            sc.dev = (new_mo, out["quats"], out["scales"])
+            ev = torch.cuda.Event()
+            ev.record(sc.stream)
+        req.result = out
+        self.inflight.append((req, sc, ev, (disp, vis, (mo, q, s))))
+
+    def poll(self):
+        """Retire completed requests; admit waiting ones.  Returns the newly
+        finished requests."""
+        done = []
+        still = []
+        retry = []
+        for item in self.inflight:
+            req, sc, ev, (_, _, prev) = item
+            if ev.query():
+                sc.busy = False
+                try:
+                    sc.ctx.sync(sc.stream)
+                except TspError as e:
+                    if e.status != TSP.ERR_OVERFLOW:
+                        raise
+                    # the pair buffer was too small for this frame; the library has
+                    # grown it, so the frame runs again from the previous state
+                    sc.dev = prev
+                    self.retries += 1
+                    retry.append(req)
+                    continue
+                req.done = self.now()
+                sc.last_used = req.done
+                done.append(req)
+            else:
+                still.append(item)
+        self.waiting.extendleft(reversed(retry))
+        self.inflight = still
+        self._admit()
+        self.finished.extend(done)
+        return done
+
+    def run(self, requests, rate_scale=1.0, poll_s=5e-5):
+        """Serve ``requests`` (sorted by arrival, seconds) in real time: each is
+        submitted when its arrival time comes.  Returns the finished requests."""
+        self.t0 = time.perf_counter()
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        while pending or self.waiting or self.inflight:
+            t = self.now()
+            while pending and pending[0].arrival * rate_scale <= t:
+                r = pending.popleft()
+                r.arrival *= rate_scale
+                self.submit(r)
+            self.poll()
+            if not self.inflight and self.waiting and not pending:
+                # nothing can run: a request larger than the budget
+                raise RuntimeError(f"request {self.waiting[0].rid} does not fit the device budget")
+            time.sleep(poll_s)
+        return self.finished
+
+    def close(self):
+        for sc in self.scenes.values():
+            if sc.ctx is not None:
+                sc.ctx.close()
+                sc.ctx = None
+
+
+def one_at_a_time(requests, scenes, device=0, poll_s=5e-5, **options):
+    """The plain path: one context and one stream; each request starts when it
+    has arrived and the previous one has finished."""
+    import torch
+    dev = torch.device("cuda", device)
+    state = {sid: tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev) for a in g)
+             for sid, g in scenes.items()}
+    ctx = Context(device, **dict(dict(async_pairs=0), **options))
+    t0 = time.perf_counter()
+    out = []
+    for req in sorted(requests, key=lambda r: r.arrival):
+        while time.perf_counter() - t0 < req.arrival:
+            time.sleep(poll_s)
+        req.start = time.perf_counter() - t0
+        disp = [_to_device(d, dev) for d in req.disp]
+        vis = [_to_device(v, dev) for v in req.vis]
+        mo, q, s = state[req.scene]
+        r = ctx.fit_motion(mo, q, s, req.cams, disp, vis, sync=True)
+        state[req.scene] = (r["means"], r["quats"], r["scales"])
+        req.result = r
+        req.done = time.perf_counter() - t0
+        out.append(req)
+    ctx.close()
+    return out
+
+
+def latency_stats(reqs, units_of):
+    lat = np.array([r.latency for r in reqs]) * 1e3
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    return dict(requests=len(reqs), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                mean_ms=float(lat.mean()), fits_per_s=float(sum(units_of(r) for r in reqs) / span),
+                req_per_s=len(reqs) / span)
