@@ -40,10 +40,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch"],
+    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve"],
                     help="capture: 200k Gaussians x 18 views at 1352x1014 (the metric's workload); "
                          "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound); "
-                         "batch: 8 uneven frame pairs, batched vs one at a time")
+                         "batch: 8 uneven frame pairs, batched vs one at a time; "
+                         "serve: Poisson requests at 40/s, request loop vs one at a time")
+    ap.add_argument("--rate", type=float, default=40.0, help="serve: mean requests per second")
+    ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds of arrivals")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
@@ -471,10 +474,84 @@ def measure_batch(a, scenes, metric):
     return line
 
 
+def serve_scenes(seed=51, count=8):
+    """Scene pool: Gaussian counts log-uniform in 20k-500k, 4-24 views at
+    640x360, 960x540 or 1352x1014, one rigid motion each."""
+    import synth
+    rng = np.random.default_rng(seed)
+    res = [(640, 360, 473.0), (960, 540, 710.0), (1352, 1014, 1000.0)]
+    out = []
+    for k in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(20_000), np.log(500_000)))))
+        W, H, f = res[int(rng.integers(0, 3))]
+        out.append(synth.make_scene("frame", seed=seed * 100 + k, n=n, views=int(rng.integers(4, 25)),
+                                    width=W, height=H, focal=f))
+    return out
+
+
+def run_serve(a):
+    """Poisson arrivals of frame-pair requests over a pool of scenes, served by the
+    request loop (scene-resident, overlapped, HBM-budgeted) and by the plain
+    one-at-a-time path on the same arrival times; tracks come from pinned host
+    memory inside each request."""
+    import copy
+    import torch
+    from paper_2604_02586_b300 import build as tbuild
+    from paper_2604_02586_b300.serve import MotionServer, Request, latency_stats, one_at_a_time
+    tbuild.build()
+    torch.cuda.set_device(0)
+    scenes = serve_scenes()
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    tracks = [([pin(d) for d in s.disp], [pin(v) for v in s.vis]) for s in scenes]
+    rng = np.random.default_rng(7)
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / a.rate)
+        if t > a.duration:
+            break
+        k = int(rng.integers(0, len(scenes)))
+        reqs.append(Request(len(reqs), f"s{k}", scenes[k], tracks[k][0], tracks[k][1], arrival=t))
+    units = lambda r: int(scenes[int(r.scene[1:])].n) * int(scenes[int(r.scene[1:])].num_views)
+
+    def serve():
+        srv = MotionServer(0, budget_bytes=120 << 30, max_inflight=8, chain=False)
+        for k, s in enumerate(scenes):
+            srv.add_scene(f"s{k}", s.means_opacity, s.quats, s.scales)
+        # one warm-up frame per scene (contexts, workspaces, CUDA modules)
+        srv.run([Request(-1 - k, f"s{k}", s, tracks[k][0], tracks[k][1]) for k, s in enumerate(scenes)])
+        srv.finished = []
+        done = srv.run(copy.copy(r) for r in reqs)
+        stats = latency_stats(done, units)
+        stats.update(evictions=srv.evictions, retries=srv.retries, peak_budget_bytes=srv.peak_bytes)
+        srv.close()
+        return stats
+
+    def plain():
+        return latency_stats(one_at_a_time([copy.copy(r) for r in reqs],
+                                           {f"s{k}": (s.means_opacity, s.quats, s.scales)
+                                            for k, s in enumerate(scenes)}, chain=False), units)
+
+    plain()                                                    # warm-up of the plain path
+    srv_stats, plain_stats = serve(), plain()
+    line = {"metric": f"frame-pair requests: p50/p99 latency and fits/s at {a.rate:g} req/s (Poisson)",
+            "value": srv_stats["fits_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": len(scenes),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "scenes: " + ", ".join(f"{s.n}x{s.num_views}@{int(s.width[0])}x{int(s.height[0])}"
+                                                          for s in scenes),
+                       "rate_per_s": a.rate, "duration_s": a.duration, "budget_bytes": 120 << 30,
+                       "max_inflight": 8, "tracks": "pinned host memory, copied inside each request"},
+            "p50_ms": srv_stats["p50_ms"], "p99_ms": srv_stats["p99_ms"], "server": srv_stats,
+            "one_at_a_time": plain_stats}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.preset == "batch":
         run_batch(a)
+    elif a.preset == "serve":
+        run_serve(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

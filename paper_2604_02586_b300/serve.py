@@ -85,7 +85,8 @@ class _Scene:
 
 
 class MotionServer:
-    def __init__(self, device=0, budget_bytes=120 << 30, max_inflight=8, keep_inputs=False, **options):
+    def __init__(self, device=0, budget_bytes=120 << 30, max_inflight=8, keep_inputs=False, chain=True,
+                 **options):
         import torch
         self.torch = torch
         self.device = device
@@ -93,6 +94,7 @@ class MotionServer:
         self.budget = int(budget_bytes)
         self.max_inflight = int(max_inflight)
         self.keep_inputs = keep_inputs
+        self.chain = chain                     # False: every frame starts from the resident first frame
         self.options = dict(async_pairs=1)
         self.options.update(options)
         self.scenes: dict[str, _Scene] = {}
@@ -193,9 +195,8 @@ class MotionServer:
             if self.keep_inputs:
                 req.inputs = dict(means_opacity=mo.clone(), quats=q.clone(), scales=s.clone())
             out = sc.ctx.fit_motion(mo, q, s, req.cams, disp, vis, stream=sc.stream)
-            # the solved Gaussians are the next frame's input
-            new_mo = out["means"]
-            sc.dev = (new_mo, out["quats"], out["scales"])
+            if self.chain:                     # the solved Gaussians are the next frame's input
+                sc.dev = (out["means"], out["quats"], out["scales"])
             ev = torch.cuda.Event()
             ev.record(sc.stream)
         req.result = out
@@ -258,7 +259,7 @@ class MotionServer:
                 sc.ctx = None
 
 
-def one_at_a_time(requests, scenes, device=0, poll_s=5e-5, **options):
+def one_at_a_time(requests, scenes, device=0, poll_s=5e-5, chain=True, **options):
     """The plain path: one context and one stream; each request starts when it
     has arrived and the previous one has finished."""
     import torch
@@ -276,7 +277,8 @@ def one_at_a_time(requests, scenes, device=0, poll_s=5e-5, **options):
         vis = [_to_device(v, dev) for v in req.vis]
         mo, q, s = state[req.scene]
         r = ctx.fit_motion(mo, q, s, req.cams, disp, vis, sync=True)
-        state[req.scene] = (r["means"], r["quats"], r["scales"])
+        if chain:
+            state[req.scene] = (r["means"], r["quats"], r["scales"])
         req.result = r
         req.done = time.perf_counter() - t0
         out.append(req)
