@@ -83,6 +83,8 @@ def lib():
                                     P, P, P]
         _lib.orc_render_bruteforce.argtypes = [C.c_int, P, P, P, P, C.c_int, P, C.c_int, C.c_int,
                                                C.c_int, P, P]
+        _lib.orc_render_grad.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_int, P, C.c_int, C.c_int,
+                                         P, P, P, P, P, P, P]
         _lib.orc_naive_ls.argtypes = [C.c_int, P, P, P, P]
         _lib.orc_project.argtypes = [P, P, P, P, P, P, P]
         _lib.orc_eig3.argtypes = [P, P, P]
@@ -193,6 +195,30 @@ def render(scene, tile=(16, 16)):
                      C.cast(cameras(scene), C.c_void_p), tile[0], tile[1],
                      C.cast(pa, C.c_void_p), C.cast(pt, C.c_void_p), C.cast(pf, C.c_void_p))
     return rgb, T, fl
+
+
+def render_grad(scene, W, tile=(16, 16), gradient=True):
+    """L = sum over views, pixels and channels of W[v] * colour (float32 weights
+    [V] x [H,W,3]) and, with gradient=True, dL/d(means [n,3], linear scales [n,3],
+    raw quaternions [n,4], opacity [n], colour coefficients [n, (deg+1)^2, 3]),
+    in FP64 with the blend's decisions held fixed."""
+    mo, q, s = _gauss(scene)
+    n, V = scene.n, scene.num_views
+    nb = (int(scene.sh_degree) + 1) ** 2
+    Ws = [np.ascontiguousarray(w, np.float32) for w in W]
+    pw = (C.c_void_p * max(V, 1))(*[w.ctypes.data for w in Ws])
+    sh = np.ascontiguousarray(scene.sh, np.float32)
+    loss = np.zeros(1)
+    out = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               opacity=np.zeros(n), sh=np.zeros((n, nb, 3))) if gradient else None
+    g = (lambda k: _ptr(out[k])) if gradient else (lambda k: None)
+    lib().orc_render_grad(n, V, _ptr(mo), _ptr(q), _ptr(s), _ptr(sh), int(scene.sh_degree),
+                          C.cast(cameras(scene), C.c_void_p), tile[0], tile[1], C.cast(pw, C.c_void_p),
+                          _ptr(loss), g("means"), g("scales"), g("quats"), g("opacity"), g("sh"))
+    if not gradient:
+        return float(loss[0])
+    out["loss"] = float(loss[0])
+    return out
 
 
 def render_bruteforce(scene, view: int, use_rect: bool, tile=(16, 16)):

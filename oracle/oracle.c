@@ -1023,6 +1023,310 @@ int orc_render(int n, int V, const float* means_opacity, const float* quats, con
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Render gradient (the adjoint of the blend, for gradient refinement)         */
+/* ------------------------------------------------------------------------- */
+/* For L = sum over views, pixels and channels of W[v][p][ch] * C[v][p][ch], C the
+ * colour orc_render gives, the gradient with respect to every Gaussian's mean,
+ * linear scales, raw (unnormalised) quaternion, opacity and colour coefficients.
+ * The chain rule runs through the blend of Sec. 3.1 (C = sum c_i alpha_i T_i with
+ * its decisions -- tile rectangle, alpha >= 1/255, the transmittance cut-off,
+ * the clamps of alpha at 0.99 and of the colour at 0 -- held fixed), the inverse
+ * of the dilated Sigma_2D, Sigma_2D = (J W) Sigma_3D (J W)^T and the perspective
+ * map (Eq. 1), Sigma_3D = R(q) diag(s^2) R(q)^T, and the colour basis along the
+ * direction from the camera centre.  Written from those definitions; no step of
+ * it is shared with the GPU code. */
+
+typedef struct {
+    proj64 P;
+    double p[3];          /* camera-space mean */
+    double T[2][3];       /* J W */
+    double S[3][3];       /* Sigma_3D */
+    double R[3][3];       /* R(q) */
+    double qn[4], qnorm;
+    double dir[3], dist;  /* unit direction camera centre -> mean, distance */
+    double Y[16];
+    double raw[3];        /* colour before the clamp at 0 */
+} vgauss;
+
+static void vgauss_make(const float* mo, const float* q, const float* s, const float* sh, int deg,
+                        const orc_camera* c, vgauss* G)
+{
+    project64(mo, q, s, c, &G->P);
+    const double X[3] = {mo[0], mo[1], mo[2]};
+    jw_at(c, X, G->T, G->p);
+    cov3d(q, s, G->S);
+    quat_to_rot(q, G->R, G->qn);
+    G->qnorm = sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3]);
+    double Cc[3];
+    for (int i = 0; i < 3; ++i)
+        Cc[i] = -(c->R[i] * (double)c->t[0] + c->R[3 + i] * (double)c->t[1] + c->R[6 + i] * (double)c->t[2]);
+    double d[3] = {X[0] - Cc[0], X[1] - Cc[1], X[2] - Cc[2]};
+    G->dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int i = 0; i < 3; ++i) G->dir[i] = d[i] / G->dist;
+    sh_basis(G->dir[0], G->dir[1], G->dir[2], G->Y);
+    const int nb = (deg + 1) * (deg + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.5;
+        for (int k = 0; k < nb; ++k) acc += G->Y[k] * sh[k * 3 + ch];
+        G->raw[ch] = acc;
+        G->P.color[ch] = acc > 0 ? acc : 0;
+    }
+}
+
+/* Gradient of each basis function with respect to (x, y, z), the functions read
+ * as polynomials (their restriction to the unit sphere is the basis). */
+static void sh_basis_grad(double x, double y, double z, double dY[16][3])
+{
+    const double pi = 3.14159265358979323846;
+    const double k1 = sqrt(3.0 / (4.0 * pi));
+    const double k2a = 0.5 * sqrt(15.0 / pi), k2b = 0.25 * sqrt(5.0 / pi), k2c = 0.25 * sqrt(15.0 / pi);
+    const double k3a = 0.25 * sqrt(35.0 / (2.0 * pi)), k3b = 0.5 * sqrt(105.0 / pi);
+    const double k3c = 0.25 * sqrt(21.0 / (2.0 * pi)), k3d = 0.25 * sqrt(7.0 / pi);
+    const double k3e = 0.25 * sqrt(105.0 / pi);
+    const double xx = x * x, yy = y * y, zz = z * z;
+    const double g[16][3] = {
+        {0, 0, 0},
+        {0, -k1, 0}, {0, 0, k1}, {-k1, 0, 0},
+        {k2a * y, k2a * x, 0}, {0, -k2a * z, -k2a * y}, {-2 * k2b * x, -2 * k2b * y, 4 * k2b * z},
+        {-k2a * z, 0, -k2a * x}, {2 * k2c * x, -2 * k2c * y, 0},
+        {-6 * k3a * x * y, -3 * k3a * (xx - yy), 0},
+        {k3b * y * z, k3b * x * z, k3b * x * y},
+        {2 * k3c * x * y, -k3c * (4 * zz - xx - 3 * yy), -8 * k3c * y * z},
+        {-6 * k3d * x * z, -6 * k3d * y * z, k3d * (6 * zz - 3 * xx - 3 * yy)},
+        {-k3c * (4 * zz - 3 * xx - yy), 2 * k3c * x * y, -8 * k3c * x * z},
+        {2 * k3e * x * z, -2 * k3e * y * z, k3e * (xx - yy)},
+        {-3 * k3a * (xx - yy), 6 * k3a * x * y, 0}};
+    memcpy(dY, g, sizeof(g));
+}
+
+typedef struct { int g; double a, T, G; int clamped; double dx, dy; } contrib;
+
+/* One view: the loss (optional) and, with gp != NULL, the gradient with respect
+ * to each Gaussian's 2D quantities: gp[g] = (mu_x, mu_y, conic 00, conic 01 (the
+ * off-diagonal parameter), conic 11, opacity, colour r, g, b). */
+static void grad_view(int v, const binctx* B, const int64_t* offsets, const uint64_t* entries,
+                      const vgauss* VG, const orc_camera* cam, const float* W, double* loss, double* gp)
+{
+    const int tw = B->tw, th = B->th, Wd = cam->width, H = cam->height;
+    int64_t cap = 256;
+    contrib* cs = malloc(sizeof(contrib) * cap);
+    double L = 0.0;
+    for (int ty = 0; ty < B->tiles_y[v]; ++ty)
+        for (int tx = 0; tx < B->tiles_x[v]; ++tx) {
+            const int64_t t = B->toff[v] + (int64_t)ty * B->tiles_x[v] + tx;
+            const int64_t e0 = offsets[t], e1 = offsets[t + 1];
+            if (e1 - e0 > cap) { cap = e1 - e0; cs = realloc(cs, sizeof(contrib) * cap); }
+            for (int py = ty * th; py < (ty + 1) * th && py < H; ++py)
+                for (int px = tx * tw; px < (tx + 1) * tw && px < Wd; ++px) {
+                    const double xc = px + 0.5, yc = py + 0.5;
+                    double T = 1.0, C[3] = {0, 0, 0};
+                    int m = 0;
+                    for (int64_t e = e0; e < e1; ++e) {
+                        const int g = (int)(uint32_t)entries[e];
+                        const proj64* G = &VG[g].P;
+                        const double dx = xc - G->mx, dy = yc - G->my;
+                        const double qf = G->conic[0] * dx * dx + 2.0 * G->conic[1] * dx * dy
+                                        + G->conic[2] * dy * dy;
+                        const double Gv = exp(-0.5 * qf);
+                        double a = G->opacity * Gv;
+                        const int clamped = a > ALPHA_MAX;
+                        if (clamped) a = ALPHA_MAX;
+                        if (a < ALPHA_MIN) continue;
+                        const double Tn = T * (1.0 - a);
+                        if (Tn < T_MIN) break;
+                        for (int ch = 0; ch < 3; ++ch) C[ch] += a * T * G->color[ch];
+                        cs[m++] = (contrib){g, a, T, Gv, clamped, dx, dy};
+                        T = Tn;
+                    }
+                    const float* w = W + 3 * ((size_t)py * Wd + px);
+                    L += w[0] * C[0] + w[1] * C[1] + w[2] * C[2];
+                    if (!gp) continue;
+                    double P[3] = {0, 0, 0};
+                    for (int i = 0; i < m; ++i) {
+                        const contrib* k = &cs[i];
+                        const proj64* G = &VG[k->g].P;
+                        double ga = 0.0;
+                        for (int ch = 0; ch < 3; ++ch) {
+                            P[ch] += k->a * k->T * G->color[ch];
+                            /* dC/dalpha_i = c_i T_i - (C - P_i) / (1 - alpha_i) */
+                            ga += w[ch] * (G->color[ch] * k->T - (C[ch] - P[ch]) / (1.0 - k->a));
+                        }
+                        double* o = gp + 9 * (size_t)k->g;
+                        for (int ch = 0; ch < 3; ++ch) o[6 + ch] += k->a * k->T * w[ch];
+                        if (k->clamped) continue;
+                        o[5] += k->G * ga;                                   /* alpha = o G */
+                        const double gG = G->opacity * ga;
+                        /* G = exp(-d^T Q d / 2), d = x - mu: dG/dmu = G Q d */
+                        o[0] += gG * k->G * (G->conic[0] * k->dx + G->conic[1] * k->dy);
+                        o[1] += gG * k->G * (G->conic[1] * k->dx + G->conic[2] * k->dy);
+                        o[2] += gG * (-0.5 * k->G * k->dx * k->dx);
+                        o[3] += gG * (-k->G * k->dx * k->dy);
+                        o[4] += gG * (-0.5 * k->G * k->dy * k->dy);
+                    }
+                }
+        }
+    free(cs);
+    if (loss) *loss = L;
+}
+
+/* The 2D gradient gp (grad_view's layout) of Gaussian G in camera c, carried back
+ * to the 3D parameters and added to gm[3], gs[3], gq[4], *go, gsh[nb][3]. */
+static void chain_view(const vgauss* G, const double* gp, const orc_camera* c, const float* sh, int deg,
+                       const float* s_lin, double* gm, double* gs, double* gq, double* go, double* gsh)
+{
+    /* conic = inverse of the dilated Sigma_2D [[a, b], [b, d]] */
+    const double a = G->P.cov[0] + DILATION, b = G->P.cov[1], d = G->P.cov[2] + DILATION;
+    const double det = a * d - b * b, i2 = 1.0 / (det * det);
+    const double q00 = gp[2], q01 = gp[3], q11 = gp[4];
+    const double ga = q00 * (-d * d * i2) + q01 * (b * d * i2) + q11 * (1.0 / det - a * d * i2);
+    const double gd = q00 * (1.0 / det - a * d * i2) + q01 * (a * b * i2) + q11 * (-a * a * i2);
+    const double gb = q00 * (2.0 * b * d * i2) + q01 * (-1.0 / det - 2.0 * b * b * i2) + q11 * (2.0 * a * b * i2);
+    const double G2[2][2] = {{ga, 0.5 * gb}, {0.5 * gb, gd}};   /* dL/dSigma_2D, symmetric */
+    /* Sigma_2D = T S T^T */
+    double gS[3][3], gT[2][3], TS[2][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int u = 0; u < 2; ++u)
+                for (int w = 0; w < 2; ++w) acc += G->T[u][i] * G2[u][w] * G->T[w][j];
+            gS[i][j] = acc;
+        }
+    for (int u = 0; u < 2; ++u)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += G->T[u][k] * G->S[k][j];
+            TS[u][j] = acc;
+        }
+    for (int u = 0; u < 2; ++u)
+        for (int j = 0; j < 3; ++j) gT[u][j] = 2.0 * (G2[u][0] * TS[0][j] + G2[u][1] * TS[1][j]);
+    /* T = J W with W the camera rotation (row-major R) */
+    double gJ[2][3];
+    for (int u = 0; u < 2; ++u)
+        for (int k = 0; k < 3; ++k)
+            gJ[u][k] = gT[u][0] * c->R[3 * k] + gT[u][1] * c->R[3 * k + 1] + gT[u][2] * c->R[3 * k + 2];
+    const double px = G->p[0], py = G->p[1], pz = G->p[2], fx = c->fx, fy = c->fy;
+    const double iz = 1.0 / pz, iz2 = iz * iz, iz3 = iz2 * iz;
+    double gpc[3];
+    gpc[0] = gJ[0][2] * (-fx * iz2) + gp[0] * fx * iz;
+    gpc[1] = gJ[1][2] * (-fy * iz2) + gp[1] * fy * iz;
+    gpc[2] = gJ[0][0] * (-fx * iz2) + gJ[0][2] * (2.0 * fx * px * iz3) + gJ[1][1] * (-fy * iz2)
+           + gJ[1][2] * (2.0 * fy * py * iz3) - gp[0] * fx * px * iz2 - gp[1] * fy * py * iz2;
+    for (int j = 0; j < 3; ++j) gm[j] += c->R[j] * gpc[0] + c->R[3 + j] * gpc[1] + c->R[6 + j] * gpc[2];
+    /* colour: c = max(0, 0.5 + sum_k Y_k(dir) sh_k) */
+    const int nb = (deg + 1) * (deg + 1);
+    double gY[16] = {0};
+    for (int ch = 0; ch < 3; ++ch) {
+        if (!(G->raw[ch] > 0)) continue;
+        for (int k = 0; k < nb; ++k) {
+            gsh[3 * k + ch] += G->Y[k] * gp[6 + ch];
+            gY[k] += sh[3 * k + ch] * gp[6 + ch];
+        }
+    }
+    double dY[16][3], gdir[3] = {0, 0, 0};
+    sh_basis_grad(G->dir[0], G->dir[1], G->dir[2], dY);
+    for (int k = 0; k < nb; ++k)
+        for (int i = 0; i < 3; ++i) gdir[i] += gY[k] * dY[k][i];
+    const double dd = G->dir[0] * gdir[0] + G->dir[1] * gdir[1] + G->dir[2] * gdir[2];
+    for (int i = 0; i < 3; ++i) gm[i] += (gdir[i] - G->dir[i] * dd) / G->dist;
+    *go += gp[5];
+    /* Sigma_3D = R D R^T, D = diag(s^2) */
+    const double s2[3] = {(double)s_lin[0] * s_lin[0], (double)s_lin[1] * s_lin[1], (double)s_lin[2] * s_lin[2]};
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) acc += G->R[i][k] * gS[i][j] * G->R[j][k];
+        gs[k] += 2.0 * s_lin[k] * acc;
+    }
+    double gR[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0;
+            for (int j = 0; j < 3; ++j) acc += gS[i][j] * G->R[j][k];
+            gR[i][k] = 2.0 * acc * s2[k];
+        }
+    const double w = G->qn[0], x = G->qn[1], y = G->qn[2], z = G->qn[3];
+    const double dRw[3][3] = {{0, -2 * z, 2 * y}, {2 * z, 0, -2 * x}, {-2 * y, 2 * x, 0}};
+    const double dRx[3][3] = {{0, 2 * y, 2 * z}, {2 * y, -4 * x, -2 * w}, {2 * z, 2 * w, -4 * x}};
+    const double dRy[3][3] = {{-4 * y, 2 * x, 2 * w}, {2 * x, 0, 2 * z}, {-2 * w, 2 * z, -4 * y}};
+    const double dRz[3][3] = {{-4 * z, -2 * w, 2 * x}, {2 * w, -4 * z, 2 * y}, {2 * x, 2 * y, 0}};
+    double gh[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            gh[0] += gR[i][j] * dRw[i][j]; gh[1] += gR[i][j] * dRx[i][j];
+            gh[2] += gR[i][j] * dRy[i][j]; gh[3] += gR[i][j] * dRz[i][j];
+        }
+    const double hq = gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z;
+    gq[0] += (gh[0] - w * hq) / G->qnorm;
+    gq[1] += (gh[1] - x * hq) / G->qnorm;
+    gq[2] += (gh[2] - y * hq) / G->qnorm;
+    gq[3] += (gh[3] - z * hq) / G->qnorm;
+}
+
+int orc_render_grad(int n, int V, const float* means_opacity, const float* quats, const float* scales,
+                    const float* sh, int sh_degree, const orc_camera* cams, int tile_w, int tile_h,
+                    const float* const* W, double* loss, double* g_means, double* g_scales, double* g_quats,
+                    double* g_opacity, double* g_sh)
+{
+    binctx B;
+    binctx_init(&B, n, V, means_opacity, quats, scales, cams, tile_w, tile_h);
+    const int64_t K = count_pairs(&B);
+    int64_t* offsets = malloc(sizeof(int64_t) * (B.NT + 1));
+    uint64_t* entries = malloc(sizeof(uint64_t) * (K > 0 ? K : 1));
+    build_lists(&B, offsets, entries);
+    const int nb = (sh_degree + 1) * (sh_degree + 1);
+    const int want = g_means != NULL;
+    const size_t per = (size_t)n * (3 + 3 + 4 + 1 + 3 * nb);
+    double* acc = want ? calloc((size_t)V * per + 1, sizeof(double)) : NULL;
+    double* lv = calloc((size_t)V + 1, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int v = 0; v < V; ++v) {
+        vgauss* VG = calloc((size_t)n + 1, sizeof(vgauss));
+        for (int g = 0; g < n; ++g)
+            if (B.keys[(size_t)v * n + g].visible)
+                vgauss_make(means_opacity + 4 * (size_t)g, quats + 4 * (size_t)g, scales + 4 * (size_t)g,
+                            sh + (size_t)g * nb * 3, sh_degree, &cams[v], &VG[g]);
+        double* gp = want ? calloc((size_t)n * 9 + 1, sizeof(double)) : NULL;
+        grad_view(v, &B, offsets, entries, VG, &cams[v], W[v], &lv[v], gp);
+        if (want) {
+            double* a = acc + (size_t)v * per;
+            for (int g = 0; g < n; ++g) {
+                if (!B.keys[(size_t)v * n + g].visible) continue;
+                double* base = a + (size_t)g * (11 + 3 * nb);
+                chain_view(&VG[g], gp + 9 * (size_t)g, &cams[v], sh + (size_t)g * nb * 3, sh_degree,
+                           scales + 4 * (size_t)g, base, base + 3, base + 6, base + 10, base + 11);
+            }
+            free(gp);
+        }
+        free(VG);
+    }
+    double L = 0;
+    for (int v = 0; v < V; ++v) L += lv[v];
+    if (loss) *loss = L;
+    if (want) {
+        for (int g = 0; g < n; ++g) {
+            double* om = g_means + 3 * (size_t)g; double* os = g_scales + 3 * (size_t)g;
+            double* oq = g_quats + 4 * (size_t)g; double* osh = g_sh + (size_t)g * nb * 3;
+            for (int i = 0; i < 3; ++i) { om[i] = 0; os[i] = 0; }
+            for (int i = 0; i < 4; ++i) oq[i] = 0;
+            g_opacity[g] = 0;
+            for (int i = 0; i < 3 * nb; ++i) osh[i] = 0;
+            for (int v = 0; v < V; ++v) {
+                const double* b = acc + (size_t)v * per + (size_t)g * (11 + 3 * nb);
+                for (int i = 0; i < 3; ++i) { om[i] += b[i]; os[i] += b[3 + i]; }
+                for (int i = 0; i < 4; ++i) oq[i] += b[6 + i];
+                g_opacity[g] += b[10];
+                for (int i = 0; i < 3 * nb; ++i) osh[i] += b[11 + i];
+            }
+        }
+        free(acc);
+    }
+    free(lv);
+    free(offsets); free(entries);
+    binctx_free(&B);
+    return 0;
+}
+
 /* Brute-force render of one view: every Gaussian that passes the key path is
  * blended at every pixel, in (depth bits, index) order, with no tiles.  With
  * use_rect != 0 a Gaussian only reaches pixels inside its tile rectangle, which

@@ -592,3 +592,67 @@ def test_ground_truth_accuracy_report():
     e_fit = np.linalg.norm(r["out_mean"][ok] - gt[ok], axis=1)
     e_still = np.linalg.norm(s.means_opacity[ok, :3] - gt[ok], axis=1)
     assert np.median(e_fit) < np.median(e_still)
+
+
+def _masked_weights(sc, rng, margin=0.05):
+    """Random loss weights, zero at pixels where some Gaussian's alpha lies within
+    `margin` of the 1/255 cut or the 0.99 clamp: there a small parameter change
+    could flip a blend decision, which the gradient (like any derivative of the
+    blend) holds fixed."""
+    cams = oracle.cameras(sc)
+    W = []
+    for v in range(sc.num_views):
+        H, Wd = int(sc.height[v]), int(sc.width[v])
+        w = rng.normal(size=(H, Wd, 3)).astype(np.float32)
+        ys, xs = np.mgrid[0:H, 0:Wd] + 0.5
+        mask = np.zeros((H, Wd), bool)
+        for g in range(sc.n):
+            m2, _, cn = oracle.project(sc.means_opacity[g], sc.quats[g], sc.scales[g], cams[v])
+            dx, dy = xs - m2[0], ys - m2[1]
+            a = sc.means_opacity[g, 3] * np.exp(-0.5 * (cn[0] * dx * dx + 2 * cn[1] * dx * dy + cn[2] * dy * dy))
+            mask |= (np.abs(a * 255 - 1) < margin) | (np.abs(a / 0.99 - 1) < margin)
+        w[mask] = 0
+        W.append(w)
+    return W
+
+
+def test_render_gradient_matches_fp64_finite_differences():
+    """The oracle's analytic render gradient (means, linear scales, raw quaternions,
+    opacity, all 48 colour coefficients of 5 overlapping Gaussians in 2 views)
+    against FP64 central differences of its own loss, taken at two step sizes that
+    must agree (a tile-rectangle change would make them differ)."""
+    import copy
+    rng = np.random.default_rng(3)
+    n = 5
+    X = rng.uniform(-0.15, 0.15, (n, 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    s = rng.uniform(0.04, 0.09, (n, 3))
+    sc = S.with_gaussians(S.base_cameras(), X, q, s, rng.uniform(0.3, 0.9, n)).subset_views([0, 1])
+    sc.sh_degree = 3
+    sc.sh = rng.normal(0, 0.2, (n, 16, 3)).astype(np.float32)
+    W = _masked_weights(sc, rng)
+    gr = oracle.render_grad(sc, W)
+
+    def fd(field, idx, h):
+        a, b = copy.deepcopy(sc), copy.deepcopy(sc)
+        getattr(a, field)[idx] += h
+        getattr(b, field)[idx] -= h
+        return (oracle.render_grad(a, W, gradient=False) - oracle.render_grad(b, W, gradient=False)) / (2 * h)
+
+    rows = []
+    for g in range(n):
+        rows += [("means_opacity", (g, k), gr["means"][g, k], 1e-4) for k in range(3)]
+        rows += [("scales", (g, k), gr["scales"][g, k], 1e-3 * s[g, k]) for k in range(3)]
+        rows += [("quats", (g, k), gr["quats"][g, k], 1e-4) for k in range(4)]
+        rows += [("means_opacity", (g, 3), gr["opacity"][g], 1e-4)]
+        rows += [("sh", (g, k, c), gr["sh"][g, k, c], 1e-3) for k in range(16) for c in range(3)]
+    skipped = 0
+    for field, idx, an, h in rows:
+        f1, f2 = fd(field, idx, h), fd(field, idx, h / 2)
+        if not abs(f1 - f2) <= 1e-3 * max(abs(f1), 1e-3):
+            skipped += 1
+            continue
+        assert abs(an - f2) <= 2e-3 * max(abs(f2), 1e-3), (field, idx, an, f2)
+    assert skipped <= len(rows) // 20
+    assert np.abs(gr["means"]).max() > 0.1 and np.abs(gr["sh"]).max() > 0.01
