@@ -222,6 +222,27 @@ tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh,
                       const tsp_camera* cams, int num_views, float* const* rgb,
                       float* const* final_T, void* stream);
 
+/* Gradients of a render with respect to the Gaussians (gradient refinement). */
+typedef struct tsp_render_grads {
+    float* means;               /* [n][4]: dL/d(mean x, y, z), dL/dopacity in w    */
+    float* scales;              /* [n][4]: dL/d(linear scale x, y, z), 0           */
+    float* quats;               /* [n][4]: dL/d(raw quaternion w, x, y, z)         */
+    float* sh;                  /* [n][(sh_degree+1)^2][3]                         */
+} tsp_render_grads;
+
+/* Adjoint of tsp_render (the blend of Sec. 3.1): given the colour rgb that
+ * tsp_render gave for these Gaussians, colour coefficients and cameras, and
+ * grad_rgb = dL/dcolour ([num_views] device pointers to [H][W][3] FP32 each), the
+ * gradient of L with respect to every Gaussian's mean, opacity, linear scales,
+ * raw quaternion and colour coefficients, with the blend's decisions (tile
+ * rectangle, footprint box, alpha >= 1/255, transmittance cut-off, clamps of
+ * alpha at 0.99 and of the colour at 0) held fixed.  The tile lists are rebuilt
+ * and the blend is recomputed tile by tile; nothing per pixel is kept between the
+ * two calls.  All arrays are device memory.  Errors as tsp_render. */
+tsp_status tsp_render_backward(tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
+                               const tsp_camera* cams, int num_views, const float* const* rgb,
+                               const float* const* grad_rgb, const tsp_render_grads* out, void* stream);
+
 /* Wait up to timeout_ms (< 0: forever) for `stream`, then read and clear the
  * device status word.  Returns OK, TIMEOUT (work still running; call again),
  * OVERFLOW (the last step ran out of pair capacity; its results are invalid and

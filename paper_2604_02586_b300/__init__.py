@@ -56,6 +56,10 @@ class Frame(C.Structure):
                 ("tracks", C.c_void_p), ("out", Result)]
 
 
+class RenderGrads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("sh", C.c_void_p)]
+
+
 class Options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("det_min", C.c_float),
                 ("sumw_min_view", C.c_float), ("min_px_view", C.c_int32), ("lam_min_px2", C.c_float),
@@ -85,6 +89,7 @@ def lib():
         L.tsp_fit_motion_batch.argtypes = [P, P, I, P]
         L.tsp_autotune.argtypes = [P, P, I, I, P, P, P]
         L.tsp_render.argtypes = [P, P, P, I, P, I, P, P, P]
+        L.tsp_render_backward.argtypes = [P, P, P, I, P, I, P, P, P, P]
         L.tsp_sync.argtypes = [P, P, I]
         L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
         L.tsp_workspace_bytes.argtypes = [P, P]
@@ -97,7 +102,8 @@ def lib():
         L.tsp_last_error.restype = C.c_char_p
         L.tsp_version.restype = I
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
-                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render", "tsp_sync", "tsp_inspect",
+                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render",
+                     "tsp_render_backward", "tsp_sync", "tsp_inspect",
                      "tsp_workspace_bytes", "tsp_stage_times"):
             getattr(L, name).restype = I
         _lib = L
@@ -357,6 +363,41 @@ class Context:
         if sync:
             self.sync(stream)
         return rgb, T
+
+    def render_backward(self, means_opacity, quats, scales, sh, sh_degree, cams, rgb, grad_rgb, stream=None,
+                        sync=False):
+        """Adjoint of render: given its colour images ``rgb`` and dL/dcolour
+        ``grad_rgb`` ([V] x [H,W,3] CUDA tensors), returns dL/d(means_opacity,
+        quats, scales, sh) with the shapes of those inputs (scales' w = 0)."""
+        import torch
+        n = int(means_opacity.shape[0])
+        carr, V = _cams(cams)
+        dev = means_opacity.device
+        for name, t in (("means_opacity", means_opacity), ("quats", quats), ("scales", scales)):
+            _need(t, (n, 4), torch.float32, dev, name)
+        nb = (int(sh_degree) + 1) ** 2
+        _need(sh, (n, nb, 3), torch.float32, dev, "sh")
+        if len(rgb) < V or len(grad_rgb) < V:
+            raise ValueError("need one colour and one gradient image per camera")
+        for v in range(V):
+            shp = (carr[v].height, carr[v].width, 3)
+            _need(rgb[v], shp, torch.float32, dev, f"rgb[{v}]")
+            _need(grad_rgb[v], shp, torch.float32, dev, f"grad_rgb[{v}]")
+        out = dict(means_opacity=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                   quats=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                   scales=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                   sh=torch.empty((n, nb, 3), dtype=torch.float32, device=dev))
+        g = Gaussians(n, means_opacity.data_ptr(), quats.data_ptr(), scales.data_ptr())
+        pr = (C.c_void_p * max(V, 1))(*[x.data_ptr() for x in rgb[:V]])
+        pg = (C.c_void_p * max(V, 1))(*[x.data_ptr() for x in grad_rgb[:V]])
+        r = RenderGrads(out["means_opacity"].data_ptr(), out["scales"].data_ptr(), out["quats"].data_ptr(),
+                        out["sh"].data_ptr())
+        self._check(lib().tsp_render_backward(self._h, C.byref(g), C.c_void_p(sh.data_ptr()), int(sh_degree),
+                                              carr, V, pr, pg, C.byref(r), _stream_handle(stream)),
+                    "tsp_render_backward")
+        if sync:
+            self.sync(stream)
+        return out
 
     def sync(self, stream=None, timeout_ms: int = -1):
         st = C.c_void_p(0) if stream is None and not _torch_cuda() else _stream_handle(stream)

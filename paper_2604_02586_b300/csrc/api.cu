@@ -31,6 +31,7 @@ struct tsp_context {
     Buf rect, depth, touched, geom0, geom1, dref, oref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
     Buf tiles, tile_off, span_sum, queue;
+    Buf gacc;                       // render backward: per (view, Gaussian) 2D gradients
     int resident_ctas = 0;          // CTAs of the persistent raster resident at once
     // pairs
     Buf pairs, pairs_tmp;
@@ -548,7 +549,7 @@ tsp_status tsp_destroy(tsp_context* ctx)
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->oref, &ctx->color,
-                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum, &ctx->queue,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum, &ctx->queue, &ctx->gacc,
                   &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
                   &ctx->st_tracks};
     for (Buf* b : all) release(ctx, *b);
@@ -705,6 +706,60 @@ tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh,
     TSP_CUDA(mark(ctx, 6, st));
     TSP_CUDA(mark(ctx, 7, st));
     ctx->timed = ctx->opt.stage_timing != 0;
+    return TSP_OK;
+}
+
+tsp_status tsp_render_backward(tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
+                               const tsp_camera* cams, int num_views, const float* const* rgb,
+                               const float* const* grad_rgb, const tsp_render_grads* out, void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    tsp_status s;
+    if ((s = check_gaussians(ctx, g, true))) return s;
+    if (sh_degree < 0 || sh_degree > 3) return fail(ctx, TSP_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    const int n = g->n, V = num_views;
+    if (n > 0 && (!sh || !device_accessible(sh, ctx->device)))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "sh must be device memory");
+    if (!out) return fail(ctx, TSP_ERR_INVALID_ARG, "out is NULL");
+    if (n > 0) {
+        const void* ps[4] = {out->means, out->scales, out->quats, out->sh};
+        for (int k = 0; k < 4; ++k)
+            if (!ps[k] || !aligned(ps[k], k < 3 ? 16 : 4) || !device_accessible(ps[k], ctx->device))
+                return fail(ctx, TSP_ERR_INVALID_ARG, "gradient output is not aligned device memory");
+    }
+    ViewSet vs;
+    uint32_t NT = 0;
+    uint64_t R = 0;
+    tsp_frame fr{};
+    fr.g = *g;
+    fr.cams = cams;
+    fr.num_views = V;
+    if ((s = make_viewset(ctx, &fr, 1, vs, NT, R))) return s;
+    if (V > 0 && (!rgb || !grad_rgb)) return fail(ctx, TSP_ERR_INVALID_ARG, "rgb / grad_rgb is NULL");
+    RenderGrad rg{};
+    for (int v = 0; v < V; ++v) {
+        if (!rgb[v] || !grad_rgb[v] || !aligned(rgb[v], 4) || !aligned(grad_rgb[v], 4) ||
+            !device_accessible(rgb[v], ctx->device) || !device_accessible(grad_rgb[v], ctx->device))
+            return fail(ctx, TSP_ERR_INVALID_ARG, "view " + std::to_string(v) + ": bad colour or gradient image");
+        rg.rgb[v] = rgb[v];
+        rg.grad[v] = grad_rgb[v];
+    }
+    Work w{};
+    if ((s = ensure_work(ctx, R, NT, true, w))) return s;
+    if ((s = ensure(ctx, ctx->gacc, (size_t)std::max<uint64_t>(R, 1) * kGradStride * 4))) return s;
+    ctx->last_R = (size_t)R;
+    ctx->last_NT = NT;
+    rg.acc = (float*)ctx->gacc.p;
+    rg.g_means = (float4*)out->means;
+    rg.g_scales = (float4*)out->scales;
+    rg.g_quats = (float4*)out->quats;
+    rg.g_sh = out->sh;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->timed = false;
+    if (n == 0) return TSP_OK;
+    if ((s = bin_front(ctx, vs, sh, sh_degree, 1, NT, w, st))) return s;   // the render's tile lists again
+    TSP_CUDA(launch_render_backward(vs, w, NT, rg, sh, sh_degree, (size_t)R, st));
     return TSP_OK;
 }
 

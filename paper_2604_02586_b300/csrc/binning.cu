@@ -17,24 +17,8 @@ namespace {
 
 __device__ __forceinline__ void sh_colour(const float* sh, int deg, float x, float y, float z, float* rgb)
 {
-    // Real spherical harmonics (Condon-Shortley phase) up to degree 3:
-    // k0 = 1/(2 sqrt(pi)), k1 = sqrt(3/(4 pi)), k2a = sqrt(15/pi)/2, k2b = sqrt(5/pi)/4,
-    // k2c = sqrt(15/pi)/4, k3a = sqrt(35/(2 pi))/4, k3b = sqrt(105/pi)/2,
-    // k3c = sqrt(21/(2 pi))/4, k3d = sqrt(7/pi)/4, k3e = sqrt(105/pi)/4.
-    const float k0 = 0.28209479177387814f, k1 = 0.4886025119029199f;
-    const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.5462742152960396f;
-    const float k3a = 0.5900435899266435f, k3b = 2.890611442640554f, k3c = 0.4570457994644658f;
-    const float k3d = 0.3731763325901154f, k3e = 1.445305721320277f;
     float Y[16];
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[0] = k0;
-    Y[1] = -k1 * y; Y[2] = k1 * z; Y[3] = -k1 * x;
-    Y[4] = k2a * x * y; Y[5] = -k2a * y * z; Y[6] = k2b * (2.f * zz - xx - yy);
-    Y[7] = -k2a * x * z; Y[8] = k2c * (xx - yy);
-    Y[9] = -k3a * y * (3.f * xx - yy); Y[10] = k3b * x * y * z;
-    Y[11] = -k3c * y * (4.f * zz - xx - yy); Y[12] = k3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
-    Y[13] = -k3c * x * (4.f * zz - xx - yy); Y[14] = k3e * z * (xx - yy);
-    Y[15] = -k3a * x * (xx - 3.f * yy);
+    sh_basis16(x, y, z, Y);
     const int nb = (deg + 1) * (deg + 1);
     float r = 0.5f, g = 0.5f, b = 0.5f;
     for (int k = 0; k < nb; ++k) {

@@ -93,6 +93,18 @@ struct Work {
     uint32_t* queue;       // [1] work-queue head of the persistent raster
 };
 
+// Inputs and outputs of the render backward.
+constexpr int kGradStride = 12;   // floats per (view, Gaussian) 2D-gradient record (9 used)
+struct RenderGrad {
+    const float* rgb[kMaxViews];  // forward colour [H][W][3]
+    const float* grad[kMaxViews]; // dL/dcolour [H][W][3]
+    float* acc;                   // [R][kGradStride]: d mu_2D (2), d Q (00, 01, 11), d opacity, d colour (3)
+    float4* g_means;              // [n] (dL/dmean xyz, dL/dopacity)
+    float4* g_scales;             // [n] (dL/dscale xyz, 0)
+    float4* g_quats;              // [n] dL/d(raw quaternion)
+    float* g_sh;                  // [n][(deg+1)^2][3]
+};
+
 struct FitParams {
     float det_min, sumw_min_view, lam_min_px2, sumw_min_total, cov_rcond_min;
     int min_px_view, min_views, min_px_total;
@@ -296,6 +308,144 @@ __device__ __forceinline__ float3 blend_factor(const KeyProj& p)
     const float l22sq = r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3 + 0.3f;
     const float l22 = sqrtf(l22sq);
     return make_float3(kHalfLog2eSqrt / l11, f, kHalfLog2eSqrt / l22);
+}
+
+// Real spherical harmonics (Condon-Shortley phase) up to degree 3 at the unit
+// direction (x, y, z): k0 = 1/(2 sqrt(pi)), k1 = sqrt(3/(4 pi)), k2a = sqrt(15/pi)/2,
+// k2b = sqrt(5/pi)/4, k2c = sqrt(15/pi)/4, k3a = sqrt(35/(2 pi))/4,
+// k3b = sqrt(105/pi)/2, k3c = sqrt(21/(2 pi))/4, k3d = sqrt(7/pi)/4, k3e = sqrt(105/pi)/4.
+// With dY, also each function's gradient with respect to (x, y, z), the functions
+// read as polynomials (their restriction to the sphere is the basis).
+constexpr float kSH0 = 0.28209479177387814f, kSH1 = 0.4886025119029199f;
+constexpr float kSH2a = 1.0925484305920792f, kSH2b = 0.31539156525252005f, kSH2c = 0.5462742152960396f;
+constexpr float kSH3a = 0.5900435899266435f, kSH3b = 2.890611442640554f, kSH3c = 0.4570457994644658f;
+constexpr float kSH3d = 0.3731763325901154f, kSH3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float (&Y)[16])
+{
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = kSH0;
+    Y[1] = -kSH1 * y; Y[2] = kSH1 * z; Y[3] = -kSH1 * x;
+    Y[4] = kSH2a * x * y; Y[5] = -kSH2a * y * z; Y[6] = kSH2b * (2.f * zz - xx - yy);
+    Y[7] = -kSH2a * x * z; Y[8] = kSH2c * (xx - yy);
+    Y[9] = -kSH3a * y * (3.f * xx - yy); Y[10] = kSH3b * x * y * z;
+    Y[11] = -kSH3c * y * (4.f * zz - xx - yy); Y[12] = kSH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -kSH3c * x * (4.f * zz - xx - yy); Y[14] = kSH3e * z * (xx - yy);
+    Y[15] = -kSH3a * x * (xx - 3.f * yy);
+}
+
+__device__ __forceinline__ void sh_basis16_grad(float x, float y, float z, float (&dY)[16][3])
+{
+    const float xx = x * x, yy = y * y, zz = z * z;
+    const float g[16][3] = {
+        {0.f, 0.f, 0.f},
+        {0.f, -kSH1, 0.f}, {0.f, 0.f, kSH1}, {-kSH1, 0.f, 0.f},
+        {kSH2a * y, kSH2a * x, 0.f}, {0.f, -kSH2a * z, -kSH2a * y},
+        {-2.f * kSH2b * x, -2.f * kSH2b * y, 4.f * kSH2b * z},
+        {-kSH2a * z, 0.f, -kSH2a * x}, {2.f * kSH2c * x, -2.f * kSH2c * y, 0.f},
+        {-6.f * kSH3a * x * y, -3.f * kSH3a * (xx - yy), 0.f},
+        {kSH3b * y * z, kSH3b * x * z, kSH3b * x * y},
+        {2.f * kSH3c * x * y, -kSH3c * (4.f * zz - xx - 3.f * yy), -8.f * kSH3c * y * z},
+        {-6.f * kSH3d * x * z, -6.f * kSH3d * y * z, kSH3d * (6.f * zz - 3.f * xx - 3.f * yy)},
+        {-kSH3c * (4.f * zz - 3.f * xx - yy), 2.f * kSH3c * x * y, -8.f * kSH3c * x * z},
+        {2.f * kSH3e * x * z, -2.f * kSH3e * y * z, kSH3e * (xx - yy)},
+        {-3.f * kSH3a * (xx - yy), 6.f * kSH3a * x * y, 0.f}};
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dY[k][i] = g[k][i];
+}
+
+// Blend record with its mean moved from the Gaussian's rectangle corner to this
+// tile's corner (an exact integer shift, so the staged mean keeps its precision).
+__device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty)
+{
+    g0.x += (float)((r.x - tx) * kTile);
+    g0.y += (float)((r.y - ty) * kTile);
+    return g0;
+}
+
+// Tile-local box outside which alpha = min(0.99, o exp2(-p)) < 1/255 for sure:
+// p <= log2(255 o) is the ellipse z1^2 + z2^2 <= pm, whose extents follow from
+// the factor (i11, k, i22); the 0.1 % widening covers FP32 rounding of p.
+// Gaussians that cannot reach 1/255 anywhere get an empty box.
+__device__ __forceinline__ float4 footprint_box(float4 g0, float4 g1)
+{
+    const float pm = log2f(255.0f * g1.y);
+    if (!(pm > 0.0f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
+    const float sp = sqrtf(pm) * 1.001f;
+    const float ix = 1.0f / g0.z, iy = 1.0f / g1.x;
+    const float hx = sp * ix + 1e-3f;
+    const float hy = sp * sqrtf(g0.w * g0.w * ix * ix + iy * iy) + 1e-3f;
+    return make_float4(g0.x - hx, g0.x + hx, g0.y - hy, g0.y + hy);
+}
+
+// Pixel of thread tid inside its 16x16 tile: warp w -> block (w & 1, w >> 1) of
+// 8x4 pixels, lane l -> (l & 7, l >> 3) inside it.
+__device__ __forceinline__ void pixel_of(int tid, int& lx, int& ly)
+{
+    const int warp = tid >> 5, lane = tid & 31;
+    lx = (warp & 1) * 8 + (lane & 7);
+    ly = (warp >> 1) * 4 + (lane >> 3);
+}
+
+// Sum of v[k] over the warp for k = lane >> 1, returned in every lane.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 8];
+        const float keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 4];
+        const float keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 2];
+        const float keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Blend constants (3DGS conventions): alpha = min(0.99, o G), contributions below
+// 1/255 are skipped, the walk stops before a Gaussian that would take T below 1e-4.
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+// Colour-render blend of one (pixel, Gaussian): alpha = min(0.99, o 2^-p) with
+// p = z1^2 + z2^2 in the factor form of the staged record (tile-local mean g0.xy,
+// i11 = g0.z, k = g0.w, i22 = g1.x, opacity g1.y) at the tile-local pixel centre
+// (xc, yc), and the transmittance after it.  Every operation is spelled with a
+// correctly rounded intrinsic, so the forward render and its backward, which
+// recomputes the blend tile by tile, take bit-identical decisions.
+__device__ __forceinline__ float render_alpha(float4 g0, float4 g1, float xc, float yc)
+{
+    const float ex = __fsub_rn(xc, g0.x), ey = __fsub_rn(yc, g0.y);
+    const float z1 = __fmul_rn(ex, g0.z);
+    const float z2 = __fmul_rn(__fmaf_rn(-g0.w, ex, ey), g1.x);
+    const float pw = __fmaf_rn(z2, z2, __fmul_rn(z1, z1));
+    return fminf(kAlphaMax, __fmul_rn(g1.y, exp2f(-pw)));
+}
+
+__device__ __forceinline__ float render_transmit(float T, float alpha)
+{
+    return __fmul_rn(T, __fsub_rn(1.0f, alpha));
 }
 
 __device__ __forceinline__ void view_of_tile(const ViewSet& vs, uint32_t tile, int& v, int& tx, int& ty)

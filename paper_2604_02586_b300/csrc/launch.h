@@ -29,6 +29,11 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
 cudaError_t raster_prepare();
 // CTAs of the persistent raster that fit on the device at once.
 int raster_resident_ctas(int device);
+// the render's adjoint: dL/dcolour -> per (view, Gaussian) 2D gradients
+// (tile-recomputed blend) -> dL/d(mean, opacity, scales, quaternion, colour
+// coefficients) per Gaussian.
+cudaError_t launch_render_backward(const ViewSet& vs, const Work& w, uint32_t NT, const RenderGrad& rg,
+                                   const float* sh, int sh_degree, size_t records, cudaStream_t st);
 // render colour and final transmittance.
 cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
                                  float* const* final_T, cudaStream_t st);

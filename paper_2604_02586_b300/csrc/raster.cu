@@ -27,9 +27,6 @@ namespace {
 
 constexpr int kBatch = 64;
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr float kAlphaMin = 1.0f / 255.0f;
-constexpr float kAlphaMax = 0.99f;
-constexpr float kTMin = 1e-4f;
 
 // 2^x by the SFU's approximate exponential (flush-to-zero; |rel. error| ~ 2^-22).
 // x <= 0 here, and a result below 2^-126 (alpha < 1/255 by far) flushes to 0.
@@ -38,72 +35,6 @@ __device__ __forceinline__ float sfu_exp2(float x)
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// Blend record with its mean moved from the Gaussian's rectangle corner to this
-// tile's corner (an exact integer shift, so the staged mean keeps its precision).
-__device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty)
-{
-    g0.x += (float)((r.x - tx) * kTile);
-    g0.y += (float)((r.y - ty) * kTile);
-    return g0;
-}
-
-// Tile-local box outside which alpha = min(0.99, o exp2(-p)) < 1/255 for sure:
-// p <= log2(255 o) is the ellipse z1^2 + z2^2 <= pm, whose extents follow from
-// the factor (i11, k, i22); the 0.1 % widening covers FP32 rounding of p.
-// Gaussians that cannot reach 1/255 anywhere get an empty box.
-__device__ __forceinline__ float4 footprint_box(float4 g0, float4 g1)
-{
-    const float pm = log2f(255.0f * g1.y);
-    if (!(pm > 0.0f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
-    const float sp = sqrtf(pm) * 1.001f;
-    const float ix = 1.0f / g0.z, iy = 1.0f / g1.x;
-    const float hx = sp * ix + 1e-3f;
-    const float hy = sp * sqrtf(g0.w * g0.w * ix * ix + iy * iy) + 1e-3f;
-    return make_float4(g0.x - hx, g0.x + hx, g0.y - hy, g0.y + hy);
-}
-
-// Pixel of thread tid inside its 16x16 tile: warp w -> block (w & 1, w >> 1) of
-// 8x4 pixels, lane l -> (l & 7, l >> 3) inside it.
-__device__ __forceinline__ void pixel_of(int tid, int& lx, int& ly)
-{
-    const int warp = tid >> 5, lane = tid & 31;
-    lx = (warp & 1) * 8 + (lane & 7);
-    ly = (warp >> 1) * 4 + (lane >> 3);
-}
-
-// Sum of v[k] over the warp for k = lane >> 1, returned in every lane.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
-{
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool up = lane & 16;
-        const float send = up ? v[i] : v[i + 8];
-        const float keep = up ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(kFull, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = lane & 8;
-        const float send = up ? v[i] : v[i + 4];
-        const float keep = up ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(kFull, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = lane & 4;
-        const float send = up ? v[i] : v[i + 2];
-        const float keep = up ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(kFull, send, 4);
-    }
-    {
-        const bool up = lane & 2;
-        const float send = up ? v[0] : v[1];
-        const float keep = up ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(kFull, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
 // kStats = true is a measurement variant: the same walk, plus exact counts of the
@@ -594,13 +525,9 @@ __global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, con
             if (bb.x > bx1 || bb.y < bx0 || bb.z > by1 || bb.w < by0) continue;
             const float4 g0 = s_g0[j];
             const float4 g1 = s_g1[j];
-            const float ex = xc - g0.x, ey = yc - g0.y;
-            const float z1 = ex * g0.z;
-            const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
-            const float pw = fmaf(z2, z2, z1 * z1);
-            const float alpha = fminf(kAlphaMax, g1.y * exp2f(-pw));
+            const float alpha = render_alpha(g0, g1, xc, yc);
             if (alpha < kAlphaMin) continue;
-            const float Tn = T * (1.0f - alpha);
+            const float Tn = render_transmit(T, alpha);
             if (Tn < kTMin) { done = true; break; }
             const float wgt = alpha * T;
             const float4 c = s_c[j];

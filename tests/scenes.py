@@ -125,3 +125,26 @@ def rigid_apply(scene, Rg, tg):
     s.R = np.einsum("vij,kj->vik", R, Rg).astype(np.float32)          # R Rg^T
     s.t = (t - np.einsum("vij,j->vi", s.R.astype(np.float64), tg)).astype(np.float32)
     return s
+
+
+def masked_weights(sc, rng, margin=0.05):
+    """Random loss weights, zero at pixels where some Gaussian's alpha lies within
+    `margin` of the 1/255 cut or the 0.99 clamp: there a small parameter change
+    could flip a blend decision, which the gradient (like any derivative of the
+    blend) holds fixed."""
+    import oracle
+    cams = oracle.cameras(sc)
+    W = []
+    for v in range(sc.num_views):
+        H, Wd = int(sc.height[v]), int(sc.width[v])
+        w = rng.normal(size=(H, Wd, 3)).astype(np.float32)
+        ys, xs = np.mgrid[0:H, 0:Wd] + 0.5
+        mask = np.zeros((H, Wd), bool)
+        for g in range(sc.n):
+            m2, _, cn = oracle.project(sc.means_opacity[g], sc.quats[g], sc.scales[g], cams[v])
+            dx, dy = xs - m2[0], ys - m2[1]
+            a = sc.means_opacity[g, 3] * np.exp(-0.5 * (cn[0] * dx * dx + 2 * cn[1] * dx * dy + cn[2] * dy * dy))
+            mask |= (np.abs(a * 255 - 1) < margin) | (np.abs(a / 0.99 - 1) < margin)
+        w[mask] = 0
+        W.append(w)
+    return W

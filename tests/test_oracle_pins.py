@@ -594,28 +594,6 @@ def test_ground_truth_accuracy_report():
     assert np.median(e_fit) < np.median(e_still)
 
 
-def _masked_weights(sc, rng, margin=0.05):
-    """Random loss weights, zero at pixels where some Gaussian's alpha lies within
-    `margin` of the 1/255 cut or the 0.99 clamp: there a small parameter change
-    could flip a blend decision, which the gradient (like any derivative of the
-    blend) holds fixed."""
-    cams = oracle.cameras(sc)
-    W = []
-    for v in range(sc.num_views):
-        H, Wd = int(sc.height[v]), int(sc.width[v])
-        w = rng.normal(size=(H, Wd, 3)).astype(np.float32)
-        ys, xs = np.mgrid[0:H, 0:Wd] + 0.5
-        mask = np.zeros((H, Wd), bool)
-        for g in range(sc.n):
-            m2, _, cn = oracle.project(sc.means_opacity[g], sc.quats[g], sc.scales[g], cams[v])
-            dx, dy = xs - m2[0], ys - m2[1]
-            a = sc.means_opacity[g, 3] * np.exp(-0.5 * (cn[0] * dx * dx + 2 * cn[1] * dx * dy + cn[2] * dy * dy))
-            mask |= (np.abs(a * 255 - 1) < margin) | (np.abs(a / 0.99 - 1) < margin)
-        w[mask] = 0
-        W.append(w)
-    return W
-
-
 def test_render_gradient_matches_fp64_finite_differences():
     """The oracle's analytic render gradient (means, linear scales, raw quaternions,
     opacity, all 48 colour coefficients of 5 overlapping Gaussians in 2 views)
@@ -631,7 +609,7 @@ def test_render_gradient_matches_fp64_finite_differences():
     sc = S.with_gaussians(S.base_cameras(), X, q, s, rng.uniform(0.3, 0.9, n)).subset_views([0, 1])
     sc.sh_degree = 3
     sc.sh = rng.normal(0, 0.2, (n, 16, 3)).astype(np.float32)
-    W = _masked_weights(sc, rng)
+    W = S.masked_weights(sc, rng)
     gr = oracle.render_grad(sc, W)
 
     def fd(field, idx, h):

@@ -1,0 +1,163 @@
+"""The render's adjoint (tsp_render_backward and the autograd Function) on a
+B300, against the FP64 oracle's gradient and against finite differences of the
+GPU render, on 500 Gaussians with degree-3 colour coefficients in 4 views at
+64x64.  Loss weights are zeroed where a blend decision lies within 5 % of its
+threshold (there FP32 and FP64 may decide differently, and a finite difference
+would step across a jump).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu_ready():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_02586_b300 import build as tbuild
+    tbuild.build()
+    return True
+
+
+@pytest.fixture(scope="module")
+def case(gpu_ready):
+    rng = np.random.default_rng(5)
+    s = synth.make_scene("tiny", 31, n=500, views=4, width=64, height=64, focal=64.0, tracks=False)
+    s.sh_degree = 3
+    s.sh = rng.normal(0, 0.2, (s.n, 16, 3)).astype(np.float32)
+    W = S.masked_weights(s, rng)
+    return s, W
+
+
+def dev(s):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    return t(s.means_opacity), t(s.quats), t(s.scales), t(s.sh)
+
+
+def gpu_grad(s, W):
+    import torch
+    import paper_2604_02586_b300 as tsp
+    mo, q, sc, sh = dev(s)
+    with tsp.Context(0) as ctx:
+        rgb, _ = ctx.render(mo, q, sc, sh, s.sh_degree, s, sync=True)
+        gW = [torch.from_numpy(w).cuda() for w in W]
+        g = ctx.render_backward(mo, q, sc, sh, s.sh_degree, s, rgb, gW, sync=True)
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+
+
+def close(a, b, rtol, atol_frac):
+    atol = atol_frac * np.abs(b).max()
+    bad = np.abs(a - b) > atol + rtol * np.abs(b)
+    return bad.mean(), np.abs(a - b).max(), np.abs(b).max()
+
+
+def test_gradient_matches_the_oracle(case):
+    s, W = case
+    o = oracle.render_grad(s, W)
+    g = gpu_grad(s, W)
+    pairs = [("means", g["means_opacity"][:, :3], o["means"]), ("opacity", g["means_opacity"][:, 3], o["opacity"]),
+             ("scales", g["scales"][:, :3], o["scales"]), ("quats", g["quats"], o["quats"]),
+             ("sh", g["sh"], o["sh"])]
+    for name, a, b in pairs:
+        frac, err, mag = close(a, b, rtol=1e-3, atol_frac=1e-5)
+        assert frac == 0.0, (name, frac, err, mag)
+        assert mag > 0
+    assert np.all(g["scales"][:, 3] == 0)
+
+
+def test_gradient_matches_finite_differences(gpu_ready):
+    """Central differences of the GPU render's loss on 60 sampled parameters.  The
+    Gaussians are enlarged 3x so that a step (2e-4 for means, 3e-3 of the scale,
+    1e-3 for the other parameters) moves no blend decision past the 5 % margin
+    while the loss change stays well above the float32 rounding of the rendered
+    colours; the h and h/2 estimates must agree, which a tile-rectangle change would
+    break (at most 15 % of the samples may be set aside that way), and their
+    difference widens the tolerance."""
+    import copy
+    import torch
+    import paper_2604_02586_b300 as tsp
+    rng = np.random.default_rng(11)
+    s = synth.make_scene("tiny", 32, n=500, views=4, width=64, height=64, focal=64.0, tracks=False)
+    s.scales[:, :3] *= 3.0
+    s.sh_degree = 3
+    s.sh = rng.normal(0, 0.2, (s.n, 16, 3)).astype(np.float32)
+    W = S.masked_weights(s, rng)
+    g = gpu_grad(s, W)
+    Wt = [torch.from_numpy(w).cuda().double() for w in W]
+    ctx = tsp.Context(0)
+
+    def loss(sc):
+        mo, q, scl, sh = dev(sc)
+        rgb, _ = ctx.render(mo, q, scl, sh, sc.sh_degree, sc, sync=True)
+        return float(sum((r.double() * w).sum() for r, w in zip(rgb, Wt)))
+
+    def fd(field, idx, h):
+        a, b = copy.deepcopy(s), copy.deepcopy(s)
+        getattr(a, field)[idx] += h
+        getattr(b, field)[idx] -= h
+        return (loss(a) - loss(b)) / (2 * h)
+
+    checked = skipped = 0
+    for _ in range(60):
+        gi = int(rng.integers(0, s.n))
+        kind = rng.choice(["mean", "scale", "quat", "opacity", "sh"])
+        if kind == "mean":
+            field, idx, h = "means_opacity", (gi, int(rng.integers(0, 3))), 2e-4
+            an = g["means_opacity"][idx]
+        elif kind == "opacity":
+            field, idx, h = "means_opacity", (gi, 3), 1e-3
+            an = g["means_opacity"][idx]
+        elif kind == "scale":
+            k = int(rng.integers(0, 3))
+            field, idx, h = "scales", (gi, k), 3e-3 * float(s.scales[gi, k])
+            an = g["scales"][idx]
+        elif kind == "quat":
+            field, idx, h = "quats", (gi, int(rng.integers(0, 4))), 1e-3
+            an = g["quats"][idx]
+        else:
+            field, idx, h = "sh", (gi, int(rng.integers(0, 16)), int(rng.integers(0, 3))), 1e-3
+            an = g["sh"][idx]
+        f1, f2 = fd(field, idx, h), fd(field, idx, h / 2)
+        tol = 5e-3 + 3e-2 * abs(f1)
+        if abs(f1 - f2) > tol:
+            skipped += 1
+            continue
+        tol += 2 * abs(f1 - f2)
+        assert abs(an - f1) <= tol, (kind, idx, an, f1, f2)
+        checked += 1
+    ctx.close()
+    assert skipped <= 9 and checked >= 51
+
+
+def test_autograd_function_chains_log_scales_and_logits(case):
+    """Through torch.autograd: d/dlog_scale = s dL/ds, d/dlogit = o (1 - o) dL/do,
+    and the other gradients equal the library's."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    from paper_2604_02586_b300.autograd import render
+    s, W = case
+    g = gpu_grad(s, W)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    o = np.clip(s.means_opacity[:, 3].astype(np.float64), 1e-6, 1 - 1e-6)
+    means = t(s.means_opacity[:, :3]).requires_grad_()
+    logs = t(np.log(s.scales[:, :3])).requires_grad_()
+    quats = t(s.quats).requires_grad_()
+    logits = t(np.log(o / (1 - o))).requires_grad_()
+    sh = t(s.sh).requires_grad_()
+    with tsp.Context(0) as ctx:
+        img = render(means, logs, quats, logits, sh, s, ctx)
+        L = (img * torch.stack([torch.from_numpy(w).cuda() for w in W])).sum()
+        L.backward()
+    np.testing.assert_allclose(means.grad.cpu().numpy(), g["means_opacity"][:, :3], rtol=1e-3, atol=1e-4)
+    np.testing.assert_allclose(logs.grad.cpu().numpy(), g["scales"][:, :3] * s.scales[:, :3], rtol=1e-2, atol=1e-4)
+    sig = torch.sigmoid(logits.detach()).cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(logits.grad.cpu().numpy(), g["means_opacity"][:, 3] * sig * (1 - sig),
+                               rtol=1e-2, atol=1e-4)
+    np.testing.assert_allclose(sh.grad.cpu().numpy(), g["sh"], rtol=1e-3, atol=1e-5)
