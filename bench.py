@@ -40,11 +40,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve"],
+    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve", "train"],
                     help="capture: 200k Gaussians x 18 views at 1352x1014 (the metric's workload); "
                          "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound); "
                          "batch: 8 uneven frame pairs, batched vs one at a time; "
-                         "serve: Poisson requests at 40/s, request loop vs one at a time")
+                         "serve: Poisson requests at 40/s, request loop vs one at a time; "
+                         "train: render forward + L1 + backward, 300k Gaussians x 16 views")
     ap.add_argument("--rate", type=float, default=40.0, help="serve: mean requests per second")
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds of arrivals")
     ap.add_argument("--n", type=int, default=None)
@@ -546,8 +547,92 @@ def run_serve(a):
     print(json.dumps(line), flush=True)
 
 
+def run_train(a):
+    """One gradient-refinement step: the differentiable render (forward) of 300k
+    Gaussians with degree-3 colour in 16 views at 1352x1014, an L1 loss against
+    renders of the ground-truth-moved Gaussians, and the hand-written backward
+    with respect to means, log-scales, quaternions, opacity logits and colour."""
+    import torch
+    from scipy.spatial.transform import Rotation
+    import paper_2604_02586_b300 as tsp
+    from paper_2604_02586_b300 import build as tbuild
+    from paper_2604_02586_b300.autograd import render
+    import synth
+    tbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    s = synth.make_scene("capture", seed=4, n=300_000, views=16, tracks=False)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+    # targets: renders of the Gaussians after their ground-truth rigid motion
+    qx = s.quats[:, [1, 2, 3, 0]].astype(np.float64)
+    rot = Rotation.from_matrix(s.motion_R[s.labels]) * Rotation.from_quat(qx)
+    qm = rot.as_quat()[:, [3, 0, 1, 2]]
+    mo_gt = np.concatenate([s.gt_means(), s.means_opacity[:, 3:4]], 1)
+    ctx = tsp.Context(0)
+    tgt, _ = ctx.render(t(mo_gt), t(qm), t(s.scales), t(s.sh), s.sh_degree, s, sync=True)
+    target = torch.stack(tgt)
+    o = np.clip(s.means_opacity[:, 3].astype(np.float64), 1e-6, 1 - 1e-6)
+    params = dict(means=t(s.means_opacity[:, :3]), log_scales=t(np.log(s.scales[:, :3])), quats=t(s.quats),
+                  logits=t(np.log(o / (1 - o))), sh=t(s.sh))
+    for v in params.values():
+        v.requires_grad_()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for v in params.values():
+            v.grad = None
+        img = render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], s, ctx)
+        loss = (img - target).abs().mean()
+        loss.backward()
+        return loss
+
+    def fwd():
+        with torch.no_grad():
+            return render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], s, ctx)
+
+    def timed(fn, steps):
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        with ClockSampler(0) as clk:
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        return ms, clk.summary()
+
+    step_ms, clocks = timed(step, a.steps)
+    fwd_ms, _ = timed(fwd, a.steps)
+    loss = float(step().detach())
+    gnorm = {k: float(v.grad.norm()) for k, v in params.items()}
+    ctx.close()
+    units = s.n * s.num_views
+    line = {"metric": "gradient-refinement step (render + L1 + backward): Gaussian·view gradients/s",
+            "value": units / (float(np.mean(step_ms)) / 1e3), "unit": "Gaussian·view/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": float(np.mean(step_ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{s.n} Gaussians, SH degree {s.sh_degree}, {s.num_views} views at "
+                                   f"{int(s.width[0])}x{int(s.height[0])}, L1 loss against the ground-truth-moved render",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "forward_render_ms": float(np.mean(fwd_ms)),
+            "backward_and_loss_ms": float(np.mean(step_ms)) - float(np.mean(fwd_ms)),
+            "loss": loss, "grad_norms": gnorm, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.preset == "train":
+        run_train(a)
+        return
     if a.preset == "batch":
         run_batch(a)
     elif a.preset == "serve":
