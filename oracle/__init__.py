@@ -85,6 +85,9 @@ def lib():
                                                C.c_int, P, P]
         _lib.orc_render_grad.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_int, P, C.c_int, C.c_int,
                                          P, P, P, P, P, P, P]
+        _lib.orc_static_flags.argtypes = [C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_int, P]
+        _lib.orc_knn.argtypes = [C.c_int, P, P, C.c_int, P]
+        _lib.orc_regularize.argtypes = [C.c_int, P, P, P, P, P, P, P, P, C.c_int, P, P, P, P]
         _lib.orc_naive_ls.argtypes = [C.c_int, P, P, P, P]
         _lib.orc_project.argtypes = [P, P, P, P, P, P, P]
         _lib.orc_eig3.argtypes = [P, P, P]
@@ -314,3 +317,43 @@ def sh_basis(d):
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+REG_STATIC, REG_POS_MEDIAN, REG_POS_PROPAGATED, REG_COV_MEDIAN, REG_COV_PROPAGATED = 1, 2, 4, 8, 16
+
+
+def static_flags(npix, nstat, min_px=9.0, frac=0.9, min_views=2):
+    """Sec. 4.5.2 static Gaussians from per-view pixel counts [V, n] (float)."""
+    npix = np.ascontiguousarray(npix, np.float32)
+    nstat = np.ascontiguousarray(nstat, np.float32)
+    V, n = npix.shape
+    out = np.zeros(n, np.uint8)
+    lib().orc_static_flags(n, V, _ptr(npix), _ptr(nstat), float(min_px), float(frac), int(min_views), _ptr(out))
+    return out
+
+
+def knn(means_opacity, mask, k=8):
+    """The k nearest members of mask (other than the point) of every point, by
+    FP32 squared distance then index; -1 pads."""
+    mo = np.ascontiguousarray(means_opacity, np.float32)
+    m = np.ascontiguousarray(mask, np.uint8)
+    n = mo.shape[0]
+    out = np.zeros((n, k), np.int32)
+    lib().orc_knn(n, _ptr(mo), _ptr(m), int(k), _ptr(out))
+    return out
+
+
+def regularize(before, after, status, is_static, k=8):
+    """Motion regularization (Sec. 4.5): before/after = (means_opacity, quats,
+    scales) [n, 4] float32 of the first frame and of the fit; status the fit's
+    status bits.  Returns dict(means_opacity, quats, scales, flags)."""
+    b = [np.ascontiguousarray(a, np.float32) for a in before]
+    a = [np.ascontiguousarray(x, np.float32) for x in after]
+    st = np.ascontiguousarray(status, np.uint32)
+    stat = np.ascontiguousarray(is_static, np.uint8)
+    n = b[0].shape[0]
+    mo, q, sc = np.zeros((n, 4), np.float32), np.zeros((n, 4), np.float32), np.zeros((n, 4), np.float32)
+    fl = np.zeros(n, np.uint32)
+    lib().orc_regularize(n, _ptr(b[0]), _ptr(b[1]), _ptr(b[2]), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(st),
+                         _ptr(stat), int(k), _ptr(mo), _ptr(q), _ptr(sc), _ptr(fl))
+    return dict(means_opacity=mo, quats=q, scales=sc, flags=fl)

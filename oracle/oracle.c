@@ -1530,3 +1530,235 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Motion regularization (Sec. 4.5)                                            */
+/* ------------------------------------------------------------------------- */
+/* Readings (the text leaves them open):
+ *  - a Gaussian's motion components are its position change dmu = mu' - mu
+ *    (available when its position was solved) and, when its covariance was
+ *    solved, its scale change ds = s' - s (linear scales) and rotation change
+ *    dR = R' R^T as Euler angles (x, y, z) with dR = Rz(ez) Ry(ey) Rx(ex);
+ *  - static (Sec. 4.5.2): hit by more than min_px pixels with more than frac of
+ *    them static in at least min_views views; its motion is discarded;
+ *  - median filtering (Sec. 4.5.1): a Gaussian with a component gets, per
+ *    coordinate, the median over itself and its K nearest other Gaussians with
+ *    that component (static ones excluded);
+ *  - propagation (Sec. 4.5.2), after the filtering: a non-static Gaussian
+ *    without a component gets the mean of the filtered component over its K
+ *    nearest Gaussians with it;
+ *  - nearness: squared distance between first-frame means, in FP32 as
+ *    ((dx*dx + dy*dy) + dz*dz) with dx = x_q - x_p (the same decisions as the
+ *    FP32 implementation), ties by index.
+ * The new parameters are mu + dmu, s + ds, R(e) R (quaternion sign kept close
+ * to the old one). */
+
+#define REG_STATIC 1u
+#define REG_POS_MEDIAN 2u
+#define REG_POS_PROPAGATED 4u
+#define REG_COV_MEDIAN 8u
+#define REG_COV_PROPAGATED 16u
+
+static float dist2_f32(const float* a, const float* b)
+{
+    const float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+    const float s = xx + yy;
+    return s + zz;
+}
+
+/* The k nearest members of `mask` other than q (by (d2, index)); returns their count. */
+static int knn_brute(int n, const float* mo, const uint8_t* mask, int q, int k, int* out)
+{
+    float bd[64];
+    int bi[64], m = 0;
+    for (int p = 0; p < n; ++p) {
+        if (p == q || !mask[p]) continue;
+        const float d = dist2_f32(mo + 4 * (size_t)q, mo + 4 * (size_t)p);
+        if (m == k && !(d < bd[k - 1] || (d == bd[k - 1] && p < bi[k - 1]))) continue;
+        int j = m < k ? m++ : k - 1;
+        while (j > 0 && (d < bd[j - 1] || (d == bd[j - 1] && p < bi[j - 1]))) {
+            bd[j] = bd[j - 1]; bi[j] = bi[j - 1]; --j;
+        }
+        bd[j] = d; bi[j] = p;
+    }
+    for (int j = 0; j < m; ++j) out[j] = bi[j];
+    return m;
+}
+
+static int cmp_double(const void* a, const void* b)
+{
+    const double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : x > y;
+}
+
+static double median_of(double* v, int m)
+{
+    qsort(v, (size_t)m, sizeof(double), cmp_double);
+    return (m & 1) ? v[m / 2] : 0.5 * (v[m / 2 - 1] + v[m / 2]);
+}
+
+static void rot_of_quat(const float* q, double R[3][3])
+{
+    double qn[4];
+    quat_to_rot(q, R, qn);
+}
+
+static void euler_of(const double R[3][3], double e[3])
+{
+    /* R = Rz(c) Ry(b) Rx(a): R20 = -sin b, R21 = cos b sin a, R22 = cos b cos a,
+     * R10 = sin c cos b, R00 = cos c cos b */
+    double sb = -R[2][0];
+    if (sb > 1) sb = 1;
+    if (sb < -1) sb = -1;
+    e[1] = asin(sb);
+    e[0] = atan2(R[2][1], R[2][2]);
+    e[2] = atan2(R[1][0], R[0][0]);
+}
+
+static void rot_of_euler(const double e[3], double R[3][3])
+{
+    const double ca = cos(e[0]), sa = sin(e[0]), cb = cos(e[1]), sb = sin(e[1]), cc = cos(e[2]), sc = sin(e[2]);
+    R[0][0] = cc * cb; R[0][1] = cc * sb * sa - sc * ca; R[0][2] = cc * sb * ca + sc * sa;
+    R[1][0] = sc * cb; R[1][1] = sc * sb * sa + cc * ca; R[1][2] = sc * sb * ca - cc * sa;
+    R[2][0] = -sb;     R[2][1] = cb * sa;                R[2][2] = cb * ca;
+}
+
+static void quat_of_rot(const double R[3][3], double q[4])
+{
+    /* the largest of 1 + tr and 1 + 2 R_kk - tr picks the stable branch */
+    const double tr = R[0][0] + R[1][1] + R[2][2];
+    if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) {
+        const double h = 2.0 * sqrt(1.0 + tr);
+        q[0] = 0.25 * h; q[1] = (R[2][1] - R[1][2]) / h; q[2] = (R[0][2] - R[2][0]) / h; q[3] = (R[1][0] - R[0][1]) / h;
+    } else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) {
+        const double h = 2.0 * sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]);
+        q[0] = (R[2][1] - R[1][2]) / h; q[1] = 0.25 * h; q[2] = (R[0][1] + R[1][0]) / h; q[3] = (R[0][2] + R[2][0]) / h;
+    } else if (R[1][1] >= R[2][2]) {
+        const double h = 2.0 * sqrt(1.0 - R[0][0] + R[1][1] - R[2][2]);
+        q[0] = (R[0][2] - R[2][0]) / h; q[1] = (R[0][1] + R[1][0]) / h; q[2] = 0.25 * h; q[3] = (R[1][2] + R[2][1]) / h;
+    } else {
+        const double h = 2.0 * sqrt(1.0 - R[0][0] - R[1][1] + R[2][2]);
+        q[0] = (R[1][0] - R[0][1]) / h; q[1] = (R[0][2] + R[2][0]) / h; q[2] = (R[1][2] + R[2][1]) / h; q[3] = 0.25 * h;
+    }
+}
+
+/* Static test of Sec. 4.5.2 from per-view counts npix[V][n], nstat[V][n], in
+ * FP32 (nstat > frac * npix) as the FP32 implementation takes it. */
+int orc_static_flags(int n, int V, const float* npix, const float* nstat, float min_px, float frac, int min_views,
+                     uint8_t* is_static)
+{
+    for (int g = 0; g < n; ++g) {
+        int views = 0;
+        for (int v = 0; v < V; ++v) {
+            const float np = npix[(size_t)v * n + g], ns = nstat[(size_t)v * n + g];
+            if (np > min_px && ns > frac * np) ++views;
+        }
+        is_static[g] = views >= min_views;
+    }
+    return 0;
+}
+
+int orc_knn(int n, const float* means_opacity, const uint8_t* mask, int k, int* nbr /* [n][k], -1 pad */)
+{
+    if (k > 64) return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int q = 0; q < n; ++q) {
+        int out[64];
+        const int m = knn_brute(n, means_opacity, mask, q, k, out);
+        for (int j = 0; j < k; ++j) nbr[(size_t)q * k + j] = j < m ? out[j] : -1;
+    }
+    return 0;
+}
+
+int orc_regularize(int n, const float* mo0, const float* q0, const float* s0, const float* mo1, const float* q1,
+                   const float* s1, const uint32_t* status, const uint8_t* is_static, int k,
+                   float* mo_out, float* q_out, float* s_out, uint32_t* flags)
+{
+    if (k > 64) return -1;
+    uint8_t* has_pos = calloc((size_t)n + 1, 1);
+    uint8_t* has_cov = calloc((size_t)n + 1, 1);
+    double* dpos = calloc((size_t)n * 3 + 1, sizeof(double));
+    double* dcov = calloc((size_t)n * 6 + 1, sizeof(double));    /* ds (3), rotation Euler angles (3) */
+    for (int g = 0; g < n; ++g) {
+        has_pos[g] = !is_static[g] && (status[g] & OS_POS_OK);
+        has_cov[g] = !is_static[g] && (status[g] & OS_COV_OK);
+        for (int i = 0; i < 3; ++i) dpos[3 * g + i] = (double)mo1[4 * g + i] - (double)mo0[4 * g + i];
+        double Ra[3][3], Rb[3][3], D[3][3];
+        rot_of_quat(q0 + 4 * (size_t)g, Ra);
+        rot_of_quat(q1 + 4 * (size_t)g, Rb);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) D[i][j] = Rb[i][0] * Ra[j][0] + Rb[i][1] * Ra[j][1] + Rb[i][2] * Ra[j][2];
+        for (int i = 0; i < 3; ++i) dcov[6 * g + i] = (double)s1[4 * g + i] - (double)s0[4 * g + i];
+        euler_of(D, dcov + 6 * (size_t)g + 3);
+    }
+    int* np = malloc(sizeof(int) * ((size_t)n * k + 1));
+    int* nc = malloc(sizeof(int) * ((size_t)n * k + 1));
+    orc_knn(n, mo0, has_pos, k, np);
+    orc_knn(n, mo0, has_cov, k, nc);
+    /* pass 1: median filter of every Gaussian that has the component */
+    double* fpos = calloc((size_t)n * 3 + 1, sizeof(double));
+    double* fcov = calloc((size_t)n * 6 + 1, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int g = 0; g < n; ++g) {
+        double vals[65];
+        for (int part = 0; part < 2; ++part) {
+            const int* nb = (part == 0 ? np : nc) + (size_t)g * k;
+            const uint8_t* has = part == 0 ? has_pos : has_cov;
+            const double* d = part == 0 ? dpos : dcov;
+            double* fo = part == 0 ? fpos : fcov;
+            const int dim = part == 0 ? 3 : 6;
+            if (!has[g]) continue;
+            int m = 0;
+            while (m < k && nb[m] >= 0) ++m;
+            for (int c = 0; c < dim; ++c) {
+                vals[0] = d[(size_t)dim * g + c];
+                for (int j = 0; j < m; ++j) vals[1 + j] = d[(size_t)dim * nb[j] + c];
+                fo[(size_t)dim * g + c] = median_of(vals, m + 1);
+            }
+        }
+    }
+    /* pass 2: propagation of the filtered motion; new parameters */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int g = 0; g < n; ++g) {
+        uint32_t fl = is_static[g] ? REG_STATIC : 0u;
+        double newpos[3] = {0, 0, 0}, newcov[6] = {0, 0, 0, 0, 0, 0};
+        for (int part = 0; part < 2; ++part) {
+            const int* nb = (part == 0 ? np : nc) + (size_t)g * k;
+            const uint8_t* has = part == 0 ? has_pos : has_cov;
+            const double* fd = part == 0 ? fpos : fcov;
+            const int dim = part == 0 ? 3 : 6;
+            double* out = part == 0 ? newpos : newcov;
+            if (is_static[g]) continue;                          /* motion discarded */
+            int m = 0;
+            while (m < k && nb[m] >= 0) ++m;
+            if (has[g]) {
+                for (int c = 0; c < dim; ++c) out[c] = fd[(size_t)dim * g + c];
+                fl |= part == 0 ? REG_POS_MEDIAN : REG_COV_MEDIAN;
+            } else if (m > 0) {
+                for (int c = 0; c < dim; ++c) {
+                    double acc = 0;
+                    for (int j = 0; j < m; ++j) acc += fd[(size_t)dim * nb[j] + c];
+                    out[c] = acc / m;
+                }
+                fl |= part == 0 ? REG_POS_PROPAGATED : REG_COV_PROPAGATED;
+            }
+        }
+        for (int i = 0; i < 3; ++i) mo_out[4 * g + i] = (float)((double)mo0[4 * g + i] + newpos[i]);
+        mo_out[4 * g + 3] = mo0[4 * g + 3];
+        for (int i = 0; i < 3; ++i) s_out[4 * g + i] = (float)((double)s0[4 * g + i] + newcov[i]);
+        s_out[4 * g + 3] = s0[4 * g + 3];
+        double Ra[3][3], E[3][3], Rn[3][3], qn[4];
+        rot_of_quat(q0 + 4 * (size_t)g, Ra);
+        rot_of_euler(newcov + 3, E);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Rn[i][j] = E[i][0] * Ra[0][j] + E[i][1] * Ra[1][j] + E[i][2] * Ra[2][j];
+        quat_of_rot(Rn, qn);
+        const double dot = qn[0] * q0[4 * g] + qn[1] * q0[4 * g + 1] + qn[2] * q0[4 * g + 2] + qn[3] * q0[4 * g + 3];
+        for (int i = 0; i < 4; ++i) q_out[4 * g + i] = (float)(dot < 0 ? -qn[i] : qn[i]);
+        flags[g] = fl;
+    }
+    free(fpos); free(fcov);
+    free(has_pos); free(has_cov); free(dpos); free(dcov); free(np); free(nc);
+    return 0;
+}

@@ -634,3 +634,100 @@ def test_render_gradient_matches_fp64_finite_differences():
         assert abs(an - f2) <= 2e-3 * max(abs(f2), 1e-3), (field, idx, an, f2)
     assert skipped <= len(rows) // 20
     assert np.abs(gr["means"]).max() > 0.1 and np.abs(gr["sh"]).max() > 0.01
+
+
+def test_knn_matches_fp64_brute_force_away_from_ties():
+    """Sec. 4.5.1 neighbours: the oracle's FP32 nearest neighbours equal an FP64
+    brute force wherever the k-th and (k+1)-th FP64 distances are apart."""
+    rng = np.random.default_rng(21)
+    n, k = 1500, 8
+    mo = np.zeros((n, 4), np.float32)
+    mo[:, :3] = rng.uniform(-1, 1, (n, 3))
+    mask = rng.random(n) < 0.8
+    nb = oracle.knn(mo, mask, k)
+    X = mo[:, :3].astype(np.float64)
+    d2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    d2[:, ~mask] = np.inf
+    np.fill_diagonal(d2, np.inf)
+    order = np.argsort(d2, axis=1, kind="stable")
+    checked = 0
+    for q in range(n):
+        dk, dk1 = d2[q, order[q, k - 1]], d2[q, order[q, k]]
+        if dk1 - dk < 1e-5 * dk1:
+            continue
+        assert set(nb[q]) == set(order[q, :k]), q
+        checked += 1
+    assert checked > 0.95 * n
+
+
+def test_static_rule_by_construction():
+    """Sec. 4.5.2: more than 9 pixels, more than 90 % static, in at least 2 views."""
+    npix = np.array([[10, 10, 9, 20, 10], [10, 0, 9, 20, 10]], np.float32)
+    nstat = np.array([[10, 10, 9, 18, 10], [10, 0, 9, 19, 9]], np.float32)
+    # g0: both views 10/10 -> static; g1: one view; g2: 9 px is not > 9;
+    # g3: 18/20 = 0.9 is not > 0.9 in view 0; g4: 9/10 in view 1
+    assert list(oracle.static_flags(npix, nstat)) == [1, 0, 0, 0, 0]
+
+
+def _grid_gaussians(side=7, spacing=0.1):
+    g = np.arange(side) * spacing
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    n = X.shape[0]
+    mo = np.concatenate([X, np.full((n, 1), 0.5)], 1).astype(np.float32)
+    rng = np.random.default_rng(4)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    s = np.concatenate([rng.uniform(0.01, 0.03, (n, 3)), np.zeros((n, 1))], 1)
+    return mo, q.astype(np.float32), s.astype(np.float32)
+
+
+def _moved(mo, q, s, Rm, t, ds):
+    from scipy.spatial.transform import Rotation
+    mo2 = mo.copy()
+    mo2[:, :3] = (mo[:, :3].astype(np.float64) @ Rm.T + t).astype(np.float32)
+    r = Rotation.from_matrix(Rm) * Rotation.from_quat(q[:, [1, 2, 3, 0]].astype(np.float64))
+    q2 = r.as_quat()[:, [3, 0, 1, 2]].astype(np.float32)
+    q2 *= np.sign((q2 * q).sum(1))[:, None]
+    s2 = s.copy()
+    s2[:, :3] += ds
+    return mo2, q2, s2
+
+
+def test_regularization_median_filter_and_propagation():
+    """A common motion (translation, small rotation about the grid's origin, scale
+    change): the median filter keeps it, removes an outlier's salt-and-pepper
+    motion, gives an unsolvable Gaussian its neighbours' motion, and a static
+    Gaussian keeps its first-frame parameters."""
+    from scipy.spatial.transform import Rotation
+    mo, q, s = _grid_gaussians()
+    n = mo.shape[0]
+    Rm = Rotation.from_euler("xyz", [0.02, -0.015, 0.01]).as_matrix()
+    t = np.array([0.05, -0.02, 0.03])
+    Rm_small = np.eye(3)                      # translation-dominated: means move rigidly by t
+    mo2, q2, s2 = _moved(mo, q, s, Rm_small, t, 0.002)
+    # every Gaussian's rotation also turns by Rm (world frame), means only translate
+    r2 = Rotation.from_matrix(Rm) * Rotation.from_quat(q[:, [1, 2, 3, 0]].astype(np.float64))
+    q2 = r2.as_quat()[:, [3, 0, 1, 2]].astype(np.float32)
+    q2 *= np.sign((q2 * q).sum(1))[:, None]
+    status = np.full(n, 3, np.uint32)         # position and covariance solved
+    out_i, unsolved_i, static_i = 171, 172, 100
+    mo2[out_i, :3] += 0.5                     # an outlier
+    status[unsolved_i] = 0
+    is_static = np.zeros(n, np.uint8)
+    is_static[static_i] = 1
+    r = oracle.regularize((mo, q, s), (mo2, q2, s2), status, is_static)
+    keep = np.ones(n, bool)
+    keep[[static_i]] = False
+    np.testing.assert_allclose(r["means_opacity"][keep, :3], mo[keep, :3] + t, atol=2e-6)
+    np.testing.assert_allclose(r["scales"][keep, :3], s[keep, :3] + 0.002, atol=2e-6)
+    qa = r["quats"][keep].astype(np.float64)
+    qb = q2[keep].astype(np.float64)
+    qa /= np.linalg.norm(qa, axis=1, keepdims=True)
+    qb /= np.linalg.norm(qb, axis=1, keepdims=True)
+    ang = 2 * np.arccos(np.clip(np.abs((qa * qb).sum(1)), 0, 1))
+    assert ang.max() < 1e-5
+    assert r["flags"][out_i] & oracle.REG_POS_MEDIAN
+    assert r["flags"][unsolved_i] & oracle.REG_POS_PROPAGATED and r["flags"][unsolved_i] & oracle.REG_COV_PROPAGATED
+    assert r["flags"][static_i] == oracle.REG_STATIC
+    np.testing.assert_array_equal(r["means_opacity"][static_i], mo[static_i])
+    np.testing.assert_array_equal(r["scales"][static_i], s[static_i])
