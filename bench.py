@@ -40,12 +40,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve", "train"],
+    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve", "train", "reg"],
                     help="capture: 200k Gaussians x 18 views at 1352x1014 (the metric's workload); "
                          "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound); "
                          "batch: 8 uneven frame pairs, batched vs one at a time; "
                          "serve: Poisson requests at 40/s, request loop vs one at a time; "
-                         "train: render forward + L1 + backward, 300k Gaussians x 16 views")
+                         "train: render forward + L1 + backward, 300k Gaussians x 16 views; "
+                         "reg: motion regularization after the capture frame's fit")
     ap.add_argument("--rate", type=float, default=40.0, help="serve: mean requests per second")
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds of arrivals")
     ap.add_argument("--n", type=int, default=None)
@@ -628,10 +629,92 @@ def run_train(a):
     print(json.dumps(line), flush=True)
 
 
+def run_reg(a):
+    """Motion regularization (Sec. 4.5) of the capture frame pair: the fit of
+    200k Gaussians x 18 views runs once, then tsp_regularize (static flags from
+    the context's moments, exact 8-nearest neighbours of both components, median
+    filter, propagation) is timed alone and together with the fit."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    from paper_2604_02586_b300 import build as tbuild
+    import synth
+    tbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    s = synth.make_scene("capture", seed=rank_seed(0), n=a.n, views=a.views)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    mo, q, sc = t(s.means_opacity), t(s.quats), t(s.scales)
+    disp, vis = [t(d) for d in s.disp], [t(v) for v in s.vis]
+    ctx = tsp.Context(0)
+    out = ctx.fit_motion(mo, q, sc, s, disp, vis, sync=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def reg():
+        return ctx.regularize((mo, q, sc), out, s.num_views)
+
+    def fit_reg():
+        o = ctx.fit_motion(mo, q, sc, s, disp, vis, out=out)
+        return ctx.regularize((mo, q, sc), o, s.num_views)
+
+    def timed(fn, steps):
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        with ClockSampler(0) as clk:
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        return ms, clk.summary()
+
+    reg_ms, clocks = timed(reg, a.steps)
+    both_ms, _ = timed(fit_reg, a.steps)
+    r = reg()
+    ctx.sync()
+    fl = r["flags"].cpu().numpy().view(np.uint32)
+    counts = {name: int(((fl & bit) > 0).sum()) for name, bit in
+              (("static", 1), ("pos_median", 2), ("pos_propagated", 4), ("cov_median", 8), ("cov_propagated", 16))}
+    ctx.close()
+    cpu = None
+    if not a.no_cpu:
+        import oracle
+        m = 20_000                                       # bounded sample: the first 20k Gaussians
+        st = out["status"].cpu().numpy().view(np.uint32)[:m]
+        after = tuple(out[k].cpu().numpy()[:m] for k in ("means", "quats", "scales"))
+        is_static = (fl[:m] & 1).astype(np.uint8)
+        t0 = time.perf_counter()
+        oracle.regularize((s.means_opacity[:m], s.quats[:m], s.scales[:m]), after, st, is_static, 8)
+        dt = time.perf_counter() - t0
+        cpu = {"value": m / dt, "unit": "Gaussians/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle.regularize on the first {m} Gaussians of the fitted frame "
+                         "(brute-force neighbours, O(m^2))"}
+    line = {"metric": "motion regularization (Sec. 4.5): Gaussians regularized/s",
+            "value": s.n / (float(np.mean(reg_ms)) / 1e3), "unit": "Gaussians/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": float(np.mean(reg_ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"capture frame pair: {s.n} Gaussians x {s.num_views} views, fitted once; "
+                                   "k = 8, static rule > 9 px, > 90 %, >= 2 views",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "fit_plus_reg_ms": float(np.mean(both_ms)), "p50_ms": float(np.percentile(reg_ms, 50)),
+            "p99_ms": float(np.percentile(reg_ms, 99)), "flags": counts, "clocks": clocks,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.preset == "train":
         run_train(a)
+        return
+    if a.preset == "reg":
+        run_reg(a)
         return
     if a.preset == "batch":
         run_batch(a)

@@ -243,6 +243,74 @@ tsp_status tsp_render_backward(tsp_context* ctx, const tsp_gaussians* g, const f
                                const tsp_camera* cams, int num_views, const float* const* rgb,
                                const float* const* grad_rgb, const tsp_render_grads* out, void* stream);
 
+/* ---- Motion regularization (Sec. 4.5) ------------------------------------ */
+/* Per-Gaussian bits of tsp_reg_result.flags. */
+#define TSP_REG_STATIC 1u           /* static (Sec. 4.5.2): motion discarded           */
+#define TSP_REG_POS_MEDIAN 2u       /* position change median-filtered (Sec. 4.5.1)    */
+#define TSP_REG_POS_PROPAGATED 4u   /* position change propagated from neighbours      */
+#define TSP_REG_COV_MEDIAN 8u       /* scale and rotation change median-filtered       */
+#define TSP_REG_COV_PROPAGATED 16u  /* scale and rotation change propagated            */
+#define TSP_REG_MAX_K 16
+
+typedef struct tsp_reg_options {
+    int32_t k;                  /* nearest neighbours, 1..TSP_REG_MAX_K; Sec. 5.1: 8 */
+    float static_min_px;        /* Sec. 4.5.2: a static view has more than 9 pixels  */
+    float static_frac;          /*    and more than 0.9 of them static (|d| < 1 px), */
+    int32_t static_min_views;   /*    in at least 2 views                            */
+} tsp_reg_options;
+
+tsp_status tsp_default_reg_options(tsp_reg_options* o);
+
+typedef struct tsp_reg_result {
+    float* means_opacity;       /* [n][4] regularized (x, y, z, opacity of before)  */
+    float* quats;               /* [n][4] regularized (w, x, y, z), unit             */
+    float* scales;              /* [n][4] regularized (sx, sy, sz, w of before)      */
+    uint32_t* flags;            /* [n] TSP_REG_* bits                                */
+    int32_t* nbr_pos;           /* optional [n][k]: the k nearest Gaussians with a   */
+    int32_t* nbr_cov;           /*    solved position / covariance, -1 padded        */
+} tsp_reg_result;
+
+/* Motion regularization of one frame pair (Sec. 4.5), after tsp_fit_motion.
+ * before: the Gaussians the fit started from; fitted: its outputs (means, quats,
+ * scales, status; the optional view arrays are not read).  A Gaussian's motion
+ * components are its position change dmu = mu' - mu (when TSP_POS_OK) and, when
+ * TSP_COV_OK, its scale change ds = s' - s and rotation change dR = R' R^T as
+ * Euler angles (x, y, z), dR = Rz(ez) Ry(ey) Rx(ex).
+ *  - Static (Sec. 4.5.2): more than static_min_px pixels and more than
+ *    static_frac of them static (view_moments slots 13 and 14, compared in FP32
+ *    as nstat > frac * npix) in at least static_min_views views.  Its motion is
+ *    discarded and it takes no part in the filtering or the propagation.
+ *  - Median filter (Sec. 4.5.1): a Gaussian with a component takes, coordinate by
+ *    coordinate, the median of that component over itself and its k nearest
+ *    other Gaussians with the component.
+ *  - Propagation (Sec. 4.5.2), from the filtered values: a non-static Gaussian
+ *    without a component takes the mean of the component over its k nearest
+ *    Gaussians with it (none: unchanged).
+ *  - Nearness is the FP32 squared distance between `before` means, computed as
+ *    ((dx*dx + dy*dy) + dz*dz) with dx = x_query - x_other and no fused
+ *    multiply-add, ties by the smaller index; the neighbour sets are exact.
+ * The outputs are mu + dmu, s + ds and R(e) R (quaternion sign kept on the side
+ * of the old one).  view_moments: device [num_views][n][16] as
+ * tsp_result.view_moments, or NULL for the moments the context holds from its
+ * last tsp_fit_motion / tsp_fit_motion_host call, which must have had the same
+ * n and num_views (INVALID_ARG otherwise).  Means must be finite.  All arrays are
+ * device memory of the context's device, 16-byte aligned ([n][4]) or 4-byte
+ * aligned (flags, nbr_*); outputs must not overlap inputs.  Device-side grid
+ * sizing: no host wait; enqueues on `stream` and may be captured in a CUDA graph
+ * once the workspace for this n and k exists.  Errors: INVALID_ARG, OOM, BUDGET,
+ * CUDA. */
+tsp_status tsp_regularize(tsp_context* ctx, const tsp_gaussians* before, const tsp_result* fitted,
+                          const float* view_moments, int num_views, const tsp_reg_options* opt,
+                          const tsp_reg_result* out, void* stream);
+
+/* The k nearest members of `mask` (device uint8 [n], non-zero = member) other
+ * than the point itself, for every point of means_opacity (device [n][4]), by
+ * the FP32 squared distance and tie rule of tsp_regularize; nbr: device
+ * int32 [n][k], -1 padded when fewer than k members exist.  1 <= k <=
+ * TSP_REG_MAX_K.  Enqueues on `stream`.  Errors as tsp_regularize. */
+tsp_status tsp_knn(tsp_context* ctx, const float* means_opacity, const uint8_t* mask, int n, int k,
+                   int32_t* nbr, void* stream);
+
 /* Wait up to timeout_ms (< 0: forever) for `stream`, then read and clear the
  * device status word.  Returns OK, TIMEOUT (work still running; call again),
  * OVERFLOW (the last step ran out of pair capacity; its results are invalid and

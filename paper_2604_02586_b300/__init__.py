@@ -29,6 +29,8 @@ class TSP:
         I_VIEW_MEANS, I_VIEW_COV = range(10)
     STAGES = ("project", "scan", "emit", "tile_sort", "raster", "view_solve", "multiview")
     MAX_VIEWS = 32
+    REG_STATIC, REG_POS_MEDIAN, REG_POS_PROPAGATED, REG_COV_MEDIAN, REG_COV_PROPAGATED = 1, 2, 4, 8, 16
+    REG_MAX_K = 16
 
 
 class Camera(C.Structure):
@@ -58,6 +60,16 @@ class Frame(C.Structure):
 
 class RenderGrads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class RegOptions(C.Structure):
+    _fields_ = [("k", C.c_int32), ("static_min_px", C.c_float), ("static_frac", C.c_float),
+                ("static_min_views", C.c_int32)]
+
+
+class RegResult(C.Structure):
+    _fields_ = [("means_opacity", C.c_void_p), ("quats", C.c_void_p), ("scales", C.c_void_p),
+                ("flags", C.c_void_p), ("nbr_pos", C.c_void_p), ("nbr_cov", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -90,6 +102,9 @@ def lib():
         L.tsp_autotune.argtypes = [P, P, I, I, P, P, P]
         L.tsp_render.argtypes = [P, P, P, I, P, I, P, P, P]
         L.tsp_render_backward.argtypes = [P, P, P, I, P, I, P, P, P, P]
+        L.tsp_default_reg_options.argtypes = [P]
+        L.tsp_regularize.argtypes = [P, P, P, P, I, P, P, P]
+        L.tsp_knn.argtypes = [P, P, P, I, I, P, P]
         L.tsp_sync.argtypes = [P, P, I]
         L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
         L.tsp_workspace_bytes.argtypes = [P, P]
@@ -103,7 +118,8 @@ def lib():
         L.tsp_version.restype = I
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
                      "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render",
-                     "tsp_render_backward", "tsp_sync", "tsp_inspect",
+                     "tsp_render_backward", "tsp_sync", "tsp_inspect", "tsp_default_reg_options",
+                     "tsp_regularize", "tsp_knn",
                      "tsp_workspace_bytes", "tsp_stage_times"):
             getattr(L, name).restype = I
         _lib = L
@@ -398,6 +414,61 @@ class Context:
         if sync:
             self.sync(stream)
         return out
+
+    # -- motion regularization (Sec. 4.5) ---------------------------------------
+    def regularize(self, before, fitted, num_views, *, view_moments=None, k=8, static_min_px=9.0,
+                   static_frac=0.9, static_min_views=2, neighbours=False, stream=None, sync=False):
+        """Median filter and propagation of a fit's motion.  ``before`` =
+        (means_opacity, quats, scales) the fit started from, ``fitted`` its output
+        dict (means, quats, scales, status), CUDA tensors.  ``view_moments``
+        [V, n, 16] or None for the moments of this context's last fit_motion
+        (same n and ``num_views``).  Returns dict(means_opacity, quats, scales,
+        flags) and, with ``neighbours``, nbr_pos / nbr_cov [n, k]."""
+        import torch
+        mo, q, sc = before
+        n = int(mo.shape[0])
+        dev = mo.device
+        f32 = torch.float32
+        for name, t in (("means_opacity", mo), ("quats", q), ("scales", sc)):
+            _need(t, (n, 4), f32, dev, name)
+        for name in ("means", "quats", "scales"):
+            _need(fitted[name], (n, 4), f32, dev, f"fitted[{name}]")
+        _need(fitted["status"], (n,), torch.int32, dev, "fitted[status]")
+        if view_moments is not None:
+            _need(view_moments, (int(num_views), n, 16), f32, dev, "view_moments")
+        out = dict(means_opacity=torch.empty((n, 4), dtype=f32, device=dev),
+                   quats=torch.empty((n, 4), dtype=f32, device=dev),
+                   scales=torch.empty((n, 4), dtype=f32, device=dev),
+                   flags=torch.empty((n,), dtype=torch.int32, device=dev))
+        if neighbours:
+            out["nbr_pos"] = torch.empty((n, int(k)), dtype=torch.int32, device=dev)
+            out["nbr_cov"] = torch.empty((n, int(k)), dtype=torch.int32, device=dev)
+        g = Gaussians(n, mo.data_ptr(), q.data_ptr(), sc.data_ptr())
+        r = Result(fitted["means"].data_ptr(), fitted["quats"].data_ptr(), fitted["scales"].data_ptr(),
+                   fitted["status"].data_ptr(), None, None, None)
+        o = RegOptions(int(k), float(static_min_px), float(static_frac), int(static_min_views))
+        rr = RegResult(*[(out[x].data_ptr() if x in out else None) for x in
+                         ("means_opacity", "quats", "scales", "flags", "nbr_pos", "nbr_cov")])
+        self._check(lib().tsp_regularize(self._h, C.byref(g), C.byref(r), _dptr(view_moments), int(num_views),
+                                         C.byref(o), C.byref(rr), _stream_handle(stream)), "tsp_regularize")
+        if sync:
+            self.sync(stream)
+        return out
+
+    def knn(self, means_opacity, mask, k=8, stream=None, sync=False):
+        """The k nearest members of ``mask`` (uint8 [n]) of every point, by FP32
+        squared distance then index; int32 [n, k], -1 padded."""
+        import torch
+        n = int(means_opacity.shape[0])
+        dev = means_opacity.device
+        _need(means_opacity, (n, 4), torch.float32, dev, "means_opacity")
+        _need(mask, (n,), torch.uint8, dev, "mask")
+        nbr = torch.empty((n, int(k)), dtype=torch.int32, device=dev)
+        self._check(lib().tsp_knn(self._h, C.c_void_p(means_opacity.data_ptr()), C.c_void_p(mask.data_ptr()), n,
+                                  int(k), C.c_void_p(nbr.data_ptr()), _stream_handle(stream)), "tsp_knn")
+        if sync:
+            self.sync(stream)
+        return nbr
 
     def sync(self, stream=None, timeout_ms: int = -1):
         st = C.c_void_p(0) if stream is None and not _torch_cuda() else _stream_handle(stream)

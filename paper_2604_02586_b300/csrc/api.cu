@@ -32,6 +32,7 @@ struct tsp_context {
     // per tile
     Buf tiles, tile_off, span_sum, queue;
     Buf gacc;                       // render backward: per (view, Gaussian) 2D gradients
+    Buf reg;                        // regularization: neighbour grid, components, neighbours
     int resident_ctas = 0;          // CTAs of the persistent raster resident at once
     // pairs
     Buf pairs, pairs_tmp;
@@ -48,6 +49,8 @@ struct tsp_context {
     // last call
     size_t last_R = 0;              // (view, Gaussian) records of the last call
     uint32_t last_NT = 0;
+    // moments of the last single-frame fit: [last_fit_V][last_fit_n][16], else -1
+    int last_fit_n = -1, last_fit_V = -1;
 };
 
 namespace {
@@ -416,9 +419,14 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
         }
     }
     Work w{};
+    ctx->last_fit_n = ctx->last_fit_V = -1;
     if ((s = ensure_work(ctx, R, NT, false, w))) return s;
     ctx->last_R = (size_t)R;
     ctx->last_NT = NT;
+    if (F == 1) {
+        ctx->last_fit_n = frames[0].g.n;
+        ctx->last_fit_V = frames[0].num_views;
+    }
     if (vs.nmax == 0) return TSP_OK;
     const FitParams fp = fit_params(ctx->opt);
     const int V = vs.V;
@@ -446,6 +454,62 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
             TSP_CUDA(cudaMemcpyAsync(fr.out.view_moments, w.moments + 4 * vs.vrec[vs.fview[f]], recs * 64,
                                      cudaMemcpyDeviceToDevice, st));
     }
+    return TSP_OK;
+}
+
+// Neighbour-grid scratch (and, with rp, the regularization arrays) for n points,
+// carved from one buffer.
+tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp)
+{
+    const uint32_t C = knn_max_cells(n);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t nn = (size_t)n;
+    const size_t o_acc = take(32), o_gp = take(sizeof(GridParam)), o_st = take(16);
+    const size_t o_count = take(((size_t)C + 1) * 4), o_off = take(((size_t)C + 1) * 4);
+    const size_t o_span = take(((size_t)C / 1024 + 2) * 8), o_slot = take(nn * 8), o_sorted = take(nn * 16);
+    size_t o_mask = 0, o_vec = 0, o_nbr = 0;
+    if (rp) {
+        o_mask = take(nn);
+        o_vec = take(nn * 16 * 6);
+        o_nbr = take(nn * (size_t)k * 4 * 2);
+    }
+    tsp_status s;
+    if ((s = ensure(ctx, ctx->reg, off))) return s;
+    char* b = (char*)ctx->reg.p;
+    kw.acc = (uint32_t*)(b + o_acc);
+    kw.gp = (GridParam*)(b + o_gp);
+    kw.status = (uint32_t*)(b + o_st);
+    kw.count = (uint32_t*)(b + o_count);
+    kw.cell_off = (uint32_t*)(b + o_off);
+    kw.span_sum = (unsigned long long*)(b + o_span);
+    kw.slot = (uint2*)(b + o_slot);
+    kw.sorted = (float4*)(b + o_sorted);
+    if (rp) {
+        rp->mask = (uint8_t*)(b + o_mask);
+        float4* v = (float4*)(b + o_vec);
+        rp->dpos = v;
+        rp->dscale = v + nn;
+        rp->drot = v + 2 * nn;
+        rp->fpos = v + 3 * nn;
+        rp->fscale = v + 4 * nn;
+        rp->frot = v + 5 * nn;
+        if (!rp->nbr_pos) rp->nbr_pos = (int32_t*)(b + o_nbr);
+        if (!rp->nbr_cov) rp->nbr_cov = (int32_t*)(b + o_nbr) + nn * (size_t)k;
+    }
+    return TSP_OK;
+}
+
+tsp_status check_device_array(tsp_context* ctx, const void* p, size_t align, const char* what, bool optional)
+{
+    if (!p) return optional ? TSP_OK : fail(ctx, TSP_ERR_INVALID_ARG, std::string(what) + " is NULL");
+    if (!aligned(p, align)) return fail(ctx, TSP_ERR_INVALID_ARG, std::string(what) + " misaligned");
+    if (!device_accessible(p, ctx->device))
+        return fail(ctx, TSP_ERR_INVALID_ARG, std::string(what) + " is not device memory of the context's device");
     return TSP_OK;
 }
 
@@ -549,7 +613,7 @@ tsp_status tsp_destroy(tsp_context* ctx)
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->oref, &ctx->color,
-                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum, &ctx->queue, &ctx->gacc,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum, &ctx->queue, &ctx->gacc, &ctx->reg,
                   &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
                   &ctx->st_tracks};
     for (Buf* b : all) release(ctx, *b);
@@ -903,6 +967,107 @@ tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frame
     if (s != TSP_OK) return s;
     ctx->opt.raster_variant = best_v;
     if (chosen) *chosen = best_v;
+    return TSP_OK;
+}
+
+tsp_status tsp_default_reg_options(tsp_reg_options* o)
+{
+    if (!o) return TSP_ERR_INVALID_ARG;
+    o->k = 8;
+    o->static_min_px = 9.0f;
+    o->static_frac = 0.9f;
+    o->static_min_views = 2;
+    return TSP_OK;
+}
+
+tsp_status tsp_regularize(tsp_context* ctx, const tsp_gaussians* before, const tsp_result* fitted,
+                          const float* view_moments, int num_views, const tsp_reg_options* opt,
+                          const tsp_reg_result* out, void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    tsp_reg_options o;
+    if (opt) o = *opt;
+    else tsp_default_reg_options(&o);
+    if (o.k < 1 || o.k > TSP_REG_MAX_K) return fail(ctx, TSP_ERR_INVALID_ARG, "k must be in [1, TSP_REG_MAX_K]");
+    if (!(o.static_min_px >= 0.0f && o.static_min_px < 1e30f))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "static_min_px must be finite and >= 0");
+    if (!(o.static_frac >= 0.0f && o.static_frac <= 1.0f))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "static_frac must be in [0, 1]");
+    if (o.static_min_views < 1) return fail(ctx, TSP_ERR_INVALID_ARG, "static_min_views must be >= 1");
+    if (num_views < 0 || num_views > TSP_MAX_VIEWS) return fail(ctx, TSP_ERR_INVALID_ARG, "num_views out of range");
+    tsp_status s;
+    if ((s = check_gaussians(ctx, before, true))) return s;
+    if (!fitted || !out) return fail(ctx, TSP_ERR_INVALID_ARG, "fitted or out is NULL");
+    const int n = before->n;
+    if (n == 0) return TSP_OK;
+    if ((s = check_device_array(ctx, fitted->means, 16, "fitted means", false))) return s;
+    if ((s = check_device_array(ctx, fitted->quats, 16, "fitted quats", false))) return s;
+    if ((s = check_device_array(ctx, fitted->scales, 16, "fitted scales", false))) return s;
+    if ((s = check_device_array(ctx, fitted->status, 4, "fitted status", false))) return s;
+    if ((s = check_device_array(ctx, out->means_opacity, 16, "out means_opacity", false))) return s;
+    if ((s = check_device_array(ctx, out->quats, 16, "out quats", false))) return s;
+    if ((s = check_device_array(ctx, out->scales, 16, "out scales", false))) return s;
+    if ((s = check_device_array(ctx, out->flags, 4, "out flags", false))) return s;
+    if ((s = check_device_array(ctx, out->nbr_pos, 4, "out nbr_pos", true))) return s;
+    if ((s = check_device_array(ctx, out->nbr_cov, 4, "out nbr_cov", true))) return s;
+    const void* ins[7] = {before->means_opacity, before->quats, before->scales, fitted->means, fitted->quats,
+                          fitted->scales, fitted->status};
+    const void* outs[4] = {out->means_opacity, out->quats, out->scales, out->flags};
+    for (const void* a : ins)
+        for (const void* b : outs)
+            if (a == b) return fail(ctx, TSP_ERR_INVALID_ARG, "outputs must not overlap inputs");
+    const float* mom = view_moments;
+    if (mom) {
+        if ((s = check_device_array(ctx, mom, 4, "view_moments", false))) return s;
+    } else if (num_views > 0) {
+        if (ctx->last_fit_n != n || ctx->last_fit_V != num_views || !ctx->moments.p)
+            return fail(ctx, TSP_ERR_INVALID_ARG,
+                        "view_moments is NULL and the context's last fit had another n or number of views");
+        mom = (const float*)ctx->moments.p;
+    }
+    RegParams rp{};
+    rp.n = n;
+    rp.V = num_views;
+    rp.k = o.k;
+    rp.min_views = o.static_min_views;
+    rp.min_px = o.static_min_px;
+    rp.frac = o.static_frac;
+    rp.moments = mom;
+    rp.status = fitted->status;
+    rp.mo0 = (const float4*)before->means_opacity;
+    rp.q0 = (const float4*)before->quats;
+    rp.s0 = (const float4*)before->scales;
+    rp.mo1 = (const float4*)fitted->means;
+    rp.q1 = (const float4*)fitted->quats;
+    rp.s1 = (const float4*)fitted->scales;
+    rp.nbr_pos = out->nbr_pos;
+    rp.nbr_cov = out->nbr_cov;
+    rp.mo_out = (float4*)out->means_opacity;
+    rp.q_out = (float4*)out->quats;
+    rp.s_out = (float4*)out->scales;
+    rp.flags = out->flags;
+    KnnWork kw{};
+    if ((s = ensure_reg(ctx, n, o.k, kw, &rp))) return s;
+    TSP_CUDA(launch_regularize(rp, kw, (cudaStream_t)stream));
+    return TSP_OK;
+}
+
+tsp_status tsp_knn(tsp_context* ctx, const float* means_opacity, const uint8_t* mask, int n, int k,
+                   int32_t* nbr, void* stream)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    if (n < 0) return fail(ctx, TSP_ERR_INVALID_ARG, "n < 0");
+    if (k < 1 || k > TSP_REG_MAX_K) return fail(ctx, TSP_ERR_INVALID_ARG, "k must be in [1, TSP_REG_MAX_K]");
+    if (n == 0) return TSP_OK;
+    tsp_status s;
+    if ((s = check_device_array(ctx, means_opacity, 16, "means_opacity", false))) return s;
+    if ((s = check_device_array(ctx, mask, 1, "mask", false))) return s;
+    if ((s = check_device_array(ctx, nbr, 4, "nbr", false))) return s;
+    KnnWork kw{};
+    if ((s = ensure_reg(ctx, n, k, kw, nullptr))) return s;
+    TSP_CUDA(launch_knn((const float4*)means_opacity, mask, 0xff, n, k, kw, nbr, (cudaStream_t)stream));
     return TSP_OK;
 }
 

@@ -144,18 +144,19 @@ __device__ __forceinline__ unsigned long long block_scan_incl(unsigned long long
 }
 
 __device__ __forceinline__ void load_counts4(const uint32_t* __restrict__ cnt, uint32_t NT, uint32_t i0,
-                                             uint32_t (&c)[4])
+                                             uint32_t stride, uint32_t (&c)[4])
 {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] = (i0 + k < NT) ? cnt[(size_t)(i0 + k) * kCounterStride] : 0u;
+    for (int k = 0; k < 4; ++k) c[k] = (i0 + k < NT) ? cnt[(size_t)(i0 + k) * stride] : 0u;
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t NT,
+                                                              uint32_t stride,
                                                               unsigned long long* __restrict__ span_sum)
 {
     __shared__ unsigned long long warp_tot[32];
     uint32_t c[4];
-    load_counts4(cnt, NT, blockIdx.x * kScanSpan + 4 * threadIdx.x, c);
+    load_counts4(cnt, NT, blockIdx.x * kScanSpan + 4 * threadIdx.x, stride, c);
     unsigned long long tot;
     block_scan_incl((unsigned long long)c[0] + c[1] + c[2] + c[3], warp_tot, &tot);
     if (threadIdx.x == 0) span_sum[blockIdx.x] = tot;
@@ -184,13 +185,14 @@ __global__ void __launch_bounds__(1024) k_scan_spans(unsigned long long* __restr
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ cnt, uint32_t NT,
+                                                            uint32_t stride,
                                                             const unsigned long long* __restrict__ span_pre,
                                                             uint32_t* __restrict__ off)
 {
     __shared__ unsigned long long warp_tot[32];
     const uint32_t i0 = blockIdx.x * kScanSpan + 4 * threadIdx.x;
     uint32_t c[4];
-    load_counts4(cnt, NT, i0, c);
+    load_counts4(cnt, NT, i0, stride, c);
     const unsigned long long sum = (unsigned long long)c[0] + c[1] + c[2] + c[3];
     unsigned long long tot;
     unsigned long long run = block_scan_incl(sum, warp_tot, &tot) - sum + span_pre[blockIdx.x];
@@ -443,10 +445,16 @@ cudaError_t launch_dref(const ViewSet& vs, const Work& w, int v0, int v1, cudaSt
 
 cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st)
 {
-    const uint32_t nspan = (NT + kScanSpan - 1) / kScanSpan;
-    if (nspan > 0) k_scan_reduce<<<nspan, kScanThreads, 0, st>>>(w.tile_count, NT, w.span_sum);
-    k_scan_spans<<<1, 1024, 0, st>>>(w.span_sum, nspan, w.tile_off, NT, w.cap, w.dstatus);
-    if (nspan > 0) k_scan_down<<<nspan, kScanThreads, 0, st>>>(w.tile_count, NT, w.span_sum, w.tile_off);
+    return launch_scan_u32(w.tile_count, kCounterStride, NT, w.tile_off, w.span_sum, w.cap, w.dstatus, st);
+}
+
+cudaError_t launch_scan_u32(const uint32_t* cnt, uint32_t stride, uint32_t n, uint32_t* off,
+                            unsigned long long* span_sum, uint32_t cap, uint32_t* status, cudaStream_t st)
+{
+    const uint32_t nspan = (n + kScanSpan - 1) / kScanSpan;
+    if (nspan > 0) k_scan_reduce<<<nspan, kScanThreads, 0, st>>>(cnt, n, stride, span_sum);
+    k_scan_spans<<<1, 1024, 0, st>>>(span_sum, nspan, off, n, cap, status);
+    if (nspan > 0) k_scan_down<<<nspan, kScanThreads, 0, st>>>(cnt, n, stride, span_sum, off);
     return cudaGetLastError();
 }
 

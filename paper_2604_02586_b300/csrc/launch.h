@@ -14,6 +14,11 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float* sh, int sh_degree,
 cudaError_t launch_dref(const ViewSet& vs, const Work& w, int v0, int v1, cudaStream_t st);
 // a2: exclusive scan of the per-tile counts -> tile offsets and the pair count K.
 cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st);
+// Exclusive scan of n counts cnt[i * stride] into off[0..n] (off[n] = total);
+// span_sum: ceil(n / 1024) + 1 scratch words; status[1..2] receive the total and
+// status[0] bit 0 is set if it exceeds cap.
+cudaError_t launch_scan_u32(const uint32_t* cnt, uint32_t stride, uint32_t n, uint32_t* off,
+                            unsigned long long* span_sum, uint32_t cap, uint32_t* status, cudaStream_t st);
 // a2: emit (depth << 32 | g) into each touched tile's slice.
 cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st);
 // a3: sort each tile's slice ascending (depth, then Gaussian index).
@@ -43,5 +48,46 @@ cudaError_t launch_view_solve(const ViewSet& vs, const FitParams& fp, const Work
 // a7-a9: triangulation, covariance fit, eigen decomposition and outputs, per frame.
 cudaError_t launch_multiview(const ViewSet& vs, const FitParams& fp, const Work& w, const FrameOut& fo,
                              cudaStream_t st);
+
+// Motion regularization (Sec. 4.5).
+struct GridParam {                  // uniform grid of one component's members
+    float lo[3], inv[3], h[3];      // box corner, cells per unit, cell edge
+    int dims[3];
+    int ncell;
+    float margin;                   // FP32 slack of the cell walls
+};
+struct KnnWork {
+    uint32_t* acc;                  // 8 words: bounding box keys, member count
+    GridParam* gp;
+    uint32_t* count;                // [knn_max_cells(n) + 1]
+    uint32_t* cell_off;             // [knn_max_cells(n) + 1]
+    unsigned long long* span_sum;   // [knn_max_cells(n) / 1024 + 2]
+    uint32_t* status;               // 4 words
+    uint2* slot;                    // [n] (cell, rank in cell)
+    float4* sorted;                 // [n] members by cell: x, y, z, index bits
+};
+struct RegParams {
+    int n, V, k, min_views;
+    float min_px, frac;
+    const float* moments;           // [V][n][16]
+    const uint32_t* status;         // [n] TSP_* bits of the fit
+    const float4 *mo0, *q0, *s0;    // before
+    const float4 *mo1, *q1, *s1;    // fitted
+    uint8_t* mask;                  // [n] member / static bits
+    float4 *dpos, *dscale, *drot;   // motion components
+    float4 *fpos, *fscale, *frot;   // median-filtered components
+    int32_t *nbr_pos, *nbr_cov;     // [n][k]
+    float4 *mo_out, *q_out, *s_out;
+    uint32_t* flags;
+};
+// Cells of the neighbour grid for n points (an upper bound; the grid itself is
+// sized on the device).
+uint32_t knn_max_cells(int n);
+// k nearest members (mask & bit) of every point (k <= TSP_REG_MAX_K), -1 padded.
+cudaError_t launch_knn(const float4* mo, const uint8_t* mask, uint8_t bit, int n, int k, const KnnWork& kw,
+                       int32_t* nbr, cudaStream_t st);
+// Static flags, neighbours of both components, median filter, propagation and
+// the new parameters.
+cudaError_t launch_regularize(const RegParams& rp, const KnnWork& kw, cudaStream_t st);
 
 }  // namespace tsp

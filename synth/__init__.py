@@ -34,7 +34,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Scene", "make_scene", "PRESETS", "look_at"]
+__all__ = ["Scene", "make_scene", "PRESETS", "look_at", "motion_pair"]
 
 
 @dataclass
@@ -318,3 +318,73 @@ def _view_tracks(s: Scene, v: int, rng) -> tuple[np.ndarray, np.ndarray]:
     vis = np.zeros(H * W, np.uint8)
     vis[pix[front]] = 1
     return disp.astype(np.float32).reshape(H, W, 2), vis.reshape(H, W)
+
+
+def motion_pair(n: int, views: int = 4, seed: int = 0, extent: float = 4.0, p_pos: float = 0.85,
+                p_cov: float = 0.6, p_static: float = 0.15, outliers: float = 0.05, max_rot: float = 0.2,
+                lattice: bool = False):
+    """Inputs of the motion regularization (Sec. 4.5) without running a fit.
+
+    First-frame Gaussians (``lattice``: on an integer grid scaled by ``extent``/side,
+    so that many neighbour distances tie; else a mix of a uniform box and dense
+    blobs, with a few exact duplicates), a motion per Gaussian (a smooth field
+    plus noise, ``outliers`` of them thrown far, rotations up to ``max_rot``
+    radians, scale changes of a few per cent), fit status bits (position solved
+    with probability ``p_pos``, covariance with ``p_cov``), and per-view pixel
+    counters [views, n] (pixels, static pixels) in which about ``p_static`` of
+    the Gaussians are static in most views and some sit exactly on the rule's
+    thresholds.  Returns dict(before=(mo, q, s), after=(mo, q, s), status,
+    npix, nstat), all float32 except status (uint32)."""
+    rng = np.random.default_rng(seed)
+    if lattice:
+        side = max(2, int(round(n ** (1.0 / 3.0))) + 1)
+        grid = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        X = grid[rng.permutation(grid.shape[0])[:n]] * (extent / side)
+    else:
+        nb = n // 2
+        X = rng.uniform(-0.5 * extent, 0.5 * extent, (n, 3))
+        centres = rng.uniform(-0.4 * extent, 0.4 * extent, (8, 3))
+        X[:nb] = centres[rng.integers(0, 8, nb)] + rng.normal(0, 0.03 * extent, (nb, 3))
+        dup = rng.integers(0, n, max(1, n // 200))
+        X[rng.integers(0, n, dup.shape[0])] = X[dup]
+    mo = np.empty((n, 4), np.float32)
+    mo[:, :3] = X
+    mo[:, 3] = rng.uniform(0.05, 0.99, n)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    s = np.zeros((n, 4), np.float32)
+    s[:, :3] = np.exp(rng.normal(-4.0, 0.5, (n, 3)))
+    # motion: a smooth field plus noise
+    field_t = 0.02 * extent * np.sin(X[:, [1, 2, 0]] * (2.0 / extent))
+    dmu = field_t + rng.normal(0, 0.002 * extent, (n, 3))
+    far = rng.random(n) < outliers
+    dmu[far] += rng.normal(0, 0.2 * extent, (int(far.sum()), 3))
+    axis = rng.normal(size=(n, 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    ang = rng.uniform(0, max_rot, n)
+    dq = np.concatenate([np.cos(ang / 2)[:, None], np.sin(ang / 2)[:, None] * axis], 1)
+    w1, v1 = dq[:, :1], dq[:, 1:]
+    w2, v2 = q[:, :1], q[:, 1:]
+    q1 = np.concatenate([w1 * w2 - (v1 * v2).sum(1, keepdims=True),
+                         w1 * v2 + w2 * v1 + np.cross(v1, v2)], 1)       # dq * q
+    mo1 = mo.copy()
+    mo1[:, :3] = X + dmu
+    s1 = s.copy()
+    s1[:, :3] = s[:, :3] * rng.uniform(0.95, 1.05, (n, 3))
+    status = np.zeros(n, np.uint32)
+    status[rng.random(n) < p_pos] |= 1
+    status[rng.random(n) < p_cov] |= 2
+    # pixel counters: integers, a static group, and rows on the thresholds
+    npix = rng.integers(0, 40, (views, n)).astype(np.float32)
+    frac = rng.uniform(0, 1, (views, n))
+    stat_g = rng.random(n) < p_static
+    frac[:, stat_g] = rng.uniform(0.9, 1.0, (views, int(stat_g.sum())))
+    nstat = np.floor(npix * frac).astype(np.float32)
+    edge = rng.random((views, n)) < 0.05
+    npix[edge] = 10.0
+    nstat[edge] = 9.0                                                   # 9 > 0.9 * 10 is false in FP32
+    edge2 = rng.random((views, n)) < 0.03
+    npix[edge2] = 9.0                                                   # not more than 9 pixels
+    nstat[edge2] = 9.0
+    return dict(before=(mo, q.astype(np.float32), s), after=(mo1, q1.astype(np.float32), s1),
+                status=status, npix=npix, nstat=nstat)

@@ -216,12 +216,16 @@ def sensitivity(scene, orc, sample=None, rel=1e-6):
 
 
 def rot_angle(qa, qb):
+    """Angle of the rotation between two quaternions (either sign).  Taken as
+    4 asin(|qa - qb| / 2) with qb on qa's side: 2 acos(|qa . qb|) loses half the
+    digits near 0 (the FP32 rounding of a unit quaternion alone reads as 6e-4 rad
+    there)."""
     qa = np.asarray(qa, np.float64)
     qb = np.asarray(qb, np.float64)
     qa = qa / np.linalg.norm(qa, axis=-1, keepdims=True)
     qb = qb / np.linalg.norm(qb, axis=-1, keepdims=True)
-    d = np.abs((qa * qb).sum(-1)).clip(0, 1)
-    return 2 * np.arccos(d)
+    sgn = np.where((qa * qb).sum(-1) < 0, -1.0, 1.0)[..., None]
+    return 4 * np.arcsin(np.clip(np.linalg.norm(qa - sgn * qb, axis=-1) / 2, 0, 1))
 
 
 def quat_rot(q):

@@ -49,10 +49,21 @@ def test_default_options_match_paper_thresholds(L):
     assert L.tsp_default_options(None) == tsp.TSP.ERR_INVALID_ARG
 
 
+def test_default_reg_options_match_paper(L):
+    o = tsp.RegOptions()
+    assert L.tsp_default_reg_options(C.byref(o)) == tsp.TSP.OK
+    # Sec. 5.1: 8 nearest neighbours; Sec. 4.5.2: > 9 pixels, > 90 % static, >= 2 views
+    assert o.k == 8 and o.static_min_views == 2
+    assert o.static_min_px == 9.0 and abs(o.static_frac - 0.9) < 1e-7
+    assert L.tsp_default_reg_options(None) == tsp.TSP.ERR_INVALID_ARG
+
+
 def test_null_context_is_rejected(L):
     assert L.tsp_fit_motion(None, None, None, 0, None, None, None) == tsp.TSP.ERR_INVALID_ARG
     assert L.tsp_render(None, None, None, 0, None, 0, None, None, None) == tsp.TSP.ERR_INVALID_ARG
     assert L.tsp_sync(None, None, 0) == tsp.TSP.ERR_INVALID_ARG
+    assert L.tsp_regularize(None, None, None, None, 0, None, None, None) == tsp.TSP.ERR_INVALID_ARG
+    assert L.tsp_knn(None, None, None, 0, 8, None, None) == tsp.TSP.ERR_INVALID_ARG
     assert L.tsp_inspect(None, 0, None, 0, None) == tsp.TSP.ERR_INVALID_ARG
     assert L.tsp_destroy(None) == tsp.TSP.OK
 
@@ -72,7 +83,9 @@ def test_struct_layouts_match_header(tmp_path):
     compiler gives the header's structure (gcc, compiled here)."""
     import subprocess
     pairs = {"tsp_camera": tsp.Camera, "tsp_gaussians": tsp.Gaussians, "tsp_view_tracks": tsp.ViewTracks,
-             "tsp_result": tsp.Result, "tsp_frame": tsp.Frame, "tsp_options": tsp.Options}
+             "tsp_result": tsp.Result, "tsp_frame": tsp.Frame, "tsp_options": tsp.Options,
+             "tsp_render_grads": tsp.RenderGrads, "tsp_reg_options": tsp.RegOptions,
+             "tsp_reg_result": tsp.RegResult}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tsplat.h"', "int main(void) {"]
     for cname, py in pairs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -720,12 +720,9 @@ def test_regularization_median_filter_and_propagation():
     keep[[static_i]] = False
     np.testing.assert_allclose(r["means_opacity"][keep, :3], mo[keep, :3] + t, atol=2e-6)
     np.testing.assert_allclose(r["scales"][keep, :3], s[keep, :3] + 0.002, atol=2e-6)
-    qa = r["quats"][keep].astype(np.float64)
-    qb = q2[keep].astype(np.float64)
-    qa /= np.linalg.norm(qa, axis=1, keepdims=True)
-    qb /= np.linalg.norm(qb, axis=1, keepdims=True)
-    ang = 2 * np.arccos(np.clip(np.abs((qa * qb).sum(1)), 0, 1))
-    assert ang.max() < 1e-5
+    from tests.parity import rot_angle
+    ang = rot_angle(r["quats"][keep], q2[keep])
+    assert ang.max() < 1e-6
     assert r["flags"][out_i] & oracle.REG_POS_MEDIAN
     assert r["flags"][unsolved_i] & oracle.REG_POS_PROPAGATED and r["flags"][unsolved_i] & oracle.REG_COV_PROPAGATED
     assert r["flags"][static_i] == oracle.REG_STATIC
