@@ -294,8 +294,8 @@ typedef struct tsp_reg_result {
  * tsp_result.view_moments, or NULL for the moments the context holds from its
  * last tsp_fit_motion / tsp_fit_motion_host call, which must have had the same
  * n and num_views (INVALID_ARG otherwise).  Means must be finite.  All arrays are
- * device memory of the context's device, 16-byte aligned ([n][4]) or 4-byte
- * aligned (flags, nbr_*); outputs must not overlap inputs.  Device-side grid
+ * device memory of the context's device, 16-byte aligned ([n][4], view_moments)
+ * or 4-byte aligned (flags, nbr_*); outputs must not overlap inputs.  Device-side grid
  * sizing: no host wait; enqueues on `stream` and may be captured in a CUDA graph
  * once the workspace for this n and k exists.  Errors: INVALID_ARG, OOM, BUDGET,
  * CUDA. */

@@ -461,7 +461,8 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
 // carved from one buffer.
 tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp)
 {
-    const uint32_t C = knn_max_cells(n);
+    const size_t C = knn_max_cells(n);
+    const size_t G = kMaxGrids;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -469,9 +470,10 @@ tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp
         return o;
     };
     const size_t nn = (size_t)n;
-    const size_t o_acc = take(32), o_gp = take(sizeof(GridParam)), o_st = take(16);
-    const size_t o_count = take(((size_t)C + 1) * 4), o_off = take(((size_t)C + 1) * 4);
-    const size_t o_span = take(((size_t)C / 1024 + 2) * 8), o_slot = take(nn * 8), o_sorted = take(nn * 16);
+    const size_t zero_bytes = G * 8 * 4 + G * C * 4;
+    const size_t o_zero = take(zero_bytes), o_gp = take(G * sizeof(GridParam)), o_st = take(16);
+    const size_t o_off = take((G * C + 1) * 4), o_span = take((G * C / 1024 + 2) * 8);
+    const size_t o_slot = take(G * nn * 8), o_sorted = take(G * nn * 16);
     size_t o_mask = 0, o_vec = 0, o_nbr = 0;
     if (rp) {
         o_mask = take(nn);
@@ -481,10 +483,12 @@ tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp
     tsp_status s;
     if ((s = ensure(ctx, ctx->reg, off))) return s;
     char* b = (char*)ctx->reg.p;
-    kw.acc = (uint32_t*)(b + o_acc);
+    kw.zero = (uint32_t*)(b + o_zero);
+    kw.zero_bytes = zero_bytes;
+    kw.acc = kw.zero;
+    kw.count = kw.zero + G * 8;
     kw.gp = (GridParam*)(b + o_gp);
     kw.status = (uint32_t*)(b + o_st);
-    kw.count = (uint32_t*)(b + o_count);
     kw.cell_off = (uint32_t*)(b + o_off);
     kw.span_sum = (unsigned long long*)(b + o_span);
     kw.slot = (uint2*)(b + o_slot);
@@ -1019,7 +1023,7 @@ tsp_status tsp_regularize(tsp_context* ctx, const tsp_gaussians* before, const t
             if (a == b) return fail(ctx, TSP_ERR_INVALID_ARG, "outputs must not overlap inputs");
     const float* mom = view_moments;
     if (mom) {
-        if ((s = check_device_array(ctx, mom, 4, "view_moments", false))) return s;
+        if ((s = check_device_array(ctx, mom, 16, "view_moments", false))) return s;
     } else if (num_views > 0) {
         if (ctx->last_fit_n != n || ctx->last_fit_V != num_views || !ctx->moments.p)
             return fail(ctx, TSP_ERR_INVALID_ARG,
@@ -1067,7 +1071,8 @@ tsp_status tsp_knn(tsp_context* ctx, const float* means_opacity, const uint8_t* 
     if ((s = check_device_array(ctx, nbr, 4, "nbr", false))) return s;
     KnnWork kw{};
     if ((s = ensure_reg(ctx, n, k, kw, nullptr))) return s;
-    TSP_CUDA(launch_knn((const float4*)means_opacity, mask, 0xff, n, k, kw, nbr, (cudaStream_t)stream));
+    const uint8_t bits = 0xff;
+    TSP_CUDA(launch_knn((const float4*)means_opacity, mask, &bits, 1, n, k, kw, nbr, nbr, (cudaStream_t)stream));
     return TSP_OK;
 }
 

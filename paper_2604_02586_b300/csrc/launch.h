@@ -56,15 +56,25 @@ struct GridParam {                  // uniform grid of one component's members
     int ncell;
     float margin;                   // FP32 slack of the cell walls
 };
+constexpr int kMaxGrids = 3;        // the query order and two candidate sets
+struct GridDesc {                   // grid j's members: every point (bits 0) or mask & bits
+    int G;
+    uint8_t bits[kMaxGrids];
+};
+// Scratch of up to kMaxGrids grids over the same n points, C = knn_max_cells(n)
+// cells each, counting-sorted into one array (grid j's cell c holds
+// sorted[cell_off[j C + c], cell_off[j C + c + 1])).
 struct KnnWork {
-    uint32_t* acc;                  // 8 words: bounding box keys, member count
-    GridParam* gp;
-    uint32_t* count;                // [knn_max_cells(n) + 1]
-    uint32_t* cell_off;             // [knn_max_cells(n) + 1]
-    unsigned long long* span_sum;   // [knn_max_cells(n) / 1024 + 2]
+    uint32_t* zero;                 // acc and count, cleared together (zero_bytes)
+    size_t zero_bytes;
+    uint32_t* acc;                  // [kMaxGrids][8]: bounding box keys, member count
+    uint32_t* count;                // [kMaxGrids * C]
+    GridParam* gp;                  // [kMaxGrids]
+    uint32_t* cell_off;             // [kMaxGrids * C + 1]
+    unsigned long long* span_sum;   // [kMaxGrids * C / 1024 + 2]
     uint32_t* status;               // 4 words
-    uint2* slot;                    // [n] (cell, rank in cell)
-    float4* sorted;                 // [n] members by cell: x, y, z, index bits
+    uint2* slot;                    // [kMaxGrids][n] (cell, rank in cell)
+    float4* sorted;                 // [kMaxGrids * n] members by cell: x, y, z, index bits
 };
 struct RegParams {
     int n, V, k, min_views;
@@ -79,13 +89,16 @@ struct RegParams {
     int32_t *nbr_pos, *nbr_cov;     // [n][k]
     float4 *mo_out, *q_out, *s_out;
     uint32_t* flags;
+    const float4* qorder;           // [n] Gaussians in cell order (index bits in .w)
 };
 // Cells of the neighbour grid for n points (an upper bound; the grid itself is
 // sized on the device).
 uint32_t knn_max_cells(int n);
-// k nearest members (mask & bit) of every point (k <= TSP_REG_MAX_K), -1 padded.
-cudaError_t launch_knn(const float4* mo, const uint8_t* mask, uint8_t bit, int n, int k, const KnnWork& kw,
-                       int32_t* nbr, cudaStream_t st);
+// For every point, its k nearest members of each candidate set j < ncand
+// (mask & bits[j] != 0; ncand 1 or 2; k <= TSP_REG_MAX_K) into nbr0 / nbr1
+// [n][k], -1 padded.
+cudaError_t launch_knn(const float4* mo, const uint8_t* mask, const uint8_t* bits, int ncand, int n, int k,
+                       const KnnWork& kw, int32_t* nbr0, int32_t* nbr1, cudaStream_t st);
 // Static flags, neighbours of both components, median filter, propagation and
 // the new parameters.
 cudaError_t launch_regularize(const RegParams& rp, const KnnWork& kw, cudaStream_t st);

@@ -23,6 +23,7 @@ namespace tsp {
 namespace {
 
 constexpr int kRegThreads = 256;
+constexpr int kMembersPerCell = 3;       // grid density: members per cell on average
 
 __device__ __forceinline__ uint32_t ordered_key(float f)
 {
@@ -43,79 +44,96 @@ __device__ __forceinline__ float dist2(float qx, float qy, float qz, float4 p)
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-__device__ __forceinline__ bool member(const uint8_t* mask, uint8_t bit, int g) { return (mask[g] & bit) != 0; }
+// Grid j's members: every point (bits 0) or those with mask & bits != 0.
+__device__ __forceinline__ bool member(const uint8_t* mask, uint8_t bits, int g)
+{
+    return bits == 0 || (mask[g] & bits) != 0;
+}
 
-// acc: [0..2] ~key(min), [3..5] key(max), [6] member count; all start at 0.
+// acc[8 j + 0..2] ~key(min), [8 j + 3..5] key(max), [8 j + 6] member count of
+// grid j; all start at 0.
 __global__ void __launch_bounds__(kRegThreads) k_grid_bounds(const float4* __restrict__ mo,
-                                                            const uint8_t* __restrict__ mask, uint8_t bit, int n,
+                                                            const uint8_t* __restrict__ mask, GridDesc gd, int n,
                                                             uint32_t* __restrict__ acc)
 {
-    __shared__ uint32_t s[7][kRegThreads / 32];
-    uint32_t v[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
-        if (!member(mask, bit, g)) continue;
-        const float4 p = mo[g];
-        const float c[3] = {p.x, p.y, p.z};
+    __shared__ uint32_t s[kMaxGrids][7][kRegThreads / 32];
+    uint32_t v[kMaxGrids][7];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const uint32_t k = ordered_key(c[i]);
-            v[i] = max(v[i], ~k);
-            v[3 + i] = max(v[3 + i], k);
+    for (int j = 0; j < kMaxGrids; ++j)
+#pragma unroll
+        for (int i = 0; i < 7; ++i) v[j][i] = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const float4 p = mo[g];
+        const uint32_t k[3] = {ordered_key(p.x), ordered_key(p.y), ordered_key(p.z)};
+#pragma unroll
+        for (int j = 0; j < kMaxGrids; ++j) {
+            if (j >= gd.G || !member(mask, gd.bits[j], g)) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                v[j][i] = max(v[j][i], ~k[i]);
+                v[j][3 + i] = max(v[j][3 + i], k[i]);
+            }
+            v[j][6] += 1;
         }
-        v[6] += 1;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        uint32_t x = v[i];
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint32_t y = __shfl_xor_sync(0xffffffffu, x, o);
-            x = i == 6 ? x + y : max(x, y);
+    for (int j = 0; j < kMaxGrids; ++j)
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            uint32_t x = v[j][i];
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint32_t y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = i == 6 ? x + y : max(x, y);
+            }
+            if (lane == 0) s[j][i][wid] = x;
         }
-        if (lane == 0) s[i][wid] = x;
-    }
     __syncthreads();
-    if (threadIdx.x < 7) {
-        const int i = threadIdx.x;
+    if (threadIdx.x < 7 * gd.G) {
+        const int j = threadIdx.x / 7, i = threadIdx.x % 7;
         uint32_t x = 0;
-        for (int w = 0; w < kRegThreads / 32; ++w) x = i == 6 ? x + s[i][w] : max(x, s[i][w]);
+        for (int w = 0; w < kRegThreads / 32; ++w) x = i == 6 ? x + s[j][i][w] : max(x, s[j][i][w]);
         if (i == 6) {
-            if (x) atomicAdd(&acc[6], x);
+            if (x) atomicAdd(&acc[8 * j + 6], x);
         } else {
-            atomicMax(&acc[i], x);
+            atomicMax(&acc[8 * j + i], x);
         }
     }
 }
 
-// One thread: the grid over the members' box with about two members per cell and
-// at most max_cells cells.
-__global__ void k_grid_setup(const uint32_t* __restrict__ acc, uint32_t max_cells, GridParam* __restrict__ gp)
+// Thread j: grid j over its members' box with about kMembersPerCell members per
+// cell and at most max_cells cells.
+__global__ void k_grid_setup(const uint32_t* __restrict__ acc_all, int G, uint32_t max_cells,
+                             GridParam* __restrict__ gp_all)
 {
-    if (threadIdx.x != 0) return;
+    const int j = threadIdx.x;
+    if (j >= G) return;
+    const uint32_t* acc = acc_all + 8 * j;
+    GridParam* gp = gp_all + j;
     const uint32_t m = acc[6];
-    double lo[3], ext[3], E = 0.0, amax = 0.0;
+    float lo[3], ext[3], E = 0.0f, amax = 0.0f;
     for (int i = 0; i < 3; ++i) {
         if (m == 0) {
-            lo[i] = 0.0;
-            ext[i] = 1.0;
+            lo[i] = 0.0f;
+            ext[i] = 1.0f;
         } else {
             lo[i] = key_value(~acc[i]);
-            const double hi = key_value(acc[3 + i]);
+            const float hi = key_value(acc[3 + i]);
             ext[i] = hi - lo[i];
-            amax = fmax(amax, fmax(fabs(lo[i]), fabs(hi)));
+            amax = fmaxf(amax, fmaxf(fabsf(lo[i]), fabsf(hi)));
         }
-        if (!(ext[i] < 1e30)) ext[i] = 1.0;
-        E = fmax(E, ext[i]);
+        if (!(ext[i] < 1e30f)) ext[i] = 1.0f;
+        E = fmaxf(E, ext[i]);
     }
-    if (!(E > 0.0)) E = 1.0;
-    for (int i = 0; i < 3; ++i) ext[i] = fmax(ext[i], 1e-3 * E);
-    double target = fmax(1.0, floor(m / 2.0));
-    if (target > max_cells) target = max_cells;
+    if (!(E > 0.0f)) E = 1.0f;
+    for (int i = 0; i < 3; ++i) ext[i] = fmaxf(ext[i], 1e-3f * E);
+    float target = fmaxf(1.0f, floorf((float)m / kMembersPerCell));
+    if (target > (float)max_cells) target = (float)max_cells;
     // cubic cells; an axis shorter than one cell gets one cell and the others
     // share the count
     int d[3] = {0, 0, 0};
     for (int round = 0; round < 3; ++round) {
-        double vol = 1.0;
+        float vol = 1.0f;
         int free_axes = 0;
         for (int i = 0; i < 3; ++i)
             if (d[i] == 0) {
@@ -123,7 +141,7 @@ __global__ void k_grid_setup(const uint32_t* __restrict__ acc, uint32_t max_cell
                 ++free_axes;
             }
         if (free_axes == 0) break;
-        const double h = pow(vol / target, 1.0 / free_axes);
+        const float h = free_axes == 3 ? cbrtf(vol / target) : (free_axes == 2 ? sqrtf(vol / target) : vol / target);
         bool fixed = false;
         for (int i = 0; i < 3; ++i)
             if (d[i] == 0 && ext[i] < h) {
@@ -132,24 +150,24 @@ __global__ void k_grid_setup(const uint32_t* __restrict__ acc, uint32_t max_cell
             }
         if (!fixed) {
             for (int i = 0; i < 3; ++i)
-                if (d[i] == 0) d[i] = (int)fmin(fmax(floor(ext[i] / h), 1.0), 1048576.0);
+                if (d[i] == 0) d[i] = (int)fminf(fmaxf(floorf(ext[i] / h), 1.0f), 1048576.0f);
             break;
         }
     }
     for (int i = 0; i < 3; ++i) d[i] = d[i] > 0 ? d[i] : 1;
     while ((unsigned long long)d[0] * d[1] * d[2] > max_cells) {
-        int j = d[0] >= d[1] && d[0] >= d[2] ? 0 : (d[1] >= d[2] ? 1 : 2);
-        d[j] -= 1;
+        const int a = d[0] >= d[1] && d[0] >= d[2] ? 0 : (d[1] >= d[2] ? 1 : 2);
+        d[a] -= 1;
     }
     for (int i = 0; i < 3; ++i) {
-        gp->lo[i] = (float)lo[i];
-        gp->inv[i] = (float)(d[i] / ext[i]);
-        gp->h[i] = (float)(ext[i] / d[i]);
+        gp->lo[i] = lo[i];
+        gp->inv[i] = d[i] / ext[i];
+        gp->h[i] = ext[i] / d[i];
         gp->dims[i] = d[i];
     }
     gp->ncell = d[0] * d[1] * d[2];
     // covers the FP32 rounding of (x - lo) * inv and of the cell walls
-    gp->margin = (float)(1e-5 * E + 1e-6 * amax);
+    gp->margin = 1e-5f * E + 1e-6f * amax;
 }
 
 __device__ __forceinline__ int cell_axis(float x, float lo, float inv, int dim)
@@ -165,79 +183,128 @@ __device__ __forceinline__ void cell_of(const GridParam& gp, float x, float y, f
     cz = cell_axis(z, gp.lo[2], gp.inv[2], gp.dims[2]);
 }
 
+// count[j C + cell] of every grid; slot[j n + g] = (cell, rank within the cell)
 __global__ void __launch_bounds__(kRegThreads) k_grid_count(const float4* __restrict__ mo,
-                                                           const uint8_t* __restrict__ mask, uint8_t bit, int n,
-                                                           const GridParam* __restrict__ gpp,
+                                                           const uint8_t* __restrict__ mask, GridDesc gd, int n,
+                                                           const GridParam* __restrict__ gpp, uint32_t C,
                                                            uint32_t* __restrict__ count, uint2* __restrict__ slot)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || !member(mask, bit, g)) return;
-    const GridParam gp = *gpp;
+    if (g >= n) return;
     const float4 p = mo[g];
-    int cx, cy, cz;
-    cell_of(gp, p.x, p.y, p.z, cx, cy, cz);
-    const uint32_t c = ((uint32_t)cz * gp.dims[1] + cy) * gp.dims[0] + cx;
-    slot[g] = make_uint2(c, atomicAdd(&count[c], 1u));
+#pragma unroll
+    for (int j = 0; j < kMaxGrids; ++j) {
+        if (j >= gd.G || !member(mask, gd.bits[j], g)) continue;
+        const GridParam& gp = gpp[j];
+        int cx, cy, cz;
+        cell_of(gp, p.x, p.y, p.z, cx, cy, cz);
+        const uint32_t c = ((uint32_t)cz * gp.dims[1] + cy) * gp.dims[0] + cx;
+        slot[(size_t)j * n + g] = make_uint2(c, atomicAdd(&count[(size_t)j * C + c], 1u));
+    }
 }
 
 __global__ void __launch_bounds__(kRegThreads) k_grid_scatter(const float4* __restrict__ mo,
-                                                             const uint8_t* __restrict__ mask, uint8_t bit, int n,
-                                                             const uint2* __restrict__ slot,
+                                                             const uint8_t* __restrict__ mask, GridDesc gd, int n,
+                                                             const uint2* __restrict__ slot, uint32_t C,
                                                              const uint32_t* __restrict__ cell_off,
                                                              float4* __restrict__ sorted)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || !member(mask, bit, g)) return;
-    const uint2 s = slot[g];
+    if (g >= n) return;
     const float4 p = mo[g];
-    sorted[cell_off[s.x] + s.y] = make_float4(p.x, p.y, p.z, __int_as_float(g));
+    const float4 e = make_float4(p.x, p.y, p.z, __int_as_float(g));
+#pragma unroll
+    for (int j = 0; j < kMaxGrids; ++j) {
+        if (j >= gd.G || !member(mask, gd.bits[j], g)) continue;
+        const uint2 s = slot[(size_t)j * n + g];
+        sorted[cell_off[(size_t)j * C + s.x] + s.y] = e;
+    }
 }
 
 // (d, i) before (bd, bi)?
 __device__ __forceinline__ bool closer(float d, int i, float bd, int bi) { return d < bd || (d == bd && i < bi); }
 
+// Insert (d, i) into the sorted list (bd, bi) if it is closer than its last entry.
 template <int KMAX>
 __device__ __forceinline__ void insert(float (&bd)[KMAX], int (&bi)[KMAX], float d, int i)
 {
     if (!closer(d, i, bd[KMAX - 1], bi[KMAX - 1])) return;
+    bool c[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX - 1; ++j) c[j] = closer(d, i, bd[j], bi[j]);
+    c[KMAX - 1] = true;
 #pragma unroll
     for (int j = KMAX - 1; j > 0; --j) {
-        const bool before_prev = closer(d, i, bd[j - 1], bi[j - 1]);
-        const bool before_this = closer(d, i, bd[j], bi[j]);
-        const float nd = before_prev ? bd[j - 1] : (before_this ? d : bd[j]);
-        const int ni = before_prev ? bi[j - 1] : (before_this ? i : bi[j]);
-        bd[j] = nd;
-        bi[j] = ni;
+        bd[j] = c[j - 1] ? bd[j - 1] : (c[j] ? d : bd[j]);
+        bi[j] = c[j - 1] ? bi[j - 1] : (c[j] ? i : bi[j]);
     }
-    if (closer(d, i, bd[0], bi[0])) {
-        bd[0] = d;
-        bi[0] = i;
-    }
+    bd[0] = c[0] ? d : bd[0];
+    bi[0] = c[0] ? i : bi[0];
 }
 
-template <int KMAX>
-__device__ __forceinline__ void scan_range(const float4* __restrict__ sorted, uint32_t a, uint32_t b, int self,
-                                           float qx, float qy, float qz, float (&bd)[KMAX], int (&bi)[KMAX])
+// Squared distance from q to the cells [x0, x1] x {y} x {z}, each axis' gap
+// shrunk by the margin: a lower bound on the FP32 distance of every member there.
+__device__ __forceinline__ float seg_bound2(const GridParam& gp, float qx, float qy, float qz, int x0, int x1, int y,
+                                            int z)
 {
+    const float gx = fmaxf(fmaxf(gp.lo[0] + (float)x0 * gp.h[0] - qx, qx - (gp.lo[0] + (float)(x1 + 1) * gp.h[0])) -
+                               gp.margin, 0.0f);
+    const float gy = fmaxf(fmaxf(gp.lo[1] + (float)y * gp.h[1] - qy, qy - (gp.lo[1] + (float)(y + 1) * gp.h[1])) -
+                               gp.margin, 0.0f);
+    const float gz = fmaxf(fmaxf(gp.lo[2] + (float)z * gp.h[2] - qz, qz - (gp.lo[2] + (float)(z + 1) * gp.h[2])) -
+                               gp.margin, 0.0f);
+    return gx * gx + gy * gy + gz * gz;
+}
+
+struct KnnQuery {
+    float x, y, z;
+    int self;
+    int k;
+};
+
+// Scan the members of cells [x0, x1] x {y} x {z} unless all of them are farther
+// than the current k-th (then none can enter the list: the bound is below every
+// member's FP32 distance by more than its rounding, so "farther" is strict).
+template <int KMAX>
+__device__ __forceinline__ void scan_seg(const GridParam& gp, const uint32_t* __restrict__ co,
+                                         const float4* __restrict__ sorted, const KnnQuery& q, int x0, int x1, int y,
+                                         int z, float (&bd)[KMAX], int (&bi)[KMAX])
+{
+    float kth = INFINITY;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j == q.k - 1) kth = bd[j];
+    if (kth < INFINITY && seg_bound2(gp, q.x, q.y, q.z, x0, x1, y, z) * (1.0f - 1e-6f) >= kth) return;
+    const uint32_t row = ((uint32_t)z * gp.dims[1] + y) * gp.dims[0];
+    const uint32_t a = co[row + x0], b = co[row + x1 + 1];
     for (uint32_t j = a; j < b; ++j) {
         const float4 p = sorted[j];
         const int idx = __float_as_int(p.w);
-        if (idx == self) continue;
-        insert<KMAX>(bd, bi, dist2(qx, qy, qz, p), idx);
+        if (idx == q.self) continue;
+        insert<KMAX>(bd, bi, dist2(q.x, q.y, q.z, p), idx);
     }
 }
 
-// One thread per query: its k nearest members (k <= KMAX), -1 padded.
+// (dz, dy) of the nine rows of the 3 x 3 x 3 block, nearest first: the query's
+// own row, the four rows sharing a face with it, the four diagonal rows.
+__constant__ int8_t kBlockRows[9][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}};
+
+// Block (x, y): queries [x * blockDim, ...) in the cell order of grid 0 (every
+// point), their k nearest members of candidate grid y + 1 (k <= KMAX), -1 padded.
 template <int KMAX>
-__global__ void __launch_bounds__(kRegThreads) k_knn(const float4* __restrict__ mo, int n, int k,
-                                                    const GridParam* __restrict__ gpp,
+__global__ void __launch_bounds__(kRegThreads) k_knn(int n, int k, const GridParam* __restrict__ gpp, uint32_t C,
                                                     const uint32_t* __restrict__ cell_off,
-                                                    const float4* __restrict__ sorted, int32_t* __restrict__ nbr)
+                                                    const float4* __restrict__ sorted, int32_t* __restrict__ nbr0,
+                                                    int32_t* __restrict__ nbr1)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    const GridParam gp = *gpp;
-    const float4 q = mo[g];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int grid = blockIdx.y + 1;
+    const GridParam gp = gpp[grid];
+    const uint32_t* __restrict__ co = cell_off + (size_t)grid * C;
+    int32_t* __restrict__ nbr = blockIdx.y == 0 ? nbr0 : nbr1;
+    const float4 qp = sorted[t];
+    const KnnQuery q{qp.x, qp.y, qp.z, __float_as_int(qp.w), k};
     int c[3];
     cell_of(gp, q.x, q.y, q.z, c[0], c[1], c[2]);
     const float qc[3] = {q.x, q.y, q.z};
@@ -252,25 +319,15 @@ __global__ void __launch_bounds__(kRegThreads) k_knn(const float4* __restrict__ 
 #pragma unroll
     for (int i = 0; i < 3; ++i) rmax = max(rmax, max(c[i], gp.dims[i] - 1 - c[i]));
     const int d0 = gp.dims[0], d1 = gp.dims[1], d2 = gp.dims[2];
-    for (int r = 0; r <= rmax; ++r) {
-        const int z0 = max(c[2] - r, 0), z1 = min(c[2] + r, d2 - 1);
-        const int y0 = max(c[1] - r, 0), y1 = min(c[1] + r, d1 - 1);
-        const int x0 = max(c[0] - r, 0), x1 = min(c[0] + r, d0 - 1);
-        for (int z = z0; z <= z1; ++z) {
-            for (int y = y0; y <= y1; ++y) {
-                const uint32_t row = ((uint32_t)z * d1 + y) * d0;
-                if (abs(z - c[2]) == r || abs(y - c[1]) == r) {
-                    scan_range<KMAX>(sorted, cell_off[row + x0], cell_off[row + x1 + 1], g, q.x, q.y, q.z, bd, bi);
-                } else {
-                    if (c[0] - r >= 0)
-                        scan_range<KMAX>(sorted, cell_off[row + c[0] - r], cell_off[row + c[0] - r + 1], g, q.x,
-                                         q.y, q.z, bd, bi);
-                    if (r > 0 && c[0] + r < d0)
-                        scan_range<KMAX>(sorted, cell_off[row + c[0] + r], cell_off[row + c[0] + r + 1], g, q.x,
-                                         q.y, q.z, bd, bi);
-                }
-            }
+    {
+        const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, d0 - 1);
+        for (int r = 0; r < 9; ++r) {
+            const int z = c[2] + kBlockRows[r][0], y = c[1] + kBlockRows[r][1];
+            if (z < 0 || z >= d2 || y < 0 || y >= d1) continue;
+            scan_seg<KMAX>(gp, co, sorted, q, x0, x1, y, z, bd, bi);
         }
+    }
+    for (int r = 1;; ++r) {
         // distance to the nearest cell not yet visited
         float b = INFINITY;
 #pragma unroll
@@ -283,11 +340,25 @@ __global__ void __launch_bounds__(kRegThreads) k_knn(const float4* __restrict__ 
         for (int j = 0; j < KMAX; ++j)
             if (j == k - 1) kth = bd[j];
         b -= gp.margin;
-        if (b > 0.0f && kth < b * b * (1.0f - 1e-6f)) break;
+        if (r >= rmax || (b > 0.0f && kth < b * b * (1.0f - 1e-6f))) break;
+        const int s = r + 1;
+        const int z0 = max(c[2] - s, 0), z1 = min(c[2] + s, d2 - 1);
+        const int y0 = max(c[1] - s, 0), y1 = min(c[1] + s, d1 - 1);
+        const int x0 = max(c[0] - s, 0), x1 = min(c[0] + s, d0 - 1);
+        for (int z = z0; z <= z1; ++z) {
+            for (int y = y0; y <= y1; ++y) {
+                if (abs(z - c[2]) == s || abs(y - c[1]) == s) {
+                    scan_seg<KMAX>(gp, co, sorted, q, x0, x1, y, z, bd, bi);
+                } else {
+                    if (c[0] - s >= 0) scan_seg<KMAX>(gp, co, sorted, q, c[0] - s, c[0] - s, y, z, bd, bi);
+                    if (c[0] + s < d0) scan_seg<KMAX>(gp, co, sorted, q, c[0] + s, c[0] + s, y, z, bd, bi);
+                }
+            }
+        }
     }
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-        if (j < k) nbr[(size_t)g * k + j] = bi[j] == INT_MAX ? -1 : bi[j];
+        if (j < k) nbr[(size_t)q.self * k + j] = bi[j] == INT_MAX ? -1 : bi[j];
 }
 
 // ----------------------------------------------------------------- rotations
@@ -364,11 +435,18 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_prepare(RegParams rp)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= rp.n) return;
+    // slots 12-15 of each view's record (pixels in .y, static pixels in .z),
+    // eight views' loads in flight at a time
     int views = 0;
-    for (int v = 0; v < rp.V; ++v) {
-        const float* rec = rp.moments + ((size_t)v * rp.n + g) * 16;
-        const float npix = rec[13], nstat = rec[14];
-        if (npix > rp.min_px && nstat > __fmul_rn(rp.frac, npix)) ++views;
+    const float4* rec = reinterpret_cast<const float4*>(rp.moments) + (size_t)g * 4 + 3;
+    const size_t vstride = (size_t)rp.n * 4;
+    for (int v0 = 0; v0 < rp.V; v0 += 8) {
+        float4 c[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c[j] = v0 + j < rp.V ? __ldcs(rec + (size_t)(v0 + j) * vstride) : float4{};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (v0 + j < rp.V && c[j].y > rp.min_px && c[j].z > __fmul_rn(rp.frac, c[j].y)) ++views;
     }
     const bool is_static = views >= rp.min_views;
     const uint32_t st = rp.status[g];
@@ -394,7 +472,7 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_prepare(RegParams rp)
 // Median of the first cnt of v[0..S) (the rest +inf), by an odd-even transposition
 // network over all S slots.
 template <int S>
-__device__ __forceinline__ float median_of(float (&v)[S], int cnt)
+__device__ __forceinline__ float median_sorted(float (&v)[S], int cnt)
 {
 #pragma unroll
     for (int pass = 0; pass < S; ++pass) {
@@ -415,6 +493,44 @@ __device__ __forceinline__ float median_of(float (&v)[S], int cnt)
     return (cnt & 1) ? lo : 0.5f * (lo + hi);
 }
 
+__device__ __forceinline__ void order2(float& a, float& b)
+{
+    const float lo = fminf(a, b), hi = fmaxf(a, b);
+    a = lo;
+    b = hi;
+}
+
+__device__ __forceinline__ float median3(float a, float b, float c)
+{
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), c));
+}
+
+// Median of exactly nine values: sort each of the three triples; the median of the
+// nine is the median of (largest of the three minima, median of the three
+// medians, smallest of the three maxima).
+__device__ __forceinline__ float median9(float (&v)[9])
+{
+#pragma unroll
+    for (int t = 0; t < 9; t += 3) {
+        order2(v[t], v[t + 1]);
+        order2(v[t + 1], v[t + 2]);
+        order2(v[t], v[t + 1]);
+    }
+    const float lo = fmaxf(fmaxf(v[0], v[3]), v[6]);
+    const float mid = median3(v[1], v[4], v[7]);
+    const float hi = fminf(fminf(v[2], v[5]), v[8]);
+    return median3(lo, mid, hi);
+}
+
+template <int S>
+__device__ __forceinline__ float median_of(float (&v)[S], int cnt)
+{
+    if constexpr (S == 9) {
+        if (cnt == 9) return median9(v);
+    }
+    return median_sorted<S>(v, cnt);
+}
+
 template <int KMAX>
 __device__ __forceinline__ int neighbours(const int32_t* __restrict__ nbr, int k, int g, int (&nb)[KMAX])
 {
@@ -427,29 +543,47 @@ __device__ __forceinline__ int neighbours(const int32_t* __restrict__ nbr, int k
     return m;
 }
 
+// Coordinate-wise median of src over g and its m neighbours, into dst[g].
+template <int KMAX>
+__device__ __forceinline__ void median_filter(const float4* __restrict__ src, float4* __restrict__ dst, int g,
+                                              const int (&nb)[KMAX], int m)
+{
+    float4 x[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        x[j] = j < m ? src[nb[j]] : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    const float4 self = src[g];
+    float v[KMAX + 1];
+    float out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[0] = c == 0 ? self.x : (c == 1 ? self.y : self.z);
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) v[j + 1] = c == 0 ? x[j].x : (c == 1 ? x[j].y : x[j].z);
+        out[c] = median_of<KMAX + 1>(v, m + 1);
+    }
+    dst[g] = make_float4(out[0], out[1], out[2], 0.f);
+}
+
 // Pass 1: every Gaussian with a component takes the median over itself and its
-// neighbours with the component.
+// neighbours with the component.  Threads take the Gaussians in cell order, so a
+// warp's neighbours overlap.
 template <int KMAX>
 __global__ void __launch_bounds__(kRegThreads) k_reg_median(RegParams rp)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= rp.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rp.n) return;
+    const int g = __float_as_int(rp.qorder[t].w);
     const uint8_t m8 = rp.mask[g];
     int nb[KMAX];
-    for (int part = 0; part < 2; ++part) {
-        if (!(m8 & (part == 0 ? kPosMember : kCovMember))) continue;
-        const int m = neighbours<KMAX>(part == 0 ? rp.nbr_pos : rp.nbr_cov, rp.k, g, nb);
-        const int dim = part == 0 ? 3 : 6;
-        for (int c = 0; c < dim; ++c) {
-            const float* src = reinterpret_cast<const float*>(part == 0 ? rp.dpos : (c < 3 ? rp.dscale : rp.drot));
-            const int cc = c % 3;
-            float v[KMAX + 1];
-            v[0] = src[4 * (size_t)g + cc];
-#pragma unroll
-            for (int j = 0; j < KMAX; ++j) v[j + 1] = j < m ? src[4 * (size_t)nb[j] + cc] : INFINITY;
-            float* dst = reinterpret_cast<float*>(part == 0 ? rp.fpos : (c < 3 ? rp.fscale : rp.frot));
-            dst[4 * (size_t)g + cc] = median_of<KMAX + 1>(v, m + 1);
-        }
+    if (m8 & kPosMember) {
+        const int m = neighbours<KMAX>(rp.nbr_pos, rp.k, g, nb);
+        median_filter<KMAX>(rp.dpos, rp.fpos, g, nb, m);
+    }
+    if (m8 & kCovMember) {
+        const int m = neighbours<KMAX>(rp.nbr_cov, rp.k, g, nb);
+        median_filter<KMAX>(rp.dscale, rp.fscale, g, nb, m);
+        median_filter<KMAX>(rp.drot, rp.frot, g, nb, m);
     }
 }
 
@@ -457,8 +591,9 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_median(RegParams rp)
 template <int KMAX>
 __global__ void __launch_bounds__(kRegThreads) k_reg_apply(RegParams rp)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= rp.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rp.n) return;
+    const int g = __float_as_int(rp.qorder[t].w);
     const uint8_t m8 = rp.mask[g];
     uint32_t fl = (m8 & kStatic) ? TSP_REG_STATIC : 0u;
     float4 dp = make_float4(0.f, 0.f, 0.f, 0.f), ds = dp, dr = dp;
@@ -524,25 +659,31 @@ inline int blocks(int n) { return (n + kRegThreads - 1) / kRegThreads; }
 
 }  // namespace
 
-uint32_t knn_max_cells(int n) { return n / 2 > 1 ? (uint32_t)(n / 2) : 1u; }
+uint32_t knn_max_cells(int n) { return n / kMembersPerCell > 1 ? (uint32_t)(n / kMembersPerCell) : 1u; }
 
-cudaError_t launch_knn(const float4* mo, const uint8_t* mask, uint8_t bit, int n, int k, const KnnWork& kw,
-                       int32_t* nbr, cudaStream_t st)
+cudaError_t launch_knn(const float4* mo, const uint8_t* mask, const uint8_t* bits, int ncand, int n, int k,
+                       const KnnWork& kw, int32_t* nbr0, int32_t* nbr1, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const uint32_t C = knn_max_cells(n);
+    GridDesc gd{};
+    gd.G = ncand + 1;
+    gd.bits[0] = 0;                                   // grid 0: every point, the query order
+    for (int j = 0; j < ncand; ++j) gd.bits[j + 1] = bits[j];
     cudaError_t e;
-    if ((e = cudaMemsetAsync(kw.acc, 0, 8 * sizeof(uint32_t), st))) return e;
-    if ((e = cudaMemsetAsync(kw.count, 0, ((size_t)C + 1) * sizeof(uint32_t), st))) return e;
-    k_grid_bounds<<<min(blocks(n), 4 * 148), kRegThreads, 0, st>>>(mo, mask, bit, n, kw.acc);
-    k_grid_setup<<<1, 32, 0, st>>>(kw.acc, C, kw.gp);
-    k_grid_count<<<blocks(n), kRegThreads, 0, st>>>(mo, mask, bit, n, kw.gp, kw.count, kw.slot);
-    if ((e = launch_scan_u32(kw.count, 1, C, kw.cell_off, kw.span_sum, (uint32_t)n, kw.status, st))) return e;
-    k_grid_scatter<<<blocks(n), kRegThreads, 0, st>>>(mo, mask, bit, n, kw.slot, kw.cell_off, kw.sorted);
+    if ((e = cudaMemsetAsync(kw.zero, 0, kw.zero_bytes, st))) return e;
+    k_grid_bounds<<<min(blocks(n), 4 * 148), kRegThreads, 0, st>>>(mo, mask, gd, n, kw.acc);
+    k_grid_setup<<<1, 32, 0, st>>>(kw.acc, gd.G, C, kw.gp);
+    k_grid_count<<<blocks(n), kRegThreads, 0, st>>>(mo, mask, gd, n, kw.gp, C, kw.count, kw.slot);
+    if ((e = launch_scan_u32(kw.count, 1, (uint32_t)gd.G * C, kw.cell_off, kw.span_sum,
+                             (uint32_t)gd.G * (uint32_t)n, kw.status, st)))
+        return e;
+    k_grid_scatter<<<blocks(n), kRegThreads, 0, st>>>(mo, mask, gd, n, kw.slot, C, kw.cell_off, kw.sorted);
+    const dim3 grid(blocks(n), ncand);
     if (k <= 8)
-        k_knn<8><<<blocks(n), kRegThreads, 0, st>>>(mo, n, k, kw.gp, kw.cell_off, kw.sorted, nbr);
+        k_knn<8><<<grid, kRegThreads, 0, st>>>(n, k, kw.gp, C, kw.cell_off, kw.sorted, nbr0, nbr1);
     else
-        k_knn<16><<<blocks(n), kRegThreads, 0, st>>>(mo, n, k, kw.gp, kw.cell_off, kw.sorted, nbr);
+        k_knn<16><<<grid, kRegThreads, 0, st>>>(n, k, kw.gp, C, kw.cell_off, kw.sorted, nbr0, nbr1);
     return cudaGetLastError();
 }
 
@@ -551,14 +692,16 @@ cudaError_t launch_regularize(const RegParams& rp, const KnnWork& kw, cudaStream
     if (rp.n <= 0) return cudaSuccess;
     k_reg_prepare<<<blocks(rp.n), kRegThreads, 0, st>>>(rp);
     cudaError_t e;
-    if ((e = launch_knn(rp.mo0, rp.mask, kPosMember, rp.n, rp.k, kw, rp.nbr_pos, st))) return e;
-    if ((e = launch_knn(rp.mo0, rp.mask, kCovMember, rp.n, rp.k, kw, rp.nbr_cov, st))) return e;
+    const uint8_t bits[2] = {kPosMember, kCovMember};
+    if ((e = launch_knn(rp.mo0, rp.mask, bits, 2, rp.n, rp.k, kw, rp.nbr_pos, rp.nbr_cov, st))) return e;
+    RegParams r2 = rp;
+    r2.qorder = kw.sorted;                             // grid 0: every Gaussian in cell order
     if (rp.k <= 8) {
-        k_reg_median<8><<<blocks(rp.n), kRegThreads, 0, st>>>(rp);
-        k_reg_apply<8><<<blocks(rp.n), kRegThreads, 0, st>>>(rp);
+        k_reg_median<8><<<blocks(rp.n), kRegThreads, 0, st>>>(r2);
+        k_reg_apply<8><<<blocks(rp.n), kRegThreads, 0, st>>>(r2);
     } else {
-        k_reg_median<16><<<blocks(rp.n), kRegThreads, 0, st>>>(rp);
-        k_reg_apply<16><<<blocks(rp.n), kRegThreads, 0, st>>>(rp);
+        k_reg_median<16><<<blocks(rp.n), kRegThreads, 0, st>>>(r2);
+        k_reg_apply<16><<<blocks(rp.n), kRegThreads, 0, st>>>(r2);
     }
     return cudaGetLastError();
 }
