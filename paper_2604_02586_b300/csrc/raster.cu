@@ -317,7 +317,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         }
         // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
         stat[k] = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
-        sm.F[k][lane] = make_float4(ddx, ddy, stat[k] ? 1.f : 0.f, 0.f);
+        sm.F[k][lane] = make_float4(ddx, ddy, 1.f, stat[k] ? 1.f : 0.f);
         yc[k] = (float)ly + 0.5f;
         T[k] = 1.0f;
         done[k] = !inside;
@@ -339,25 +339,33 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         const float rx = __shfl_sync(kFull, h_hd.z, c), ry = __shfl_sync(kFull, h_hd.w, c);
         const float x0 = ((float)bxo + 0.5f) - ox;
         const float y0 = ((float)(byo + 4 * half) + 0.5f) - oy;
-        float s[13];
-#pragma unroll
-        for (int q = 0; q < 13; ++q) s[q] = 0.f;
+        // moments paired for packed FP32x2 arithmetic: (1, 2) += w (X, Y),
+        // (3, 4) += wX (X, Y), (6, 7) += w (dx, dy), (8, 9) += wX (dx, dy),
+        // (10, 11) += wY (dx, dy), (0, 12) += w (1, static); 5 += wY Y
+        float2 s12 = make_float2(0.f, 0.f), s34 = s12, s67 = s12, s89 = s12, s1011 = s12, s0st = s12;
+        float s5 = 0.f;
         const float* Wh = Wb + half * kWHalf + c;
         const float4* Fh = sm.F[half];
+        const float2 nr = make_float2(-rx, -ry);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             const float wv = Wh[i * kWRow];
             const float4 f = Fh[i];
-            const float X = x0 + (float)(i & 7), Y = y0 + (float)(i >> 3);
-            const float dx = f.x - rx, dy = f.y - ry;
-            const float wx = wv * X, wy = wv * Y;
-            s[0] += wv; s[1] += wx; s[2] += wy;
-            s[3] = fmaf(wx, X, s[3]); s[4] = fmaf(wx, Y, s[4]); s[5] = fmaf(wy, Y, s[5]);
-            s[6] = fmaf(wv, dx, s[6]); s[7] = fmaf(wv, dy, s[7]);
-            s[8] = fmaf(wx, dx, s[8]); s[9] = fmaf(wx, dy, s[9]);
-            s[10] = fmaf(wy, dx, s[10]); s[11] = fmaf(wy, dy, s[11]);
-            s[12] = fmaf(wv, f.z, s[12]);
+            const float2 XY = make_float2(x0 + (float)(i & 7), y0 + (float)(i >> 3));
+            const float2 d = __fadd2_rn(make_float2(f.x, f.y), nr);
+            const float2 ww = make_float2(wv, wv);
+            const float2 wxy = __fmul2_rn(ww, XY);
+            const float2 wxx = make_float2(wxy.x, wxy.x), wyy = make_float2(wxy.y, wxy.y);
+            s12 = __fadd2_rn(s12, wxy);
+            s34 = __ffma2_rn(wxx, XY, s34);
+            s5 = fmaf(wxy.y, XY.y, s5);
+            s67 = __ffma2_rn(ww, d, s67);
+            s89 = __ffma2_rn(wxx, d, s89);
+            s1011 = __ffma2_rn(wyy, d, s1011);
+            s0st = __ffma2_rn(ww, make_float2(f.z, f.w), s0st);
         }
+        float s[13] = {s0st.x, s12.x, s12.y, s34.x, s34.y, s5, s67.x, s67.y,
+                       s89.x, s89.y, s1011.x, s1011.y, s0st.y};
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
         if (lane < npend) {
