@@ -298,8 +298,10 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     const size_t vbase = (size_t)vs.vrec[v];
     float* const Wb = sm.W;
 
+    // T = 0 marks a pixel that is outside the image or has terminated
     float T[2];
-    bool done[2], vis[2], stat[2];
+    bool vis[2];
+    uint32_t stat_mask[2];
     const float xc = (float)(bxo + (lane & 7)) + 0.5f;
     float yc[2];
 #pragma unroll
@@ -316,11 +318,11 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             vis[k] = vs.vis[v][pix] != 0;
         }
         // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
-        stat[k] = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
-        sm.F[k][lane] = make_float4(ddx, ddy, 1.f, stat[k] ? 1.f : 0.f);
+        const bool stat = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
+        sm.F[k][lane] = make_float4(ddx, ddy, 1.f, stat ? 1.f : 0.f);
+        stat_mask[k] = __ballot_sync(kFull, stat);
         yc[k] = (float)ly + 0.5f;
-        T[k] = 1.0f;
-        done[k] = !inside;
+        T[k] = inside ? 1.0f : 0.0f;
     }
     const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
     const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
@@ -380,7 +382,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
 
     uint32_t g_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
     for (uint32_t b0 = beg; b0 < end; b0 += 32) {
-        if (!__any_sync(kFull, !done[0] || !done[1])) break;
+        if (!__any_sync(kFull, T[0] > 0.f || T[1] > 0.f)) break;
         bool hit = false;
         const uint32_t g = g_next;
         if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
@@ -419,20 +421,18 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             for (int k = 0; k < 2; ++k) {
                 const float pw = fmaf(z2[k], z2[k], z1s);
                 const float alpha = fminf(kAlphaMax, g1.y * sfu_exp2(-pw));
-                const bool pass = !done[k] && alpha >= kAlphaMin;
+                const bool pass = alpha >= kAlphaMin;
                 const float Tn = T[k] * (1.0f - alpha);
-                const bool term = pass && Tn < kTMin;
-                const bool blend = pass && !term;
+                const bool blend = pass && Tn >= kTMin;    // T = 0: Tn = 0, never blends
                 add[k] = blend && vis[k];
                 Wb[k * kWHalf + lane * kWRow + pend] = add[k] ? alpha * T[k] : 0.f;
-                if (kStats) { cnt[0] += !done[k]; cnt[1] += blend; cnt[2] += add[k]; }
-                T[k] = blend ? Tn : T[k];
-                done[k] = done[k] || term;
+                if (kStats) { cnt[0] += T[k] > 0.f; cnt[1] += blend; cnt[2] += add[k]; }
+                T[k] = blend ? Tn : (pass ? 0.f : T[k]);   // pass without blend: terminated
             }
-            const int np = __popc(__ballot_sync(kFull, add[0])) + __popc(__ballot_sync(kFull, add[1]));
-            if (np == 0) continue;                     // nothing of this block to add
-            const int ns = __popc(__ballot_sync(kFull, add[0] && stat[0])) +
-                           __popc(__ballot_sync(kFull, add[1] && stat[1]));
+            const uint32_t a0 = __ballot_sync(kFull, add[0]), a1 = __ballot_sync(kFull, add[1]);
+            if ((a0 | a1) == 0u) continue;             // nothing of this block to add
+            const int np = __popc(a0) + __popc(a1);
+            const int ns = __popc(a0 & stat_mask[0]) + __popc(a1 & stat_mask[1]);
             if (lane == pend) {
                 h_id = sm.id[j];
                 h_hd = sm.hd[j];
