@@ -328,11 +328,11 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
     if (kStats && blk == 0 && lane == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
-    // pending hit c is held by lane c: moment record, origin and reference, counts
+    // pending hit c is held by lane c: moment record, origin and reference, and the
+    // masks of the pixels it added (rows 0-3, 4-7)
     int pend = 0;
-    uint32_t h_id = 0;
+    uint32_t h_id = 0, h_m0 = 0, h_m1 = 0;
     float4 h_hd = make_float4(0.f, 0.f, 0.f, 0.f);
-    float h_np = 0.f, h_ns = 0.f;
 
     auto phase2 = [&](int npend) {
         __syncwarp();
@@ -371,6 +371,8 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
         if (lane < npend) {
+            const float h_np = (float)(__popc(h_m0) + __popc(h_m1));
+            const float h_ns = (float)(__popc(h_m0 & stat_mask[0]) + __popc(h_m1 & stat_mask[1]));
             float4* dst = &w.moments[(vbase + h_id) * 4];
             atomicAdd(dst + 0, make_float4(s[0], s[1], s[2], s[3]));
             atomicAdd(dst + 1, make_float4(s[4], s[5], s[6], s[7]));
@@ -416,28 +418,32 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             float z2[2];
             z2[0] = fmaf(-g0.w, ex, yc[0] - g0.y) * g1.x;
             z2[1] = fmaf(4.0f, g1.x, z2[0]);
+            // the lane's two pixels in packed FP32x2 where the operation is shared
+            const float2 z2p = make_float2(z2[0], z2[1]);
+            const float2 pw = __ffma2_rn(z2p, z2p, make_float2(z1s, z1s));
+            const float2 oe = __fmul2_rn(make_float2(g1.y, g1.y), make_float2(sfu_exp2(-pw.x), sfu_exp2(-pw.y)));
+            const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
+            const float2 Tp = make_float2(T[0], T[1]);
+            const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al.x, -al.y)));
+            const float2 wa = __fmul2_rn(al, Tp);
             bool add[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const float pw = fmaf(z2[k], z2[k], z1s);
-                const float alpha = fminf(kAlphaMax, g1.y * sfu_exp2(-pw));
+                const float alpha = k ? al.y : al.x, tn = k ? Tn.y : Tn.x;
                 const bool pass = alpha >= kAlphaMin;
-                const float Tn = T[k] * (1.0f - alpha);
-                const bool blend = pass && Tn >= kTMin;    // T = 0: Tn = 0, never blends
+                const bool blend = pass && tn >= kTMin;    // T = 0: Tn = 0, never blends
                 add[k] = blend && vis[k];
-                Wb[k * kWHalf + lane * kWRow + pend] = add[k] ? alpha * T[k] : 0.f;
+                Wb[k * kWHalf + lane * kWRow + pend] = add[k] ? (k ? wa.y : wa.x) : 0.f;
                 if (kStats) { cnt[0] += T[k] > 0.f; cnt[1] += blend; cnt[2] += add[k]; }
-                T[k] = blend ? Tn : (pass ? 0.f : T[k]);   // pass without blend: terminated
+                T[k] = blend ? tn : (pass ? 0.f : T[k]);   // pass without blend: terminated
             }
             const uint32_t a0 = __ballot_sync(kFull, add[0]), a1 = __ballot_sync(kFull, add[1]);
             if ((a0 | a1) == 0u) continue;             // nothing of this block to add
-            const int np = __popc(a0) + __popc(a1);
-            const int ns = __popc(a0 & stat_mask[0]) + __popc(a1 & stat_mask[1]);
             if (lane == pend) {
                 h_id = sm.id[j];
                 h_hd = sm.hd[j];
-                h_np = (float)np;
-                h_ns = (float)ns;
+                h_m0 = a0;
+                h_m1 = a1;
             }
             if (++pend == kChunk) {
                 phase2(kChunk);
