@@ -309,6 +309,26 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
     return ((uint64_t)hi << 32) | lo;
 }
 
+// In-register comparators of stride J < KPL for merge size k (k is known only at
+// run time; the stride is a template argument so the partners stay registers).
+template <int KPL, int J>
+__device__ __forceinline__ void inreg_stage(uint64_t (&x)[KPL], int k, int lane)
+{
+#pragma unroll
+    for (int i = 0; i < KPL; ++i) {
+        const int p = i ^ J;
+        if (p > i && p < KPL) {
+            const bool up = k >= KPL ? (lane & (k / KPL)) == 0 : (i & k) == 0;
+            const uint64_t a = x[i], b = x[p];
+            const bool sw = (a > b) == up;
+            x[i] = sw ? b : a;
+            x[p] = sw ? a : b;
+        }
+    }
+}
+
+// The stage loops stay rolled: a fully unrolled network of every list size does
+// not fit the instruction cache once warps of one SM sort lists of different sizes.
 template <int KPL>
 __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint32_t n, int lane)
 {
@@ -318,9 +338,9 @@ __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint
         const uint32_t e = (uint32_t)(lane * KPL + i);
         x[i] = e < n ? keys[e] : ~0ull;
     }
-#pragma unroll
+#pragma unroll 1
     for (int k = 2; k <= 32 * KPL; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= KPL) {
                 const int lj = j / KPL;
@@ -331,18 +351,14 @@ __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint
                     const uint64_t y = shfl_xor_u64(x[i], lj);
                     x[i] = take_min ? (y < x[i] ? y : x[i]) : (y > x[i] ? y : x[i]);
                 }
+            } else if (KPL >= 16 && j == 8) {
+                inreg_stage<KPL, (KPL >= 16 ? 8 : 1)>(x, k, lane);
+            } else if (KPL >= 8 && j == 4) {
+                inreg_stage<KPL, (KPL >= 8 ? 4 : 1)>(x, k, lane);
+            } else if (KPL >= 4 && j == 2) {
+                inreg_stage<KPL, (KPL >= 4 ? 2 : 1)>(x, k, lane);
             } else {
-#pragma unroll
-                for (int i = 0; i < KPL; ++i) {
-                    const int p = i ^ j;
-                    if (p > i) {
-                        const bool up = k >= KPL ? (lane & (k / KPL)) == 0 : (i & k) == 0;
-                        const uint64_t a = x[i], b = x[p];
-                        const bool sw = (a > b) == up;
-                        x[i] = sw ? b : a;
-                        x[p] = sw ? a : b;
-                    }
-                }
+                inreg_stage<KPL, 1>(x, k, lane);
             }
         }
     }
