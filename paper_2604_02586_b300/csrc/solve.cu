@@ -10,15 +10,16 @@
 // a7 (Sec. 4.4.1), one thread per Gaussian: linear triangulation in pixel units,
 //   rows (u' P3 - P1) and (v' P3 - P2) of P = K [R|t], written about the old mean
 //   (X = mu + delta) so the right-hand side is -z_mu times the per-view shift of
-//   the centre: no cancellation.  FP32 normal equations, FP64 Cholesky.
+//   the centre: no cancellation.  FP32 normal equations, double-float Cholesky.
 // a8 (Sec. 4.4.2): vech(T Sigma T^T) = vech(Sigma_2D') per solved view with
 //   T = J' W at the new mean, 6 unknowns.  Two views are always rank 5 (each T
 //   annihilates its viewing ray d, so sym(d1 d2^T) is a null vector) and are
 //   reported singular without a solve.  With 3+ views: FP32 rows, normal
-//   equations accumulated from exact products in double-float, then an FP64
-//   LDL^T with diagonal pivoting whose last pivot ratio decides rank deficiency.
+//   equations accumulated from exact products in double-float, then a
+//   double-float LDL^T with diagonal pivoting whose last pivot ratio decides rank
+//   deficiency.
 // a9 (Sec. 4.4.3): cyclic Jacobi in FP32 for the eigenvectors, eigenvalues as
-//   FP64 Rayleigh quotients; discard if an eigenvalue is <= 0; new axis k takes
+//   double-float Rayleigh quotients; discard if an eigenvalue is <= 0; new axis k takes
 //   the eigenpair whose rank matches the rank of the old scale s_k; each axis is
 //   flipped to agree with the old one; a reflection is undone on the
 //   least-aligned axis; the quaternion sign follows the old one.
@@ -27,6 +28,86 @@
 namespace tsp {
 
 namespace {
+
+// ---------------------------------------------------------------- double-float
+// A value hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2 (Dekker's
+// double-length arithmetic built on the error-free TwoSum and FMA-based TwoProd):
+// about 48 significant bits.  It replaces FP64 in the small dense solves: this
+// GPU's FP64 rate is a small fraction of its FP32 rate.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_of(float a) { return df{a, 0.f}; }
+
+__device__ __forceinline__ df df_norm(float a, float b)
+{
+    df r;
+    two_sum(a, b, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df operator+(df a, df b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    df r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df operator-(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b)
+{
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    df r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df operator*(df a, float b)
+{
+    float p, e;
+    two_prod(a.hi, b, p, e);
+    e = __fmaf_rn(a.lo, b, e);
+    df r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// a / b: an FP32 quotient corrected once by the double-float remainder.
+__device__ __forceinline__ df operator/(df a, df b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df r = a - b * q1;
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    df q;
+    fast_two_sum(q1, q2, q.hi, q.lo);
+    return q;
+}
+
+// sqrt(a) for a > 0: the FP32 root corrected by the exact remainder a - x^2.
+__device__ __forceinline__ df df_sqrt(df a)
+{
+    const float x = __fsqrt_rn(a.hi);
+    float p, e;
+    two_prod(x, x, p, e);
+    const float rem = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
+    df r;
+    fast_two_sum(x, __fdiv_rn(rem, __fmul_rn(2.f, x)), r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ bool operator<(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df a, df b) { return b < a; }
+__device__ __forceinline__ bool operator==(df a, df b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ float df_float(df a) { return __fadd_rn(a.hi, a.lo); }
 
 // Per-view records written by a6 and read by a7/a8:
 //   vres0 = (mu'_x, mu'_y, c_x, c_y) with c = mu' - mu_2D the shift of the centre,
@@ -125,45 +206,45 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const FitP
     }
 }
 
-// ---------------------------------------------------------------- FP64 helpers
+// ---------------------------------------------------------------- solvers
 
 // In-place Cholesky solve of the SPD system A x = b (A row-major N x N, lower
 // triangle used).  Returns false if a pivot falls below rel * max diagonal.
 template <int N>
-__device__ bool chol_solve(double (&A)[N][N], double (&b)[N], double rel)
+__device__ bool chol_solve(df (&A)[N][N], df (&b)[N], float rel)
 {
-    double dmax = 0.0;
+    float dmax = 0.f;
 #pragma unroll
-    for (int k = 0; k < N; ++k) dmax = fmax(dmax, A[k][k]);
-    if (!(dmax > 0.0)) return false;
+    for (int k = 0; k < N; ++k) dmax = fmaxf(dmax, A[k][k].hi);
+    if (!(dmax > 0.f)) return false;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        double d = A[k][k];
+        df d = A[k][k];
 #pragma unroll
-        for (int j = 0; j < k; ++j) d -= A[k][j] * A[k][j];
-        if (!(d > rel * dmax)) return false;
-        const double l = sqrt(d);
+        for (int j = 0; j < k; ++j) d = d - A[k][j] * A[k][j];
+        if (!(d.hi > rel * dmax)) return false;
+        const df l = df_sqrt(d);
         A[k][k] = l;
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
-            double x = A[i][k];
+            df x = A[i][k];
 #pragma unroll
-            for (int j = 0; j < k; ++j) x -= A[i][j] * A[k][j];
+            for (int j = 0; j < k; ++j) x = x - A[i][j] * A[k][j];
             A[i][k] = x / l;
         }
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {          // L y = b
-        double x = b[i];
+        df x = b[i];
 #pragma unroll
-        for (int j = 0; j < i; ++j) x -= A[i][j] * b[j];
+        for (int j = 0; j < i; ++j) x = x - A[i][j] * b[j];
         b[i] = x / A[i][i];
     }
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {     // L^T x = y
-        double x = b[i];
+        df x = b[i];
 #pragma unroll
-        for (int j = i + 1; j < N; ++j) x -= A[j][i] * b[j];
+        for (int j = i + 1; j < N; ++j) x = x - A[j][i] * b[j];
         b[i] = x / A[i][i];
     }
     return true;
@@ -190,16 +271,16 @@ __device__ __forceinline__ void df_madd(float& hi, float& lo, float a, float b)
 // Swap rows and columns k < j of a packed symmetric matrix, including the
 // already factorised columns (rows of L) left of k.
 template <int N>
-__device__ __forceinline__ void sym_swap(double (&A)[N * (N + 1) / 2], int k, int j)
+__device__ __forceinline__ void sym_swap(df (&A)[N * (N + 1) / 2], int k, int j)
 {
 #pragma unroll
     for (int m = 0; m < N; ++m) {
         if (m == k || m == j) continue;
-        const double t = A[tri(k, m)];
+        const df t = A[tri(k, m)];
         A[tri(k, m)] = A[tri(j, m)];
         A[tri(j, m)] = t;
     }
-    const double t = A[tri(k, k)];
+    const df t = A[tri(k, k)];
     A[tri(k, k)] = A[tri(j, j)];
     A[tri(j, j)] = t;
 }
@@ -210,22 +291,22 @@ __device__ __forceinline__ void sym_swap(double (&A)[N * (N + 1) / 2], int k, in
 // when a pivot is <= rel * (largest diagonal of A); otherwise b holds x.  Every
 // index is a compile-time constant after unrolling, so A stays in registers.
 template <int N>
-__device__ __forceinline__ bool ldl_solve_pivoted(double (&A)[N * (N + 1) / 2], double (&b)[N], double rel)
+__device__ __forceinline__ bool ldl_solve_pivoted(df (&A)[N * (N + 1) / 2], df (&b)[N], float rel)
 {
     static_assert(N <= 8, "permutation packed as 4-bit fields");
     uint32_t perm = 0;                       // original index of row i in bits 4i..4i+3
-    double dinv[N];
-    double dmax = 0.0;
+    df dinv[N];
+    float dmax = 0.f;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         perm |= (uint32_t)k << (4 * k);
-        dmax = fmax(dmax, A[tri(k, k)]);
+        dmax = fmaxf(dmax, A[tri(k, k)].hi);
     }
-    if (!(dmax > 0.0)) return false;
+    if (!(dmax > 0.f)) return false;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         int p = k;
-        double best = A[tri(k, k)];
+        df best = A[tri(k, k)];
 #pragma unroll
         for (int j = k + 1; j < N; ++j)
             if (A[tri(j, j)] > best) { best = A[tri(j, j)]; p = j; }
@@ -233,39 +314,39 @@ __device__ __forceinline__ bool ldl_solve_pivoted(double (&A)[N * (N + 1) / 2], 
         for (int j = k + 1; j < N; ++j)
             if (p == j) {
                 sym_swap<N>(A, k, j);
-                const double tb = b[k]; b[k] = b[j]; b[j] = tb;
+                const df tb = b[k]; b[k] = b[j]; b[j] = tb;
                 const uint32_t x = ((perm >> (4 * k)) ^ (perm >> (4 * j))) & 15u;
                 perm ^= (x << (4 * k)) | (x << (4 * j));
             }
-        const double d = A[tri(k, k)];
-        if (!(d > rel * dmax)) return false;
-        const double di = 1.0 / d;
+        const df d = A[tri(k, k)];
+        if (!(d.hi > rel * dmax)) return false;
+        const df di = df_of(1.f) / d;
         dinv[k] = di;
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {          // Schur complement of the pivot
-            const double li = A[tri(i, k)] * di;
+            const df li = A[tri(i, k)] * di;
 #pragma unroll
-            for (int j = k + 1; j <= i; ++j) A[tri(i, j)] -= li * A[tri(j, k)];
+            for (int j = k + 1; j <= i; ++j) A[tri(i, j)] = A[tri(i, j)] - li * A[tri(j, k)];
         }
 #pragma unroll
-        for (int i = k + 1; i < N; ++i) A[tri(i, k)] *= di;   // column k of L
+        for (int i = k + 1; i < N; ++i) A[tri(i, k)] = A[tri(i, k)] * di;   // column k of L
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {                  // L z = P b, then D^-1
 #pragma unroll
-        for (int m = 0; m < i; ++m) b[i] -= A[tri(i, m)] * b[m];
+        for (int m = 0; m < i; ++m) b[i] = b[i] - A[tri(i, m)] * b[m];
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) b[i] *= dinv[i];
+    for (int i = 0; i < N; ++i) b[i] = b[i] * dinv[i];
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {             // L^T y = z
 #pragma unroll
-        for (int m = i + 1; m < N; ++m) b[i] -= A[tri(m, i)] * b[m];
+        for (int m = i + 1; m < N; ++m) b[i] = b[i] - A[tri(m, i)] * b[m];
     }
-    double x[N];
+    df x[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {                  // x = P^T y
-        x[j] = 0.0;
+        x[j] = df_of(0.f);
 #pragma unroll
         for (int i = 0; i < N; ++i)
             if (((perm >> (4 * i)) & 15u) == (uint32_t)j) x[j] = b[i];
@@ -306,17 +387,18 @@ __device__ __forceinline__ bool jacobi_rotate(float (&S)[3][3], float (&E)[3][3]
 }
 
 // Cyclic Jacobi on the FP32 copy of S (at most 8 sweeps; quadratic convergence
-// ends it in 2-4), eigenvalues refined as FP64 Rayleigh quotients e^T S e / e^T e.
+// ends it in 2-4), eigenvalues refined as double-float Rayleigh quotients
+// e^T S e / e^T e.
 // The Rayleigh quotient error is second order in the FP32 eigenvector error, so
 // the small eigenvalues of an elongated Gaussian keep their relative accuracy.
-__device__ __forceinline__ void eig_sym3(const double (&S)[3][3], double (&lam)[3], float (&E)[3][3])
+__device__ __forceinline__ void eig_sym3(const df (&S)[3][3], df (&lam)[3], float (&E)[3][3])
 {
     float A[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            A[i][j] = (float)S[i][j];
+            A[i][j] = df_float(S[i][j]);
             E[i][j] = i == j ? 1.f : 0.f;
         }
     for (int sweep = 0; sweep < 8; ++sweep) {
@@ -327,11 +409,12 @@ __device__ __forceinline__ void eig_sym3(const double (&S)[3][3], double (&lam)[
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double e0 = E[0][k], e1 = E[1][k], e2 = E[2][k];
-        const double se0 = S[0][0] * e0 + S[0][1] * e1 + S[0][2] * e2;
-        const double se1 = S[1][0] * e0 + S[1][1] * e1 + S[1][2] * e2;
-        const double se2 = S[2][0] * e0 + S[2][1] * e1 + S[2][2] * e2;
-        lam[k] = (e0 * se0 + e1 * se1 + e2 * se2) / (e0 * e0 + e1 * e1 + e2 * e2);
+        const float e0 = E[0][k], e1 = E[1][k], e2 = E[2][k];
+        const df se0 = S[0][0] * e0 + S[0][1] * e1 + S[0][2] * e2;
+        const df se1 = S[1][0] * e0 + S[1][1] * e1 + S[1][2] * e2;
+        const df se2 = S[2][0] * e0 + S[2][1] * e1 + S[2][2] * e2;
+        const df ee = df_of(e0) * df_of(e0) + df_of(e1) * df_of(e1) + df_of(e2) * df_of(e2);
+        lam[k] = (se0 * e0 + se1 * e1 + se2 * e2) / ee;
     }
 }
 
@@ -419,14 +502,16 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
         N11 += ay * ay + by * by; N12 += ay * az + by * bz; N22 += az * az + bz * bz;
         r0 += ax * ra + bx * rb; r1 += ay * ra + by * rb; r2 += az * ra + bz * rb;
     }
-    double Nt[3][3] = {{N00, N01, N02}, {N01, N11, N12}, {N02, N12, N22}};
-    double dl[3] = {r0, r1, r2};
-    if (!chol_solve<3>(Nt, dl, 1e-24)) {
+    df Nt[3][3] = {{df_of(N00), df_of(N01), df_of(N02)},
+                   {df_of(N01), df_of(N11), df_of(N12)},
+                   {df_of(N02), df_of(N12), df_of(N22)}};
+    df dl[3] = {df_of(r0), df_of(r1), df_of(r2)};
+    if (!chol_solve<3>(Nt, dl, 1e-24f)) {
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_TRI_SINGULAR;
         return;
     }
-    const float X0 = (float)((double)m.x + dl[0]), X1 = (float)((double)m.y + dl[1]),
-                X2 = (float)((double)m.z + dl[2]);
+    const float X0 = df_float(df_of(m.x) + dl[0]), X1 = df_float(df_of(m.y) + dl[1]),
+                X2 = df_float(df_of(m.z) + dl[2]);
     st |= TSP_POS_OK;
     outm = make_float4(X0, X1, X2, m.w);
 
@@ -480,23 +565,23 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
             }
         }
     }
-    double A6[21], b6[6];
+    df A6[21], b6[6];
 #pragma unroll
-    for (int u = 0; u < 21; ++u) A6[u] = (double)Ah[u] + (double)Al[u];
+    for (int u = 0; u < 21; ++u) A6[u] = df_norm(Ah[u], Al[u]);
 #pragma unroll
-    for (int u = 0; u < 6; ++u) b6[u] = (double)bh[u] + (double)bl[u];
-    const double rc2 = (double)fp.cov_rcond_min * (double)fp.cov_rcond_min;
+    for (int u = 0; u < 6; ++u) b6[u] = df_norm(bh[u], bl[u]);
+    const float rc2 = fp.cov_rcond_min * fp.cov_rcond_min;
     if (!ldl_solve_pivoted<6>(A6, b6, rc2)) {
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_COV_SINGULAR;
         return;
     }
-    const double S[3][3] = {{b6[0], b6[1], b6[2]}, {b6[1], b6[3], b6[4]}, {b6[2], b6[4], b6[5]}};
+    const df S[3][3] = {{b6[0], b6[1], b6[2]}, {b6[1], b6[3], b6[4]}, {b6[2], b6[4], b6[5]}};
 
     // ---- a9 eigen decomposition and the reorder / sign rules
-    double lam[3];
+    df lam[3];
     float E[3][3];
     eig_sym3(S, lam, E);
-    if (!(lam[0] > 0.0) || !(lam[1] > 0.0) || !(lam[2] > 0.0)) {
+    if (!(lam[0].hi > 0.f) || !(lam[1].hi > 0.f) || !(lam[2].hi > 0.f)) {
         om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_NEG_EIG;
         return;
     }
@@ -512,7 +597,7 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
     ranks3(so, ro);
     ranks3(lam, rn);
     float Rn[3][3], al[3];
-    double ln[3];
+    df ln[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)          // old axis k takes the eigenpair of equal rank
 #pragma unroll
@@ -551,7 +636,7 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
 #pragma unroll
         for (int k = 0; k < 4; ++k) qq[k] = -qq[k];
     outq = make_float4(qq[0], qq[1], qq[2], qq[3]);
-    outs = make_float4(sqrtf((float)ln[0]), sqrtf((float)ln[1]), sqrtf((float)ln[2]), 0.f);
+    outs = make_float4(sqrtf(df_float(ln[0])), sqrtf(df_float(ln[1])), sqrtf(df_float(ln[2])), 0.f);
     om[g] = outm; oq[g] = outq; os[g] = outs; ost[g] = st | TSP_COV_OK;
 }
 
