@@ -332,8 +332,10 @@ typedef enum {
                              /* collect_stats = 1: (pixel, Gaussian) evaluations,     */
                              /* blended contributions, moment additions, list entries */
     TSP_I_VIEW_MEANS = 8,    /* float[V][n][4]: mu_2D' (x, y) and its shift from mu_2D */
-    TSP_I_VIEW_COV = 9       /* float[V][n][8]: rows of B with Sigma_2D' = B B^T     */
+    TSP_I_VIEW_COV = 9,      /* float[V][n][8]: rows of B with Sigma_2D' = B B^T     */
                              /* (B00 B01 B02 sum-w, B10 B11 B12 0)                     */
+    TSP_I_KNN_PATH = 10      /* uint32[2]: neighbour search of the last tsp_knn /     */
+                             /* tsp_regularize per candidate set: 0 grid, 1 BVH       */
 } tsp_intermediate;
 tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, size_t* size_out);
 

@@ -26,7 +26,7 @@ class TSP:
     POS_OK, COV_OK, NEG_EIG, FEW_VIEWS, LOW_ALPHA, FEW_PX, COV_SINGULAR, TRI_SINGULAR = \
         1, 2, 4, 8, 16, 32, 64, 128
     I_COUNTS, I_RECT, I_DEPTH, I_TILES_TOUCHED, I_TILE_OFFSETS, I_PAIRS, I_MOMENTS, I_STATS, \
-        I_VIEW_MEANS, I_VIEW_COV = range(10)
+        I_VIEW_MEANS, I_VIEW_COV, I_KNN_PATH = range(11)
     STAGES = ("project", "scan", "emit", "tile_sort", "raster", "view_solve", "multiview")
     MAX_VIEWS = 32
     REG_STATIC, REG_POS_MEDIAN, REG_POS_PROPAGATED, REG_COV_MEDIAN, REG_COV_PROPAGATED = 1, 2, 4, 8, 16
@@ -481,7 +481,7 @@ class Context:
         dtype = {TSP.I_COUNTS: np.int64, TSP.I_RECT: np.int16, TSP.I_DEPTH: np.uint32,
                  TSP.I_TILES_TOUCHED: np.uint32, TSP.I_TILE_OFFSETS: np.uint32,
                  TSP.I_PAIRS: np.uint64, TSP.I_MOMENTS: np.float32, TSP.I_STATS: np.uint64,
-                 TSP.I_VIEW_MEANS: np.float32, TSP.I_VIEW_COV: np.float32}[which]
+                 TSP.I_VIEW_MEANS: np.float32, TSP.I_VIEW_COV: np.float32, TSP.I_KNN_PATH: np.uint32}[which]
         a = np.empty(size.value // np.dtype(dtype).itemsize, dtype)
         self._check(lib().tsp_inspect(self._h, which, _hptr(a), size.value, None), "tsp_inspect")
         return a

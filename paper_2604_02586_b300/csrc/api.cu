@@ -51,6 +51,7 @@ struct tsp_context {
     uint32_t last_NT = 0;
     // moments of the last single-frame fit: [last_fit_V][last_fit_n][16], else -1
     int last_fit_n = -1, last_fit_V = -1;
+    const uint32_t* last_knn_path = nullptr;   // device [2] of the last neighbour search
 };
 
 namespace {
@@ -474,6 +475,13 @@ tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp
     const size_t o_zero = take(zero_bytes), o_gp = take(G * sizeof(GridParam)), o_st = take(16);
     const size_t o_off = take((G * C + 1) * 4), o_span = take((G * C / 1024 + 2) * 8);
     const size_t o_slot = take(G * nn * 8), o_sorted = take(G * nn * 16);
+    // BVH fallback (two candidate sets)
+    const size_t K = kMortonBuckets;
+    const size_t bvh_zero_bytes = 2 * K * 4 + 2 * nn * 4 + 2 * 8 + 4 * 4;
+    const size_t o_bzero = take(bvh_zero_bytes), o_boff = take((2 * K + 1) * 4);
+    const size_t o_bspan = take((2 * K / 1024 + 2) * 8), o_bst = take(16), o_bslot = take(2 * nn * 8);
+    const size_t o_keys = take(2 * nn * 8), o_ktmp = take(2 * nn * 8), o_long = take(2 * K * 4 + 4);
+    const size_t o_nodes = take(2 * nn * 64), o_par = take(2 * 2 * nn * 4);
     size_t o_mask = 0, o_vec = 0, o_nbr = 0;
     if (rp) {
         o_mask = take(nn);
@@ -482,6 +490,11 @@ tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp
     }
     tsp_status s;
     if ((s = ensure(ctx, ctx->reg, off))) return s;
+    if (!ctx->dstatus.p) {
+        if ((s = ensure(ctx, ctx->dstatus, 16))) return s;
+        TSP_CUDA(cudaMemset(ctx->dstatus.p, 0, 16));
+    }
+    kw.err = (uint32_t*)ctx->dstatus.p;
     char* b = (char*)ctx->reg.p;
     kw.zero = (uint32_t*)(b + o_zero);
     kw.zero_bytes = zero_bytes;
@@ -493,6 +506,23 @@ tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp
     kw.span_sum = (unsigned long long*)(b + o_span);
     kw.slot = (uint2*)(b + o_slot);
     kw.sorted = (float4*)(b + o_sorted);
+    kw.bvh_zero = (uint32_t*)(b + o_bzero);
+    kw.bvh_zero_bytes = bvh_zero_bytes;
+    kw.bcount = kw.bvh_zero;
+    kw.flag = kw.bcount + 2 * K;
+    kw.skew = (unsigned long long*)(kw.flag + 2 * nn);                  // even word offset: 8-byte aligned
+    kw.use_bvh = (uint32_t*)(kw.skew + 2);
+    ctx->last_knn_path = kw.use_bvh;
+    kw.boff = (uint32_t*)(b + o_boff);
+    kw.bspan = (unsigned long long*)(b + o_bspan);
+    kw.bstatus = (uint32_t*)(b + o_bst);
+    kw.bslot = (uint2*)(b + o_bslot);
+    kw.keys = (uint64_t*)(b + o_keys);
+    kw.keys_tmp = (uint64_t*)(b + o_ktmp);
+    kw.long_list = (uint32_t*)(b + o_long);
+    kw.long_count = kw.long_list + 2 * K;
+    kw.nodes = (float4*)(b + o_nodes);
+    kw.parent = (int32_t*)(b + o_par);
     if (rp) {
         rp->mask = (uint8_t*)(b + o_mask);
         float4* v = (float4*)(b + o_vec);
@@ -853,6 +883,11 @@ tsp_status tsp_sync(tsp_context* ctx, void* stream, int timeout_ms)
     if (!ctx->dstatus.p) return TSP_OK;
     TSP_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->dstatus.p, 16, cudaMemcpyDeviceToHost, st));
     TSP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->h_status[0] & kStatusInternal) {
+        TSP_CUDA(cudaMemsetAsync(ctx->dstatus.p, 0, 4, st));
+        TSP_CUDA(cudaStreamSynchronize(st));
+        return fail(ctx, TSP_ERR_CUDA, "a bounded device loop gave up (neighbour search); results are invalid");
+    }
     if (ctx->h_status[0] & kStatusOverflow) {
         const uint64_t K = (uint64_t)ctx->h_status[1] | ((uint64_t)ctx->h_status[2] << 32);
         ctx->want_pairs = K + K / 4;
@@ -892,6 +927,7 @@ tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, siz
     }
     case TSP_I_MOMENTS: src = ctx->moments.p; size = vn * 64; break;
     case TSP_I_STATS: src = ctx->stats.p; size = ctx->stats.p ? 32 : 0; break;
+    case TSP_I_KNN_PATH: src = ctx->last_knn_path; size = ctx->last_knn_path ? 8 : 0; break;
     case TSP_I_VIEW_MEANS: src = ctx->vres0.p; size = vn * 16; break;
     case TSP_I_VIEW_COV: {
         // two planes (vres1, vres3) interleaved per (view, Gaussian) on the host

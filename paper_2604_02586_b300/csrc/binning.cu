@@ -9,6 +9,8 @@
 // per pair to place) followed by a per-tile sort in shared memory.  Each pair is
 // written once and read once by the sort, instead of the 6-8 read/write passes of
 // a global radix sort over (view, tile, depth) keys.
+#include <algorithm>
+
 #include "launch.h"
 
 namespace tsp {
@@ -152,8 +154,10 @@ __device__ __forceinline__ void load_counts4(const uint32_t* __restrict__ cnt, u
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t NT,
                                                               uint32_t stride,
-                                                              unsigned long long* __restrict__ span_sum)
+                                                              unsigned long long* __restrict__ span_sum,
+                                                              const uint32_t* __restrict__ enable)
 {
+    if (enable && !*enable) return;
     __shared__ unsigned long long warp_tot[32];
     uint32_t c[4];
     load_counts4(cnt, NT, blockIdx.x * kScanSpan + 4 * threadIdx.x, stride, c);
@@ -164,8 +168,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 
 __global__ void __launch_bounds__(1024) k_scan_spans(unsigned long long* __restrict__ span_sum, uint32_t nspan,
                                                      uint32_t* __restrict__ off, uint32_t NT, uint32_t cap,
-                                                     uint32_t* dstatus)
+                                                     uint32_t* dstatus, const uint32_t* __restrict__ enable)
 {
+    if (enable && !*enable) return;
     __shared__ unsigned long long warp_tot[32];
     unsigned long long carry = 0;
     for (uint32_t b = 0; b < nspan; b += 1024) {
@@ -187,8 +192,10 @@ __global__ void __launch_bounds__(1024) k_scan_spans(unsigned long long* __restr
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ cnt, uint32_t NT,
                                                             uint32_t stride,
                                                             const unsigned long long* __restrict__ span_pre,
-                                                            uint32_t* __restrict__ off)
+                                                            uint32_t* __restrict__ off,
+                                                            const uint32_t* __restrict__ enable)
 {
+    if (enable && !*enable) return;
     __shared__ unsigned long long warp_tot[32];
     const uint32_t i0 = blockIdx.x * kScanSpan + 4 * threadIdx.x;
     uint32_t c[4];
@@ -374,8 +381,10 @@ __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint
 __global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restrict__ off,
                                                         uint64_t* __restrict__ pairs, uint32_t cap,
                                                         uint32_t NT, uint32_t* __restrict__ long_list,
-                                                        uint32_t* __restrict__ long_count)
+                                                        uint32_t* __restrict__ long_count,
+                                                        const uint32_t* __restrict__ enable)
 {
+    if (enable && !*enable) return;
     const uint32_t t = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= NT) return;
@@ -398,8 +407,10 @@ __global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restri
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(const uint32_t* __restrict__ off,
                                                             uint64_t* pairs, uint64_t* tmp, uint32_t cap,
                                                             const uint32_t* __restrict__ long_list,
-                                                            const uint32_t* __restrict__ long_count)
+                                                            const uint32_t* __restrict__ long_count,
+                                                            const uint32_t* __restrict__ enable)
 {
+    if (enable && !*enable) return;
     __shared__ uint64_t s[kSortCap];
     const uint32_t count = *long_count;
     for (uint32_t li = blockIdx.x; li < count; li += gridDim.x) {
@@ -465,12 +476,24 @@ cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st)
 }
 
 cudaError_t launch_scan_u32(const uint32_t* cnt, uint32_t stride, uint32_t n, uint32_t* off,
-                            unsigned long long* span_sum, uint32_t cap, uint32_t* status, cudaStream_t st)
+                            unsigned long long* span_sum, uint32_t cap, uint32_t* status, cudaStream_t st,
+                            const uint32_t* enable)
 {
     const uint32_t nspan = (n + kScanSpan - 1) / kScanSpan;
-    if (nspan > 0) k_scan_reduce<<<nspan, kScanThreads, 0, st>>>(cnt, n, stride, span_sum);
-    k_scan_spans<<<1, 1024, 0, st>>>(span_sum, nspan, off, n, cap, status);
-    if (nspan > 0) k_scan_down<<<nspan, kScanThreads, 0, st>>>(cnt, n, stride, span_sum, off);
+    if (nspan > 0) k_scan_reduce<<<nspan, kScanThreads, 0, st>>>(cnt, n, stride, span_sum, enable);
+    k_scan_spans<<<1, 1024, 0, st>>>(span_sum, nspan, off, n, cap, status, enable);
+    if (nspan > 0) k_scan_down<<<nspan, kScanThreads, 0, st>>>(cnt, n, stride, span_sum, off, enable);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_sort(const uint32_t* off, uint64_t* keys, uint64_t* tmp, uint32_t cap, uint32_t nseg,
+                                uint32_t* long_list, uint32_t* long_count, cudaStream_t st, const uint32_t* enable)
+{
+    if (nseg == 0) return cudaSuccess;
+    const cudaError_t e = cudaMemsetAsync(long_count, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    k_tile_sort_warp<<<(nseg + 7) / 8, 256, 0, st>>>(off, keys, cap, nseg, long_list, long_count, enable);
+    k_tile_sort<<<64, kSortThreads, 0, st>>>(off, keys, tmp, cap, long_list, long_count, enable);
     return cudaGetLastError();
 }
 
@@ -486,10 +509,10 @@ cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
 {
     if (NT == 0) return cudaSuccess;
     // tile_fill is free once the pairs are scattered: it holds the long-list tiles
-    k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill,
-                                                   &w.dstatus[3]);
+    k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill, &w.dstatus[3],
+                                                   nullptr);
     k_tile_sort<<<64, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
-                                              &w.dstatus[3]);
+                                              &w.dstatus[3], nullptr);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,7 @@ struct FitParams {
 };
 
 constexpr uint32_t kStatusOverflow = 1u;
+constexpr uint32_t kStatusInternal = 2u;   // a bounded device loop gave up (reported by tsp_sync)
 
 // --------------------------------------------------------------------------
 // Key path: culling, depth key and tile rectangle in FP32 with a fixed order of

@@ -17,8 +17,17 @@ cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st);
 // Exclusive scan of n counts cnt[i * stride] into off[0..n] (off[n] = total);
 // span_sum: ceil(n / 1024) + 1 scratch words; status[1..2] receive the total and
 // status[0] bit 0 is set if it exceeds cap.
+// With enable != nullptr every kernel returns at once when *enable == 0.
 cudaError_t launch_scan_u32(const uint32_t* cnt, uint32_t stride, uint32_t n, uint32_t* off,
-                            unsigned long long* span_sum, uint32_t cap, uint32_t* status, cudaStream_t st);
+                            unsigned long long* span_sum, uint32_t cap, uint32_t* status, cudaStream_t st,
+                            const uint32_t* enable = nullptr);
+// Sort each of nseg segments [off[s], off[s + 1]) of 64-bit keys ascending (keys
+// unique within a segment); tmp: as many keys as keys, long_list: nseg words,
+// long_count: one word.  With enable != nullptr the kernels return at once when
+// *enable == 0.
+cudaError_t launch_segment_sort(const uint32_t* off, uint64_t* keys, uint64_t* tmp, uint32_t cap, uint32_t nseg,
+                                uint32_t* long_list, uint32_t* long_count, cudaStream_t st,
+                                const uint32_t* enable = nullptr);
 // a2: emit (depth << 32 | g) into each touched tile's slice.
 cudaError_t launch_scatter(const ViewSet& vs, const Work& w, cudaStream_t st);
 // a3: sort each tile's slice ascending (depth, then Gaussian index).
@@ -75,7 +84,27 @@ struct KnnWork {
     uint32_t* status;               // 4 words
     uint2* slot;                    // [kMaxGrids][n] (cell, rank in cell)
     float4* sorted;                 // [kMaxGrids * n] members by cell: x, y, z, index bits
+    // BVH fallback of the candidate sets (skewed point sets): Morton buckets,
+    // sorted keys, nodes, parents, refit flags, per-set switch
+    uint32_t* bvh_zero;             // bcount, flag, skew, use: cleared together
+    size_t bvh_zero_bytes;
+    uint32_t* bcount;               // [2 * kMortonBuckets]
+    uint32_t* flag;                 // [2][n]
+    unsigned long long* skew;       // [2] sum over cells of count^2
+    uint32_t* use_bvh;              // [2], then [2] = use_bvh[0] | use_bvh[1]
+    uint32_t* boff;                 // [2 * kMortonBuckets + 1]
+    unsigned long long* bspan;      // [2 * kMortonBuckets / 1024 + 2]
+    uint32_t* bstatus;              // 4 words
+    uint2* bslot;                   // [2][n]
+    uint64_t* keys;                 // [2n] (Morton code << 32 | index), sorted per bucket
+    uint64_t* keys_tmp;             // [2n]
+    uint32_t* long_list;            // [2 * kMortonBuckets]
+    uint32_t* long_count;           // 1 word
+    float4* nodes;                  // [2][n][4]: child boxes (lo0 + child0, hi0, lo1 + child1, hi1)
+    int32_t* parent;                // [2][2n]: internal node i at [i], leaf k at [n + k]
+    uint32_t* err;                  // the context's device status word (kStatusInternal)
 };
+constexpr int kMortonBuckets = 1 << 16;
 struct RegParams {
     int n, V, k, min_views;
     float min_px, frac;

@@ -14,6 +14,22 @@
 // not yet visited, less a margin that covers the FP32 rounding of the cell
 // assignment; so the k nearest found are the exact k nearest under the pinned
 // FP32 distance and (distance, index) order.
+//
+// Skewed point sets.  A uniform grid sized by the members' box and count fails
+// when the density varies by orders of magnitude (dense surfaces with a sparse
+// far field of floaters, tight clusters): the dense regions crowd few cells.
+// When the grid's occupancy statistic (sum over cells of count^2 / members) is
+// far above a Poisson grid's, the set is searched with a bounding-volume
+// hierarchy instead: members sorted by 30-bit Morton code (bucketed by the top
+// 16 bits, buckets sorted by (code, index)), a binary radix tree built from the
+// sorted keys (Karras 2012, "Maximizing parallelism in the construction of BVHs,
+// octrees, and k-d trees"), child boxes refitted bottom-up, and a depth-first
+// walk, nearer child first, that skips a subtree whose box distance exceeds the
+// current k-th.  The box distance is computed with the same FP32 operations as
+// the point distance from per-axis gaps that no member's offset can undercut,
+// so by monotone rounding it is a lower bound of every member's FP32 distance:
+// the pruning is exact.  The switch is taken on the device; both paths are
+// always launched and the unused one returns at once.
 #include <cfloat>
 #include <cmath>
 
@@ -24,6 +40,9 @@ namespace {
 
 constexpr int kRegThreads = 256;
 constexpr int kMembersPerCell = 3;       // grid density: members per cell on average
+// BVH when sum(count^2) / members exceeds this (a Poisson grid gives about
+// kMembersPerCell + 1)
+constexpr float kSkewLimit = 16.0f;
 
 __device__ __forceinline__ uint32_t ordered_key(float f)
 {
@@ -295,10 +314,10 @@ template <int KMAX>
 __global__ void __launch_bounds__(kRegThreads) k_knn(int n, int k, const GridParam* __restrict__ gpp, uint32_t C,
                                                     const uint32_t* __restrict__ cell_off,
                                                     const float4* __restrict__ sorted, int32_t* __restrict__ nbr0,
-                                                    int32_t* __restrict__ nbr1)
+                                                    int32_t* __restrict__ nbr1, const uint32_t* __restrict__ use_bvh)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    if (t >= n || use_bvh[blockIdx.y]) return;
     const int grid = blockIdx.y + 1;
     const GridParam gp = gpp[grid];
     const uint32_t* __restrict__ co = cell_off + (size_t)grid * C;
@@ -359,6 +378,330 @@ __global__ void __launch_bounds__(kRegThreads) k_knn(int n, int k, const GridPar
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
         if (j < k) nbr[(size_t)q.self * k + j] = bi[j] == INT_MAX ? -1 : bi[j];
+}
+
+// ----------------------------------------------------------------- BVH fallback
+
+constexpr int kBvhStack = 64;          // > tree depth: unique 64-bit keys give at most 64 levels
+
+// Sum over the cells of candidate grid y + 1 of count^2.
+__global__ void __launch_bounds__(kRegThreads) k_grid_skew(const uint32_t* __restrict__ count, uint32_t C,
+                                                          unsigned long long* __restrict__ skew)
+{
+    __shared__ unsigned long long s[kRegThreads / 32];
+    const uint32_t* c = count + (size_t)(blockIdx.y + 1) * C;
+    unsigned long long v = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x)
+        v += (unsigned long long)c[i] * c[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kRegThreads / 32; ++w) t += s[w];
+        if (t) atomicAdd(&skew[blockIdx.y], t);
+    }
+}
+
+// use_bvh[c] for each candidate set, use_bvh[2] = any of them.
+__global__ void k_bvh_decide(const uint32_t* __restrict__ acc, const unsigned long long* __restrict__ skew, int ncand,
+                             uint32_t* __restrict__ use_bvh)
+{
+    if (threadIdx.x != 0) return;
+    uint32_t any = 0u;
+    for (int c = 0; c < ncand; ++c) {
+        const uint32_t m = acc[8 * (c + 1) + 6];
+        const uint32_t u = (m > 1u && (float)skew[c] > kSkewLimit * (float)m) ? 1u : 0u;
+        use_bvh[c] = u;
+        any |= u;
+    }
+    use_bvh[2] = any;
+}
+
+// Spread the low 10 bits of x to every third bit.
+__device__ __forceinline__ uint32_t spread3(uint32_t x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t morton30(float4 p, const uint32_t* acc)
+{
+    const float c[3] = {p.x, p.y, p.z};
+    uint32_t code = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = key_value(~acc[i]), hi = key_value(acc[3 + i]);
+        const float ext = hi - lo;
+        const float inv = ext > 0.f ? 1024.0f / ext : 0.f;
+        const uint32_t qi = (uint32_t)fminf(fmaxf((c[i] - lo) * inv, 0.f), 1023.f);
+        code |= spread3(qi) << (2 - i);
+    }
+    return code;
+}
+
+// Members of candidate set y: bucket by the top 16 bits of the Morton code.
+__global__ void __launch_bounds__(kRegThreads) k_bvh_codes(const float4* __restrict__ mo,
+                                                          const uint8_t* __restrict__ mask, GridDesc gd, int n,
+                                                          const uint32_t* __restrict__ acc,
+                                                          const uint32_t* __restrict__ use_bvh,
+                                                          uint32_t* __restrict__ bcount, uint2* __restrict__ bslot)
+{
+    const int c = blockIdx.y;
+    if (!use_bvh[c]) return;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        if (!member(mask, gd.bits[c + 1], g)) continue;
+        const uint32_t code = morton30(mo[g], acc + 8 * (c + 1));
+        const uint32_t b = (uint32_t)c * kMortonBuckets + (code >> 14);      // top 16 of 30 bits
+        bslot[(size_t)c * n + g] = make_uint2(b, atomicAdd(&bcount[b], 1u));
+    }
+}
+
+__global__ void __launch_bounds__(kRegThreads) k_bvh_scatter(const float4* __restrict__ mo,
+                                                            const uint8_t* __restrict__ mask, GridDesc gd, int n,
+                                                            const uint32_t* __restrict__ acc,
+                                                            const uint32_t* __restrict__ use_bvh,
+                                                            const uint2* __restrict__ bslot,
+                                                            const uint32_t* __restrict__ boff,
+                                                            uint64_t* __restrict__ keys)
+{
+    const int c = blockIdx.y;
+    if (!use_bvh[c]) return;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        if (!member(mask, gd.bits[c + 1], g)) continue;
+        const uint32_t code = morton30(mo[g], acc + 8 * (c + 1));
+        const uint2 s = bslot[(size_t)c * n + g];
+        keys[boff[s.x] + s.y] = ((uint64_t)code << 32) | (uint32_t)g;
+    }
+}
+
+// Common-prefix length of sorted keys i and j (-1 outside [0, m)); keys are unique.
+__device__ __forceinline__ int bvh_delta(const uint64_t* __restrict__ keys, long long m, long long i, long long j)
+{
+    if (j < 0 || j >= m) return -1;
+    return __clzll((long long)(keys[i] ^ keys[j]));
+}
+
+// Karras' construction of internal node i of a binary radix tree over m sorted keys.
+// Child encoding: >= 0 an internal node, < 0 the member with index -(c + 1).
+__device__ __forceinline__ void bvh_node(const uint64_t* __restrict__ keys, long long m, long long i, int n,
+                                              float4* __restrict__ nodes, int32_t* __restrict__ parent)
+{
+    const int d = bvh_delta(keys, m, i, i + 1) > bvh_delta(keys, m, i, i - 1) ? 1 : -1;
+    const int dmin = bvh_delta(keys, m, i, i - d);
+    long long lmax = 2;
+    while (bvh_delta(keys, m, i, i + lmax * d) > dmin) lmax <<= 1;
+    long long l = 0;
+    for (long long t = lmax >> 1; t >= 1; t >>= 1)
+        if (bvh_delta(keys, m, i, i + (l + t) * d) > dmin) l += t;
+    const long long j = i + l * d;
+    const int dnode = bvh_delta(keys, m, i, j);
+    long long s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (bvh_delta(keys, m, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const long long gam = i + s * d + (d < 0 ? -1 : 0);
+    const long long lo = i < j ? i : j, hi = i < j ? j : i;
+    int c0, c1;
+    if (lo == gam) {
+        c0 = -(int)(uint32_t)(keys[gam] & 0xffffffffu) - 1;
+        parent[n + gam] = (int)i;
+    } else {
+        c0 = (int)gam;
+        parent[gam] = (int)i;
+    }
+    if (hi == gam + 1) {
+        c1 = -(int)(uint32_t)(keys[gam + 1] & 0xffffffffu) - 1;
+        parent[n + gam + 1] = (int)i;
+    } else {
+        c1 = (int)(gam + 1);
+        parent[gam + 1] = (int)i;
+    }
+    nodes[4 * i + 0].w = __int_as_float(c0);
+    nodes[4 * i + 2].w = __int_as_float(c1);
+    if (i == 0) parent[0] = -1;
+}
+
+__global__ void __launch_bounds__(kRegThreads) k_bvh_build(int n, const uint32_t* __restrict__ acc,
+                                                          const uint32_t* __restrict__ use_bvh,
+                                                          const uint32_t* __restrict__ boff,
+                                                          const uint64_t* __restrict__ keys_all,
+                                                          float4* __restrict__ nodes_all,
+                                                          int32_t* __restrict__ parent_all)
+{
+    const int c = blockIdx.y;
+    if (!use_bvh[c]) return;
+    const long long m = acc[8 * (c + 1) + 6];
+    const uint64_t* keys = keys_all + boff[(size_t)c * kMortonBuckets];
+    float4* nodes = nodes_all + (size_t)c * n * 4;
+    int32_t* parent = parent_all + (size_t)c * 2 * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m - 1;
+         i += (long long)gridDim.x * blockDim.x)
+        bvh_node(keys, m, i, n, nodes, parent);
+}
+
+
+__device__ __forceinline__ void child_box(const float4* __restrict__ nodes, const float4* __restrict__ mo, int ch,
+                                          float3& lo, float3& hi)
+{
+    if (ch < 0) {
+        const float4 p = mo[-(ch + 1)];
+        lo = make_float3(p.x, p.y, p.z);
+        hi = lo;
+    } else {
+        const float4 a = __ldcg(nodes + 4 * ch), b = __ldcg(nodes + 4 * ch + 1);
+        const float4 e = __ldcg(nodes + 4 * ch + 2), f = __ldcg(nodes + 4 * ch + 3);
+        lo = make_float3(fminf(a.x, e.x), fminf(a.y, e.y), fminf(a.z, e.z));
+        hi = make_float3(fmaxf(b.x, f.x), fmaxf(b.y, f.y), fmaxf(b.z, f.z));
+    }
+}
+
+// From leaf k upwards: the second child to finish a node computes its child boxes.
+__device__ __forceinline__ void bvh_refit_leaf(int n, const float4* __restrict__ mo, float4* __restrict__ nodes,
+                                               const int32_t* __restrict__ parent, uint32_t* __restrict__ flag,
+                                               uint32_t* __restrict__ status, long long k)
+{
+    int node = parent[n + k];
+    for (int level = 0; node >= 0; ++level) {
+        if (level > kBvhStack) {                   // deeper than any valid tree: report, stop
+            atomicOr(status, kStatusInternal);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&flag[node], 1u) == 0u) return;       // the other child is not done yet
+        __threadfence();
+        const int c0 = __float_as_int(__ldcg(nodes + 4 * node).w), c1 = __float_as_int(__ldcg(nodes + 4 * node + 2).w);
+        float3 lo0, hi0, lo1, hi1;
+        child_box(nodes, mo, c0, lo0, hi0);
+        child_box(nodes, mo, c1, lo1, hi1);
+        __stcg(nodes + 4 * node + 0, make_float4(lo0.x, lo0.y, lo0.z, __int_as_float(c0)));
+        __stcg(nodes + 4 * node + 1, make_float4(hi0.x, hi0.y, hi0.z, 0.f));
+        __stcg(nodes + 4 * node + 2, make_float4(lo1.x, lo1.y, lo1.z, __int_as_float(c1)));
+        __stcg(nodes + 4 * node + 3, make_float4(hi1.x, hi1.y, hi1.z, 0.f));
+        node = parent[node];
+    }
+}
+
+// Bottom-up boxes: the second child to finish a node computes its child boxes.
+__global__ void __launch_bounds__(kRegThreads) k_bvh_refit(int n, const float4* __restrict__ mo,
+                                                          const uint32_t* __restrict__ acc,
+                                                          const uint32_t* __restrict__ use_bvh,
+                                                          float4* __restrict__ nodes_all,
+                                                          const int32_t* __restrict__ parent_all,
+                                                          uint32_t* __restrict__ flag_all, uint32_t* __restrict__ status)
+{
+    const int c = blockIdx.y;
+    if (!use_bvh[c]) return;
+    const long long m = acc[8 * (c + 1) + 6];
+    float4* nodes = nodes_all + (size_t)c * n * 4;
+    const int32_t* parent = parent_all + (size_t)c * 2 * n;
+    uint32_t* flag = flag_all + (size_t)c * n;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (long long)gridDim.x * blockDim.x)
+        bvh_refit_leaf(n, mo, nodes, parent, flag, status, k);
+}
+
+// Lower bound of the pinned FP32 distance from q to any point of the box [lo, hi]:
+// the same operations on per-axis gaps, which no member's |offset| undercuts.
+__device__ __forceinline__ float box_dist2(float qx, float qy, float qz, float4 lo, float4 hi)
+{
+    const float gx = fmaxf(fmaxf(__fsub_rn(lo.x, qx), __fsub_rn(qx, hi.x)), 0.f);
+    const float gy = fmaxf(fmaxf(__fsub_rn(lo.y, qy), __fsub_rn(qy, hi.y)), 0.f);
+    const float gz = fmaxf(fmaxf(__fsub_rn(lo.z, qz), __fsub_rn(qz, hi.z)), 0.f);
+    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+
+// Query qp (position, index bits): its k nearest members by the BVH of m >= 2
+// members.
+template <int KMAX>
+__device__ __forceinline__ void knn_bvh_query(float4 qp, int k, long long m, const float4* __restrict__ nodes,
+                                              int32_t* __restrict__ nbr, uint32_t* __restrict__ status)
+{
+    const float qx = qp.x, qy = qp.y, qz = qp.z;
+    const int self = __float_as_int(qp.w);
+    float bd[KMAX];
+    int bi[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        bd[j] = INFINITY;
+        bi[j] = INT_MAX;
+    }
+    int stk[kBvhStack];
+    float stkd[kBvhStack];
+    int sp = 0;
+    int cur = 0;                                   // the root (members >= 2)
+    const long long max_visits = 2 * m + 8;        // each internal node at most once
+    for (long long visit = 0;; ++visit) {
+        if (visit > max_visits) {
+            atomicOr(status, kStatusInternal);
+            break;
+        }
+        float kth = INFINITY;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+            if (j == k - 1) kth = bd[j];
+        const float4 a = __ldg(nodes + 4 * cur), b = __ldg(nodes + 4 * cur + 1);
+        const float4 e = __ldg(nodes + 4 * cur + 2), f = __ldg(nodes + 4 * cur + 3);
+        const int c0 = __float_as_int(a.w), c1 = __float_as_int(e.w);
+        const float d0 = box_dist2(qx, qy, qz, a, b), d1 = box_dist2(qx, qy, qz, e, f);
+        // a member child is its own box: its box distance is its distance
+        if (c0 < 0 && -(c0 + 1) != self) insert<KMAX>(bd, bi, d0, -(c0 + 1));
+        if (c1 < 0 && -(c1 + 1) != self) insert<KMAX>(bd, bi, d1, -(c1 + 1));
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+            if (j == k - 1) kth = bd[j];
+        const bool v0 = c0 >= 0 && d0 <= kth, v1 = c1 >= 0 && d1 <= kth;
+        if (v0 && v1) {
+            const bool first0 = d0 <= d1;
+            if (sp < kBvhStack) {
+                stk[sp] = first0 ? c1 : c0;
+                stkd[sp] = first0 ? d1 : d0;
+                ++sp;
+            } else {
+                atomicOr(status, kStatusInternal);   // cannot happen for trees of depth < 64
+            }
+            cur = first0 ? c0 : c1;
+            continue;
+        }
+        if (v0) { cur = c0; continue; }
+        if (v1) { cur = c1; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stkd[sp] <= kth) {
+                cur = stk[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j < k) nbr[(size_t)self * k + j] = bi[j] == INT_MAX ? -1 : bi[j];
+}
+
+// Queries in the cell order of grid 0; k nearest members of set y by the BVH.
+template <int KMAX>
+__global__ void __launch_bounds__(kRegThreads) k_knn_bvh(int n, int k, const uint32_t* __restrict__ acc,
+                                                        const uint32_t* __restrict__ use_bvh,
+                                                        const float4* __restrict__ sorted,
+                                                        const float4* __restrict__ nodes_all,
+                                                        int32_t* __restrict__ nbr0, int32_t* __restrict__ nbr1,
+                                                        uint32_t* __restrict__ status)
+{
+    const int c = blockIdx.y;
+    if (!use_bvh[c]) return;
+    const long long m = acc[8 * (c + 1) + 6];
+    const float4* __restrict__ nodes = nodes_all + (size_t)c * n * 4;
+    int32_t* __restrict__ nbr = c == 0 ? nbr0 : nbr1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        knn_bvh_query<KMAX>(sorted[t], k, m, nodes, nbr, status);
 }
 
 // ----------------------------------------------------------------- rotations
@@ -679,11 +1022,37 @@ cudaError_t launch_knn(const float4* mo, const uint8_t* mask, const uint8_t* bit
                              (uint32_t)gd.G * (uint32_t)n, kw.status, st)))
         return e;
     k_grid_scatter<<<blocks(n), kRegThreads, 0, st>>>(mo, mask, gd, n, kw.slot, C, kw.cell_off, kw.sorted);
+    // grid or BVH per candidate set, decided on the device
+    if ((e = cudaMemsetAsync(kw.bvh_zero, 0, kw.bvh_zero_bytes, st))) return e;
+    k_grid_skew<<<dim3(min((int)((C + kRegThreads - 1) / kRegThreads), 4 * 148), ncand), kRegThreads, 0, st>>>(
+        kw.count, C, kw.skew);
+    k_bvh_decide<<<1, 32, 0, st>>>(kw.acc, kw.skew, ncand, kw.use_bvh);
     const dim3 grid(blocks(n), ncand);
     if (k <= 8)
-        k_knn<8><<<grid, kRegThreads, 0, st>>>(n, k, kw.gp, C, kw.cell_off, kw.sorted, nbr0, nbr1);
+        k_knn<8><<<grid, kRegThreads, 0, st>>>(n, k, kw.gp, C, kw.cell_off, kw.sorted, nbr0, nbr1, kw.use_bvh);
     else
-        k_knn<16><<<grid, kRegThreads, 0, st>>>(n, k, kw.gp, C, kw.cell_off, kw.sorted, nbr0, nbr1);
+        k_knn<16><<<grid, kRegThreads, 0, st>>>(n, k, kw.gp, C, kw.cell_off, kw.sorted, nbr0, nbr1, kw.use_bvh);
+    // the BVH path: small grid-stride grids, every kernel returns at once unless a
+    // set needs it (use_bvh[2] gates the generic scan and sort)
+    const dim3 bgrid(min(blocks(n), 8 * 148), ncand);
+    const uint32_t* any = kw.use_bvh + 2;
+    k_bvh_codes<<<bgrid, kRegThreads, 0, st>>>(mo, mask, gd, n, kw.acc, kw.use_bvh, kw.bcount, kw.bslot);
+    const uint32_t nb = (uint32_t)ncand * kMortonBuckets;
+    if ((e = launch_scan_u32(kw.bcount, 1, nb, kw.boff, kw.bspan, (uint32_t)ncand * (uint32_t)n, kw.bstatus, st,
+                             any)))
+        return e;
+    k_bvh_scatter<<<bgrid, kRegThreads, 0, st>>>(mo, mask, gd, n, kw.acc, kw.use_bvh, kw.bslot, kw.boff, kw.keys);
+    if ((e = launch_segment_sort(kw.boff, kw.keys, kw.keys_tmp, (uint32_t)ncand * (uint32_t)n, nb, kw.long_list,
+                                 kw.long_count, st, any)))
+        return e;
+    k_bvh_build<<<bgrid, kRegThreads, 0, st>>>(n, kw.acc, kw.use_bvh, kw.boff, kw.keys, kw.nodes, kw.parent);
+    k_bvh_refit<<<bgrid, kRegThreads, 0, st>>>(n, mo, kw.acc, kw.use_bvh, kw.nodes, kw.parent, kw.flag, kw.err);
+    if (k <= 8)
+        k_knn_bvh<8><<<bgrid, kRegThreads, 0, st>>>(n, k, kw.acc, kw.use_bvh, kw.sorted, kw.nodes, nbr0, nbr1,
+                                                    kw.err);
+    else
+        k_knn_bvh<16><<<bgrid, kRegThreads, 0, st>>>(n, k, kw.acc, kw.use_bvh, kw.sorted, kw.nodes, nbr0, nbr1,
+                                                     kw.err);
     return cudaGetLastError();
 }
 

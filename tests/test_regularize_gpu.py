@@ -62,6 +62,15 @@ def points(kind, n, rng):
         mo[:, :3] = base[rng.integers(0, len(base), n)]
     elif kind == "offset":                                            # far from the origin
         mo[:, :3] = 1000.0 + rng.uniform(0, 1, (n, 3))
+    elif kind in ("spheres_far", "blobs"):
+        c = rng.uniform(-2, 2, (20, 3))
+        if kind == "blobs":
+            mo[:, :3] = c[rng.integers(0, 20, n)] + rng.normal(0, 0.02, (n, 3))
+        else:                                                         # surfaces and floaters
+            d = rng.normal(size=(n, 3))
+            d /= np.linalg.norm(d, axis=1, keepdims=True)
+            mo[:, :3] = c[rng.integers(0, 20, n)] + 0.3 * d
+            mo[: n // 20, :3] = rng.uniform(-20, 20, (n // 20, 3))
     mo[:, 3] = 0.5
     return mo
 
@@ -84,7 +93,8 @@ def mask_of(kind, n, rng):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("kind", ["uniform", "clustered", "lattice", "flat", "duplicates", "offset"])
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "lattice", "flat", "duplicates", "offset", "spheres_far",
+                                  "blobs"])
 @pytest.mark.parametrize("mkind", ["all", "half", "sparse", "none", "one"])
 def test_knn_bit_exact(ctx, kind, mkind):
     rng = np.random.default_rng(zlib.crc32(f"{kind}/{mkind}".encode()))
@@ -108,13 +118,34 @@ def test_knn_tiny(ctx, n):
     np.testing.assert_array_equal(got, oracle.knn(mo, mask, 8))
 
 
-def test_knn_large_sampled(ctx):
-    """200,000 points in a 4-unit box (the capture workload's Gaussians): sampled
-    queries against an FP32 brute force over all points."""
+def test_knn_path_follows_the_point_distribution(ctx):
+    """A near-uniform set is searched on the grid; sets whose density varies by
+    orders of magnitude switch to the BVH (both give the exact lists)."""
+    import paper_2604_02586_b300 as tsp
+    rng = np.random.default_rng(5)
+    n = 20000
+    for kind, want in (("uniform", 0), ("lattice", 0), ("blobs", 1), ("spheres_far", 1)):
+        mo = points(kind, n, rng)
+        mask = np.ones(n, np.uint8)
+        got = ctx.knn(cuda(mo), cuda(mask), 8, sync=True).cpu().numpy()
+        assert ctx.inspect(tsp.TSP.I_KNN_PATH)[0] == want, kind
+        q = rng.choice(n, 200, replace=False)
+        X = mo[:, :3]
+        for i in q:
+            d = X[i] - X
+            d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+            d2[i] = np.inf
+            np.testing.assert_array_equal(got[i], np.lexsort((np.arange(n), d2))[:8])
+
+
+@pytest.mark.parametrize("kind", ["uniform", "spheres_far"])
+def test_knn_large_sampled(ctx, kind):
+    """200,000 points, uniform in a 4-unit box (the capture workload's Gaussians)
+    or on sphere surfaces with a far field: sampled queries against an FP32 brute
+    force over all points."""
     rng = np.random.default_rng(77)
     n, k = 200_000, 8
-    mo = np.zeros((n, 4), np.float32)
-    mo[:, :3] = rng.uniform(-2, 2, (n, 3))
+    mo = points(kind, n, rng)
     mask = (rng.random(n) < 0.85).astype(np.uint8)
     got = ctx.knn(cuda(mo), cuda(mask), k, sync=True).cpu().numpy()
     q = rng.choice(n, 300, replace=False)
