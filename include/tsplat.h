@@ -295,10 +295,13 @@ typedef struct tsp_reg_result {
  * last tsp_fit_motion / tsp_fit_motion_host call, which must have had the same
  * n and num_views (INVALID_ARG otherwise).  Means must be finite.  All arrays are
  * device memory of the context's device, 16-byte aligned ([n][4], view_moments)
- * or 4-byte aligned (flags, nbr_*); outputs must not overlap inputs.  Device-side grid
- * sizing: no host wait; enqueues on `stream` and may be captured in a CUDA graph
- * once the workspace for this n and k exists.  Errors: INVALID_ARG, OOM, BUDGET,
- * CUDA. */
+ * or 4-byte aligned (flags, nbr_*); outputs must not overlap inputs.  The neighbour
+ * search (a uniform grid, or an exact bounding-volume hierarchy for point sets
+ * whose density varies by orders of magnitude) is sized and chosen on the device:
+ * no host wait; enqueues on `stream` and may be captured in a CUDA graph once the
+ * workspace for this n and k exists.  Errors: INVALID_ARG, OOM, BUDGET, CUDA; a
+ * search whose bounded walk gave up (not expected for finite means) is reported
+ * by the next tsp_sync as CUDA. */
 tsp_status tsp_regularize(tsp_context* ctx, const tsp_gaussians* before, const tsp_result* fitted,
                           const float* view_moments, int num_views, const tsp_reg_options* opt,
                           const tsp_reg_result* out, void* stream);
