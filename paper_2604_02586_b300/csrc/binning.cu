@@ -277,6 +277,9 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
 
 constexpr int kSortCap = 4096;      // entries sorted in shared memory at once
 constexpr int kSortThreads = 256;
+// CTAs of the long-list sort: one tile each at a time; enough to fill 148 SMs
+// (a dense frame has thousands of lists longer than kWarpSortMax)
+constexpr int kLongSortCtas = 148 * 4;
 
 // Bitonic sort of n <= kSortCap keys at src (global) in shared memory, written back.
 __device__ void smem_sort(uint64_t* src, uint32_t n, uint64_t* s)
@@ -493,7 +496,7 @@ cudaError_t launch_segment_sort(const uint32_t* off, uint64_t* keys, uint64_t* t
     const cudaError_t e = cudaMemsetAsync(long_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     k_tile_sort_warp<<<(nseg + 7) / 8, 256, 0, st>>>(off, keys, cap, nseg, long_list, long_count, enable);
-    k_tile_sort<<<64, kSortThreads, 0, st>>>(off, keys, tmp, cap, long_list, long_count, enable);
+    k_tile_sort<<<kLongSortCtas, kSortThreads, 0, st>>>(off, keys, tmp, cap, long_list, long_count, enable);
     return cudaGetLastError();
 }
 
@@ -511,7 +514,7 @@ cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
     // tile_fill is free once the pairs are scattered: it holds the long-list tiles
     k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill, &w.dstatus[3],
                                                    nullptr);
-    k_tile_sort<<<64, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
+    k_tile_sort<<<kLongSortCtas, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
                                               &w.dstatus[3], nullptr);
     return cudaGetLastError();
 }

@@ -499,63 +499,104 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(cons
     }
 }
 
-__global__ void __launch_bounds__(kTilePx) k_raster_render(const ViewSet vs, const Work w,
-                                                           const RenderOut ro)
+// Colour render (Sec. 3.1), one 128-thread CTA per tile: warp w walks the tile's
+// depth-ordered list for its 8x8 block (w & 1, w >> 1) on its own, lane l owning
+// pixels (l & 7, (l >> 3) + 4k), k = 0, 1.  Entries are culled per block as in the
+// accumulate walk (an entry whose alpha >= 1/255 ellipse misses every pixel centre
+// of the block cannot change any of them), so each pixel sees the same Gaussians in
+// the same order with the same arithmetic (render_alpha, render_transmit) as a
+// pixel-by-pixel walk of the whole list, which the adjoint recomputes.
+struct RenderSmem {
+    float4 g0[32];
+    float4 g1[32];
+    float4 c[32];
+};
+
+__device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, const RenderOut& ro, uint32_t tile,
+                                             int blk, RenderSmem& sm)
 {
-    __shared__ float4 s_g0[kBatch];
-    __shared__ float4 s_g1[kBatch];
-    __shared__ float4 s_box[kBatch];
-    __shared__ float4 s_c[kBatch];
-    const uint32_t tile = blockIdx.x;
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    int lx, ly;
-    pixel_of(tid, lx, ly);
+    const int lane = threadIdx.x & 31;
+    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < W && py < H;
-    const float xc = (float)lx + 0.5f, yc = (float)ly + 0.5f;
-    const float bx0 = (float)((warp & 1) * 8) + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)((warp >> 1) * 4) + 0.5f, by1 = by0 + 3.0f;
-    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
-    bool done = !inside;
     const size_t vbase = (size_t)vs.vrec[v];
-    for (uint32_t b0 = beg; b0 < end; b0 += kBatch) {
-        const int nb = (int)min((uint32_t)kBatch, end - b0);
-        if (tid < nb) {
-            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+    const float xc = (float)(bxo + (lane & 7)) + 0.5f;
+    float yc[2], T[2], cr[2], cg[2], cb[2];
+    bool done[2], inside[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int ly = byo + (lane >> 3) + 4 * k;
+        inside[k] = tx * kTile + bxo + (lane & 7) < W && ty * kTile + ly < H;
+        yc[k] = (float)ly + 0.5f;
+        T[k] = 1.0f;
+        cr[k] = cg[k] = cb[k] = 0.f;
+        done[k] = !inside[k];
+    }
+    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
+    uint32_t g_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
+    for (uint32_t b0 = beg; b0 < end; b0 += 32) {
+        if (!__any_sync(kFull, !done[0] || !done[1])) break;
+        bool hit = false;
+        const uint32_t g = g_next;
+        if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
+        if (b0 + lane < end) {
             const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
             const float4 g1 = w.geom1[vbase + g];
-            s_g0[tid] = g0;
-            s_g1[tid] = g1;
-            s_box[tid] = footprint_box(g0, g1);
-            s_c[tid] = w.color[vbase + g];
+            const float4 bb = footprint_box(g0, g1);
+            hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
+            if (hit)
+                hit = block_min_power(g0, g1.x, bx0, bx1, by0, by1) <=
+                      log2f(255.0f * g1.y) * 1.002f + 1e-4f;
+            if (hit) {
+                sm.g0[lane] = g0;
+                sm.g1[lane] = g1;
+                sm.c[lane] = w.color[vbase + g];
+            }
         }
-        __syncthreads();
-        for (int j = 0; j < nb && !done; ++j) {
-            const float4 bb = s_box[j];
-            if (bb.x > bx1 || bb.y < bx0 || bb.z > by1 || bb.w < by0) continue;
-            const float4 g0 = s_g0[j];
-            const float4 g1 = s_g1[j];
-            const float alpha = render_alpha(g0, g1, xc, yc);
-            if (alpha < kAlphaMin) continue;
-            const float Tn = render_transmit(T, alpha);
-            if (Tn < kTMin) { done = true; break; }
-            const float wgt = alpha * T;
-            const float4 c = s_c[j];
-            cr = fmaf(wgt, c.x, cr); cg = fmaf(wgt, c.y, cg); cb = fmaf(wgt, c.z, cb);
-            T = Tn;
+        uint32_t m = __ballot_sync(kFull, hit);
+        __syncwarp();
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 g0 = sm.g0[j], g1 = sm.g1[j];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (done[k]) continue;
+                const float alpha = render_alpha(g0, g1, xc, yc[k]);
+                if (alpha < kAlphaMin) continue;
+                const float Tn = render_transmit(T[k], alpha);
+                if (Tn < kTMin) {
+                    done[k] = true;
+                    continue;
+                }
+                const float wgt = alpha * T[k];
+                const float4 c = sm.c[j];
+                cr[k] = fmaf(wgt, c.x, cr[k]);
+                cg[k] = fmaf(wgt, c.y, cg[k]);
+                cb[k] = fmaf(wgt, c.z, cb[k]);
+                T[k] = Tn;
+            }
         }
-        if (__syncthreads_count(!done) == 0) break;
+        __syncwarp();                                  // staging is rewritten next
     }
-    if (inside) {
-        const size_t pix = (size_t)py * W + px;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!inside[k]) continue;
+        const size_t pix = (size_t)(ty * kTile + byo + (lane >> 3) + 4 * k) * W + (tx * kTile + bxo + (lane & 7));
         float* o = ro.rgb[v] + 3 * pix;
-        o[0] = cr; o[1] = cg; o[2] = cb;
-        ro.T[v][pix] = T;
+        o[0] = cr[k]; o[1] = cg[k]; o[2] = cb[k];
+        ro.T[v][pix] = T[k];
     }
+}
+
+__global__ void __launch_bounds__(128) k_raster_render(const ViewSet vs, const Work w, const RenderOut ro)
+{
+    __shared__ RenderSmem sm[4];
+    const int warp = threadIdx.x >> 5;
+    render_block(vs, w, ro, blockIdx.x, warp, sm[warp]);
 }
 
 }  // namespace
@@ -620,7 +661,7 @@ cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, 
     if (NT == 0) return cudaSuccess;
     RenderOut ro;
     for (int v = 0; v < vs.V; ++v) { ro.rgb[v] = rgb[v]; ro.T[v] = final_T[v]; }
-    k_raster_render<<<NT, kTilePx, 0, st>>>(vs, w, ro);
+    k_raster_render<<<NT, 128, 0, st>>>(vs, w, ro);
     return cudaGetLastError();
 }
 
