@@ -11,11 +11,21 @@
 // with d = pixel centre - mu_2D and Q the inverse of the dilated Sigma_2D.
 //
 // k_render_backward recomputes each tile's blend front to back from the tile
-// lists (no per-pixel lists are stored; the forward colour C is an input), with
-// the same layout, staging and decisions as the forward render kernel, and folds
-// each (8x4 warp block, Gaussian) contribution to the 9 per-(view, Gaussian)
-// quantities (d mu_2D, d Q, d opacity, d colour) with one transposing butterfly
-// before its atomics.  k_render_backward_project then carries them, one thread
+// lists (no per-pixel lists are stored; the forward colour C is an input) with the
+// forward render's walk: warp w takes the 8x8 block (w & 1, w >> 1), lane l its
+// pixels (l & 7, (l >> 3) + 4k), entries culled by the exact ellipse-block test,
+// the same arithmetic and decisions per pixel.  Two phases, as in the moment
+// accumulation:
+//   phase 1 (pixel-parallel), per hit: h = G dL/dalpha (0 where alpha is clamped)
+//   and the weight alpha T of each pixel into a warp-private buffer;
+//   phase 2 (hit-parallel), per 8 pending hits: the block sums S0 = sum h,
+//   S1, S2 = sum h (x~, y~), S3, S4, S5 = sum h (x~^2, x~ y~, y~^2) with
+//   (x~, y~) = pixel centre - mu_2D, and sum alpha T dL/dC per channel.  With
+//   G = 2^-p, p = z1^2 + z2^2, z1 = x~ i11, z2 = (y~ - k x~) i22, the per-(view,
+//   Gaussian) quantities are dL/dmu_2D = o ln2 dp/d(x~, y~) applied to (S1, S2),
+//   dL/dQ = -o/2 (S3, 2 S4, S5) and dL/do = S0; 3 float4 atomics per (block, hit).
+// The colour term of dL/dalpha uses the running scalar Q = dL/dC . P, so a pixel
+// keeps 4 numbers of state.  k_render_backward_project then carries them, one thread
 // per Gaussian over its views, through Q = inverse(Sigma_2D + 0.3 I),
 // Sigma_2D = (J W) Sigma_3D (J W)^T, the perspective map, the colour basis along
 // the viewing direction and Sigma_3D = R(q) diag(s^2) R(q)^T.
@@ -25,112 +35,210 @@ namespace tsp {
 
 namespace {
 
-constexpr int kBBatch = 64;
 constexpr float kLn2 = 0.69314718055994531f;
+constexpr uint32_t kFull = 0xffffffffu;
 
-__global__ void __launch_bounds__(kTilePx) k_render_backward(const ViewSet vs, const Work w,
-                                                             const RenderGrad rg)
+// Smallest value of p = z1^2 + z2^2 over the pixel-centre rectangle of a block
+// (the same test as the accumulate walk): 0 when the mean is inside.
+__device__ __forceinline__ float bwd_block_min_power(float4 g0, float i22, float bx0, float bx1, float by0, float by1)
 {
-    __shared__ float4 s_g0[kBBatch];
-    __shared__ float4 s_g1[kBBatch];
-    __shared__ float4 s_box[kBBatch];
-    __shared__ float4 s_c[kBBatch];
-    __shared__ uint32_t s_id[kBBatch];
-    const uint32_t tile = blockIdx.x;
+    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
+    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
+    float pv = 3.0e38f, ph = 3.0e38f;
+    if (outx) {
+        const float e = ex0 > 0.f ? ex0 : ex1;
+        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
+        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
+        pv = fmaf(z1, z1, z2 * z2);
+    }
+    if (outy) {
+        const float f = ey0 > 0.f ? ey0 : ey1;
+        const float i22s = i22 * i22;
+        const float a = fmaf(g0.z, g0.z, g0.w * g0.w * i22s);
+        const float ex = fminf(fmaxf(g0.w * i22s * f / a, ex0), ex1);
+        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
+        ph = fmaf(z1, z1, z2 * z2);
+    }
+    return (outx || outy) ? fminf(pv, ph) : 0.f;
+}
+
+constexpr int kBChunk = 8;                       // pending hits per phase 2
+constexpr int kBRow = 2 * kBChunk + 2;           // words per pixel: (h, w) per hit, padded
+constexpr int kBQuarter = 16 * kBRow + 16;       // 16 pixels; = 16 (mod 32) words
+constexpr int kBWords = 4 * kBQuarter;
+
+struct BwdSmem {
+    float4 g0[32];
+    float4 g1[32];
+    float4 c[32];
+    uint32_t id[32];
+    float4 pg0[kBChunk];                         // pending hits: blend parameters, record
+    float4 pg1[kBChunk];
+    uint32_t pid[kBChunk];
+    float HW[kBWords];                           // (h, w) of pixel 16 q + j, hit c at q kBQuarter + j kBRow + 2c
+    float4 gC[64];                               // dL/dC of each pixel
+};
+
+__device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w, const RenderGrad& rg, uint32_t tile,
+                                               int blk, BwdSmem& sm)
+{
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     if (beg >= end) return;
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int lx, ly;
-    pixel_of(tid, lx, ly);
+    const int lane = threadIdx.x & 31;
+    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < W && py < H;
-    const float xc = (float)lx + 0.5f, yc = (float)ly + 0.5f;
-    const float bx0 = (float)((warp & 1) * 8) + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)((warp >> 1) * 4) + 0.5f, by1 = by0 + 3.0f;
-    float Cf[3] = {0.f, 0.f, 0.f}, gC[3] = {0.f, 0.f, 0.f}, P[3] = {0.f, 0.f, 0.f};
-    if (inside) {
-        const size_t pix = 3 * ((size_t)py * W + px);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            Cf[ch] = rg.rgb[v][pix + ch];
-            gC[ch] = rg.grad[v][pix + ch];
-        }
-    }
-    float T = 1.0f;
-    bool done = !inside;
     const size_t vbase = (size_t)vs.vrec[v];
-    for (uint32_t b0 = beg; b0 < end; b0 += kBBatch) {
-        const int nb = (int)min((uint32_t)kBBatch, end - b0);
-        if (tid < nb) {
-            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+    const float xc = (float)(bxo + (lane & 7)) + 0.5f;
+    float yc[2], T[2], D[2], Q[2], gc[2][3];
+    bool done[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int ly = byo + (lane >> 3) + 4 * k;
+        const int px = tx * kTile + bxo + (lane & 7), py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        float cf[3] = {0.f, 0.f, 0.f};
+        gc[k][0] = gc[k][1] = gc[k][2] = 0.f;
+        if (inside) {
+            const size_t pix = 3 * ((size_t)py * W + px);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                cf[ch] = rg.rgb[v][pix + ch];
+                gc[k][ch] = rg.grad[v][pix + ch];
+            }
+        }
+        sm.gC[lane + 32 * k] = make_float4(gc[k][0], gc[k][1], gc[k][2], 0.f);
+        D[k] = gc[k][0] * cf[0] + gc[k][1] * cf[1] + gc[k][2] * cf[2];   // dL/dC . C
+        Q[k] = 0.f;                                                     // dL/dC . P
+        yc[k] = (float)ly + 0.5f;
+        T[k] = 1.0f;
+        done[k] = !inside;
+    }
+    // column 0 of pixel p = lane (+ 32: two quarters further) in the (h, w) buffer
+    const int hofs = (lane >> 4) * kBQuarter + (lane & 15) * kBRow;
+    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
+    int pend = 0;
+
+    auto phase2 = [&](int npend) {
+        __syncwarp();
+        const int c = lane & 7, q = lane >> 3;
+        const float4 p0 = sm.pg0[c];
+        float s[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) s[m] = 0.f;
+        const float* hq = sm.HW + q * kBQuarter + 2 * c;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int p = 16 * q + j;
+            const float2 hw = *reinterpret_cast<const float2*>(hq + j * kBRow);
+            const float X = (float)(bxo + (p & 7)) + 0.5f - p0.x;
+            const float Y = (float)(byo + (p >> 3)) + 0.5f - p0.y;
+            const float4 g = sm.gC[p];
+            const float hx = hw.x * X, hy = hw.x * Y;
+            s[0] += hw.x;
+            s[1] += hx;
+            s[2] += hy;
+            s[3] = fmaf(hx, X, s[3]);
+            s[4] = fmaf(hx, Y, s[4]);
+            s[5] = fmaf(hy, Y, s[5]);
+            s[6] = fmaf(hw.y, g.x, s[6]);
+            s[7] = fmaf(hw.y, g.y, s[7]);
+            s[8] = fmaf(hw.y, g.z, s[8]);
+        }
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            s[m] += __shfl_xor_sync(kFull, s[m], 8);
+            s[m] += __shfl_xor_sync(kFull, s[m], 16);
+        }
+        if (q == 0 && c < npend) {
+            const float4 p1 = sm.pg1[c];
+            const float o = p1.y, i22s = p1.x * p1.x;
+            // dp/d(x~, y~) = 2 (A x~ + B y~, B x~ + Cc y~)
+            const float A = fmaf(p0.z, p0.z, p0.w * p0.w * i22s), B = -p0.w * i22s, Cc = i22s;
+            const float f = 2.f * o * kLn2;
+            float* dst = rg.acc + (vbase + sm.pid[c]) * kGradStride;
+            atomicAdd(reinterpret_cast<float4*>(dst),
+                      make_float4(f * fmaf(A, s[1], B * s[2]), f * fmaf(B, s[1], Cc * s[2]), -0.5f * o * s[3],
+                                  -o * s[4]));
+            atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(-0.5f * o * s[5], s[0], s[6], s[7]));
+            atomicAdd(dst + 8, s[8]);
+        }
+        __syncwarp();
+    };
+
+    for (uint32_t b0 = beg; b0 < end; b0 += 32) {
+        if (!__any_sync(kFull, !done[0] || !done[1])) break;
+        bool hit = false;
+        if (b0 + lane < end) {
+            const uint32_t g = (uint32_t)w.pairs[b0 + lane];
             const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
             const float4 g1 = w.geom1[vbase + g];
-            s_g0[tid] = g0;
-            s_g1[tid] = g1;
-            s_box[tid] = footprint_box(g0, g1);
-            s_c[tid] = w.color[vbase + g];
-            s_id[tid] = g;
+            const float4 bb = footprint_box(g0, g1);
+            hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
+            if (hit)
+                hit = bwd_block_min_power(g0, g1.x, bx0, bx1, by0, by1) <= log2f(255.0f * g1.y) * 1.002f + 1e-4f;
+            if (hit) {
+                sm.g0[lane] = g0;
+                sm.g1[lane] = g1;
+                sm.c[lane] = w.color[vbase + g];
+                sm.id[lane] = g;
+            }
         }
-        __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            const float4 bb = s_box[j];                       // warp-uniform, as in the forward
-            if (bb.x > bx1 || bb.y < bx0 || bb.z > by1 || bb.w < by0) continue;
-            const float4 g0 = s_g0[j];
-            const float4 g1 = s_g1[j];
-            const float4 c = s_c[j];
-            float val[16];
+        uint32_t m = __ballot_sync(kFull, hit);
+        __syncwarp();
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 g0 = sm.g0[j], g1 = sm.g1[j], c = sm.c[j];
+            float hv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f};
+            bool add[2] = {false, false};
 #pragma unroll
-            for (int k = 0; k < 16; ++k) val[k] = 0.f;
-            bool add = false;
-            if (!done) {
-                const float alpha = render_alpha(g0, g1, xc, yc);
-                if (alpha >= kAlphaMin) {
-                    const float Tn = render_transmit(T, alpha);
-                    if (Tn < kTMin) {
-                        done = true;
-                    } else {
-                        add = true;
-                        const float wgt = alpha * T;
-                        const float cc[3] = {c.x, c.y, c.z};
-                        float ga = 0.f;
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            P[ch] = fmaf(wgt, cc[ch], P[ch]);
-                            ga = fmaf(gC[ch], cc[ch] * T - (Cf[ch] - P[ch]) / (1.0f - alpha), ga);
-                            val[6 + ch] = wgt * gC[ch];
-                        }
-                        const float ex = xc - g0.x, ey = yc - g0.y;
-                        const float z1 = ex * g0.z;
-                        const float z2 = fmaf(-g0.w, ex, ey) * g1.x;
-                        const float G = exp2f(-fmaf(z2, z2, z1 * z1));
-                        if (__fmul_rn(g1.y, G) < 0.99f) {             // alpha = o G, not clamped
-                            val[5] = G * ga;
-                            const float gG = g1.y * ga;
-                            // G = 2^-(z1^2 + z2^2): dG/dmu = ln2 G dp/d(ex, ey)
-                            const float dpx = 2.f * (z1 * g0.z - z2 * g0.w * g1.x);
-                            const float dpy = 2.f * z2 * g1.x;
-                            val[0] = gG * kLn2 * G * dpx;
-                            val[1] = gG * kLn2 * G * dpy;
-                            // G = exp(-d^T Q d / 2): dG/dQ
-                            val[2] = gG * (-0.5f * G * ex * ex);
-                            val[3] = gG * (-G * ex * ey);
-                            val[4] = gG * (-0.5f * G * ey * ey);
-                        }
-                        T = Tn;
-                    }
+            for (int k = 0; k < 2; ++k) {
+                if (done[k]) continue;
+                float G;
+                const float alpha = render_alpha_g(g0, g1, xc, yc[k], G);
+                if (alpha < kAlphaMin) continue;
+                const float Tn = render_transmit(T[k], alpha);
+                if (Tn < kTMin) {
+                    done[k] = true;
+                    continue;
                 }
+                const float wgt = alpha * T[k];
+                const float gcc = fmaf(gc[k][0], c.x, fmaf(gc[k][1], c.y, gc[k][2] * c.z));   // dL/dC . c
+                Q[k] = fmaf(wgt, gcc, Q[k]);
+                // dL/dalpha = dL/dC . (c T - (C - P) / (1 - alpha)), P including this Gaussian
+                const float ga = fmaf(gcc, T[k], -__fdividef(D[k] - Q[k], 1.0f - alpha));
+                hv[k] = __fmul_rn(g1.y, G) < kAlphaMax ? ga * G : 0.f;           // alpha = o G, not clamped
+                wv[k] = wgt;
+                add[k] = true;
+                T[k] = Tn;
             }
-            if (__any_sync(0xffffffffu, add)) {
-                const float r = warp_transpose_sum16(val, lane);
-                if ((lane & 1) == 0 && (lane >> 1) < 9)
-                    atomicAdd(&rg.acc[(vbase + s_id[j]) * kGradStride + (lane >> 1)], r);
+            if (!__any_sync(kFull, add[0] || add[1])) continue;               // nothing of this block
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                *reinterpret_cast<float2*>(&sm.HW[hofs + 2 * k * kBQuarter + 2 * pend]) = make_float2(hv[k], wv[k]);
+            if (lane == 0) {
+                sm.pg0[pend] = g0;
+                sm.pg1[pend] = g1;
+                sm.pid[pend] = sm.id[j];
+            }
+            if (++pend == kBChunk) {
+                phase2(kBChunk);
+                pend = 0;
             }
         }
-        if (__syncthreads_count(!done) == 0) break;
+        __syncwarp();                                   // staging is rewritten next
     }
+    if (pend) phase2(pend);
+}
+
+__global__ void __launch_bounds__(128) k_render_backward(const ViewSet vs, const Work w, const RenderGrad rg)
+{
+    __shared__ BwdSmem sm[4];
+    const int warp = threadIdx.x >> 5;
+    backward_block(vs, w, rg, blockIdx.x, warp, sm[warp]);
 }
 
 // grid (ceil(nmax / 128), F): one thread per Gaussian of frame blockIdx.y.
@@ -309,7 +417,7 @@ cudaError_t launch_render_backward(const ViewSet& vs, const Work& w, uint32_t NT
     if (vs.nmax == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(rg.acc, 0, records * kGradStride * sizeof(float), st);
     if (e != cudaSuccess) return e;
-    if (NT > 0) k_render_backward<<<NT, kTilePx, 0, st>>>(vs, w, rg);
+    if (NT > 0) k_render_backward<<<NT, 128, 0, st>>>(vs, w, rg);
     dim3 grid((vs.nmax + 127) / 128, vs.F);
     k_render_backward_project<<<grid, 128, 0, st>>>(vs, w, rg, sh, sh_degree);
     return cudaGetLastError();

@@ -444,6 +444,18 @@ __device__ __forceinline__ float render_alpha(float4 g0, float4 g1, float xc, fl
     return fminf(kAlphaMax, __fmul_rn(g1.y, exp2f(-pw)));
 }
 
+// render_alpha that also returns G = exp2(-power) (the same operations, so alpha
+// is bit-identical).
+__device__ __forceinline__ float render_alpha_g(float4 g0, float4 g1, float xc, float yc, float& G)
+{
+    const float ex = __fsub_rn(xc, g0.x), ey = __fsub_rn(yc, g0.y);
+    const float z1 = __fmul_rn(ex, g0.z);
+    const float z2 = __fmul_rn(__fmaf_rn(-g0.w, ex, ey), g1.x);
+    const float pw = __fmaf_rn(z2, z2, __fmul_rn(z1, z1));
+    G = exp2f(-pw);
+    return fminf(kAlphaMax, __fmul_rn(g1.y, G));
+}
+
 __device__ __forceinline__ float render_transmit(float T, float alpha)
 {
     return __fmul_rn(T, __fsub_rn(1.0f, alpha));
