@@ -238,7 +238,11 @@ typedef struct tsp_render_grads {
  * rectangle, footprint box, alpha >= 1/255, transmittance cut-off, clamps of
  * alpha at 0.99 and of the colour at 0) held fixed.  The tile lists are rebuilt
  * and the blend is recomputed tile by tile; nothing per pixel is kept between the
- * two calls.  All arrays are device memory.  Errors as tsp_render. */
+ * two calls.  When the previous binning on this context was tsp_render with the
+ * same Gaussian and colour arrays and cameras (the render whose rgb is passed in),
+ * its tile lists are still in the workspace and are reused; any other binning in
+ * between (a fit, another render) makes the call build them again.  All arrays are
+ * device memory.  Errors as tsp_render. */
 tsp_status tsp_render_backward(tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
                                const tsp_camera* cams, int num_views, const float* const* rgb,
                                const float* const* grad_rgb, const tsp_render_grads* out, void* stream);

@@ -52,6 +52,12 @@ struct tsp_context {
     // moments of the last single-frame fit: [last_fit_V][last_fit_n][16], else -1
     int last_fit_n = -1, last_fit_V = -1;
     const uint32_t* last_knn_path = nullptr;   // device [2] of the last neighbour search
+    // the tile lists in the workspace come from tsp_render with these arguments
+    // (then tsp_render_backward on the same arguments reuses them)
+    bool render_bins = false;
+    const void* render_ptrs[4] = {};
+    int render_n = 0, render_deg = 0;
+    std::vector<tsp_camera> render_cams;
 };
 
 namespace {
@@ -421,6 +427,7 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
     }
     Work w{};
     ctx->last_fit_n = ctx->last_fit_V = -1;
+    ctx->render_bins = false;
     if ((s = ensure_work(ctx, R, NT, false, w))) return s;
     ctx->last_R = (size_t)R;
     ctx->last_NT = NT;
@@ -545,6 +552,31 @@ tsp_status check_device_array(tsp_context* ctx, const void* p, size_t align, con
     if (!device_accessible(p, ctx->device))
         return fail(ctx, TSP_ERR_INVALID_ARG, std::string(what) + " is not device memory of the context's device");
     return TSP_OK;
+}
+
+void note_render_bins(tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
+                      const tsp_camera* cams, int V)
+{
+    ctx->render_bins = true;
+    ctx->render_ptrs[0] = g->means_opacity;
+    ctx->render_ptrs[1] = g->quats;
+    ctx->render_ptrs[2] = g->scales;
+    ctx->render_ptrs[3] = sh;
+    ctx->render_n = g->n;
+    ctx->render_deg = sh_degree;
+    ctx->render_cams.assign(cams, cams + V);
+}
+
+bool same_render_bins(const tsp_context* ctx, const tsp_gaussians* g, const float* sh, int sh_degree,
+                      const tsp_camera* cams, int V)
+{
+    if (!ctx->render_bins || ctx->render_n != g->n || ctx->render_deg != sh_degree ||
+        (int)ctx->render_cams.size() != V)
+        return false;
+    if (ctx->render_ptrs[0] != g->means_opacity || ctx->render_ptrs[1] != g->quats ||
+        ctx->render_ptrs[2] != g->scales || ctx->render_ptrs[3] != sh)
+        return false;
+    return V == 0 || std::memcmp(ctx->render_cams.data(), cams, sizeof(tsp_camera) * (size_t)V) == 0;
 }
 
 // One frame as a batch of one.
@@ -798,7 +830,9 @@ tsp_status tsp_render(tsp_context* ctx, const tsp_gaussians* g, const float* sh,
     ctx->last_NT = NT;
     cudaStream_t st = (cudaStream_t)stream;
     ctx->timed = false;
+    ctx->render_bins = false;
     if ((s = bin_front(ctx, vs, sh, sh_degree, 1, NT, w, st))) return s;
+    note_render_bins(ctx, g, sh, sh_degree, cams, V);
     TSP_CUDA(launch_raster_render(vs, w, NT, rgb, final_T, st));
     TSP_CUDA(mark(ctx, 5, st));
     TSP_CUDA(mark(ctx, 6, st));
@@ -856,7 +890,13 @@ tsp_status tsp_render_backward(tsp_context* ctx, const tsp_gaussians* g, const f
     cudaStream_t st = (cudaStream_t)stream;
     ctx->timed = false;
     if (n == 0) return TSP_OK;
-    if ((s = bin_front(ctx, vs, sh, sh_degree, 1, NT, w, st))) return s;   // the render's tile lists again
+    // the tile lists of the render this call differentiates: still in the
+    // workspace when the previous binning was that render, else built again
+    if (!same_render_bins(ctx, g, sh, sh_degree, cams, V)) {
+        ctx->render_bins = false;
+        if ((s = bin_front(ctx, vs, sh, sh_degree, 1, NT, w, st))) return s;
+        note_render_bins(ctx, g, sh, sh_degree, cams, V);
+    }
     TSP_CUDA(launch_render_backward(vs, w, NT, rg, sh, sh_degree, (size_t)R, st));
     return TSP_OK;
 }

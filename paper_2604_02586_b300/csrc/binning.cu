@@ -17,18 +17,43 @@ namespace tsp {
 
 namespace {
 
-__device__ __forceinline__ void sh_colour(const float* sh, int deg, float x, float y, float z, float* rgb)
+// grid (ceil(nmax/128), F): one thread per Gaussian, its view-dependent colour
+// (real SH up to degree 3 along the unit direction camera centre -> mean, + 0.5,
+// clamped at 0) in every view of its frame; the coefficients are read once.
+__global__ void __launch_bounds__(128) k_colour(const ViewSet vs, const float* __restrict__ sh, int sh_degree,
+                                                Work w)
 {
-    float Y[16];
-    sh_basis16(x, y, z, Y);
-    const int nb = (deg + 1) * (deg + 1);
-    float r = 0.5f, g = 0.5f, b = 0.5f;
-    for (int k = 0; k < nb; ++k) {
-        r += Y[k] * sh[3 * k];
-        g += Y[k] * sh[3 * k + 1];
-        b += Y[k] * sh[3 * k + 2];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = blockIdx.y;
+    if (g >= vs.fn[f]) return;
+    const int nb = (sh_degree + 1) * (sh_degree + 1);
+    float c[16][3];
+    const float* s = sh + (size_t)g * nb * 3;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) c[k][ch] = k < nb ? s[3 * k + ch] : 0.f;
+    const float4 m = vs.fmo[f][g];
+    for (int v = vs.fview[f]; v < vs.fview[f + 1]; ++v) {
+        const DevCam& cm = vs.cam[v];
+        // camera centre C = -R^T t
+        const float Cx = -(cm.R[0] * cm.t[0] + cm.R[3] * cm.t[1] + cm.R[6] * cm.t[2]);
+        const float Cy = -(cm.R[1] * cm.t[0] + cm.R[4] * cm.t[1] + cm.R[7] * cm.t[2]);
+        const float Cz = -(cm.R[2] * cm.t[0] + cm.R[5] * cm.t[1] + cm.R[8] * cm.t[2]);
+        float dx = m.x - Cx, dy = m.y - Cy, dz = m.z - Cz;
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv; dy *= inv; dz *= inv;
+        float Y[16];
+        sh_basis16(dx, dy, dz, Y);
+        float r = 0.5f, gg = 0.5f, b = 0.5f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            r += Y[k] * c[k][0];
+            gg += Y[k] * c[k][1];
+            b += Y[k] * c[k][2];
+        }
+        w.color[(size_t)vs.vrec[v] + g] = make_float4(fmaxf(r, 0.f), fmaxf(gg, 0.f), fmaxf(b, 0.f), 0.f);
     }
-    rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(g, 0.f); rgb[2] = fmaxf(b, 0.f);
 }
 
 // grid (ceil(nmax/256), V): one thread per (view, Gaussian), Gaussian index fastest.
@@ -74,19 +99,6 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
         const int ox = min(max((int)floorf(ux.x + ux.y + dlt.x), 0), W - 1);
         const int oy = min(max((int)floorf(uy.x + uy.y + dlt.y), 0), H - 1);
         w.oref[i] = (uint32_t)oy * (uint32_t)W + (uint32_t)ox;
-    }
-    if (mode == 1) {
-        const DevCam& c = vs.cam[v];
-        // camera centre C = -R^T t; colour depends on the unit direction C -> mean
-        const float Cx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
-        const float Cy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
-        const float Cz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
-        float dx = m.x - Cx, dy = m.y - Cy, dz = m.z - Cz;
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv; dy *= inv; dz *= inv;
-        float rgb[3];
-        sh_colour(sh + (size_t)g * (sh_degree + 1) * (sh_degree + 1) * 3, sh_degree, dx, dy, dz, rgb);
-        w.color[i] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
     }
     const uint32_t base = vs.toff[v];
     const int tx_n = vs.tiles_x[v];
@@ -458,10 +470,12 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float* sh, int sh_degree,
 {
     if (vs.nmax == 0 || vs.V == 0) return cudaSuccess;
     dim3 grid((vs.nmax + 255) / 256, vs.V);
-    if (mode == 0)
+    if (mode == 0) {
         k_preprocess<0><<<grid, 256, 0, st>>>(vs, sh, sh_degree, w);
-    else
+    } else {
         k_preprocess<1><<<grid, 256, 0, st>>>(vs, sh, sh_degree, w);
+        k_colour<<<dim3((vs.nmax + 127) / 128, vs.F), 128, 0, st>>>(vs, sh, sh_degree, w);
+    }
     return cudaGetLastError();
 }
 

@@ -161,3 +161,25 @@ def test_autograd_function_chains_log_scales_and_logits(case):
     np.testing.assert_allclose(logits.grad.cpu().numpy(), g["means_opacity"][:, 3] * sig * (1 - sig),
                                rtol=1e-2, atol=1e-4)
     np.testing.assert_allclose(sh.grad.cpu().numpy(), g["sh"], rtol=1e-3, atol=1e-5)
+
+
+def test_backward_reuses_the_render_tile_lists(case):
+    """The adjoint right after the render (tile lists reused) equals the adjoint
+    after an intervening fit (tile lists rebuilt)."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s, W = case
+    mo, q, sc, sh = dev(s)
+    with tsp.Context(0) as ctx:
+        rgb, _ = ctx.render(mo, q, sc, sh, s.sh_degree, s, sync=True)
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        grad = [torch.randn(x.shape, generator=gen, device="cuda") for x in rgb]
+        g1 = ctx.render_backward(mo, q, sc, sh, s.sh_degree, s, rgb, grad, sync=True)
+        t = synth.make_scene("tiny", 3, n=300, views=2)
+        tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        ctx.fit_motion(tt(t.means_opacity), tt(t.quats), tt(t.scales), t, [tt(x) for x in t.disp],
+                       [tt(x) for x in t.vis], sync=True)
+        g2 = ctx.render_backward(mo, q, sc, sh, s.sh_degree, s, rgb, grad, sync=True)
+    for key in g1:
+        a, b = g1[key].cpu().numpy(), g2[key].cpu().numpy()
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * max(1e-30, np.abs(b).max()))
