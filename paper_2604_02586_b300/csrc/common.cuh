@@ -432,16 +432,24 @@ constexpr float kTMin = 1e-4f;
 // Colour-render blend of one (pixel, Gaussian): alpha = min(0.99, o 2^-p) with
 // p = z1^2 + z2^2 in the factor form of the staged record (tile-local mean g0.xy,
 // i11 = g0.z, k = g0.w, i22 = g1.x, opacity g1.y) at the tile-local pixel centre
-// (xc, yc), and the transmittance after it.  Every operation is spelled with a
-// correctly rounded intrinsic, so the forward render and its backward, which
-// recomputes the blend tile by tile, take bit-identical decisions.
+// (xc, yc), and the transmittance after it.  Every operation is a fixed
+// instruction (correctly rounded intrinsics and the SFU's 2^x, relative error
+// ~2^-22), so the forward render and its backward, which recomputes the blend tile
+// by tile, take bit-identical decisions.
+__device__ __forceinline__ float sfu_exp2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float render_alpha(float4 g0, float4 g1, float xc, float yc)
 {
     const float ex = __fsub_rn(xc, g0.x), ey = __fsub_rn(yc, g0.y);
     const float z1 = __fmul_rn(ex, g0.z);
     const float z2 = __fmul_rn(__fmaf_rn(-g0.w, ex, ey), g1.x);
     const float pw = __fmaf_rn(z2, z2, __fmul_rn(z1, z1));
-    return fminf(kAlphaMax, __fmul_rn(g1.y, exp2f(-pw)));
+    return fminf(kAlphaMax, __fmul_rn(g1.y, sfu_exp2_approx(-pw)));
 }
 
 // render_alpha that also returns G = exp2(-power) (the same operations, so alpha
@@ -452,7 +460,7 @@ __device__ __forceinline__ float render_alpha_g(float4 g0, float4 g1, float xc, 
     const float z1 = __fmul_rn(ex, g0.z);
     const float z2 = __fmul_rn(__fmaf_rn(-g0.w, ex, ey), g1.x);
     const float pw = __fmaf_rn(z2, z2, __fmul_rn(z1, z1));
-    G = exp2f(-pw);
+    G = sfu_exp2_approx(-pw);
     return fminf(kAlphaMax, __fmul_rn(g1.y, G));
 }
 
