@@ -192,28 +192,54 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
             const int j = __ffs(m) - 1;
             m &= m - 1;
             const float4 g0 = sm.g0[j], g1 = sm.g1[j], c = sm.c[j];
-            float hv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f};
-            bool add[2] = {false, false};
+            // render_alpha_g / render_transmit of the lane's two pixels in packed
+            // FP32x2 (each component the same correctly rounded operation)
+            const float ex = __fsub_rn(xc, g0.x);
+            const float z1 = __fmul_rn(ex, g0.z);
+            const float z1s = __fmul_rn(z1, z1);
+            const float2 ey = __fadd2_rn(make_float2(yc[0], yc[1]), make_float2(-g0.y, -g0.y));
+            const float2 t = __ffma2_rn(make_float2(-g0.w, -g0.w), make_float2(ex, ex), ey);
+            const float2 z2 = __fmul2_rn(t, make_float2(g1.x, g1.x));
+            const float2 pw = __ffma2_rn(z2, z2, make_float2(z1s, z1s));
+            const float2 G = make_float2(sfu_exp2_approx(-pw.x), sfu_exp2_approx(-pw.y));
+            const float2 oG = __fmul2_rn(make_float2(g1.y, g1.y), G);
+            const float2 al = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+            const float2 Tp = make_float2(T[0], T[1]);
+            const float2 om = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al.x, -al.y));
+            const float2 Tn = __fmul2_rn(Tp, om);
+            const float2 wp = __fmul2_rn(al, Tp);
+            bool add[2];
+            float wk[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (done[k]) continue;
-                float G;
-                const float alpha = render_alpha_g(g0, g1, xc, yc[k], G);
-                if (alpha < kAlphaMin) continue;
-                const float Tn = render_transmit(T[k], alpha);
-                if (Tn < kTMin) {
-                    done[k] = true;
-                    continue;
+                const float alpha = k ? al.y : al.x, tn = k ? Tn.y : Tn.x;
+                const bool pass = !done[k] && alpha >= kAlphaMin;
+                const bool term = pass && tn < kTMin;
+                add[k] = pass && !term;
+                wk[k] = add[k] ? (k ? wp.y : wp.x) : 0.f;
+                done[k] = done[k] || term;
+            }
+            // dL/dC . c, the running dL/dC . P (this Gaussian included) and dL/dalpha
+            const float2 w2 = make_float2(wk[0], wk[1]);
+            const float2 gcc = __ffma2_rn(make_float2(gc[0][0], gc[1][0]), make_float2(c.x, c.x),
+                                          __ffma2_rn(make_float2(gc[0][1], gc[1][1]), make_float2(c.y, c.y),
+                                                     __fmul2_rn(make_float2(gc[0][2], gc[1][2]),
+                                                                make_float2(c.z, c.z))));
+            const float2 Q2 = __ffma2_rn(w2, gcc, make_float2(Q[0], Q[1]));
+            float hv[2], wv[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float q = k ? Q2.y : Q2.x;
+                if (add[k]) {
+                    Q[k] = q;
+                    const float ga = fmaf(k ? gcc.y : gcc.x, T[k], -__fdividef(D[k] - q, k ? om.y : om.x));
+                    const float Gk = k ? G.y : G.x;
+                    hv[k] = (k ? oG.y : oG.x) < kAlphaMax ? ga * Gk : 0.f;   // alpha = o G, not clamped
+                    T[k] = k ? Tn.y : Tn.x;
+                } else {
+                    hv[k] = 0.f;
                 }
-                const float wgt = alpha * T[k];
-                const float gcc = fmaf(gc[k][0], c.x, fmaf(gc[k][1], c.y, gc[k][2] * c.z));   // dL/dC . c
-                Q[k] = fmaf(wgt, gcc, Q[k]);
-                // dL/dalpha = dL/dC . (c T - (C - P) / (1 - alpha)), P including this Gaussian
-                const float ga = fmaf(gcc, T[k], -__fdividef(D[k] - Q[k], 1.0f - alpha));
-                hv[k] = __fmul_rn(g1.y, G) < kAlphaMax ? ga * G : 0.f;           // alpha = o G, not clamped
-                wv[k] = wgt;
-                add[k] = true;
-                T[k] = Tn;
+                wv[k] = wk[k];
             }
             if (!__any_sync(kFull, add[0] || add[1])) continue;               // nothing of this block
 #pragma unroll

@@ -562,23 +562,39 @@ __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, c
             const int j = __ffs(m) - 1;
             m &= m - 1;
             const float4 g0 = sm.g0[j], g1 = sm.g1[j];
+            // render_alpha and render_transmit for the lane's two pixels in packed
+            // FP32x2: each component is the same correctly rounded operation, so
+            // the values (and the adjoint's recomputed decisions) are unchanged
+            const float ex = __fsub_rn(xc, g0.x);
+            const float z1 = __fmul_rn(ex, g0.z);
+            const float z1s = __fmul_rn(z1, z1);
+            const float2 ey = __fadd2_rn(make_float2(yc[0], yc[1]), make_float2(-g0.y, -g0.y));
+            const float2 t = __ffma2_rn(make_float2(-g0.w, -g0.w), make_float2(ex, ex), ey);
+            const float2 z2 = __fmul2_rn(t, make_float2(g1.x, g1.x));
+            const float2 pw = __ffma2_rn(z2, z2, make_float2(z1s, z1s));
+            const float2 oG = __fmul2_rn(make_float2(g1.y, g1.y),
+                                         make_float2(sfu_exp2_approx(-pw.x), sfu_exp2_approx(-pw.y)));
+            const float2 al = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+            const float2 Tp = make_float2(T[0], T[1]);
+            const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al.x, -al.y)));
+            const float2 wp = __fmul2_rn(al, Tp);
+            float wk[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (done[k]) continue;
-                const float alpha = render_alpha(g0, g1, xc, yc[k]);
-                if (alpha < kAlphaMin) continue;
-                const float Tn = render_transmit(T[k], alpha);
-                if (Tn < kTMin) {
-                    done[k] = true;
-                    continue;
-                }
-                const float wgt = alpha * T[k];
-                const float4 c = sm.c[j];
-                cr[k] = fmaf(wgt, c.x, cr[k]);
-                cg[k] = fmaf(wgt, c.y, cg[k]);
-                cb[k] = fmaf(wgt, c.z, cb[k]);
-                T[k] = Tn;
+                const float alpha = k ? al.y : al.x, tn = k ? Tn.y : Tn.x;
+                const bool pass = !done[k] && alpha >= kAlphaMin;
+                const bool term = pass && tn < kTMin;
+                const bool blend = pass && !term;
+                wk[k] = blend ? (k ? wp.y : wp.x) : 0.f;
+                T[k] = blend ? tn : T[k];
+                done[k] = done[k] || term;
             }
+            const float4 c = sm.c[j];
+            const float2 w2 = make_float2(wk[0], wk[1]);
+            const float2 r2 = __ffma2_rn(w2, make_float2(c.x, c.x), make_float2(cr[0], cr[1]));
+            const float2 g2 = __ffma2_rn(w2, make_float2(c.y, c.y), make_float2(cg[0], cg[1]));
+            const float2 b2 = __ffma2_rn(w2, make_float2(c.z, c.z), make_float2(cb[0], cb[1]));
+            cr[0] = r2.x; cr[1] = r2.y; cg[0] = g2.x; cg[1] = g2.y; cb[0] = b2.x; cb[1] = b2.y;
         }
         __syncwarp();                                  // staging is rewritten next
     }
