@@ -38,29 +38,6 @@ namespace {
 constexpr float kLn2 = 0.69314718055994531f;
 constexpr uint32_t kFull = 0xffffffffu;
 
-// Smallest value of p = z1^2 + z2^2 over the pixel-centre rectangle of a block
-// (the same test as the accumulate walk): 0 when the mean is inside.
-__device__ __forceinline__ float bwd_block_min_power(float4 g0, float i22, float bx0, float bx1, float by0, float by1)
-{
-    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
-    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
-    float pv = 3.0e38f, ph = 3.0e38f;
-    if (outx) {
-        const float e = ex0 > 0.f ? ex0 : ex1;
-        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
-        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
-        pv = fmaf(z1, z1, z2 * z2);
-    }
-    if (outy) {
-        const float f = ey0 > 0.f ? ey0 : ey1;
-        const float i22s = i22 * i22;
-        const float a = fmaf(g0.z, g0.z, g0.w * g0.w * i22s);
-        const float ex = fminf(fmaxf(g0.w * i22s * f / a, ex0), ex1);
-        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
-        ph = fmaf(z1, z1, z2 * z2);
-    }
-    return (outx || outy) ? fminf(pv, ph) : 0.f;
-}
 
 constexpr int kBChunk = 8;                       // pending hits per phase 2
 constexpr int kBRow = 2 * kBChunk + 2;           // words per pixel: (h, w) per hit, padded
@@ -178,7 +155,7 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
             const float4 bb = footprint_box(g0, g1);
             hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
             if (hit)
-                hit = bwd_block_min_power(g0, g1.x, bx0, bx1, by0, by1) <= log2f(255.0f * g1.y) * 1.002f + 1e-4f;
+                hit = block_min_power(g0, g1.x, bx0, bx1, by0, by1) <= log2f(255.0f * g1.y) * 1.002f + 1e-4f;
             if (hit) {
                 sm.g0[lane] = g0;
                 sm.g1[lane] = g1;

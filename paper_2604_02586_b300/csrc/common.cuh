@@ -464,6 +464,36 @@ __device__ __forceinline__ float render_alpha_g(float4 g0, float4 g1, float xc, 
     return fminf(kAlphaMax, __fmul_rn(g1.y, G));
 }
 
+// Smallest value of p = z1^2 + z2^2 (z1 = ex i11, z2 = (ey - k ex) i22) over the
+// pixel-centre rectangle [bx0, bx1] x [by0, by1] of a warp block, for the
+// tile-local mean (g0.x, g0.y) and factor (i11, k, i22) = (g0.z, g0.w, i22).
+// p is convex, so when the mean lies outside the rectangle the minimum sits on
+// an edge facing the mean: along a vertical edge ex = e it is at ey = k e, along
+// a horizontal edge ey = f at ex = k i22^2 f / (i11^2 + k^2 i22^2), each clamped
+// to the edge.  Returns 0 when the mean is inside.
+__device__ __forceinline__ float block_min_power(float4 g0, float i22, float bx0, float bx1,
+                                                 float by0, float by1)
+{
+    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
+    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
+    float pv = 3.0e38f, ph = 3.0e38f;
+    if (outx) {
+        const float e = ex0 > 0.f ? ex0 : ex1;
+        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
+        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
+        pv = fmaf(z1, z1, z2 * z2);
+    }
+    if (outy) {
+        const float f = ey0 > 0.f ? ey0 : ey1;
+        const float i22s = i22 * i22;
+        const float a = fmaf(g0.z, g0.z, g0.w * g0.w * i22s);
+        const float ex = fminf(fmaxf(g0.w * i22s * f / a, ex0), ex1);
+        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
+        ph = fmaf(z1, z1, z2 * z2);
+    }
+    return (outx || outy) ? fminf(pv, ph) : 0.f;
+}
+
 __device__ __forceinline__ float render_transmit(float T, float alpha)
 {
     return __fmul_rn(T, __fsub_rn(1.0f, alpha));

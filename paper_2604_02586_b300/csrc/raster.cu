@@ -1,4 +1,4 @@
-// raster.cu -- a5 raster-accumulate (Sec. 4.3.5) and the colour render (Sec. 3.1).
+// raster.cu -- a5 raster-accumulate (Sec. 4.3.5).
 //
 // One CTA per 16x16 tile.  The tile's depth-sorted list is walked in batches of
 // kBatch Gaussians whose blend parameters are staged in shared memory together
@@ -220,35 +220,6 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
     }
 }
 
-// Smallest value of p = z1^2 + z2^2 (z1 = ex i11, z2 = (ey - k ex) i22) over the
-// pixel-centre rectangle [bx0, bx1] x [by0, by1] of a warp block, for the
-// tile-local mean (g0.x, g0.y) and factor (i11, k, i22) = (g0.z, g0.w, i22).
-// p is convex, so when the mean lies outside the rectangle the minimum sits on
-// an edge facing the mean: along a vertical edge ex = e it is at ey = k e, along
-// a horizontal edge ey = f at ex = k i22^2 f / (i11^2 + k^2 i22^2), each clamped
-// to the edge.  Returns 0 when the mean is inside.
-__device__ __forceinline__ float block_min_power(float4 g0, float i22, float bx0, float bx1,
-                                                 float by0, float by1)
-{
-    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
-    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
-    float pv = 3.0e38f, ph = 3.0e38f;
-    if (outx) {
-        const float e = ex0 > 0.f ? ex0 : ex1;
-        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
-        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
-        pv = fmaf(z1, z1, z2 * z2);
-    }
-    if (outy) {
-        const float f = ey0 > 0.f ? ey0 : ey1;
-        const float i22s = i22 * i22;
-        const float a = fmaf(g0.z, g0.z, g0.w * g0.w * i22s);
-        const float ex = fminf(fmaxf(g0.w * i22s * f / a, ex0), ex1);
-        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
-        ph = fmaf(z1, z1, z2 * z2);
-    }
-    return (outx || outy) ? fminf(pv, ph) : 0.f;
-}
 
 // Two-phase accumulate (the default).  Warp w owns the 8x8 block (w & 1, w >> 1)
 // of the tile, lane l the pixels (l & 7, (l >> 3) + 4h), h = 0, 1, and walks the
@@ -499,122 +470,6 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(cons
     }
 }
 
-// Colour render (Sec. 3.1), one 128-thread CTA per tile: warp w walks the tile's
-// depth-ordered list for its 8x8 block (w & 1, w >> 1) on its own, lane l owning
-// pixels (l & 7, (l >> 3) + 4k), k = 0, 1.  Entries are culled per block as in the
-// accumulate walk (an entry whose alpha >= 1/255 ellipse misses every pixel centre
-// of the block cannot change any of them), so each pixel sees the same Gaussians in
-// the same order with the same arithmetic (render_alpha, render_transmit) as a
-// pixel-by-pixel walk of the whole list, which the adjoint recomputes.
-struct RenderSmem {
-    float4 g0[32];
-    float4 g1[32];
-    float4 c[32];
-};
-
-__device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, const RenderOut& ro, uint32_t tile,
-                                             int blk, RenderSmem& sm)
-{
-    const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
-    int v, tx, ty;
-    view_of_tile(vs, tile, v, tx, ty);
-    const int lane = threadIdx.x & 31;
-    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
-    const int W = vs.cam[v].W, H = vs.cam[v].H;
-    const size_t vbase = (size_t)vs.vrec[v];
-    const float xc = (float)(bxo + (lane & 7)) + 0.5f;
-    float yc[2], T[2], cr[2], cg[2], cb[2];
-    bool done[2], inside[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int ly = byo + (lane >> 3) + 4 * k;
-        inside[k] = tx * kTile + bxo + (lane & 7) < W && ty * kTile + ly < H;
-        yc[k] = (float)ly + 0.5f;
-        T[k] = 1.0f;
-        cr[k] = cg[k] = cb[k] = 0.f;
-        done[k] = !inside[k];
-    }
-    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
-    uint32_t g_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
-    for (uint32_t b0 = beg; b0 < end; b0 += 32) {
-        if (!__any_sync(kFull, !done[0] || !done[1])) break;
-        bool hit = false;
-        const uint32_t g = g_next;
-        if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
-        if (b0 + lane < end) {
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
-            const float4 g1 = w.geom1[vbase + g];
-            const float4 bb = footprint_box(g0, g1);
-            hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
-            if (hit)
-                hit = block_min_power(g0, g1.x, bx0, bx1, by0, by1) <=
-                      log2f(255.0f * g1.y) * 1.002f + 1e-4f;
-            if (hit) {
-                sm.g0[lane] = g0;
-                sm.g1[lane] = g1;
-                sm.c[lane] = w.color[vbase + g];
-            }
-        }
-        uint32_t m = __ballot_sync(kFull, hit);
-        __syncwarp();
-        while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1;
-            const float4 g0 = sm.g0[j], g1 = sm.g1[j];
-            // render_alpha and render_transmit for the lane's two pixels in packed
-            // FP32x2: each component is the same correctly rounded operation, so
-            // the values (and the adjoint's recomputed decisions) are unchanged
-            const float ex = __fsub_rn(xc, g0.x);
-            const float z1 = __fmul_rn(ex, g0.z);
-            const float z1s = __fmul_rn(z1, z1);
-            const float2 ey = __fadd2_rn(make_float2(yc[0], yc[1]), make_float2(-g0.y, -g0.y));
-            const float2 t = __ffma2_rn(make_float2(-g0.w, -g0.w), make_float2(ex, ex), ey);
-            const float2 z2 = __fmul2_rn(t, make_float2(g1.x, g1.x));
-            const float2 pw = __ffma2_rn(z2, z2, make_float2(z1s, z1s));
-            const float2 oG = __fmul2_rn(make_float2(g1.y, g1.y),
-                                         make_float2(sfu_exp2_approx(-pw.x), sfu_exp2_approx(-pw.y)));
-            const float2 al = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
-            const float2 Tp = make_float2(T[0], T[1]);
-            const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al.x, -al.y)));
-            const float2 wp = __fmul2_rn(al, Tp);
-            float wk[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float alpha = k ? al.y : al.x, tn = k ? Tn.y : Tn.x;
-                const bool pass = !done[k] && alpha >= kAlphaMin;
-                const bool term = pass && tn < kTMin;
-                const bool blend = pass && !term;
-                wk[k] = blend ? (k ? wp.y : wp.x) : 0.f;
-                T[k] = blend ? tn : T[k];
-                done[k] = done[k] || term;
-            }
-            const float4 c = sm.c[j];
-            const float2 w2 = make_float2(wk[0], wk[1]);
-            const float2 r2 = __ffma2_rn(w2, make_float2(c.x, c.x), make_float2(cr[0], cr[1]));
-            const float2 g2 = __ffma2_rn(w2, make_float2(c.y, c.y), make_float2(cg[0], cg[1]));
-            const float2 b2 = __ffma2_rn(w2, make_float2(c.z, c.z), make_float2(cb[0], cb[1]));
-            cr[0] = r2.x; cr[1] = r2.y; cg[0] = g2.x; cg[1] = g2.y; cb[0] = b2.x; cb[1] = b2.y;
-        }
-        __syncwarp();                                  // staging is rewritten next
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (!inside[k]) continue;
-        const size_t pix = (size_t)(ty * kTile + byo + (lane >> 3) + 4 * k) * W + (tx * kTile + bxo + (lane & 7));
-        float* o = ro.rgb[v] + 3 * pix;
-        o[0] = cr[k]; o[1] = cg[k]; o[2] = cb[k];
-        ro.T[v][pix] = T[k];
-    }
-}
-
-__global__ void __launch_bounds__(128) k_raster_render(const ViewSet vs, const Work w, const RenderOut ro)
-{
-    __shared__ RenderSmem sm[4];
-    const int warp = threadIdx.x >> 5;
-    render_block(vs, w, ro, blockIdx.x, warp, sm[warp]);
-}
-
 }  // namespace
 
 cudaError_t raster_prepare()
@@ -671,14 +526,5 @@ int raster_resident_ctas(int device)
     return std::max(1, sms * std::max(1, per_sm));
 }
 
-cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, float* const* rgb,
-                                 float* const* final_T, cudaStream_t st)
-{
-    if (NT == 0) return cudaSuccess;
-    RenderOut ro;
-    for (int v = 0; v < vs.V; ++v) { ro.rgb[v] = rgb[v]; ro.T[v] = final_T[v]; }
-    k_raster_render<<<NT, 128, 0, st>>>(vs, w, ro);
-    return cudaGetLastError();
-}
 
 }  // namespace tsp
