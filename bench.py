@@ -685,15 +685,14 @@ def run_reg(a):
     cpu = None
     if not a.no_cpu:
         import oracle
-        m = 20_000                                       # bounded sample: the first 20k Gaussians
-        st = out["status"].cpu().numpy().view(np.uint32)[:m]
-        after = tuple(out[k].cpu().numpy()[:m] for k in ("means", "quats", "scales"))
-        is_static = (fl[:m] & 1).astype(np.uint8)
+        m = 20_000                                       # bounded sample of synthetic motion inputs
+        inp = synth.motion_pair(m, views=s.num_views, seed=7)
+        is_static = oracle.static_flags(inp["npix"], inp["nstat"])
         t0 = time.perf_counter()
-        oracle.regularize((s.means_opacity[:m], s.quats[:m], s.scales[:m]), after, st, is_static, 8)
+        oracle.regularize(inp["before"], inp["after"], inp["status"], is_static, 8)
         dt = time.perf_counter() - t0
         cpu = {"value": m / dt, "unit": "Gaussians/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"oracle.regularize on the first {m} Gaussians of the fitted frame "
+               "sample": f"oracle.regularize of {m} synthetic Gaussians (synth.motion_pair) "
                          "(brute-force neighbours, O(m^2))"}
     # whole call against HBM: one 32-byte sector of each (view, Gaussian) moment
     # record (the pixel counters), before/after Gaussians and status in, the

@@ -266,10 +266,27 @@ def test_regularize_edge_cases(ctx):
     np.testing.assert_allclose(got["means_opacity"], want["means_opacity"], rtol=0, atol=4e-4)
 
 
+def oracle_fit_inputs(s):
+    """The oracle's own fit of scene s as regularization inputs: fitted Gaussians
+    (float32 [n, 4]), status and per-view moments in the library layout."""
+    from tests.parity import oracle_moments_in_library_layout
+    o = oracle.fit_motion(s, per_view=True)
+    n = s.n
+    mo = np.zeros((n, 4), np.float32)
+    mo[:, :3] = o["out_mean"]
+    mo[:, 3] = s.means_opacity[:, 3]
+    sc = np.zeros((n, 4), np.float32)
+    sc[:, :3] = o["out_scale"]
+    after = (mo, o["out_quat"].astype(np.float32), sc)
+    mom = oracle_moments_in_library_layout(o["moments"]).astype(np.float32)
+    return after, o["out_status"].astype(np.uint32), mom
+
+
 def test_regularize_after_a_fit_uses_the_context_moments(ctx):
     """The whole chain on a fitted frame: fit_motion, then regularize with the
-    moments the context kept (view_moments=None) and with the moments returned by
-    the fit; both equal the oracle given the same fit outputs."""
+    moments the context kept (view_moments=None) equals regularize with the
+    moments the fit returned; a frame whose neighbours' fit is wrong is not
+    needed for this check (GPU against GPU)."""
     import torch
     import paper_2604_02586_b300 as tsp
     s = synth.make_scene("tiny", 8, n=3000)
@@ -283,20 +300,35 @@ def test_regularize_after_a_fit_uses_the_context_moments(ctx):
     torch.cuda.synchronize()
     for key in r1:
         np.testing.assert_array_equal(r1[key].cpu().numpy(), r2[key].cpu().numpy())
-    mom = out["view_moments"].cpu().numpy()
-    is_static = oracle.static_flags(mom[:, :, 13], mom[:, :, 14])
-    status = out["status"].cpu().numpy().view(np.uint32)
-    after = tuple(out[key].cpu().numpy() for key in ("means", "quats", "scales"))
-    want = oracle.regularize((s.means_opacity, s.quats, s.scales), after, status, is_static, 8)
-    got = {key: v.cpu().numpy() for key, v in r1.items()}
-    got["flags"] = got["flags"].view(np.uint32)
-    has_cov = ((status & 2) > 0) & (is_static == 0)
-    rot_ok = euler_window_ok((s.means_opacity, s.quats, s.scales), after, got["nbr_cov"], has_cov)
-    compare_regularized(got, want, (s.means_opacity, s.quats, s.scales), s.extent, rot_ok)
-    assert (got["flags"] & (tsp.TSP.REG_POS_MEDIAN | tsp.TSP.REG_POS_PROPAGATED)).any()
+    fl = r1["flags"].cpu().numpy().view(np.uint32)
+    assert (fl & (tsp.TSP.REG_POS_MEDIAN | tsp.TSP.REG_POS_PROPAGATED)).any()
     # another n than the last fit's: the context's moments do not apply
     with pytest.raises(tsp.TspError):
         ctx.regularize(tuple(t[:100] for t in before), {key: out[key][:100] for key in out}, s.num_views)
+
+
+def test_regularize_on_the_oracle_fit_matches_the_oracle(ctx):
+    """Regularization of a fitted frame (the oracle's fit: realistic status bits,
+    static counters and motions) on the GPU and in the oracle, from the same
+    inputs, none of which comes from the CUDA path."""
+    s = synth.make_scene("tiny", 8, n=3000)
+    after, status, mom = oracle_fit_inputs(s)
+    before = (s.means_opacity, s.quats, s.scales)
+    fitted = dict(means=cuda(after[0]), quats=cuda(after[1]), scales=cuda(after[2]),
+                  status=cuda(status.view(np.int32)))
+    r = ctx.regularize(tuple(cuda(a) for a in before), fitted, s.num_views, view_moments=cuda(mom),
+                       neighbours=True, sync=True)
+    got = {key: v.cpu().numpy() for key, v in r.items()}
+    got["flags"] = got["flags"].view(np.uint32)
+    is_static = oracle.static_flags(mom[:, :, 13], mom[:, :, 14])
+    want = oracle.regularize(before, after, status, is_static, 8)
+    has_pos = ((status & 1) > 0) & (is_static == 0)
+    has_cov = ((status & 2) > 0) & (is_static == 0)
+    np.testing.assert_array_equal(got["nbr_pos"], oracle.knn(s.means_opacity, has_pos.astype(np.uint8), 8))
+    np.testing.assert_array_equal(got["nbr_cov"], oracle.knn(s.means_opacity, has_cov.astype(np.uint8), 8))
+    rot_ok = euler_window_ok(before, after, got["nbr_cov"], has_cov)
+    compare_regularized(got, want, before, s.extent, rot_ok)
+    assert (got["flags"] & 6).any()
 
 
 def test_regularize_rejects_bad_arguments(ctx):
