@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // their (record, tile) items: a warp scan of the tile counts numbers the items,
 // lane l takes items l, l + 32, ..., finds the owning record as the last lane
 // whose exclusive count is <= the item (a 5-step shuffle search), and 8 items per
-// lane have their slot atomics in flight before any result is used.  Lanes stay
+// lane have their slot atomics (and their lists' start offsets) in flight before
+// any result is used.  Lanes stay
 // busy whatever the mix of culled, small and large records.
 __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
 {
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
     const uint32_t base = vs.toff[v];
     const int tx_n = vs.tiles_x[v];
     for (uint32_t it0 = 0; it0 < total; it0 += 32 * kIlp) {
-        uint32_t t[kIlp], slot[kIlp], k0[kIlp], k1[kIlp];
+        uint32_t toff[kIlp], slot[kIlp], k0[kIlp], k1[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const uint32_t item = it0 + (uint32_t)(u * 32 + lane);
@@ -275,13 +276,17 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
             k1[u] = __shfl_sync(0xffffffffu, khi, own);
             const uint32_t x0 = xy & 0xffffu, y0 = xy >> 16, rw = (zw & 0xffffu) - x0;
             const uint32_t dy = rw ? off / rw : 0u, dx = off - dy * rw;
-            t[u] = base + (y0 + dy) * (uint32_t)tx_n + x0 + dx;
-            if (item < total) slot[u] = atomicAdd(&w.tile_fill[(size_t)t[u] * kCounterStride], 1u);
+            const uint32_t t = base + (y0 + dy) * (uint32_t)tx_n + x0 + dx;
+            // the list's start is fetched while the slot atomic is in flight
+            if (item < total) {
+                slot[u] = atomicAdd(&w.tile_fill[(size_t)t * kCounterStride], 1u);
+                toff[u] = w.tile_off[t];
+            }
         }
 #pragma unroll
         for (int u = 0; u < kIlp; ++u)
             if (it0 + (uint32_t)(u * 32 + lane) < total) {
-                const uint64_t pos = (uint64_t)w.tile_off[t[u]] + slot[u];
+                const uint64_t pos = (uint64_t)toff[u] + slot[u];
                 if (pos < w.cap) w.pairs[pos] = ((uint64_t)k1[u] << 32) | k0[u];
             }
     }
@@ -318,10 +323,12 @@ __device__ void smem_sort(uint64_t* src, uint32_t n, uint64_t* s)
 
 // One warp per tile list of 2 <= n <= 32 * KPL keys, bitonic-sorted in registers:
 // lane l holds list positions l * KPL + i, i < KPL, padded with ~0 (keys are
-// unique and never ~0).  Exchanges across a stride j < KPL stay inside a lane;
-// strides j >= KPL pair lane l with lane l ^ (j / KPL) through a shuffle.  The
-// direction of a comparator is set by bit k of the position (ascending where it
-// is 0), which is a bit of i for k < KPL and a bit of the lane otherwise.
+// unique and never ~0).  The network is the bitonic sort in its "flip" form: the
+// merge of two sorted runs into one of size k starts by comparing position p
+// with its mirror p ^ (k - 1), and every later stage compares p with p ^ j
+// (j = k/4, ..., 1); all comparators put the smaller key at the lower position,
+// so no stage needs a direction.  Strides below KPL stay inside a lane (fixed
+// register pairs); larger ones pair lane l with lane l ^ m through shuffles.
 constexpr int kWarpSortMax = 512;
 
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
@@ -331,26 +338,55 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
     return ((uint64_t)hi << 32) | lo;
 }
 
-// In-register comparators of stride J < KPL for merge size k (k is known only at
-// run time; the stride is a template argument so the partners stay registers).
+// a gets the smaller key, b the larger
+__device__ __forceinline__ void cmp_swap(uint64_t& a, uint64_t& b)
+{
+    const bool sw = b < a;
+    const uint64_t lo = sw ? b : a, hi = sw ? a : b;
+    a = lo;
+    b = hi;
+}
+
+// The key this lane keeps of the pair (own x, partner's y): the smaller one at
+// the lower position of the pair, the larger one at the upper.
+__device__ __forceinline__ uint64_t keep(uint64_t x, uint64_t y, bool lower)
+{
+    return ((y < x) == lower) ? y : x;
+}
+
+// In-lane stage of stride J: pairs (i, i + J) for the i with bit J clear.
 template <int KPL, int J>
-__device__ __forceinline__ void inreg_stage(uint64_t (&x)[KPL], int k, int lane)
+__device__ __forceinline__ void lane_stage(uint64_t (&x)[KPL])
 {
 #pragma unroll
-    for (int i = 0; i < KPL; ++i) {
-        const int p = i ^ J;
-        if (p > i && p < KPL) {
-            const bool up = k >= KPL ? (lane & (k / KPL)) == 0 : (i & k) == 0;
-            const uint64_t a = x[i], b = x[p];
-            const bool sw = (a > b) == up;
-            x[i] = sw ? b : a;
-            x[p] = sw ? a : b;
-        }
+    for (int i = 0; i < KPL; ++i)
+        if ((i & J) == 0) cmp_swap(x[i], x[i ^ J]);
+}
+
+// In-lane stages of strides J, J/2, ..., 1.
+template <int KPL, int J>
+__device__ __forceinline__ void lane_stages(uint64_t (&x)[KPL])
+{
+    if constexpr (J >= 1) {
+        lane_stage<KPL, J>(x);
+        lane_stages<KPL, J / 2>(x);
     }
 }
 
-// The stage loops stay rolled: a fully unrolled network of every list size does
-// not fit the instruction cache once warps of one SM sort lists of different sizes.
+// Sorts each lane's KPL keys: merges of size K = 2, 4, ..., KPL, each a mirror
+// stage followed by strides K/4, ..., 1.
+template <int KPL, int K>
+__device__ __forceinline__ void lane_sort(uint64_t (&x)[KPL])
+{
+    if constexpr (K <= KPL) {
+#pragma unroll
+        for (int i = 0; i < KPL; ++i)
+            if ((i & (K / 2)) == 0) cmp_swap(x[i], x[i ^ (K - 1)]);
+        lane_stages<KPL, K / 4>(x);
+        lane_sort<KPL, 2 * K>(x);
+    }
+}
+
 template <int KPL>
 __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint32_t n, int lane)
 {
@@ -360,29 +396,31 @@ __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint
         const uint32_t e = (uint32_t)(lane * KPL + i);
         x[i] = e < n ? keys[e] : ~0ull;
     }
+    lane_sort<KPL, 2>(x);
+    // merges across lanes stay rolled: unrolling every list size overflows the
+    // instruction cache once warps of one SM sort lists of different sizes
 #pragma unroll 1
-    for (int k = 2; k <= 32 * KPL; k <<= 1) {
-#pragma unroll 1
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= KPL) {
-                const int lj = j / KPL;
-                const bool up = (lane & (k / KPL)) == 0;       // k > j >= KPL
-                const bool take_min = up == ((lane & lj) == 0);
+    for (int kl = 2; kl <= 32; kl <<= 1) {         // merged run = kl lanes
+        {
+            // mirror stage: lane l with l ^ (kl - 1), element i with KPL - 1 - i
+            const int m = kl - 1;
+            const bool lower = (lane & (kl >> 1)) == 0;
 #pragma unroll
-                for (int i = 0; i < KPL; ++i) {
-                    const uint64_t y = shfl_xor_u64(x[i], lj);
-                    x[i] = take_min ? (y < x[i] ? y : x[i]) : (y > x[i] ? y : x[i]);
-                }
-            } else if (KPL >= 16 && j == 8) {
-                inreg_stage<KPL, (KPL >= 16 ? 8 : 1)>(x, k, lane);
-            } else if (KPL >= 8 && j == 4) {
-                inreg_stage<KPL, (KPL >= 8 ? 4 : 1)>(x, k, lane);
-            } else if (KPL >= 4 && j == 2) {
-                inreg_stage<KPL, (KPL >= 4 ? 2 : 1)>(x, k, lane);
-            } else {
-                inreg_stage<KPL, 1>(x, k, lane);
+            for (int i = 0; i < KPL / 2; ++i) {
+                const uint64_t ya = shfl_xor_u64(x[KPL - 1 - i], m);
+                const uint64_t yb = shfl_xor_u64(x[i], m);
+                x[i] = keep(x[i], ya, lower);
+                x[KPL - 1 - i] = keep(x[KPL - 1 - i], yb, lower);
             }
+            if constexpr (KPL == 1) x[0] = keep(x[0], shfl_xor_u64(x[0], m), lower);
         }
+#pragma unroll 1
+        for (int jl = kl >> 2; jl >= 1; jl >>= 1) {
+            const bool lower = (lane & jl) == 0;
+#pragma unroll
+            for (int i = 0; i < KPL; ++i) x[i] = keep(x[i], shfl_xor_u64(x[i], jl), lower);
+        }
+        lane_stages<KPL, KPL / 2>(x);
     }
 #pragma unroll
     for (int i = 0; i < KPL; ++i) {

@@ -465,14 +465,48 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
     float4* __restrict__ os = fo.scales[f];
     uint32_t* __restrict__ ost = fo.status[f];
     const float4 m = vs.fmo[f][g], qi = vs.fq[f][g], si = vs.fs[f][g];
+
+    // One pass over the views gathers the view counts (status) and a7's normal
+    // equations about the old mean.  The records of kChunkA views are loaded
+    // before any of them is used, whatever their flags (every record of the
+    // frame exists), so the pass pays one memory latency per chunk, not two per
+    // view; sums are still taken in view order.
+    constexpr int kChunkA = 6;
     int nv = 0;
     float sw = 0.f, npx = 0.f;
-    for (int v = v0; v < v1; ++v) {
-        const uint2 f = w.vres2[(size_t)vs.vrec[v] + g];
-        if (f.x & TSP_VIEW_OK) {
+    float N00 = 0.f, N01 = 0.f, N02 = 0.f, N11 = 0.f, N12 = 0.f, N22 = 0.f;
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+    for (int vb = v0; vb < v1; vb += kChunkA) {
+        uint2 fl[kChunkA];
+        float swv[kChunkA];
+        float4 a[kChunkA];
+#pragma unroll
+        for (int u = 0; u < kChunkA; ++u) {
+            fl[u] = make_uint2(0u, 0u);
+            swv[u] = 0.f;
+            a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (vb + u < v1) {
+                const size_t i = (size_t)vs.vrec[vb + u] + g;
+                fl[u] = w.vres2[i];
+                swv[u] = w.vres1[i].w;
+                a[u] = w.vres0[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kChunkA; ++u) {
+            if (!(fl[u].x & TSP_VIEW_OK)) continue;      // also every slot past v1
+            const DevCam& c = vs.cam[vb + u];
             ++nv;
-            sw += w.vres1[(size_t)vs.vrec[v] + g].w;
-            npx += (float)f.y;
+            sw += swv[u];
+            npx += (float)fl[u].y;
+            const float zmu = c.R[6] * m.x + c.R[7] * m.y + c.R[8] * m.z + c.t[2];
+            const float du = a[u].x - c.cx, dv = a[u].y - c.cy;
+            const float ax = du * c.R[6] - c.fx * c.R[0], ay = du * c.R[7] - c.fx * c.R[1], az = du * c.R[8] - c.fx * c.R[2];
+            const float bx = dv * c.R[6] - c.fy * c.R[3], by = dv * c.R[7] - c.fy * c.R[4], bz = dv * c.R[8] - c.fy * c.R[5];
+            const float ra = -zmu * a[u].z, rb = -zmu * a[u].w;
+            N00 += ax * ax + bx * bx; N01 += ax * ay + bx * by; N02 += ax * az + bx * bz;
+            N11 += ay * ay + by * by; N12 += ay * az + by * bz; N22 += az * az + bz * bz;
+            r0 += ax * ra + bx * rb; r1 += ay * ra + by * rb; r2 += az * ra + bz * rb;
         }
     }
     uint32_t st = (uint32_t)min(nv, 255) << 16;
@@ -486,22 +520,6 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
     }
 
     // ---- a7 triangulation about the old mean
-    float N00 = 0.f, N01 = 0.f, N02 = 0.f, N11 = 0.f, N12 = 0.f, N22 = 0.f;
-    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-    for (int v = v0; v < v1; ++v) {
-        const size_t i = (size_t)vs.vrec[v] + g;
-        if (!(w.vres2[i].x & TSP_VIEW_OK)) continue;
-        const DevCam& c = vs.cam[v];
-        const float4 a = w.vres0[i];
-        const float zmu = c.R[6] * m.x + c.R[7] * m.y + c.R[8] * m.z + c.t[2];
-        const float du = a.x - c.cx, dv = a.y - c.cy;
-        const float ax = du * c.R[6] - c.fx * c.R[0], ay = du * c.R[7] - c.fx * c.R[1], az = du * c.R[8] - c.fx * c.R[2];
-        const float bx = dv * c.R[6] - c.fy * c.R[3], by = dv * c.R[7] - c.fy * c.R[4], bz = dv * c.R[8] - c.fy * c.R[5];
-        const float ra = -zmu * a.z, rb = -zmu * a.w;
-        N00 += ax * ax + bx * bx; N01 += ax * ay + bx * by; N02 += ax * az + bx * bz;
-        N11 += ay * ay + by * by; N12 += ay * az + by * bz; N22 += az * az + bz * bz;
-        r0 += ax * ra + bx * rb; r1 += ay * ra + by * rb; r2 += az * ra + bz * rb;
-    }
     df Nt[3][3] = {{df_of(N00), df_of(N01), df_of(N02)},
                    {df_of(N01), df_of(N11), df_of(N12)},
                    {df_of(N02), df_of(N12), df_of(N22)}};
@@ -527,9 +545,19 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
     for (int u = 0; u < 21; ++u) { Ah[u] = 0.f; Al[u] = 0.f; }
 #pragma unroll
     for (int u = 0; u < 6; ++u) { bh[u] = 0.f; bl[u] = 0.f; }
+    // the next view's records are loaded while this view's equations are added
+    uint32_t fl_n = w.vres2[(size_t)vs.vrec[v0] + g].x;
+    float4 b0_n = w.vres1[(size_t)vs.vrec[v0] + g], b1_n = w.vres3[(size_t)vs.vrec[v0] + g];
     for (int v = v0; v < v1; ++v) {
-        const size_t i = (size_t)vs.vrec[v] + g;
-        if (!(w.vres2[i].x & TSP_VIEW_OK)) continue;
+        const uint32_t flv = fl_n;
+        const float4 b0v = b0_n, b1v = b1_n;
+        if (v + 1 < v1) {
+            const size_t i1 = (size_t)vs.vrec[v + 1] + g;
+            fl_n = w.vres2[i1].x;
+            b0_n = w.vres1[i1];
+            b1_n = w.vres3[i1];
+        }
+        if (!(flv & TSP_VIEW_OK)) continue;
         const DevCam& c = vs.cam[v];
         const float p0 = fmaf(c.R[0], X0, fmaf(c.R[1], X1, fmaf(c.R[2], X2, c.t[0])));
         const float p1 = fmaf(c.R[3], X0, fmaf(c.R[4], X1, fmaf(c.R[5], X2, c.t[1])));
@@ -543,7 +571,6 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
             T[0][k] = fmaf(j00, c.R[k], j02 * c.R[6 + k]);
             T[1][k] = fmaf(j11, c.R[3 + k], j12 * c.R[6 + k]);
         }
-        const float4 b0v = w.vres1[i], b1v = w.vres3[i];
         const float rhs[3] = {fmaf(b0v.x, b0v.x, fmaf(b0v.y, b0v.y, b0v.z * b0v.z)),
                               fmaf(b0v.x, b1v.x, fmaf(b0v.y, b1v.y, b0v.z * b1v.z)),
                               fmaf(b1v.x, b1v.x, fmaf(b1v.y, b1v.y, b1v.z * b1v.z))};
