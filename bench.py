@@ -258,13 +258,14 @@ def run_ours(a):
     vis = [t(v) for v in scene.vis]
 
     # size the pair buffer once (synchronous call), then run asynchronously
+    cams = tsp.cameras(scene)            # built once, as a serving loop would
     probe = tsp.Context(local)
-    out = probe.fit_motion(mo, q, s, scene, disp, vis, sync=True)
+    out = probe.fit_motion(mo, q, s, cams, disp, vis, sync=True)
     K = int(probe.inspect(tsp.TSP.I_COUNTS)[0])
     probe.close()
     # exact raster work for the ALU roofline (counting variant, untimed)
     cnt = tsp.Context(local, collect_stats=1, async_pairs=1, pair_capacity=int(K * 1.1) + 1024)
-    cnt.fit_motion(mo, q, s, scene, disp, vis, out=out, sync=True)
+    cnt.fit_motion(mo, q, s, cams, disp, vis, out=out, sync=True)
     n_eval, n_blend, n_add, n_list = [int(x) for x in cnt.inspect(tsp.TSP.I_STATS)]
     cnt.close()
 
@@ -272,7 +273,7 @@ def run_ours(a):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(a.warmup):
-        ctx.fit_motion(mo, q, s, scene, disp, vis, out=out)
+        ctx.fit_motion(mo, q, s, cams, disp, vis, out=out)
     ctx.sync()
     step_ms, raster_ms, stages = [], [], []
     if world > 1:
@@ -284,7 +285,7 @@ def run_ours(a):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.fit_motion(mo, q, s, scene, disp, vis, out=out)
+            ctx.fit_motion(mo, q, s, cams, disp, vis, out=out)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -310,11 +311,11 @@ def run_ours(a):
                  ("scales", (scene.n, 4), torch.float32), ("status", (scene.n,), torch.int32))}
         hout["status"] = hout["status"].view(np.uint32)
         for _ in range(2):
-            ctx.fit_motion_host(hmo, hq, hs, scene, hd, hv, out=hout)
+            ctx.fit_motion_host(hmo, hq, hs, cams, hd, hv, out=hout)
         ts = []
         for _ in range(max(3, a.steps // 2)):
             t0 = time.perf_counter()
-            ctx.fit_motion_host(hmo, hq, hs, scene, hd, hv, out=hout)
+            ctx.fit_motion_host(hmo, hq, hs, cams, hd, hv, out=hout)
             ts.append(time.perf_counter() - t0)
         h2d = 3 * 16 * scene.n + sum(int(d.nbytes) + int(v.nbytes) for d, v in zip(hd, hv))
         d2h = 52 * scene.n
@@ -417,7 +418,7 @@ def measure_batch(a, scenes, metric):
     import paper_2604_02586_b300 as tsp
     dev = torch.device("cuda", 0)
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
-    args = [dict(means_opacity=t(s.means_opacity), quats=t(s.quats), scales=t(s.scales), cams=s,
+    args = [dict(means_opacity=t(s.means_opacity), quats=t(s.quats), scales=t(s.scales), cams=tsp.cameras(s),
                  disp=[t(d) for d in s.disp], vis=[t(v) for v in s.vis]) for s in scenes]
     units = sum(s.n * s.num_views for s in scenes)
     with tsp.Context(0) as probe:
@@ -505,6 +506,7 @@ def run_serve(a):
     memory inside each request."""
     import copy
     import torch
+    import paper_2604_02586_b300 as tsp
     from paper_2604_02586_b300 import build as tbuild
     from paper_2604_02586_b300.serve import MotionServer, Request, latency_stats, one_at_a_time
     tbuild.build()
@@ -512,6 +514,7 @@ def run_serve(a):
     scenes = serve_scenes()
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
     tracks = [([pin(d) for d in s.disp], [pin(v) for v in s.vis]) for s in scenes]
+    cams = [tsp.cameras(s) for s in scenes]      # each scene's camera rig, built once
     rng = np.random.default_rng(7)
     t, reqs = 0.0, []
     while True:
@@ -519,7 +522,7 @@ def run_serve(a):
         if t > a.duration:
             break
         k = int(rng.integers(0, len(scenes)))
-        reqs.append(Request(len(reqs), f"s{k}", scenes[k], tracks[k][0], tracks[k][1], arrival=t))
+        reqs.append(Request(len(reqs), f"s{k}", cams[k], tracks[k][0], tracks[k][1], arrival=t))
     units = lambda r: int(scenes[int(r.scene[1:])].n) * int(scenes[int(r.scene[1:])].num_views)
 
     def serve():
@@ -527,7 +530,7 @@ def run_serve(a):
         for k, s in enumerate(scenes):
             srv.add_scene(f"s{k}", s.means_opacity, s.quats, s.scales)
         # one warm-up frame per scene (contexts, workspaces, CUDA modules)
-        srv.run([Request(-1 - k, f"s{k}", s, tracks[k][0], tracks[k][1]) for k, s in enumerate(scenes)])
+        srv.run([Request(-1 - k, f"s{k}", cams[k], tracks[k][0], tracks[k][1]) for k in range(len(scenes))])
         srv.finished = []
         done = srv.run(copy.copy(r) for r in reqs)
         stats = latency_stats(done, units)
@@ -587,17 +590,19 @@ def run_train(a):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    cams = tsp.cameras(s)
+
     def step():
         for v in params.values():
             v.grad = None
-        img = render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], s, ctx)
+        img = render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], cams, ctx)
         loss = (img - target).abs().mean()
         loss.backward()
         return loss
 
     def fwd():
         with torch.no_grad():
-            return render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], s, ctx)
+            return render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], cams, ctx)
 
     def timed(fn, steps):
         for _ in range(a.warmup):
@@ -653,7 +658,8 @@ def run_reg(a):
     mo, q, sc = t(s.means_opacity), t(s.quats), t(s.scales)
     disp, vis = [t(d) for d in s.disp], [t(v) for v in s.vis]
     ctx = tsp.Context(0)
-    out = ctx.fit_motion(mo, q, sc, s, disp, vis, sync=True)
+    cams = tsp.cameras(s)
+    out = ctx.fit_motion(mo, q, sc, cams, disp, vis, sync=True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -661,7 +667,7 @@ def run_reg(a):
         return ctx.regularize((mo, q, sc), out, s.num_views)
 
     def fit_reg():
-        o = ctx.fit_motion(mo, q, sc, s, disp, vis, out=out)
+        o = ctx.fit_motion(mo, q, sc, cams, disp, vis, out=out)
         return ctx.regularize((mo, q, sc), o, s.num_views)
 
     def timed(fn, steps):

@@ -157,6 +157,14 @@ def _cams(cams):
     return cameras_from(cams.width, cams.height, cams.fx, cams.fy, cams.cx, cams.cy, cams.R, cams.t)
 
 
+def cameras(cam_set):
+    """The (tsp_camera array, view count) pair of a camera set (an object with
+    per-view width, height, fx, fy, cx, cy, R, t).  Every call taking ``cams``
+    accepts either form; a caller that fits the same views repeatedly builds the
+    pair once and saves rebuilding it (~0.13 ms for 18 views) on every call."""
+    return _cams(cam_set)
+
+
 def _dptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 

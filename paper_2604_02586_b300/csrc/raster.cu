@@ -232,16 +232,20 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
 //   the block are dropped.
 //   Phase 2 (moments, hit-parallel): once 16 hits are pending, lane l sums the
 //   13 weighted moments of hit l & 15 over pixel half l >> 4 (32 pixels) from
-//   the buffer; the halves are joined with one shuffle per value and lanes 0-15
-//   add the result to global memory with 4 float4 atomics.
-// Buffer layout: weight of hit c at pixel i of half h at h * kWHalf + i * kWRow + c.
-// A row stride of 17 words makes both the phase-1 writes (lanes = pixels) and
-// the phase-2 reads (lanes = hits) conflict-free, and kWHalf = 16 (mod 32)
-// keeps the two halves on different banks.
+//   the buffer, two horizontally adjacent pixels at a time in packed FP32x2
+//   arithmetic (each moment as an (even pixel, odd pixel) pair, joined at the
+//   end; two passes, position then displacement moments, so the pairs of sums
+//   fit the 72 registers of 7 CTAs per SM); the halves are joined with one
+//   shuffle per value and lanes 0-15 add the result to global memory with 4
+//   float4 atomics.
+// Buffer layout: the weights of hit c at the pixel pair p (pixels 2p, 2p + 1)
+// of half h are the float2 at h * kWHalf + p * kWRow + 2c.  A row stride of 34
+// words makes the phase-1 writes (lane l: pair l >> 1, word l & 1) hit 32
+// different banks and the phase-2 reads (lanes = hits) 32 consecutive words.
 constexpr int kChunk = 16;
-constexpr int kWRow = 17;
-constexpr int kWHalf = 32 * kWRow + 16;
-constexpr int kWWords = kWHalf + 32 * kWRow;
+constexpr int kWRow = 2 * kChunk + 2;
+constexpr int kWHalf = 16 * kWRow;
+constexpr int kWWords = 2 * kWHalf;
 
 // Warp-private shared memory of the two-phase walk.
 struct WarpSmem {
@@ -250,7 +254,8 @@ struct WarpSmem {
     float4 hd[32];                 // (origin x, origin y, reference x, reference y)
     uint32_t id[32];
     float W[kWWords];
-    float4 F[2][33];               // (d_x, d_y, static, 0) per pixel, halves padded
+    float4 D[2][16];               // per half and pixel pair: (d_x, d_x', d_y, d_y')
+    float2 S[2][16];               // per half and pixel pair: static flags (0 or 1)
 };
 
 // One warp, one 8x8 block `blk` of tile `tile`: the two-phase walk above.  Work
@@ -290,7 +295,10 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         }
         // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
         const bool stat = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
-        sm.F[k][lane] = make_float4(ddx, ddy, 1.f, stat ? 1.f : 0.f);
+        float* const dp = reinterpret_cast<float*>(&sm.D[k][lane >> 1]);
+        dp[lane & 1] = ddx;
+        dp[2 + (lane & 1)] = ddy;
+        reinterpret_cast<float*>(&sm.S[k][lane >> 1])[lane & 1] = stat ? 1.f : 0.f;
         stat_mask[k] = __ballot_sync(kFull, stat);
         yc[k] = (float)ly + 0.5f;
         T[k] = inside ? 1.0f : 0.0f;
@@ -312,33 +320,54 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         const float rx = __shfl_sync(kFull, h_hd.z, c), ry = __shfl_sync(kFull, h_hd.w, c);
         const float x0 = ((float)bxo + 0.5f) - ox;
         const float y0 = ((float)(byo + 4 * half) + 0.5f) - oy;
-        // moments paired for packed FP32x2 arithmetic: (1, 2) += w (X, Y),
-        // (3, 4) += wX (X, Y), (6, 7) += w (dx, dy), (8, 9) += wX (dx, dy),
-        // (10, 11) += wY (dx, dy), (0, 12) += w (1, static); 5 += wY Y
-        float2 s12 = make_float2(0.f, 0.f), s34 = s12, s67 = s12, s89 = s12, s1011 = s12, s0st = s12;
-        float s5 = 0.f;
-        const float* Wh = Wb + half * kWHalf + c;
-        const float4* Fh = sm.F[half];
-        const float2 nr = make_float2(-rx, -ry);
+        // every moment as an (even pixel, odd pixel) pair: a[q] sums moment q
+        // over the pixels 2p and 2p + 1 of every pair p; two passes over the
+        // pairs (the position moments, then the displacement moments)
+        const float2 z = make_float2(0.f, 0.f);
+        float2 a0 = z, a1 = z, a2 = z, a3 = z, a4 = z, a5 = z, a6 = z, a7 = z, a8 = z, a9 = z, a10 = z,
+               a11 = z, a12 = z;
+        const float* Wh = Wb + half * kWHalf + 2 * c;
+        const float4* Dh = sm.D[half];
+        const float2* Sh = sm.S[half];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const float wv = Wh[i * kWRow];
-            const float4 f = Fh[i];
-            const float2 XY = make_float2(x0 + (float)(i & 7), y0 + (float)(i >> 3));
-            const float2 d = __fadd2_rn(make_float2(f.x, f.y), nr);
-            const float2 ww = make_float2(wv, wv);
-            const float2 wxy = __fmul2_rn(ww, XY);
-            const float2 wxx = make_float2(wxy.x, wxy.x), wyy = make_float2(wxy.y, wxy.y);
-            s12 = __fadd2_rn(s12, wxy);
-            s34 = __ffma2_rn(wxx, XY, s34);
-            s5 = fmaf(wxy.y, XY.y, s5);
-            s67 = __ffma2_rn(ww, d, s67);
-            s89 = __ffma2_rn(wxx, d, s89);
-            s1011 = __ffma2_rn(wyy, d, s1011);
-            s0st = __ffma2_rn(ww, make_float2(f.z, f.w), s0st);
+        for (int p = 0; p < 16; ++p) {
+            const float2 w2 = *reinterpret_cast<const float2*>(Wh + p * kWRow);
+            const float2 st2 = Sh[p];
+            const int col = 2 * (p & 3);
+            const float2 X = make_float2(x0 + (float)col, x0 + (float)(col + 1));
+            const float yv = y0 + (float)(p >> 2);
+            const float2 Y = make_float2(yv, yv);
+            const float2 wX = __fmul2_rn(w2, X), wY = __fmul2_rn(w2, Y);
+            a0 = __fadd2_rn(a0, w2);
+            a1 = __fadd2_rn(a1, wX);
+            a2 = __fadd2_rn(a2, wY);
+            a3 = __ffma2_rn(wX, X, a3);
+            a4 = __ffma2_rn(wX, Y, a4);
+            a5 = __ffma2_rn(wY, Y, a5);
+            a12 = __ffma2_rn(w2, st2, a12);
         }
-        float s[13] = {s0st.x, s12.x, s12.y, s34.x, s34.y, s5, s67.x, s67.y,
-                       s89.x, s89.y, s1011.x, s1011.y, s0st.y};
+        const float2 nrx = make_float2(-rx, -rx), nry = make_float2(-ry, -ry);
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            const float2 w2 = *reinterpret_cast<const float2*>(Wh + p * kWRow);
+            const float4 dd = Dh[p];
+            const int col = 2 * (p & 3);
+            const float2 X = make_float2(x0 + (float)col, x0 + (float)(col + 1));
+            const float yv = y0 + (float)(p >> 2);
+            const float2 Y = make_float2(yv, yv);
+            const float2 dX = __fadd2_rn(make_float2(dd.x, dd.y), nrx);
+            const float2 dY = __fadd2_rn(make_float2(dd.z, dd.w), nry);
+            const float2 wX = __fmul2_rn(w2, X), wY = __fmul2_rn(w2, Y);
+            a6 = __ffma2_rn(w2, dX, a6);
+            a7 = __ffma2_rn(w2, dY, a7);
+            a8 = __ffma2_rn(wX, dX, a8);
+            a9 = __ffma2_rn(wX, dY, a9);
+            a10 = __ffma2_rn(wY, dX, a10);
+            a11 = __ffma2_rn(wY, dY, a11);
+        }
+        float s[13] = {a0.x + a0.y, a1.x + a1.y, a2.x + a2.y, a3.x + a3.y, a4.x + a4.y,
+                       a5.x + a5.y, a6.x + a6.y, a7.x + a7.y, a8.x + a8.y, a9.x + a9.y,
+                       a10.x + a10.y, a11.x + a11.y, a12.x + a12.y};
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
         if (lane < npend) {
@@ -404,7 +433,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
                 const bool pass = alpha >= kAlphaMin;
                 const bool blend = pass && tn >= kTMin;    // T = 0: Tn = 0, never blends
                 add[k] = blend && vis[k];
-                Wb[k * kWHalf + lane * kWRow + pend] = add[k] ? (k ? wa.y : wa.x) : 0.f;
+                Wb[k * kWHalf + (lane >> 1) * kWRow + 2 * pend + (lane & 1)] = add[k] ? (k ? wa.y : wa.x) : 0.f;
                 if (kStats) { cnt[0] += T[k] > 0.f; cnt[1] += blend; cnt[2] += add[k]; }
                 T[k] = blend ? tn : (pass ? 0.f : T[k]);   // pass without blend: terminated
             }

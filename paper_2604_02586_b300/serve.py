@@ -42,7 +42,7 @@ class Request:
     """One frame pair of a scene: host (pinned) tracks for each of its views."""
     rid: int
     scene: str
-    cams: object                 # object with width/height/fx/fy/cx/cy/R/t per view
+    cams: object                 # camera set (width/height/fx/fy/cx/cy/R/t per view) or cameras() pair
     disp: list                   # host float32 [H, W, 2] per view (numpy or pinned tensor)
     vis: list                    # host uint8 [H, W] per view
     arrival: float = 0.0         # seconds, relative to the start of the run
