@@ -59,6 +59,11 @@ __global__ void __launch_bounds__(128) k_colour(const ViewSet vs, const float* _
 // grid (ceil(nmax/256), V): one thread per (view, Gaussian), Gaussian index fastest.
 // kMode 0: motion fit (zero the moment record, note the moment origin's pixel);
 // kMode 1: render (view-dependent colour; one frame).
+// The tile counters are raised once per (record, tile) item.  A warp's items are
+// spread evenly over its lanes (a warp scan numbers them; each lane finds the
+// owner of its item by a 5-step shuffle search), so the warp issues about
+// (its items) / 32 atomic instructions instead of one per tile of its largest
+// rectangle.
 template <int kMode>
 __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const float* __restrict__ sh,
                                                     int sh_degree, Work w)
@@ -66,45 +71,73 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
     constexpr int mode = kMode;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
-    if (g >= vs.vn[v]) return;
-    const size_t i = (size_t)vs.vrec[v] + g;
-    const int fr = vs.vframe[v];
-    if (mode == 0) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        w.moments[4 * i] = z; w.moments[4 * i + 1] = z; w.moments[4 * i + 2] = z; w.moments[4 * i + 3] = z;
+    const int lane = threadIdx.x & 31;
+    uint32_t cnt = 0u, rxy = 0u, rw = 0u;         // items, rectangle corner and width
+    if (g < vs.vn[v]) {
+        const size_t i = (size_t)vs.vrec[v] + g;
+        const int fr = vs.vframe[v];
+        if (mode == 0) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            w.moments[4 * i] = z; w.moments[4 * i + 1] = z; w.moments[4 * i + 2] = z; w.moments[4 * i + 3] = z;
+        }
+        const float4 m = vs.fmo[fr][g];
+        KeyProj p;
+        if (!key_project(vs.cam[v], m, vs.fq[fr][g], vs.fs[fr][g], vs.tiles_x[v], vs.tiles_y[v], p)) {
+            w.rect[i] = make_short4(0, 0, 0, 0);
+            w.touched[i] = 0u;
+            w.depth[i] = 0u;
+        } else {
+            w.rect[i] = make_short4((short)p.x0, (short)p.y0, (short)p.x1, (short)p.y1);
+            cnt = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
+            rxy = (uint32_t)p.x0 | ((uint32_t)p.y0 << 16);
+            rw = (uint32_t)(p.x1 - p.x0);
+            w.touched[i] = cnt;
+            w.depth[i] = __float_as_uint(p.pz);
+            const float3 f = blend_factor(p);
+            // mean relative to the rectangle's corner pixel (x0*16, y0*16), to ~1e-6 px
+            float2 ux, uy;
+            mean2d_df(vs.cam[v], m, ux, uy);
+            const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * kTile)), ux.y);
+            const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * kTile)), uy.y);
+            w.geom0[i] = make_float4(rx, ry, f.x, f.y);
+            const float2 dlt = moment_origin_shift(ux, uy, vs.cam[v].W, vs.cam[v].H);
+            w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);
+            if (mode == 0) {
+                // the pixel holding the moment origin; k_dref reads the track there
+                const int W = vs.cam[v].W, H = vs.cam[v].H;
+                const int ox = min(max((int)floorf(ux.x + ux.y + dlt.x), 0), W - 1);
+                const int oy = min(max((int)floorf(uy.x + uy.y + dlt.y), 0), H - 1);
+                w.oref[i] = (uint32_t)oy * (uint32_t)W + (uint32_t)ox;
+            }
+        }
     }
-    const float4 m = vs.fmo[fr][g];
-    KeyProj p;
-    if (!key_project(vs.cam[v], m, vs.fq[fr][g], vs.fs[fr][g], vs.tiles_x[v], vs.tiles_y[v], p)) {
-        w.rect[i] = make_short4(0, 0, 0, 0);
-        w.touched[i] = 0u;
-        w.depth[i] = 0u;
-        return;
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
     }
-    w.rect[i] = make_short4((short)p.x0, (short)p.y0, (short)p.x1, (short)p.y1);
-    w.touched[i] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
-    w.depth[i] = __float_as_uint(p.pz);
-    const float3 f = blend_factor(p);
-    // mean relative to the rectangle's corner pixel (x0*16, y0*16), to ~1e-6 px
-    float2 ux, uy;
-    mean2d_df(vs.cam[v], m, ux, uy);
-    const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * kTile)), ux.y);
-    const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * kTile)), uy.y);
-    w.geom0[i] = make_float4(rx, ry, f.x, f.y);
-    const float2 dlt = moment_origin_shift(ux, uy, vs.cam[v].W, vs.cam[v].H);
-    w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);
-    if (mode == 0) {
-        // the pixel holding the moment origin; k_dref reads the track there
-        const int W = vs.cam[v].W, H = vs.cam[v].H;
-        const int ox = min(max((int)floorf(ux.x + ux.y + dlt.x), 0), W - 1);
-        const int oy = min(max((int)floorf(uy.x + uy.y + dlt.y), 0), H - 1);
-        w.oref[i] = (uint32_t)oy * (uint32_t)W + (uint32_t)ox;
-    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t exc = inc - cnt;
     const uint32_t base = vs.toff[v];
-    const int tx_n = vs.tiles_x[v];
-    for (int ty = p.y0; ty < p.y1; ++ty)
-        for (int tx = p.x0; tx < p.x1; ++tx)
-            atomicAdd(&w.tile_count[(size_t)(base + (uint32_t)(ty * tx_n + tx)) * kCounterStride], 1u);
+    const uint32_t tx_n = (uint32_t)vs.tiles_x[v];
+    for (uint32_t it0 = 0; it0 < total; it0 += 32) {
+        const uint32_t item = it0 + (uint32_t)lane;
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, exc, own + step);
+            if (e <= item) own += step;
+        }
+        const uint32_t off = item - __shfl_sync(0xffffffffu, exc, own);
+        const uint32_t xy = __shfl_sync(0xffffffffu, rxy, own);
+        const uint32_t wd = __shfl_sync(0xffffffffu, rw, own);
+        if (item < total) {
+            const uint32_t dy = wd ? off / wd : 0u, dx = off - dy * wd;
+            const uint32_t t = base + ((xy >> 16) + dy) * tx_n + (xy & 0xffffu) + dx;
+            atomicAdd(&w.tile_count[(size_t)t * kCounterStride], 1u);
+        }
+    }
 }
 
 // Reference displacement of every (view, Gaussian) record of views v0.. (grid.y
