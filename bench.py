@@ -29,8 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian·view track fits/s at 200k Gaussians×18 views; p50/p99 frame latency"
 UNIT = "fits/s"
-REG_LAUNCHES = 23            # tsp_regularize kernels: prepare; grids: bounds, setup, count, scan x3, scatter; skew, decide, grid KNN; BVH: codes, scan x3, scatter, sort x2, build, refit, walk; median, apply
-KERNELS_PER_STEP = 11         # project, scan (3), emit, tile sort (2), reference gather, raster, view solve, multi-view
+REG_LAUNCHES = 24            # tsp_regularize kernels: prepare; grids: bounds, setup, count, scan x3, scatter; skew, decide, grid KNN; BVH: codes, scan x3, scatter, sort x3, build, refit, walk; median, apply
+KERNELS_PER_STEP = 12         # project, scan (3), emit, tile sort (3), reference gather, raster, view solve, multi-view
 RASTER_SRC = os.path.join(ROOT, "paper_2604_02586_b300", "csrc", "raster.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "raster_accumulate_traffic.json")
 

@@ -463,7 +463,8 @@ __device__ __forceinline__ void warp_sort_list(uint64_t* __restrict__ keys, uint
 }
 
 // Eight tiles per 256-thread CTA, one per warp; tiles whose lists are longer than
-// kWarpSortMax are appended to long_list (count in *long_count) for k_tile_sort.
+// kWarpSortMax are appended to long_list (count in *long_count) for
+// k_tile_sort_warp_long (up to kWarpSortLong keys) and k_tile_sort (longer).
 __global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restrict__ off,
                                                         uint64_t* __restrict__ pairs, uint32_t cap,
                                                         uint32_t NT, uint32_t* __restrict__ long_list,
@@ -486,7 +487,29 @@ __global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restri
     else if (lane == 0) long_list[atomicAdd(long_count, 1u)] = t;
 }
 
-// Lists longer than kWarpSortMax, one CTA at a time per listed tile.  Up to
+// Listed lists of kWarpSortMax < n <= kWarpSortLong keys: one warp each, 32 keys
+// a lane (the same network; 64 registers of keys), the warps of the grid taking
+// the listed tiles in turn.
+constexpr int kWarpSortLong = 1024;
+
+__global__ void __launch_bounds__(256) k_tile_sort_warp_long(const uint32_t* __restrict__ off,
+                                                             uint64_t* __restrict__ pairs, uint32_t cap,
+                                                             const uint32_t* __restrict__ long_list,
+                                                             const uint32_t* __restrict__ long_count,
+                                                             const uint32_t* __restrict__ enable)
+{
+    if (enable && !*enable) return;
+    const uint32_t count = *long_count;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; li < count; li += nw) {
+        const uint32_t t = long_list[li];
+        const uint32_t b = min(off[t], cap), e = min(off[t + 1], cap);
+        if (e - b <= (uint32_t)kWarpSortLong) warp_sort_list<32>(pairs + b, e - b, lane);
+    }
+}
+
+// Listed lists longer than kWarpSortLong, one CTA at a time per tile.  Up to
 // kSortCap keys sort in shared memory; longer lists sort kSortCap-sized runs there
 // and then merge runs pairwise in global memory (each key finds its output slot
 // by a binary search in the partner run; keys are unique).
@@ -503,6 +526,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(const uint32_t* __re
         const uint32_t t = long_list[li];
         const uint32_t b = min(off[t], cap), e = min(off[t + 1], cap);
         const uint32_t n = e - b;
+        if (n <= (uint32_t)kWarpSortLong) continue;          // sorted by k_tile_sort_warp_long
         if (n <= (uint32_t)kSortCap) {
             smem_sort(pairs + b, n, s);
             continue;
@@ -581,6 +605,7 @@ cudaError_t launch_segment_sort(const uint32_t* off, uint64_t* keys, uint64_t* t
     const cudaError_t e = cudaMemsetAsync(long_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     k_tile_sort_warp<<<(nseg + 7) / 8, 256, 0, st>>>(off, keys, cap, nseg, long_list, long_count, enable);
+    k_tile_sort_warp_long<<<kLongSortCtas, 256, 0, st>>>(off, keys, cap, long_list, long_count, enable);
     k_tile_sort<<<kLongSortCtas, kSortThreads, 0, st>>>(off, keys, tmp, cap, long_list, long_count, enable);
     return cudaGetLastError();
 }
@@ -599,6 +624,8 @@ cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
     // tile_fill is free once the pairs are scattered: it holds the long-list tiles
     k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill, &w.dstatus[3],
                                                    nullptr);
+    k_tile_sort_warp_long<<<kLongSortCtas, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, w.tile_fill, &w.dstatus[3],
+                                                         nullptr);
     k_tile_sort<<<kLongSortCtas, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,
                                               &w.dstatus[3], nullptr);
     return cudaGetLastError();
