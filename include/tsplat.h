@@ -204,8 +204,8 @@ tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frame
 /* Same step for callers that hold everything in host memory: g, tracks and out
  * point to host arrays (pinned memory gives full copy speed and lets the copies
  * overlap the computation).  The Gaussians are copied on `stream` and projected,
- * binned and sorted while the tracks are copied on a context-owned stream in
- * about six view groups; each group's raster starts once its tracks have landed.
+ * binned and sorted while the tracks are copied on a context-owned stream, one
+ * view at a time; each view's raster starts once its tracks have landed.
  * Results are copied back and the call returns after both streams have finished
  * with the caller's buffers.  Errors as tsp_fit_motion, plus OVERFLOW if the pair
  * buffer overflowed. */

@@ -657,7 +657,7 @@ tsp_status tsp_create(int device, const tsp_options* opt, tsp_context** out)
         delete ctx;
         return TSP_ERR_CUDA;
     }
-    if (raster_prepare() != cudaSuccess) {
+    if (raster_prepare() != cudaSuccess || backward_prepare() != cudaSuccess) {
         cudaGetLastError();
         tsp_destroy(ctx);
         return TSP_ERR_CUDA;

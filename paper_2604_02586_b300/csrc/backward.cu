@@ -237,7 +237,9 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
     if (pend) phase2(pend);
 }
 
-__global__ void __launch_bounds__(128) k_render_backward(const ViewSet vs, const Work w, const RenderGrad rg)
+// 7 CTAs per SM: 72 registers, and 7 x 31.4 KB of shared memory with the
+// largest carveout (set once per context by backward_prepare)
+__global__ void __launch_bounds__(128, 7) k_render_backward(const ViewSet vs, const Work w, const RenderGrad rg)
 {
     __shared__ BwdSmem sm[4];
     const int warp = threadIdx.x >> 5;
@@ -413,6 +415,12 @@ __global__ void __launch_bounds__(128) k_render_backward_project(const ViewSet v
 }
 
 }  // namespace
+
+cudaError_t backward_prepare()
+{
+    return cudaFuncSetAttribute((const void*)k_render_backward, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
 
 cudaError_t launch_render_backward(const ViewSet& vs, const Work& w, uint32_t NT, const RenderGrad& rg,
                                    const float* sh, int sh_degree, size_t records, cudaStream_t st)

@@ -41,6 +41,8 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
                                      bool stats, int variant, int resident_ctas, cudaStream_t st);
 // One-time kernel attributes of the raster step (shared-memory carveout).
 cudaError_t raster_prepare();
+// Shared-memory carveout of the render adjoint (once per context).
+cudaError_t backward_prepare();
 // CTAs of the persistent raster that fit on the device at once.
 int raster_resident_ctas(int device);
 // the render's adjoint: dL/dcolour -> per (view, Gaussian) 2D gradients

@@ -220,6 +220,28 @@ def test_host_entry_point_matches_device(gpu_ready):
     np.testing.assert_allclose(h["scales"], g["scales"], rtol=1e-4, atol=0)
 
 
+@pytest.mark.parametrize("n,views", [(1, 3), (2, 3), (301, 4), (300, 0), (0, 3)])
+def test_host_entry_point_edges(gpu_ready, n, views):
+    """The host-buffer call streams its results back in two halves of the
+    Gaussians (the first half may be empty); without views it copies them back
+    whole.  Both agree with the device call."""
+    import paper_2604_02586_b300 as tsp
+    s = synth.make_scene("tiny", 5, n=max(n, 1), views=max(views, 1))
+    if n == 0:
+        s = synth.make_scene("tiny", 5, n=0, views=views)
+    if views == 0:
+        s = s.subset_views([])
+    with tsp.Context(0) as ctx:
+        g = P.run_gpu(s, ctx=ctx, inspect=False)
+        h = ctx.fit_motion_host(s.means_opacity, s.quats, s.scales, s, s.disp, s.vis)
+    assert h["means"].shape == (n, 4) and h["status"].shape == (n,)
+    assert np.array_equal(h["status"] & 0xFF, g["status"] & 0xFF)
+    np.testing.assert_allclose(h["means"], g["means"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(h["scales"], g["scales"], rtol=1e-4, atol=0)
+    if views == 0:
+        assert np.array_equal(h["means"], s.means_opacity)
+
+
 def test_empty_and_degenerate_inputs(gpu_ready):
     import torch
     import paper_2604_02586_b300 as tsp
