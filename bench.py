@@ -425,7 +425,7 @@ def measure_batch(a, scenes, metric):
         probe.fit_motion_batch(args, sync=True)
         K = int(probe.inspect(tsp.TSP.I_COUNTS)[0])
     ctx = tsp.Context(0, async_pairs=1, pair_capacity=int(K * 1.1) + 1024)
-    variant, tune_ms = ctx.autotune(args, repeats=2)
+    cand, tune_ms = ctx.autotune(args, repeats=2)
     outs = ctx.fit_motion_batch(args, sync=True)
     for x, o in zip(args, outs):
         x["out"] = o
@@ -479,7 +479,8 @@ def measure_batch(a, scenes, metric):
             "batched_no_graph": {"value": fps(bat_ms), "ms_per_step": float(np.mean(bat_ms))},
             "speedup_vs_one_at_a_time": float(np.mean(one_ms)) / float(np.mean(gr_ms)),
             "status_agreement_with_one_at_a_time": same,
-            "autotune": {"chosen_raster_variant": variant, "raster_ms": tune_ms},
+            "autotune": {"chosen": {"tile": f"{cand[0]}x{cand[1]}", "raster_variant": cand[2]},
+                         "fit_ms": {f"{w}x{h} variant {v}": ms for (w, h, v), ms in tune_ms.items()}},
             "clocks": clocks}
     return line
 

@@ -119,7 +119,8 @@ typedef struct tsp_frame {
 } tsp_frame;
 
 typedef struct tsp_options {
-    int32_t tile_w, tile_h;     /* raster tile; 16 x 16 is the only supported value */
+    int32_t tile_w, tile_h;     /* raster tile: 16 x 16 (default) or 32 x 8; with */
+                                /*    32 x 8, raster_variant must be 0 or 5        */
     float det_min;              /* Sec. 5.1: 1e-12                                 */
     float sumw_min_view;        /* Sec. 5.1: 1e-3                                  */
     int32_t min_px_view;        /* Sec. 5.1: 2                                     */
@@ -190,16 +191,21 @@ tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_ca
 tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int num_frames, void* stream);
 
 /* Autotuner: runs the motion fit on the given frames (outputs are written) with
- * each candidate raster kernel -- two-phase with one CTA per tile (variant 0),
- * two-phase persistent over a work queue (5), warp-shuffle 8x8 blocks (2) --
- * `repeats` timed times after one warm-up each, and keeps the one whose median
- * raster time is lowest as the context's raster_variant.  chosen (nullable)
- * receives it, raster_ms (nullable, [TSP_TUNE_CANDIDATES]) the medians in that
- * order.  Synchronises the stream.  Errors as tsp_fit_motion_batch; the options
- * are left unchanged on error. */
-#define TSP_TUNE_CANDIDATES 3
+ * each candidate (tile shape, raster kernel), in this order:
+ *   0: 16 x 16, two-phase with one CTA per tile (variant 0)
+ *   1: 16 x 16, two-phase persistent over a work queue (variant 5)
+ *   2: 16 x 16, warp-shuffle 8x8 blocks (variant 2)
+ *   3: 32 x 8, variant 0          4: 32 x 8, variant 5
+ * `repeats` timed times after one warm-up each (the pair buffer is sized
+ * synchronously for each tile shape), and keeps the candidate whose median time
+ * of the whole fit (binning differs between tile shapes) is lowest: the context's
+ * tile_w, tile_h and raster_variant become its values.  chosen (nullable)
+ * receives its index, fit_ms (nullable, [TSP_TUNE_CANDIDATES]) the medians in
+ * that order.  Synchronises the stream.  Errors as tsp_fit_motion_batch; the
+ * options are left unchanged on error. */
+#define TSP_TUNE_CANDIDATES 5
 tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats, void* stream,
-                        int* chosen, float* raster_ms);
+                        int* chosen, float* fit_ms);
 
 /* Same step for callers that hold everything in host memory: g, tracks and out
  * point to host arrays (pinned memory gives full copy speed and lets the copies

@@ -313,11 +313,14 @@ class Context:
             self.sync(stream)
         return [p[5] for p in prep]
 
-    TUNE_CANDIDATES = (0, 5, 2)
+    # (tile_w, tile_h, raster_variant), in the order of tsp_autotune's candidates
+    TUNE_CANDIDATES = ((16, 16, 0), (16, 16, 5), (16, 16, 2), (32, 8, 0), (32, 8, 5))
 
     def autotune(self, frames, repeats=3, stream=None):
-        """Time each candidate raster kernel on ``frames`` (fit_motion_batch
-        arguments) and keep the fastest.  Returns (variant, {variant: median ms})."""
+        """Time each candidate (tile shape, raster kernel) on ``frames``
+        (fit_motion_batch arguments) by the whole fit and keep the fastest.
+        Returns (candidate, {candidate: median ms}), candidates as in
+        TUNE_CANDIDATES."""
         keys = ("means_opacity", "quats", "scales", "cams", "disp", "vis")
         prep = [self._frame(*[f[k] for k in keys], f.get("out")) for f in frames]
         arr = (Frame * max(len(prep), 1))()
@@ -328,8 +331,9 @@ class Context:
         ms = (C.c_float * len(self.TUNE_CANDIDATES))()
         self._check(lib().tsp_autotune(self._h, arr, len(prep), int(repeats), _stream_handle(stream),
                                        C.byref(chosen), ms), "tsp_autotune")
-        self.opt.raster_variant = chosen.value
-        return chosen.value, dict(zip(self.TUNE_CANDIDATES, [float(x) for x in ms]))
+        best = self.TUNE_CANDIDATES[chosen.value]
+        self.opt.tile_w, self.opt.tile_h, self.opt.raster_variant = best
+        return best, dict(zip(self.TUNE_CANDIDATES, [float(x) for x in ms]))
 
     def fit_motion_host(self, means_opacity, quats, scales, cams, disp, vis, out=None, stream=None):
         """Host path: numpy inputs and outputs; copies happen inside the library."""

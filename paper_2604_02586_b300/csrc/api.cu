@@ -63,7 +63,10 @@ struct tsp_context {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kTuneCandidates = 3;
+// Autotuner candidates (tile width, tile height, raster variant), in the order of
+// tsp_autotune's fit_ms: the warp-shuffle variant exists for 16 x 16 tiles only.
+constexpr int kTuneCandidates = TSP_TUNE_CANDIDATES;
+constexpr int kTuneTable[kTuneCandidates][3] = {{16, 16, 0}, {16, 16, 5}, {16, 16, 2}, {32, 8, 0}, {32, 8, 5}};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -148,8 +151,8 @@ bool device_accessible(const void* p, int dev)
 
 tsp_status check_options(tsp_context* ctx, const tsp_options& o)
 {
-    if (o.tile_w != kTile || o.tile_h != kTile)
-        return fail(ctx, TSP_ERR_INVALID_ARG, "only 16x16 tiles are supported");
+    const bool square = o.tile_w == 16 && o.tile_h == 16, wide = o.tile_w == 32 && o.tile_h == 8;
+    if (!square && !wide) return fail(ctx, TSP_ERR_INVALID_ARG, "tiles must be 16x16 or 32x8");
     if (!(o.det_min >= 0.f) || !(o.sumw_min_view >= 0.f) || !(o.lam_min_px2 >= 0.f) ||
         !(o.sumw_min_total >= 0.f) || !(o.cov_rcond_min >= 0.f) || !std::isfinite(o.det_min) ||
         !std::isfinite(o.sumw_min_view) || !std::isfinite(o.lam_min_px2) ||
@@ -162,6 +165,8 @@ tsp_status check_options(tsp_context* ctx, const tsp_options& o)
     if (o.raster_variant != 0 && o.raster_variant != 1 && o.raster_variant != 2 &&
         o.raster_variant != 4 && o.raster_variant != 5)
         return fail(ctx, TSP_ERR_INVALID_ARG, "raster_variant must be 0, 1, 2, 4 or 5");
+    if (!square && o.raster_variant != 0 && o.raster_variant != 5)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "32x8 tiles need raster_variant 0 or 5");
     if (o.pair_capacity < 0 || o.pair_capacity > INT32_MAX || o.budget_bytes < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "bad pair_capacity or budget_bytes");
     return TSP_OK;
@@ -191,6 +196,8 @@ tsp_status make_viewset(tsp_context* ctx, const tsp_frame* frames, int F, ViewSe
     if (F < 0 || F > TSP_MAX_FRAMES) return fail(ctx, TSP_ERR_INVALID_ARG, "num_frames must be in [0, 16]");
     if (F > 0 && !frames) return fail(ctx, TSP_ERR_INVALID_ARG, "frames is NULL");
     std::memset(&vs, 0, sizeof(vs));
+    vs.tw = ctx->opt.tile_w;
+    vs.th = ctx->opt.tile_h;
     uint64_t off = 0, rec = 0;
     int V = 0;
     for (int f = 0; f < F; ++f) {
@@ -224,8 +231,8 @@ tsp_status make_viewset(tsp_context* ctx, const tsp_frame* frames, int F, ViewSe
             d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
             std::memcpy(d.R, c.R, sizeof(d.R));
             std::memcpy(d.t, c.t, sizeof(d.t));
-            vs.tiles_x[V] = (c.width + kTile - 1) / kTile;
-            vs.tiles_y[V] = (c.height + kTile - 1) / kTile;
+            vs.tiles_x[V] = (c.width + vs.tw - 1) / vs.tw;
+            vs.tiles_y[V] = (c.height + vs.th - 1) / vs.th;
             vs.toff[V] = (uint32_t)off;
             off += (uint64_t)vs.tiles_x[V] * vs.tiles_y[V];
             vs.vframe[V] = f;
@@ -1012,27 +1019,29 @@ tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count)
 }
 
 tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats, void* stream,
-                        int* chosen, float* raster_ms)
+                        int* chosen, float* fit_ms)
 {
     if (!ctx || repeats < 1 || repeats > 100) return TSP_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
-    static const int kCandidates[kTuneCandidates] = {0, 5, 2};
     const tsp_options saved = ctx->opt;
     cudaStream_t st = (cudaStream_t)stream;
     ctx->opt.stage_timing = 1;
     ctx->opt.collect_stats = 0;
-    int best_v = saved.raster_variant;
+    ctx->opt.async_pairs = 0;                 // each tile shape sizes its own pair buffer
+    int best_c = -1;
     float best = 3.0e38f;
     tsp_status s = TSP_OK;
     for (int c = 0; c < kTuneCandidates && s == TSP_OK; ++c) {
-        ctx->opt.raster_variant = kCandidates[c];
+        ctx->opt.tile_w = kTuneTable[c][0];
+        ctx->opt.tile_h = kTuneTable[c][1];
+        ctx->opt.raster_variant = kTuneTable[c][2];
         std::vector<float> t;
         for (int r = 0; r <= repeats && s == TSP_OK; ++r) {        // the first run is a warm-up
             if ((s = fit_device(ctx, frames, num_frames, st, true))) break;
             if ((s = tsp_sync(ctx, stream, -1))) break;
             if (r == 0 || !ctx->timed) continue;
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]) != cudaSuccess) {
+            if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[7]) != cudaSuccess) {
                 cudaGetLastError();
                 s = fail(ctx, TSP_ERR_CUDA, "cudaEventElapsedTime");
                 break;
@@ -1042,13 +1051,17 @@ tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frame
         if (s != TSP_OK || t.empty()) break;
         std::sort(t.begin(), t.end());
         const float med = t[t.size() / 2];
-        if (raster_ms) raster_ms[c] = med;
-        if (med < best) { best = med; best_v = kCandidates[c]; }
+        if (fit_ms) fit_ms[c] = med;
+        if (med < best) { best = med; best_c = c; }
     }
     ctx->opt = saved;
     if (s != TSP_OK) return s;
-    ctx->opt.raster_variant = best_v;
-    if (chosen) *chosen = best_v;
+    if (best_c >= 0) {
+        ctx->opt.tile_w = kTuneTable[best_c][0];
+        ctx->opt.tile_h = kTuneTable[best_c][1];
+        ctx->opt.raster_variant = kTuneTable[best_c][2];
+    }
+    if (chosen) *chosen = best_c;
     return TSP_OK;
 }
 

@@ -56,6 +56,8 @@ struct BwdSmem {
     float4 gC[64];                               // dL/dC of each pixel
 };
 
+// TW: tile width, 16 (16 x 16 tiles) or 32 (32 x 8), known at compile time.
+template <int TW>
 __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w, const RenderGrad& rg, uint32_t tile,
                                                int blk, BwdSmem& sm)
 {
@@ -64,7 +66,9 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int lane = threadIdx.x & 31;
-    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
+    constexpr int TH = kTilePx / TW;
+    constexpr int nbx = TW / 8;                // 8x8 blocks per tile row
+    const int bxo = (blk % nbx) * 8, byo = (blk / nbx) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
     const size_t vbase = (size_t)vs.vrec[v];
     const float xc = (float)(bxo + (lane & 7)) + 0.5f;
@@ -73,7 +77,7 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int ly = byo + (lane >> 3) + 4 * k;
-        const int px = tx * kTile + bxo + (lane & 7), py = ty * kTile + ly;
+        const int px = tx * TW + bxo + (lane & 7), py = ty * TH + ly;
         const bool inside = px < W && py < H;
         float cf[3] = {0.f, 0.f, 0.f};
         gc[k][0] = gc[k][1] = gc[k][2] = 0.f;
@@ -150,7 +154,7 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
         bool hit = false;
         if (b0 + lane < end) {
             const uint32_t g = (uint32_t)w.pairs[b0 + lane];
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
             const float4 g1 = w.geom1[vbase + g];
             const float4 bb = footprint_box(g0, g1);
             hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
@@ -239,11 +243,12 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
 
 // 7 CTAs per SM: 72 registers, and 7 x 31.4 KB of shared memory with the
 // largest carveout (set once per context by backward_prepare)
+template <int TW>
 __global__ void __launch_bounds__(128, 7) k_render_backward(const ViewSet vs, const Work w, const RenderGrad rg)
 {
     __shared__ BwdSmem sm[4];
     const int warp = threadIdx.x >> 5;
-    backward_block(vs, w, rg, blockIdx.x, warp, sm[warp]);
+    backward_block<TW>(vs, w, rg, blockIdx.x, warp, sm[warp]);
 }
 
 // grid (ceil(nmax / 128), F): one thread per Gaussian of frame blockIdx.y.
@@ -418,7 +423,11 @@ __global__ void __launch_bounds__(128) k_render_backward_project(const ViewSet v
 
 cudaError_t backward_prepare()
 {
-    return cudaFuncSetAttribute((const void*)k_render_backward, cudaFuncAttributePreferredSharedMemoryCarveout,
+    const cudaError_t e = cudaFuncSetAttribute((const void*)k_render_backward<16>,
+                                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)k_render_backward<32>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -428,7 +437,8 @@ cudaError_t launch_render_backward(const ViewSet& vs, const Work& w, uint32_t NT
     if (vs.nmax == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(rg.acc, 0, records * kGradStride * sizeof(float), st);
     if (e != cudaSuccess) return e;
-    if (NT > 0) k_render_backward<<<NT, 128, 0, st>>>(vs, w, rg);
+    if (NT > 0 && vs.tw == 32) k_render_backward<32><<<NT, 128, 0, st>>>(vs, w, rg);
+    else if (NT > 0) k_render_backward<16><<<NT, 128, 0, st>>>(vs, w, rg);
     dim3 grid((vs.nmax + 127) / 128, vs.F);
     k_render_backward_project<<<grid, 128, 0, st>>>(vs, w, rg, sh, sh_degree);
     return cudaGetLastError();

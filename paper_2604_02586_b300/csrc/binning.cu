@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
         }
         const float4 m = vs.fmo[fr][g];
         KeyProj p;
-        if (!key_project(vs.cam[v], m, vs.fq[fr][g], vs.fs[fr][g], vs.tiles_x[v], vs.tiles_y[v], p)) {
+        if (!key_project(vs.cam[v], m, vs.fq[fr][g], vs.fs[fr][g], vs.tiles_x[v], vs.tiles_y[v], vs.tw, vs.th, p)) {
             w.rect[i] = make_short4(0, 0, 0, 0);
             w.touched[i] = 0u;
             w.depth[i] = 0u;
@@ -94,11 +94,11 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
             w.touched[i] = cnt;
             w.depth[i] = __float_as_uint(p.pz);
             const float3 f = blend_factor(p);
-            // mean relative to the rectangle's corner pixel (x0*16, y0*16), to ~1e-6 px
+            // mean relative to the rectangle's corner pixel (x0*tw, y0*th), to ~1e-6 px
             float2 ux, uy;
             mean2d_df(vs.cam[v], m, ux, uy);
-            const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * kTile)), ux.y);
-            const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * kTile)), uy.y);
+            const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * vs.tw)), ux.y);
+            const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * vs.th)), uy.y);
             w.geom0[i] = make_float4(rx, ry, f.x, f.y);
             const float2 dlt = moment_origin_shift(ux, uy, vs.cam[v].W, vs.cam[v].H);
             w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);

@@ -8,8 +8,9 @@
 
 namespace tsp {
 
-constexpr int kTile = 16;                 // raster tile edge (pixels)
-constexpr int kTilePx = kTile * kTile;    // threads per raster CTA
+constexpr int kTile = 16;                 // default raster tile edge (pixels); the
+                                          // warp-shuffle variants support only 16 x 16
+constexpr int kTilePx = kTile * kTile;    // pixels (and shuffle-variant threads) per tile
 // Per-tile atomic counters sit 128 bytes apart: one L2 line (one slice) each, so
 // the atomics of neighbouring hot tiles do not queue behind one another.
 constexpr int kCounterStride = 32;
@@ -32,6 +33,7 @@ struct ViewSet {
     int V;                                // view slots (all frames)
     int F;                                // frames
     int nmax;                             // largest Gaussian count of a frame
+    int tw, th;                           // raster tile: 16 x 16 or 32 x 8 pixels (four 8x8 blocks)
     DevCam cam[kMaxViews];
     int tiles_x[kMaxViews];
     int tiles_y[kMaxViews];
@@ -135,7 +137,7 @@ __device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); 
 
 // Returns false if the Gaussian is culled or touches no tile in this view.
 __device__ __forceinline__ bool key_project(const DevCam& c, float4 m, float4 q, float4 s,
-                                            int tiles_x, int tiles_y, KeyProj& o)
+                                            int tiles_x, int tiles_y, int tw, int th, KeyProj& o)
 {
     const float* R = c.R;
     const float px = ff(R[0], m.x, ff(R[1], m.y, ff(R[2], m.z, c.t[0])));
@@ -198,12 +200,12 @@ __device__ __forceinline__ bool key_project(const DevCam& c, float4 m, float4 q,
     const float disc = fmaxf(0.1f, ff(mid, mid, -det));
     const float lam = fa(mid, __fsqrt_rn(disc));
     const float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
-    const float ftw = (float)kTile;
+    const float ftw = (float)tw, fth = (float)th;
     const float gx = __int2float_rn(tiles_x), gy = __int2float_rn(tiles_y);
     const float fx0 = fminf(fmaxf(floorf(fd(fs(o.mx, r), ftw)), 0.0f), gx);
     const float fx1 = fminf(fmaxf(fa(floorf(fd(fa(o.mx, r), ftw)), 1.0f), 0.0f), gx);
-    const float fy0 = fminf(fmaxf(floorf(fd(fs(o.my, r), ftw)), 0.0f), gy);
-    const float fy1 = fminf(fmaxf(fa(floorf(fd(fa(o.my, r), ftw)), 1.0f), 0.0f), gy);
+    const float fy0 = fminf(fmaxf(floorf(fd(fs(o.my, r), fth)), 0.0f), gy);
+    const float fy1 = fminf(fmaxf(fa(floorf(fd(fa(o.my, r), fth)), 1.0f), 0.0f), gy);
     o.x0 = (int)fx0; o.x1 = (int)fx1; o.y0 = (int)fy0; o.y1 = (int)fy1;
     return o.x1 > o.x0 && o.y1 > o.y0;
 }
@@ -359,10 +361,10 @@ __device__ __forceinline__ void sh_basis16_grad(float x, float y, float z, float
 
 // Blend record with its mean moved from the Gaussian's rectangle corner to this
 // tile's corner (an exact integer shift, so the staged mean keeps its precision).
-__device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty)
+__device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty, int tw, int th)
 {
-    g0.x += (float)((r.x - tx) * kTile);
-    g0.y += (float)((r.y - ty) * kTile);
+    g0.x += (float)((r.x - tx) * tw);
+    g0.y += (float)((r.y - ty) * th);
     return g0;
 }
 

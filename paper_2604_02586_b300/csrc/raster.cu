@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
         if (kStats && tid == 0) n_list += nb;
         if (tid < nb) {
             const uint32_t g = (uint32_t)w.pairs[b0 + tid];
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, kTile, kTile);
             const float4 g1 = w.geom1[vbase + g];
             s_id[tid] = g;
             s_g0[tid] = g0;
@@ -260,7 +260,9 @@ struct WarpSmem {
 
 // One warp, one 8x8 block `blk` of tile `tile`: the two-phase walk above.  Work
 // counts (kStats) accumulate in cnt.
-template <bool kStats>
+// TW: tile width, 16 (16 x 16 tiles) or 32 (32 x 8); a compile-time value so the
+// block and pixel coordinates cost no registers.
+template <bool kStats, int TW>
 __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& w, uint32_t tile, int blk,
                                                  WarpSmem& sm, unsigned long long (&cnt)[3])
 {
@@ -269,7 +271,9 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int lane = threadIdx.x & 31;
-    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
+    constexpr int TH = kTilePx / TW;
+    constexpr int nbx = TW / 8;                // 8x8 blocks per tile row: 2 (16 x 16) or 4 (32 x 8)
+    const int bxo = (blk % nbx) * 8, byo = (blk / nbx) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
     const size_t vbase = (size_t)vs.vrec[v];
     float* const Wb = sm.W;
@@ -283,7 +287,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int ly = byo + (lane >> 3) + 4 * k;
-        const int px = tx * kTile + bxo + (lane & 7), py = ty * kTile + ly;
+        const int px = tx * TW + bxo + (lane & 7), py = ty * TH + ly;
         const bool inside = px < W && py < H;
         float ddx = 0.f, ddy = 0.f;
         vis[k] = false;
@@ -389,7 +393,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         const uint32_t g = g_next;
         if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
         if (b0 + lane < end) {
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
             const float4 g1 = w.geom1[vbase + g];
             const float4 bb = footprint_box(g0, g1);
             hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
@@ -456,14 +460,14 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
 }
 
 // Grid form: one CTA per tile, warp w takes block w.
-template <bool kStats>
+template <bool kStats, int TW>
 __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w,
                                                                           uint32_t tile_base)
 {
     __shared__ WarpSmem sm[4];
     const int warp = threadIdx.x >> 5;
     unsigned long long cnt[3] = {0ull, 0ull, 0ull};
-    accumulate_block<kStats>(vs, w, tile_base + blockIdx.x, warp, sm[warp], cnt);
+    accumulate_block<kStats, TW>(vs, w, tile_base + blockIdx.x, warp, sm[warp], cnt);
     if (kStats) {
         atomicAdd(&w.stats[0], cnt[0]);
         atomicAdd(&w.stats[1], cnt[1]);
@@ -475,7 +479,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
 // (tile, block) items from a device-side queue (one atomic per item, ascending
 // tile order) until none are left.  Warps never wait for one another and no
 // CTA is launched per tile.
-template <bool kStats>
+template <bool kStats, int TW>
 __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(const ViewSet vs, const Work w,
                                                                                      uint32_t tile_base,
                                                                                      uint32_t ntiles,
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(cons
         if (lane == 0) item = atomicAdd(queue, 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= items) break;
-        accumulate_block<kStats>(vs, w, tile_base + (item >> 2), (int)(item & 3u), sm[warp], cnt);
+        accumulate_block<kStats, TW>(vs, w, tile_base + (item >> 2), (int)(item & 3u), sm[warp], cnt);
     }
     if (kStats) {
         atomicAdd(&w.stats[0], cnt[0]);
@@ -499,15 +503,30 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(cons
     }
 }
 
+template <bool kStats, int TW>
+void launch_2p(const ViewSet& vs, const Work& w, uint32_t tb, uint32_t NT, bool persistent, int resident_ctas,
+               cudaStream_t st)
+{
+    if (!persistent) {
+        k_raster_accumulate_2p<kStats, TW><<<NT, 128, 0, st>>>(vs, w, tb);
+    } else {
+        const uint32_t grid = (uint32_t)std::max<long long>(1, std::min<long long>(resident_ctas, (long long)NT));
+        k_raster_accumulate_2p_persistent<kStats, TW><<<grid, 128, 0, st>>>(vs, w, tb, NT, w.queue);
+    }
+}
+
 }  // namespace
 
 cudaError_t raster_prepare()
 {
-    // up to seven 28.5 KB CTAs per SM need the largest shared-memory carveout; set
+    // up to seven 27 KB CTAs per SM need the largest shared-memory carveout; set
     // once per context, outside any stream capture
-    const void* kerns[] = {(const void*)k_raster_accumulate_2p<false>, (const void*)k_raster_accumulate_2p<true>,
-                           (const void*)k_raster_accumulate_2p_persistent<false>,
-                           (const void*)k_raster_accumulate_2p_persistent<true>};
+    const void* kerns[] = {(const void*)k_raster_accumulate_2p<false, 16>, (const void*)k_raster_accumulate_2p<true, 16>,
+                           (const void*)k_raster_accumulate_2p_persistent<false, 16>,
+                           (const void*)k_raster_accumulate_2p_persistent<true, 16>,
+                           (const void*)k_raster_accumulate_2p<false, 32>, (const void*)k_raster_accumulate_2p<true, 32>,
+                           (const void*)k_raster_accumulate_2p_persistent<false, 32>,
+                           (const void*)k_raster_accumulate_2p_persistent<true, 32>};
     for (const void* k : kerns) {
         const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                                    (int)cudaSharedmemCarveoutMaxShared);
@@ -521,15 +540,21 @@ cudaError_t launch_raster_accumulate(const ViewSet& vs, const Work& w, uint32_t 
 {
     if (ntiles == 0 || vs.nmax == 0) return cudaSuccess;
     const uint32_t NT = ntiles, tb = tile_base;
-    if (variant == 0) {
-        if (stats) k_raster_accumulate_2p<true><<<NT, 128, 0, st>>>(vs, w, tb);
-        else k_raster_accumulate_2p<false><<<NT, 128, 0, st>>>(vs, w, tb);
-    } else if (variant == 5) {
-        const cudaError_t e = cudaMemsetAsync(w.queue, 0, sizeof(uint32_t), st);
-        if (e != cudaSuccess) return e;
-        const uint32_t grid = (uint32_t)std::max<long long>(1, std::min<long long>(resident_ctas, (long long)NT));
-        if (stats) k_raster_accumulate_2p_persistent<true><<<grid, 128, 0, st>>>(vs, w, tb, NT, w.queue);
-        else k_raster_accumulate_2p_persistent<false><<<grid, 128, 0, st>>>(vs, w, tb, NT, w.queue);
+    if (variant == 0 || variant == 5) {
+        if (variant == 5) {
+            const cudaError_t e = cudaMemsetAsync(w.queue, 0, sizeof(uint32_t), st);
+            if (e != cudaSuccess) return e;
+        }
+        const bool pers = variant == 5;
+        if (vs.tw == 32) {
+            if (stats) launch_2p<true, 32>(vs, w, tb, NT, pers, resident_ctas, st);
+            else launch_2p<false, 32>(vs, w, tb, NT, pers, resident_ctas, st);
+        } else {
+            if (stats) launch_2p<true, 16>(vs, w, tb, NT, pers, resident_ctas, st);
+            else launch_2p<false, 16>(vs, w, tb, NT, pers, resident_ctas, st);
+        }
+    } else if (vs.tw != kTile || vs.th != kTile) {
+        return cudaErrorInvalidValue;           // the warp-shuffle kernels tile 16 x 16 only
     } else if (variant == 1) {
         if (stats) k_raster_accumulate<1, true><<<NT, kTilePx, 0, st>>>(vs, w, tb);
         else k_raster_accumulate<1, false><<<NT, kTilePx, 0, st>>>(vs, w, tb);
@@ -547,7 +572,7 @@ int raster_resident_ctas(int device)
 {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_accumulate_2p_persistent<false>, 128, 0) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_accumulate_2p_persistent<false, 16>, 128, 0) !=
             cudaSuccess) {
         cudaGetLastError();
         return 148 * 4;

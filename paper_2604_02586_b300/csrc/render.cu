@@ -21,6 +21,8 @@ struct RenderSmem {
     float4 c[32];
 };
 
+// TW: tile width, 16 (16 x 16 tiles) or 32 (32 x 8), known at compile time.
+template <int TW>
 __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, const RenderOut& ro, uint32_t tile,
                                              int blk, RenderSmem& sm)
 {
@@ -28,7 +30,9 @@ __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, c
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int lane = threadIdx.x & 31;
-    const int bxo = (blk & 1) * 8, byo = (blk >> 1) * 8;
+    constexpr int TH = kTilePx / TW;
+    constexpr int nbx = TW / 8;                // 8x8 blocks per tile row
+    const int bxo = (blk % nbx) * 8, byo = (blk / nbx) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
     const size_t vbase = (size_t)vs.vrec[v];
     const float xc = (float)(bxo + (lane & 7)) + 0.5f;
@@ -37,7 +41,7 @@ __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, c
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int ly = byo + (lane >> 3) + 4 * k;
-        inside[k] = tx * kTile + bxo + (lane & 7) < W && ty * kTile + ly < H;
+        inside[k] = tx * TW + bxo + (lane & 7) < W && ty * TH + ly < H;
         yc[k] = (float)ly + 0.5f;
         T[k] = 1.0f;
         cr[k] = cg[k] = cb[k] = 0.f;
@@ -52,7 +56,7 @@ __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, c
         const uint32_t g = g_next;
         if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
         if (b0 + lane < end) {
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty);
+            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
             const float4 g1 = w.geom1[vbase + g];
             const float4 bb = footprint_box(g0, g1);
             hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
@@ -110,18 +114,19 @@ __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, c
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (!inside[k]) continue;
-        const size_t pix = (size_t)(ty * kTile + byo + (lane >> 3) + 4 * k) * W + (tx * kTile + bxo + (lane & 7));
+        const size_t pix = (size_t)(ty * TH + byo + (lane >> 3) + 4 * k) * W + (tx * TW + bxo + (lane & 7));
         float* o = ro.rgb[v] + 3 * pix;
         o[0] = cr[k]; o[1] = cg[k]; o[2] = cb[k];
         ro.T[v][pix] = T[k];
     }
 }
 
+template <int TW>
 __global__ void __launch_bounds__(128) k_raster_render(const ViewSet vs, const Work w, const RenderOut ro)
 {
     __shared__ RenderSmem sm[4];
     const int warp = threadIdx.x >> 5;
-    render_block(vs, w, ro, blockIdx.x, warp, sm[warp]);
+    render_block<TW>(vs, w, ro, blockIdx.x, warp, sm[warp]);
 }
 
 }  // namespace
@@ -132,7 +137,8 @@ cudaError_t launch_raster_render(const ViewSet& vs, const Work& w, uint32_t NT, 
     if (NT == 0) return cudaSuccess;
     RenderOut ro;
     for (int v = 0; v < vs.V; ++v) { ro.rgb[v] = rgb[v]; ro.T[v] = final_T[v]; }
-    k_raster_render<<<NT, 128, 0, st>>>(vs, w, ro);
+    if (vs.tw == 32) k_raster_render<32><<<NT, 128, 0, st>>>(vs, w, ro);
+    else k_raster_render<16><<<NT, 128, 0, st>>>(vs, w, ro);
     return cudaGetLastError();
 }
 

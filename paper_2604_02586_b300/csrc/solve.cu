@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const FitP
                 const float co1 = (M[7] - M[1] * Y01 - M[2] * Y11) * isw + rf.y;
                 A00 = 1.0f + Y00; A01 = Y10; A10 = Y01; A11 = 1.0f + Y11;
                 KeyProj p;
-                key_project(vs.cam[v], mo[g], q[g], s[g], vs.tiles_x[v], vs.tiles_y[v], p);
+                key_project(vs.cam[v], mo[g], q[g], s[g], vs.tiles_x[v], vs.tiles_y[v], vs.tw, vs.th, p);
                 float2 mxd, myd;
                 mean2d_df(vs.cam[v], mo[g], mxd, myd);
                 // shift of the centre: mu' - mu = c_o + (I - A) delta

@@ -187,12 +187,13 @@ def fp32_moment_rounding(scene, orc, ids, rel=2.0 ** -21, seed=7):
     return res
 
 
-def sensitivity(scene, orc, sample=None, rel=1e-6):
-    """Oracle response to FP32-sized perturbations (see the module docstring)."""
+def sensitivity(scene, orc, sample=None, rel=1e-6, options=None):
+    """Oracle response to FP32-sized perturbations (see the module docstring);
+    ``options``: the oracle options ``orc`` was computed with (tile shape)."""
     n = scene.n
     ids = np.arange(n) if sample is None else np.asarray(sample)
     per_view = "view_mean2d" in orc
-    o2 = oracle.fit_motion(perturbed(scene, rel), sample=sample, per_view=per_view)
+    o2 = oracle.fit_motion(perturbed(scene, rel), options, sample=sample, per_view=per_view)
     a = _response(scene, orc, o2, ids)
     if not per_view:
         return a

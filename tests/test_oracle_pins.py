@@ -129,11 +129,12 @@ def test_two_gaussians_composite_in_depth_order():
     np.testing.assert_allclose(col[0][pix], expect_c, atol=1e-6)
 
 
-def test_tiled_render_equals_bruteforce_with_rect():
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_tiled_render_equals_bruteforce_with_rect(tile):
     s = synth.make_scene("tiny", seed=5)
-    rgb, T, _ = oracle.render(s)
+    rgb, T, _ = oracle.render(s, tile=tile)
     for v in range(s.num_views):
-        bc, bT = oracle.render_bruteforce(s, v, use_rect=True)
+        bc, bT = oracle.render_bruteforce(s, v, use_rect=True, tile=tile)
         assert np.array_equal(bc, rgb[v]) and np.array_equal(bT, T[v])
 
 
@@ -166,9 +167,11 @@ def test_colour_basis_is_orthonormal():
 # Key path and binning (pin P10)
 # --------------------------------------------------------------------------
 
-def test_keypath_agrees_with_fp64_geometry():
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_keypath_agrees_with_fp64_geometry(tile):
+    tw, th = tile
     s = synth.make_scene("tiny", seed=2, tracks=False)
-    k = oracle.keys(s)
+    k = oracle.keys(s, tile=tile)
     cams = oracle.cameras(s)
     for v in range(s.num_views):
         R = s.R[v].astype(np.float64)
@@ -183,26 +186,28 @@ def test_keypath_agrees_with_fp64_geometry():
             lam = np.linalg.eigvalsh(Cd).max()
             r = math.ceil(3 * math.sqrt(lam))
             x0, y0, x1, y1 = k["rect"][v, g]
-            ex0 = max(0, math.floor((m2[0] - r) / 16))
-            ex1 = min(8, math.floor((m2[0] + r) / 16) + 1)
-            ey0 = max(0, math.floor((m2[1] - r) / 16))
-            ey1 = min(8, math.floor((m2[1] + r) / 16) + 1)
+            ex0 = max(0, math.floor((m2[0] - r) / tw))
+            ex1 = min(128 // tw, math.floor((m2[0] + r) / tw) + 1)
+            ey0 = max(0, math.floor((m2[1] - r) / th))
+            ey1 = min(128 // th, math.floor((m2[1] + r) / th) + 1)
             assert abs(x0 - ex0) <= 1 and abs(x1 - ex1) <= 1 and abs(y0 - ey0) <= 1 and abs(y1 - ey1) <= 1
             assert k["tiles_touched"][v, g] == (x1 - x0) * (y1 - y0)
 
 
-def test_tile_lists_match_lexsort():
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_tile_lists_match_lexsort(tile):
     """Per-tile lists equal a numpy lexsort of (tile, depth bits, index)."""
     s = synth.make_scene("tiny", seed=3, tracks=False)
-    k = oracle.keys(s)
-    offsets, entries = oracle.bin_lists(s)
+    tx_n = 128 // tile[0]                      # 64 tiles per 128 x 128 view either way
+    k = oracle.keys(s, tile=tile)
+    offsets, entries = oracle.bin_lists(s, tile=tile)
     tiles, depths, ids = [], [], []
     for v in range(s.num_views):
         for g in np.nonzero(k["visible"][v])[0]:
             x0, y0, x1, y1 = k["rect"][v, g]
             for ty in range(y0, y1):
                 for tx in range(x0, x1):
-                    tiles.append(v * 64 + ty * 8 + tx)
+                    tiles.append(v * 64 + ty * tx_n + tx)
                     depths.append(int(k["depth_bits"][v, g]))
                     ids.append(int(g))
     tiles, depths, ids = map(np.array, (tiles, depths, ids))

@@ -324,11 +324,52 @@ def test_bad_pointers_are_rejected_before_launch(gpu_ready):
 def test_options_are_validated(gpu_ready):
     import paper_2604_02586_b300 as tsp
     for bad in ({"cov_rcond_min": 0.0}, {"cov_rcond_min": 1.0}, {"raster_variant": 3},
-                {"tile_w": 32}, {"det_min": -1.0}, {"min_views": -1}):
+                {"tile_w": 32}, {"tile_w": 8, "tile_h": 32}, {"tile_w": 32, "tile_h": 8, "raster_variant": 2},
+                {"det_min": -1.0}, {"min_views": -1}):
         with pytest.raises(tsp.TspError):
             tsp.Context(0, **bad)
-    for ok in ({"cov_rcond_min": 1e-12}, {"raster_variant": 4}):
+    for ok in ({"cov_rcond_min": 1e-12}, {"raster_variant": 4}, {"tile_w": 32, "tile_h": 8},
+               {"tile_w": 32, "tile_h": 8, "raster_variant": 5}):
         tsp.Context(0, **ok).close()
+
+
+@pytest.mark.parametrize("name", ["tiny", "capture_sub"])
+def test_wide_tiles_bin_and_fit(gpu_ready, name):
+    """32 x 8 tiles (four 8x8 warp blocks in a row), with both two-phase raster
+    kernels: keys and tile lists equal the oracle's for that tile shape bit for
+    bit, and moments and fitted Gaussians meet the 16 x 16 bar."""
+    s = SCENES[name]()
+    opt = oracle.default_options(tile=(32, 8))
+    o = oracle.fit_motion(s, opt)
+    sens = P.sensitivity(s, o, options=opt)
+    k = oracle.keys(s, tile=(32, 8))
+    off, ent = oracle.bin_lists(s, tile=(32, 8))
+    for variant in (0, 5):
+        g = P.run_gpu(s, tile_w=32, tile_h=8, raster_variant=variant)
+        assert np.array_equal(g["rect"].astype(np.int32), k["rect"])
+        assert np.array_equal(g["touched"], k["tiles_touched"])
+        assert int(g["counts"][0]) == len(ent) and int(g["counts"][3]) == 0
+        assert np.array_equal(g["tile_off"].astype(np.int64), off)
+        assert np.array_equal(g["pairs"], ent)
+        check_moments(o, g)
+        check_fitted(s, g, o, sens)
+
+
+def test_wide_tiles_render(gpu_ready):
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s = SCENES["capture_sub"]()
+    d = P.to_device(s)
+    with tsp.Context(0, tile_w=32, tile_h=8) as ctx:
+        rgb, T = ctx.render(d["means_opacity"], d["quats"], d["scales"],
+                            torch.from_numpy(s.sh).cuda(), s.sh_degree, s, sync=True)
+    orgb, oT, fl = oracle.render(s, tile=(32, 8))
+    for v in range(s.num_views):
+        m = fl[v] == 0
+        assert (~m).mean() < EXCLUDED_MAX
+        ec = np.abs(rgb[v].cpu().numpy() - orgb[v]).max(-1)[m]
+        eT = np.abs(T[v].cpu().numpy() - oT[v])[m]
+        assert ec.max() < PIX_TOL and eT.max() < PIX_TOL, (ec.max(), eT.max())
 
 
 def test_full_capture_sampled(gpu_ready):

@@ -41,11 +41,11 @@ def dev(s):
     return t(s.means_opacity), t(s.quats), t(s.scales), t(s.sh)
 
 
-def gpu_grad(s, W):
+def gpu_grad(s, W, **opts):
     import torch
     import paper_2604_02586_b300 as tsp
     mo, q, sc, sh = dev(s)
-    with tsp.Context(0) as ctx:
+    with tsp.Context(0, **opts) as ctx:
         rgb, _ = ctx.render(mo, q, sc, sh, s.sh_degree, s, sync=True)
         gW = [torch.from_numpy(w).cuda() for w in W]
         g = ctx.render_backward(mo, q, sc, sh, s.sh_degree, s, rgb, gW, sync=True)
@@ -58,10 +58,11 @@ def close(a, b, rtol, atol_frac):
     return bad.mean(), np.abs(a - b).max(), np.abs(b).max()
 
 
-def test_gradient_matches_the_oracle(case):
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_gradient_matches_the_oracle(case, tile):
     s, W = case
-    o = oracle.render_grad(s, W)
-    g = gpu_grad(s, W)
+    o = oracle.render_grad(s, W, tile=tile)
+    g = gpu_grad(s, W, tile_w=tile[0], tile_h=tile[1])
     pairs = [("means", g["means_opacity"][:, :3], o["means"]), ("opacity", g["means_opacity"][:, 3], o["opacity"]),
              ("scales", g["scales"][:, :3], o["scales"]), ("quats", g["quats"], o["quats"]),
              ("sh", g["sh"], o["sh"])]
