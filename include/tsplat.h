@@ -191,11 +191,11 @@ tsp_status tsp_fit_motion(tsp_context* ctx, const tsp_gaussians* g, const tsp_ca
 tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int num_frames, void* stream);
 
 /* Autotuner: runs the motion fit on the given frames (outputs are written) with
- * each candidate (tile shape, raster kernel), in this order:
- *   0: 16 x 16, two-phase with one CTA per tile (variant 0)
+ * each candidate (tile shape, raster kernel and block shape), in this order:
+ *   0: 16 x 16, two-phase, 8x8 warp blocks, one CTA per tile (variant 0)
  *   1: 16 x 16, two-phase persistent over a work queue (variant 5)
- *   2: 16 x 16, warp-shuffle 8x8 blocks (variant 2)
- *   3: 32 x 8, variant 0          4: 32 x 8, variant 5
+ *   2, 3, 4: 16 x 16, warp-shuffle with 8x8, 8x4, 8x16 blocks (variants 2, 1, 4)
+ *   5: 32 x 8, variant 0          6: 32 x 8, variant 5
  * `repeats` timed times after one warm-up each (the pair buffer is sized
  * synchronously for each tile shape), and keeps the candidate whose median time
  * of the whole fit (binning differs between tile shapes) is lowest: the context's
@@ -203,7 +203,7 @@ tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int n
  * receives its index, fit_ms (nullable, [TSP_TUNE_CANDIDATES]) the medians in
  * that order.  Synchronises the stream.  Errors as tsp_fit_motion_batch; the
  * options are left unchanged on error. */
-#define TSP_TUNE_CANDIDATES 5
+#define TSP_TUNE_CANDIDATES 7
 tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats, void* stream,
                         int* chosen, float* fit_ms);
 

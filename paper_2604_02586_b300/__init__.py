@@ -314,7 +314,7 @@ class Context:
         return [p[5] for p in prep]
 
     # (tile_w, tile_h, raster_variant), in the order of tsp_autotune's candidates
-    TUNE_CANDIDATES = ((16, 16, 0), (16, 16, 5), (16, 16, 2), (32, 8, 0), (32, 8, 5))
+    TUNE_CANDIDATES = ((16, 16, 0), (16, 16, 5), (16, 16, 2), (16, 16, 1), (16, 16, 4), (32, 8, 0), (32, 8, 5))
 
     def autotune(self, frames, repeats=3, stream=None):
         """Time each candidate (tile shape, raster kernel) on ``frames``

@@ -66,7 +66,8 @@ constexpr size_t kAlign = 256;
 // Autotuner candidates (tile width, tile height, raster variant), in the order of
 // tsp_autotune's fit_ms: the warp-shuffle variant exists for 16 x 16 tiles only.
 constexpr int kTuneCandidates = TSP_TUNE_CANDIDATES;
-constexpr int kTuneTable[kTuneCandidates][3] = {{16, 16, 0}, {16, 16, 5}, {16, 16, 2}, {32, 8, 0}, {32, 8, 5}};
+constexpr int kTuneTable[kTuneCandidates][3] = {{16, 16, 0}, {16, 16, 5}, {16, 16, 2}, {16, 16, 1},
+                                                 {16, 16, 4}, {32, 8, 0}, {32, 8, 5}};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 

@@ -321,6 +321,28 @@ def test_bad_pointers_are_rejected_before_launch(gpu_ready):
         assert L.tsp_fit_motion(ctx._h, C.byref(g), carr, 33, tr, C.byref(r), None) == tsp.TSP.ERR_INVALID_ARG
 
 
+def test_sync_timeout_is_reported_and_the_context_recovers(gpu_ready):
+    """tsp_sync with a time limit returns TIMEOUT while the stream is still
+    busy (here with a bounded spin of about 0.1 s queued before the fit), leaves
+    the work running, and a later full sync and the next call succeed."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s, g, _, _ = case("tiny")
+    d = P.to_device(s)
+    # async_pairs: the call only enqueues (no host wait for the pair count)
+    with tsp.Context(0, async_pairs=1, pair_capacity=1 << 20) as ctx:
+        torch.cuda._sleep(200_000_000)              # ~0.1 s of GPU cycles, then it ends
+        out = ctx.fit_motion(d["means_opacity"], d["quats"], d["scales"], s, d["disp"], d["vis"])
+        with pytest.raises(tsp.TspError) as e:
+            ctx.sync(timeout_ms=1)
+        assert e.value.status == tsp.TSP.ERR_TIMEOUT
+        ctx.sync()
+        st = out["status"].cpu().numpy().view(np.uint32)
+        assert np.array_equal(st & 0xFF, g["status"] & 0xFF)
+        r = P.run_gpu(s, ctx=ctx, inspect=False)
+        assert np.array_equal(r["status"] & 0xFF, g["status"] & 0xFF)
+
+
 def test_options_are_validated(gpu_ready):
     import paper_2604_02586_b300 as tsp
     for bad in ({"cov_rcond_min": 0.0}, {"cov_rcond_min": 1.0}, {"raster_variant": 3},
