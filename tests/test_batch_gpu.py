@@ -81,6 +81,31 @@ def test_batch_tile_lists_bit_exact_per_frame(batch):
     assert int(inter["counts"][0]) == total and int(inter["counts"][3]) == 0
 
 
+def test_batch_with_wide_tiles_meets_the_oracle(gpu_ready):
+    """The batched launch with 32 x 8 tiles (the 100 x 70 frame is ragged in both
+    directions): each frame's tile lists equal the oracle's for that tile shape
+    bit for bit, and its fitted Gaussians meet the oracle bar."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    ss = scenes()
+    with tsp.Context(0, tile_w=32, tile_h=8) as ctx:
+        outs = ctx.fit_motion_batch([frame_args(s) for s in ss], sync=True)
+        torch.cuda.synchronize()
+        off_all = ctx.inspect(tsp.TSP.I_TILE_OFFSETS).astype(np.int64)
+        pairs = ctx.inspect(tsp.TSP.I_PAIRS)
+    opt = oracle.default_options(tile=(32, 8))
+    t0 = 0
+    for s, out in zip(ss, outs):
+        off, ent = oracle.bin_lists(s, tile=(32, 8))
+        nt = len(off) - 1
+        seg = off_all[t0:t0 + nt + 1]
+        assert np.array_equal(seg - seg[0], off)
+        assert np.array_equal(pairs[seg[0]:seg[-1]], ent)
+        t0 += nt
+        o = oracle.fit_motion(s, opt)
+        check_fitted(s, host(out), o, P.sensitivity(s, o, options=opt))
+
+
 def test_batch_frames_meet_the_oracle_bar(batch):
     ss, outs, _, _ = batch
     for s, g in zip(ss, outs):
