@@ -377,10 +377,14 @@ def test_wide_tiles_bin_and_fit(gpu_ready, name):
         check_fitted(s, g, o, sens)
 
 
-def test_wide_tiles_render(gpu_ready):
+@pytest.mark.parametrize("ragged", [False, True])
+def test_wide_tiles_render(gpu_ready, ragged):
+    """The colour render with 32 x 8 tiles against the oracle's; the ragged case
+    (100 x 70 pixels) leaves partial tiles in both directions."""
     import torch
     import paper_2604_02586_b300 as tsp
-    s = SCENES["capture_sub"]()
+    s = (synth.make_scene("tiny", 13, n=700, views=3, width=100, height=70, focal=80.0) if ragged
+         else SCENES["capture_sub"]())
     d = P.to_device(s)
     with tsp.Context(0, tile_w=32, tile_h=8) as ctx:
         rgb, T = ctx.render(d["means_opacity"], d["quats"], d["scales"],
