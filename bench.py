@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="capture preset: skip the compact batch / serve / train records")
     return ap.parse_args()
 
 
@@ -238,11 +240,70 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def start_extras(a, world):
+    """Generate the scenes of the compact batch, serve and train records in
+    worker processes (spawned before this process touches the GPU) while the
+    main measurement runs.  None when the records are not wanted."""
+    if a.no_extras or world > 1 or a.preset != "capture":
+        return None
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    pool = cf.ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) - 1)),
+                                  mp_context=mp.get_context("spawn"))
+    futs = {"batch": [pool.submit(frame_scene, sp) for sp in batch_specs()],
+            "serve": [pool.submit(frame_scene, sp) for sp in serve_specs()],
+            "train": pool.submit(train_scene)}
+    return pool, futs
+
+
+def run_extras(a, job):
+    """Compact records of the batched launch (8 uneven frame pairs: one at a time,
+    one batch call, CUDA-graph replay), the request loop against the plain path
+    (40 requests/s and a saturating 150/s) and the gradient-refinement step, each
+    bounded to a few seconds of timed work."""
+    import copy
+    import torch
+    pool, futs = job
+    t0 = time.perf_counter()
+    ex = {}
+    b = copy.copy(a)
+    b.steps, b.warmup = 5, 3
+    bs = [f.result() for f in futs["batch"]]
+    r = measure_batch(b, bs, "batch")
+    ex["batch"] = {"workload": r["config"]["workload"], "units_per_step": r["config"]["units_per_step"],
+                   "graph_replay": {"value": r["value"], "ms_per_step": r["ms_per_step"]},
+                   "one_at_a_time": {k: r["one_at_a_time"][k] for k in ("value", "ms_per_step")},
+                   "batched_no_graph": r["batched_no_graph"],
+                   "speedup_vs_one_at_a_time": r["speedup_vs_one_at_a_time"],
+                   "autotune": r["autotune"]["chosen"], "unit": UNIT, "steps": b.steps, "clocks": r["clocks"]}
+    del bs
+    torch.cuda.empty_cache()
+    ss = [f.result() for f in futs["serve"]]
+    ex["serve"] = {"workload": "scenes: " + ", ".join(f"{s.n}x{s.num_views}@{int(s.width[0])}x{int(s.height[0])}"
+                                                      for s in ss),
+                   "budget_bytes": 120 << 30, "max_inflight": 8,
+                   "at_40_per_s": serve_measure(ss, 40.0, 4.0), "at_150_per_s": serve_measure(ss, 150.0, 3.0)}
+    del ss
+    torch.cuda.empty_cache()
+    ts = futs["train"].result()
+    pool.shutdown()
+    step_ms, fwd_ms, clocks, loss, _ = train_measure(ts, 5, 3)
+    ex["train"] = {"workload": f"{ts.n} Gaussians, SH degree {ts.sh_degree}, {ts.num_views} views at "
+                               f"{int(ts.width[0])}x{int(ts.height[0])}, render + L1 + backward",
+                   "ms_per_step": float(np.mean(step_ms)), "p50_ms": float(np.percentile(step_ms, 50)),
+                   "forward_render_ms": float(np.mean(fwd_ms)),
+                   "value": ts.n * ts.num_views / (float(np.mean(step_ms)) / 1e3), "unit": "Gaussian·view/s",
+                   "steps": 5, "clocks": clocks}
+    ex["seconds"] = time.perf_counter() - t0
+    return ex
+
+
 def run_ours(a):
+    rank, world, local = dist_env()
+    job = start_extras(a, world)
     import torch
     import paper_2604_02586_b300 as tsp
     from paper_2604_02586_b300 import build as tbuild
-    rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -266,7 +327,8 @@ def run_ours(a):
     # exact raster work for the ALU roofline (counting variant, untimed)
     cnt = tsp.Context(local, collect_stats=1, async_pairs=1, pair_capacity=int(K * 1.1) + 1024)
     cnt.fit_motion(mo, q, s, cams, disp, vis, out=out, sync=True)
-    n_eval, n_blend, n_add, n_list = [int(x) for x in cnt.inspect(tsp.TSP.I_STATS)]
+    wstats = [int(x) for x in cnt.inspect(tsp.TSP.I_STATS)]
+    n_eval, n_blend, n_add, n_list = wstats[:4]
     cnt.close()
 
     ctx = tsp.Context(local, async_pairs=1, stage_timing=1, pair_capacity=int(K * 1.1) + 1024)
@@ -356,7 +418,8 @@ def run_ours(a):
                      "kernel": "k_raster_accumulate_2p",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit counts)",
                      "work": {"evaluations": n_eval, "blended": n_blend, "moment_adds": n_add,
-                              "list_entries": n_list, "pairs_K": K},
+                              "list_entries": n_list, "pairs_K": K, "block_hits": wstats[4],
+                              "adding_hits": wstats[5], "moment_passes": wstats[6], "walk_steps": wstats[7]},
                      "kernel_ms": t_r * 1e3},
         "hbm_step": hbm_step,
         "stage_ms": stage_mean,
@@ -367,23 +430,38 @@ def run_ours(a):
     }
     if not a.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene)
+    if job is not None:
+        ctx.close()
+        del disp, vis, flush
+        torch.cuda.empty_cache()
+        line["extras"] = run_extras(a, job)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def batch_scenes(seed=31, frames=8):
+def frame_scene(spec):
+    """A "frame" preset scene from (seed, n, views, width, height, focal)."""
+    import synth
+    sd, n, V, W, H, f = spec
+    return synth.make_scene("frame", seed=sd, n=n, views=V, width=W, height=H, focal=f)
+
+
+def batch_specs(seed=31, frames=8):
     """Eight frame pairs of uneven size: 50k-300k Gaussians, 12-24 views, each at
     1352x1014 (f = 1000) or 640x360 (f = 473), one rigid motion per frame."""
-    import synth
     rng = np.random.default_rng(seed)
     out = []
     for k in range(frames):
         n = int(rng.integers(50_000, 300_001))
         V = int(rng.integers(12, 25))
         W, H, f = (1352, 1014, 1000.0) if rng.random() < 0.5 else (640, 360, 473.0)
-        out.append(synth.make_scene("frame", seed=seed * 100 + k, n=n, views=V, width=W, height=H, focal=f))
+        out.append((seed * 100 + k, n, V, W, H, f))
     return out
+
+
+def batch_scenes(seed=31, frames=8):
+    return [frame_scene(sp) for sp in batch_specs(seed, frames)]
 
 
 def small_scenes(seed=41, frames=8):
@@ -485,42 +563,46 @@ def measure_batch(a, scenes, metric):
     return line
 
 
-def serve_scenes(seed=51, count=8):
+def serve_specs(seed=51, count=8):
     """Scene pool: Gaussian counts log-uniform in 20k-500k, 4-24 views at
     640x360, 960x540 or 1352x1014, one rigid motion each."""
-    import synth
     rng = np.random.default_rng(seed)
     res = [(640, 360, 473.0), (960, 540, 710.0), (1352, 1014, 1000.0)]
     out = []
     for k in range(count):
         n = int(round(np.exp(rng.uniform(np.log(20_000), np.log(500_000)))))
         W, H, f = res[int(rng.integers(0, 3))]
-        out.append(synth.make_scene("frame", seed=seed * 100 + k, n=n, views=int(rng.integers(4, 25)),
-                                    width=W, height=H, focal=f))
+        out.append((seed * 100 + k, n, int(rng.integers(4, 25)), W, H, f))
     return out
 
 
-def run_serve(a):
-    """Poisson arrivals of frame-pair requests over a pool of scenes, served by the
-    request loop (scene-resident, overlapped, HBM-budgeted) and by the plain
-    one-at-a-time path on the same arrival times; tracks come from pinned host
-    memory inside each request."""
+def serve_scenes(seed=51, count=8):
+    return [frame_scene(sp) for sp in serve_specs(seed, count)]
+
+
+def train_scene():
+    """300k Gaussians, SH degree 3, 16 views at 1352x1014 (no tracks)."""
+    import synth
+    return synth.make_scene("capture", seed=4, n=300_000, views=16, tracks=False)
+
+
+def serve_measure(scenes, rate, duration, seed=7):
+    """Poisson arrivals at ``rate`` per second for ``duration`` seconds over a pool
+    of scenes, served by the request loop (scene-resident, overlapped,
+    HBM-budgeted) and by the plain one-at-a-time path on the same arrival times;
+    tracks come from pinned host memory inside each request."""
     import copy
     import torch
     import paper_2604_02586_b300 as tsp
-    from paper_2604_02586_b300 import build as tbuild
     from paper_2604_02586_b300.serve import MotionServer, Request, latency_stats, one_at_a_time
-    tbuild.build()
-    torch.cuda.set_device(0)
-    scenes = serve_scenes()
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
     tracks = [([pin(d) for d in s.disp], [pin(v) for v in s.vis]) for s in scenes]
     cams = [tsp.cameras(s) for s in scenes]      # each scene's camera rig, built once
-    rng = np.random.default_rng(7)
+    rng = np.random.default_rng(seed)
     t, reqs = 0.0, []
     while True:
-        t += rng.exponential(1.0 / a.rate)
-        if t > a.duration:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
             break
         k = int(rng.integers(0, len(scenes)))
         reqs.append(Request(len(reqs), f"s{k}", cams[k], tracks[k][0], tracks[k][1], arrival=t))
@@ -535,7 +617,8 @@ def run_serve(a):
         srv.finished = []
         done = srv.run(copy.copy(r) for r in reqs)
         stats = latency_stats(done, units)
-        stats.update(evictions=srv.evictions, retries=srv.retries, peak_budget_bytes=srv.peak_bytes)
+        stats.update(evictions=srv.evictions, retries=srv.retries, failed=len(srv.failed),
+                     peak_budget_bytes=srv.peak_bytes)
         srv.close()
         return stats
 
@@ -546,8 +629,19 @@ def run_serve(a):
 
     plain()                                                    # warm-up of the plain path
     srv_stats, plain_stats = serve(), plain()
+    return dict(rate_per_s=rate, duration_s=duration, requests=len(reqs), server=srv_stats, one_at_a_time=plain_stats)
+
+
+def run_serve(a):
+    import torch
+    from paper_2604_02586_b300 import build as tbuild
+    tbuild.build()
+    torch.cuda.set_device(0)
+    scenes = serve_scenes()
+    r = serve_measure(scenes, a.rate, a.duration)
+    srv_stats, plain_stats = r["server"], r["one_at_a_time"]
     line = {"metric": f"frame-pair requests: p50/p99 latency and fits/s at {a.rate:g} req/s (Poisson)",
-            "value": srv_stats["fits_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": len(scenes),
+            "value": srv_stats["fits_per_s"], "unit": UNIT, "n_gpus": 1, "steps": r["requests"], "warmup": len(scenes),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "scenes: " + ", ".join(f"{s.n}x{s.num_views}@{int(s.width[0])}x{int(s.height[0])}"
@@ -559,21 +653,17 @@ def run_serve(a):
     print(json.dumps(line), flush=True)
 
 
-def run_train(a):
-    """One gradient-refinement step: the differentiable render (forward) of 300k
-    Gaussians with degree-3 colour in 16 views at 1352x1014, an L1 loss against
-    renders of the ground-truth-moved Gaussians, and the hand-written backward
-    with respect to means, log-scales, quaternions, opacity logits and colour."""
+def train_measure(s, steps, warmup):
+    """One gradient-refinement step: the differentiable render (forward) of the
+    scene's Gaussians with degree-3 colour, an L1 loss against renders of the
+    ground-truth-moved Gaussians, and the hand-written backward with respect to
+    means, log-scales, quaternions, opacity logits and colour.  Returns
+    (per-step ms, forward-only ms, clock summary, loss, gradient norms)."""
     import torch
     from scipy.spatial.transform import Rotation
     import paper_2604_02586_b300 as tsp
-    from paper_2604_02586_b300 import build as tbuild
     from paper_2604_02586_b300.autograd import render
-    import synth
-    tbuild.build()
-    torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    s = synth.make_scene("capture", seed=4, n=300_000, views=16, tracks=False)
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
     # targets: renders of the Gaussians after their ground-truth rigid motion
     qx = s.quats[:, [1, 2, 3, 0]].astype(np.float64)
@@ -606,7 +696,7 @@ def run_train(a):
             return render(params["means"], params["log_scales"], params["quats"], params["logits"], params["sh"], cams, ctx)
 
     def timed(fn, steps):
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         ms = []
@@ -621,11 +711,21 @@ def run_train(a):
                 ms.append(e0.elapsed_time(e1))
         return ms, clk.summary()
 
-    step_ms, clocks = timed(step, a.steps)
-    fwd_ms, _ = timed(fwd, a.steps)
+    step_ms, clocks = timed(step, steps)
+    fwd_ms, _ = timed(fwd, steps)
     loss = float(step().detach())
     gnorm = {k: float(v.grad.norm()) for k, v in params.items()}
     ctx.close()
+    return step_ms, fwd_ms, clocks, loss, gnorm
+
+
+def run_train(a):
+    import torch
+    from paper_2604_02586_b300 import build as tbuild
+    tbuild.build()
+    torch.cuda.set_device(0)
+    s = train_scene()
+    step_ms, fwd_ms, clocks, loss, gnorm = train_measure(s, a.steps, a.warmup)
     units = s.n * s.num_views
     line = {"metric": "gradient-refinement step (render + L1 + backward): Gaussian·view gradients/s",
             "value": units / (float(np.mean(step_ms)) / 1e3), "unit": "Gaussian·view/s", "n_gpus": 1,

@@ -148,6 +148,15 @@ typedef struct tsp_options {
                                 /*    pixels per thread (8x4, 8x8, 8x16 blocks)     */
     int64_t pair_capacity;      /* initial (tile, Gaussian) pair capacity, 0 = auto */
     int64_t budget_bytes;       /* workspace ceiling, 0 = unlimited                */
+    int32_t checked;            /* 1: checked mode (debugging): every index a      */
+                                /*    kernel takes from data -- a (record, tile)   */
+                                /*    item's tile and list slot, tile ranges, the  */
+                                /*    moment origin's pixel, a list entry's        */
+                                /*    Gaussian -- is tested against its buffer     */
+                                /*    before use; a failed test skips the access   */
+                                /*    and is recorded in the device status word,   */
+                                /*    which tsp_sync reports as TSP_ERR_CUDA with  */
+                                /*    the site.  0 (default): no tests             */
 } tsp_options;
 
 typedef struct tsp_context tsp_context;
@@ -341,9 +350,12 @@ typedef enum {
     TSP_I_TILE_OFFSETS = 4,  /* uint32[NT+1]: tile t owns pairs [off[t], off[t+1])   */
     TSP_I_PAIRS = 5,         /* uint64[K]: depth_bits << 32 | Gaussian, sorted per tile */
     TSP_I_MOMENTS = 6,       /* float[V][n][16], layout as view_moments              */
-    TSP_I_STATS = 7,         /* uint64[4] raster work of the last call when           */
+    TSP_I_STATS = 7,         /* uint64[8] raster work of the last call when           */
                              /* collect_stats = 1: (pixel, Gaussian) evaluations,     */
-                             /* blended contributions, moment additions, list entries */
+                             /* blended contributions, moment additions, list entries;*/
+                             /* two-phase kernels also: block hits (entries whose     */
+                             /* alpha >= 1/255 ellipse meets an 8x8 block), hits that */
+                             /* add a pixel, moment passes, 32-entry walk steps       */
     TSP_I_VIEW_MEANS = 8,    /* float[V][n][4]: mu_2D' (x, y) and its shift from mu_2D */
     TSP_I_VIEW_COV = 9,      /* float[V][n][8]: rows of B with Sigma_2D' = B B^T     */
                              /* (B00 B01 B02 sum-w, B10 B11 B12 0)                     */
@@ -365,7 +377,8 @@ tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count);
  * -- code running while a CUDA graph is being captured, memory-capped tenants
  * of a shared GPU, hosts whose own allocator owns all device memory.
  * keys: device [num_keys] (depth_bits << 32 | Gaussian), sorted ascending in
- * place within each tile t's slice [offsets[t], offsets[t+1]); offsets: device
+ * place within each tile t's slice [offsets[t], offsets[t+1]); keys need not be
+ * unique (equal keys are equal values, so their order is immaterial); offsets: device
  * [num_tiles + 1], non-decreasing, offsets[num_tiles] = num_keys (slices are
  * clamped to num_keys).  Both on the current CUDA device; keys 8-byte aligned.
  * The merge scratch for long lists lives in a fixed array inside the library
@@ -379,6 +392,29 @@ tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count);
 #define TSP_NOALLOC_SORT_MAX_KEYS (1u << 20)
 tsp_status tsp_sort_tiles_noalloc(uint64_t* keys, const uint32_t* offsets, uint32_t num_tiles,
                                   uint32_t num_keys, void* stream);
+
+/* Workspace allocator hook.  The context's device buffers (sort buffers, moment
+ * records, per-view results, staging) come from alloc(bytes, device, user) and
+ * go back through release(ptr, bytes, device, user) instead of cudaMalloc and
+ * cudaFree: a host whose own allocator owns the device memory (a framework's
+ * caching allocator, a tenant with a fixed pool) hands its allocator in here.
+ * alloc returns device memory on `device`, 256-byte aligned, or NULL to refuse
+ * (the call that needed it then fails with TSP_ERR_OOM, nothing of it enqueued,
+ * and the context stays usable).  Both NULL restores cudaMalloc / cudaFree.
+ * The call waits for the device, returns the current workspace to the allocator
+ * that gave it, and installs the new pair; later calls allocate afresh.  The
+ * pointers must stay valid until the context is destroyed or the hook replaced.
+ * Errors: INVALID_ARG (ctx NULL, exactly one of alloc / release NULL), CUDA. */
+typedef void* (*tsp_alloc_fn)(size_t bytes, int device, void* user);
+typedef void (*tsp_free_fn)(void* ptr, size_t bytes, int device, void* user);
+tsp_status tsp_set_allocator(tsp_context* ctx, tsp_alloc_fn alloc, tsp_free_fn release, void* user);
+
+/* Replace the workspace ceiling (options.budget_bytes; 0 = unlimited).  A call
+ * whose workspace would grow past it fails with TSP_ERR_BUDGET before any of its
+ * work is enqueued (with async_pairs = 0, a pair buffer grown after the count
+ * fails the same way, before the scatter).  Held workspace is not shrunk.
+ * Errors: INVALID_ARG (ctx NULL, budget_bytes < 0). */
+tsp_status tsp_set_budget(tsp_context* ctx, int64_t budget_bytes);
 
 /* Bytes of device workspace the context currently holds. */
 tsp_status tsp_workspace_bytes(const tsp_context* ctx, size_t* bytes);

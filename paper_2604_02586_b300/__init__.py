@@ -78,8 +78,12 @@ class Options(C.Structure):
                 ("min_views", C.c_int32), ("sumw_min_total", C.c_float), ("min_px_total", C.c_int32),
                 ("cov_rcond_min", C.c_float), ("async_pairs", C.c_int32), ("stage_timing", C.c_int32),
                 ("collect_stats", C.c_int32), ("raster_variant", C.c_int32),
-                ("pair_capacity", C.c_int64), ("budget_bytes", C.c_int64)]
+                ("pair_capacity", C.c_int64), ("budget_bytes", C.c_int64), ("checked", C.c_int32)]
 
+
+# tsp_alloc_fn / tsp_free_fn
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_int, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p)
 
 _lib = None
 
@@ -109,6 +113,8 @@ def lib():
         L.tsp_inspect.argtypes = [P, I, P, C.c_size_t, P]
         L.tsp_workspace_bytes.argtypes = [P, P]
         L.tsp_stage_times.argtypes = [P, P, I, P]
+        L.tsp_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
+        L.tsp_set_budget.argtypes = [P, C.c_int64]
         L.tsp_sort_tiles_noalloc.argtypes = [P, P, C.c_uint32, C.c_uint32, P]
         L.tsp_sort_tiles_noalloc.restype = I
         L.tsp_status_string.argtypes = [I]
@@ -119,7 +125,7 @@ def lib():
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
                      "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render",
                      "tsp_render_backward", "tsp_sync", "tsp_inspect", "tsp_default_reg_options",
-                     "tsp_regularize", "tsp_knn",
+                     "tsp_regularize", "tsp_knn", "tsp_set_allocator", "tsp_set_budget",
                      "tsp_workspace_bytes", "tsp_stage_times"):
             getattr(L, name).restype = I
         _lib = L
@@ -232,6 +238,26 @@ class Context:
 
     def __enter__(self):
         return self
+
+    def set_allocator(self, alloc=None, free=None):
+        """Route the workspace through alloc(bytes, device) -> int device pointer
+        (256-byte aligned) or None to refuse, and free(ptr, bytes, device);
+        both None restores cudaMalloc / cudaFree (tsp_set_allocator)."""
+        if (alloc is None) != (free is None):
+            raise ValueError("give both alloc and free, or neither")
+        if alloc is None:
+            self._alloc_cb = self._free_cb = None
+            self._check(lib().tsp_set_allocator(self._h, ALLOC_FN(), FREE_FN(), None), "tsp_set_allocator")
+            return
+        a = ALLOC_FN(lambda nbytes, device, user: alloc(int(nbytes), int(device)))
+        f = FREE_FN(lambda ptr, nbytes, device, user: free(int(ptr), int(nbytes), int(device)))
+        self._check(lib().tsp_set_allocator(self._h, a, f, None), "tsp_set_allocator")
+        self._alloc_cb, self._free_cb = a, f          # the library keeps calling these
+
+    def set_budget(self, budget_bytes: int):
+        """Workspace ceiling in bytes, 0 = unlimited (tsp_set_budget)."""
+        self._check(lib().tsp_set_budget(self._h, int(budget_bytes)), "tsp_set_budget")
+        self.opt.budget_bytes = int(budget_bytes)
 
     def __exit__(self, *exc):
         self.close()

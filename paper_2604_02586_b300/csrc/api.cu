@@ -9,6 +9,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 
 using namespace tsp;
@@ -28,7 +30,7 @@ struct tsp_context {
     std::string err;
     size_t held = 0;
     // per (view, Gaussian)
-    Buf rect, depth, touched, geom0, geom1, dref, oref, color, moments, vres0, vres1, vres2, vres3;
+    Buf rect, depth, touched, geom0, geom1, cull, dref, oref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
     Buf tiles, tile_off, span_sum, queue;
     Buf gacc;                       // render backward: per (view, Gaussian) 2D gradients
@@ -38,7 +40,11 @@ struct tsp_context {
     Buf pairs, pairs_tmp;
     uint64_t want_pairs = 0;
     Buf dstatus, stats;
-    uint32_t* h_status = nullptr;   // pinned, 4 words
+    uint32_t* h_status = nullptr;   // pinned, 8 words (the device status word's copy)
+    // workspace allocator (tsp_set_allocator); nullptr: cudaMalloc / cudaFree
+    tsp_alloc_fn alloc_fn = nullptr;
+    tsp_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
     cudaEvent_t ev[8] = {};         // stage boundaries (stage_timing)
     bool timed = false;             // the last call recorded ev[]
     // staging for tsp_fit_motion_host: tracks stream in on copy_stream, one event
@@ -71,6 +77,15 @@ constexpr int kTuneTable[kTuneCandidates][3] = {{16, 16, 0}, {16, 16, 5}, {16, 1
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// An NVTX range over the launches of one pipeline step ("tsp:raster", ...), so
+// that profiler captures can be sliced by step (ncu --nvtx --nvtx-include).
+struct StageRange {
+    explicit StageRange(const char* name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange&) = delete;
+    StageRange& operator=(const StageRange&) = delete;
+};
+
 tsp_status fail(tsp_context* c, tsp_status s, const std::string& msg)
 {
     if (c) c->err = msg;
@@ -101,6 +116,8 @@ private:
     int old_ = 0;
 };
 
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
 tsp_status ensure(tsp_context* ctx, Buf& b, size_t need)
 {
     if (need <= b.bytes) return TSP_OK;
@@ -113,17 +130,35 @@ tsp_status ensure(tsp_context* ctx, Buf& b, size_t need)
                                                  " bytes exceeds the budget");
     }
     if (b.p) {
-        cudaError_t e = cudaFree(b.p);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
+        if (ctx->free_fn) {
+            // work queued earlier may still use the block: hand it back only once
+            // the device is idle, as cudaFree would
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceSynchronize");
+            ctx->free_fn(b.p, b.bytes, ctx->device, ctx->alloc_user);
+        } else {
+            cudaError_t e = cudaFree(b.p);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
+        }
         ctx->held -= b.bytes;
         b.p = nullptr;
         b.bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&b.p, nb);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        b.p = nullptr;
-        return fail(ctx, TSP_ERR_OOM, "cudaMalloc of " + std::to_string(nb) + " bytes failed");
+    if (ctx->alloc_fn) {
+        void* p = ctx->alloc_fn(nb, ctx->device, ctx->alloc_user);
+        if (!p) return fail(ctx, TSP_ERR_OOM, "the allocator refused " + std::to_string(nb) + " bytes");
+        if (!aligned(p, kAlign)) {
+            ctx->free_fn(p, nb, ctx->device, ctx->alloc_user);
+            return fail(ctx, TSP_ERR_OOM, "the allocator returned a block not aligned to 256 bytes");
+        }
+        b.p = p;
+    } else {
+        cudaError_t e = cudaMalloc(&b.p, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(ctx, TSP_ERR_OOM, "cudaMalloc of " + std::to_string(nb) + " bytes failed");
+        }
     }
     b.bytes = nb;
     ctx->held += nb;
@@ -132,12 +167,29 @@ tsp_status ensure(tsp_context* ctx, Buf& b, size_t need)
 
 void release(tsp_context* ctx, Buf& b)
 {
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        if (ctx->free_fn) ctx->free_fn(b.p, b.bytes, ctx->device, ctx->alloc_user);
+        else cudaFree(b.p);
+    }
     ctx->held -= b.bytes;
     b = Buf{};
 }
 
-bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+// Every device buffer of the workspace (not the pinned status words).
+void release_workspace(tsp_context* ctx)
+{
+    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->cull, &ctx->dref, &ctx->oref, &ctx->color,
+                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off,
+                  &ctx->span_sum, &ctx->queue, &ctx->gacc, &ctx->reg, &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus,
+                  &ctx->stats, &ctx->st_in, &ctx->st_out, &ctx->st_tracks};
+    for (Buf* b : all) release(ctx, *b);
+    ctx->last_R = 0;
+    ctx->last_NT = 0;
+    ctx->last_fit_n = ctx->last_fit_V = -1;
+    ctx->last_knn_path = nullptr;
+    ctx->render_bins = false;
+}
+
 
 bool device_accessible(const void* p, int dev)
 {
@@ -170,6 +222,7 @@ tsp_status check_options(tsp_context* ctx, const tsp_options& o)
         return fail(ctx, TSP_ERR_INVALID_ARG, "32x8 tiles need raster_variant 0 or 5");
     if (o.pair_capacity < 0 || o.pair_capacity > INT32_MAX || o.budget_bytes < 0)
         return fail(ctx, TSP_ERR_INVALID_ARG, "bad pair_capacity or budget_bytes");
+    if (o.checked != 0 && o.checked != 1) return fail(ctx, TSP_ERR_INVALID_ARG, "checked must be 0 or 1");
     return TSP_OK;
 }
 
@@ -301,6 +354,7 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     if ((s = ensure(ctx, ctx->touched, vn1 * 4))) return s;
     if ((s = ensure(ctx, ctx->geom0, vn1 * 16))) return s;
     if ((s = ensure(ctx, ctx->geom1, vn1 * 16))) return s;
+    if ((s = ensure(ctx, ctx->cull, vn1 * 16))) return s;
     if ((s = ensure(ctx, ctx->dref, vn1 * 8))) return s;
     if (!render && (s = ensure(ctx, ctx->oref, vn1 * 4))) return s;
     if (render) {
@@ -322,14 +376,15 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     if (cap > (uint64_t)INT32_MAX) cap = INT32_MAX;
     if ((s = ensure(ctx, ctx->pairs, cap * 8))) return s;
     if ((s = ensure(ctx, ctx->pairs_tmp, cap * 8))) return s;
-    if ((s = ensure(ctx, ctx->dstatus, 16))) return s;
-    if ((s = ensure(ctx, ctx->stats, 32))) return s;
+    if ((s = ensure(ctx, ctx->dstatus, 32))) return s;
+    if ((s = ensure(ctx, ctx->stats, 64))) return s;
     w.stats = (unsigned long long*)ctx->stats.p;
     w.rect = (short4*)ctx->rect.p;
     w.depth = (uint32_t*)ctx->depth.p;
     w.touched = (uint32_t*)ctx->touched.p;
     w.geom0 = (float4*)ctx->geom0.p;
     w.geom1 = (float4*)ctx->geom1.p;
+    w.cull = (float4*)ctx->cull.p;
     w.dref = (float2*)ctx->dref.p;
     w.oref = (uint32_t*)ctx->oref.p;
     w.color = (float4*)ctx->color.p;
@@ -348,6 +403,8 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     const uint64_t have = ctx->pairs.bytes / 8 < ctx->pairs_tmp.bytes / 8 ? ctx->pairs.bytes / 8 : ctx->pairs_tmp.bytes / 8;
     w.cap = (uint32_t)(have > (uint64_t)INT32_MAX ? INT32_MAX : have);
     w.dstatus = (uint32_t*)ctx->dstatus.p;
+    w.nt = NT;
+    w.checked = ctx->opt.checked ? 1u : 0u;
     return TSP_OK;
 }
 
@@ -361,12 +418,18 @@ tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const float* sh, int s
                      uint32_t NT, Work& w, cudaStream_t st)
 {
     TSP_CUDA(mark(ctx, 0, st));
-    TSP_CUDA(cudaMemsetAsync(ctx->tiles.p, 0, (size_t)2 * (NT + 1) * kCounterStride * 4, st));
-    TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 16, st));
-    if (ctx->opt.collect_stats) TSP_CUDA(cudaMemsetAsync(w.stats, 0, 32, st));
-    TSP_CUDA(launch_preprocess(vs, sh, sh_degree, mode, w, st));
+    {
+        StageRange r("tsp:project");
+        TSP_CUDA(cudaMemsetAsync(ctx->tiles.p, 0, (size_t)2 * (NT + 1) * kCounterStride * 4, st));
+        TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 32, st));
+        if (ctx->opt.collect_stats) TSP_CUDA(cudaMemsetAsync(w.stats, 0, 64, st));
+        TSP_CUDA(launch_preprocess(vs, sh, sh_degree, mode, w, st));
+    }
     TSP_CUDA(mark(ctx, 1, st));
-    TSP_CUDA(launch_scan(w, NT, st));
+    {
+        StageRange r("tsp:scan");
+        TSP_CUDA(launch_scan(w, NT, st));
+    }
     TSP_CUDA(mark(ctx, 2, st));
     if (!ctx->opt.async_pairs) {
         TSP_CUDA(cudaMemcpyAsync(ctx->h_status, w.dstatus, 16, cudaMemcpyDeviceToHost, st));
@@ -385,9 +448,15 @@ tsp_status bin_front(tsp_context* ctx, const ViewSet& vs, const float* sh, int s
             TSP_CUDA(cudaMemsetAsync(w.dstatus, 0, 4, st));
         }
     }
-    TSP_CUDA(launch_scatter(vs, w, st));
+    {
+        StageRange r("tsp:emit");
+        TSP_CUDA(launch_scatter(vs, w, st));
+    }
     TSP_CUDA(mark(ctx, 3, st));
-    TSP_CUDA(launch_tile_sort(w, NT, st));
+    {
+        StageRange r("tsp:tile_sort");
+        TSP_CUDA(launch_tile_sort(w, NT, st));
+    }
     TSP_CUDA(mark(ctx, 4, st));
     return TSP_OK;
 }
@@ -449,18 +518,27 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
     ctx->timed = false;
     if ((s = bin_front(ctx, vs, nullptr, 0, 0, NT, w, st))) return s;
     if (group <= 0) group = V;
-    for (int v0 = 0, k = 0; v0 < V; v0 += group, ++k) {
-        const int v1 = std::min(V, v0 + group);
-        if (ready) TSP_CUDA(cudaStreamWaitEvent(st, ready[k], 0));
-        TSP_CUDA(launch_dref(vs, w, v0, v1, st));
-        TSP_CUDA(launch_raster_accumulate(vs, w, vs.toff[v0], vs.toff[v1] - vs.toff[v0],
-                                          ctx->opt.collect_stats != 0, ctx->opt.raster_variant,
-                                          ctx->resident_ctas, st));
+    {
+        StageRange r("tsp:raster");
+        for (int v0 = 0, k = 0; v0 < V; v0 += group, ++k) {
+            const int v1 = std::min(V, v0 + group);
+            if (ready) TSP_CUDA(cudaStreamWaitEvent(st, ready[k], 0));
+            TSP_CUDA(launch_dref(vs, w, v0, v1, st));
+            TSP_CUDA(launch_raster_accumulate(vs, w, vs.toff[v0], vs.toff[v1] - vs.toff[v0],
+                                              ctx->opt.collect_stats != 0, ctx->opt.raster_variant,
+                                              ctx->resident_ctas, st));
+        }
     }
     TSP_CUDA(mark(ctx, 5, st));
-    TSP_CUDA(launch_view_solve(vs, fp, w, fo, st));
+    {
+        StageRange r("tsp:view_solve");
+        TSP_CUDA(launch_view_solve(vs, fp, w, fo, st));
+    }
     TSP_CUDA(mark(ctx, 6, st));
-    TSP_CUDA(launch_multiview(vs, fp, w, fo, st));
+    {
+        StageRange r("tsp:multiview");
+        TSP_CUDA(launch_multiview(vs, fp, w, fo, st));
+    }
     TSP_CUDA(mark(ctx, 7, st));
     ctx->timed = ctx->opt.stage_timing != 0;
     for (int f = 0; f < F; ++f) {
@@ -506,7 +584,7 @@ tsp_status ensure_reg(tsp_context* ctx, int n, int k, KnnWork& kw, RegParams* rp
     tsp_status s;
     if ((s = ensure(ctx, ctx->reg, off))) return s;
     if (!ctx->dstatus.p) {
-        if ((s = ensure(ctx, ctx->dstatus, 16))) return s;
+        if ((s = ensure(ctx, ctx->dstatus, 32))) return s;
         TSP_CUDA(cudaMemset(ctx->dstatus.p, 0, 16));
     }
     kw.err = (uint32_t*)ctx->dstatus.p;
@@ -660,7 +738,7 @@ tsp_status tsp_create(int device, const tsp_options* opt, tsp_context** out)
     tsp_status s = check_options(ctx, ctx->opt);
     if (s) { delete ctx; return s; }
     DeviceGuard dg(device);
-    if (cudaMallocHost(&ctx->h_status, 16) != cudaSuccess) {
+    if (cudaMallocHost(&ctx->h_status, 32) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return TSP_ERR_CUDA;
@@ -686,11 +764,7 @@ tsp_status tsp_destroy(tsp_context* ctx)
     if (!ctx) return TSP_OK;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->dref, &ctx->oref, &ctx->color,
-                  &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off, &ctx->span_sum, &ctx->queue, &ctx->gacc, &ctx->reg,
-                  &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus, &ctx->stats, &ctx->st_in, &ctx->st_out,
-                  &ctx->st_tracks};
-    for (Buf* b : all) release(ctx, *b);
+    release_workspace(ctx);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->group_ev)
@@ -698,6 +772,25 @@ tsp_status tsp_destroy(tsp_context* ctx)
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
+    return TSP_OK;
+}
+
+tsp_status tsp_set_allocator(tsp_context* ctx, tsp_alloc_fn alloc, tsp_free_fn release_fn, void* user)
+{
+    if (!ctx || (alloc == nullptr) != (release_fn == nullptr)) return TSP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    TSP_CUDA(cudaDeviceSynchronize());
+    release_workspace(ctx);
+    ctx->alloc_fn = alloc;
+    ctx->free_fn = release_fn;
+    ctx->alloc_user = user;
+    return TSP_OK;
+}
+
+tsp_status tsp_set_budget(tsp_context* ctx, int64_t budget_bytes)
+{
+    if (!ctx || budget_bytes < 0) return TSP_ERR_INVALID_ARG;
+    ctx->opt.budget_bytes = budget_bytes;
     return TSP_OK;
 }
 
@@ -931,8 +1024,16 @@ tsp_status tsp_sync(tsp_context* ctx, void* stream, int timeout_ms)
         }
     }
     if (!ctx->dstatus.p) return TSP_OK;
-    TSP_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->dstatus.p, 16, cudaMemcpyDeviceToHost, st));
+    TSP_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->dstatus.p, 32, cudaMemcpyDeviceToHost, st));
     TSP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->h_status[0] & kStatusChecked) {
+        const uint32_t site = ctx->h_status[4], count = ctx->h_status[5];
+        TSP_CUDA(cudaMemsetAsync(ctx->dstatus.p, 0, 32, st));
+        TSP_CUDA(cudaStreamSynchronize(st));
+        return fail(ctx, TSP_ERR_CUDA, std::string("checked mode: an index left its buffer at ") +
+                                           check_site_name(site) + " (site " + std::to_string(site) + ", " +
+                                           std::to_string(count) + " times); results are invalid");
+    }
     if (ctx->h_status[0] & kStatusInternal) {
         TSP_CUDA(cudaMemsetAsync(ctx->dstatus.p, 0, 4, st));
         TSP_CUDA(cudaStreamSynchronize(st));
@@ -976,7 +1077,7 @@ tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, siz
         src = ctx->pairs.p; size = (size_t)K * 8; break;
     }
     case TSP_I_MOMENTS: src = ctx->moments.p; size = vn * 64; break;
-    case TSP_I_STATS: src = ctx->stats.p; size = ctx->stats.p ? 32 : 0; break;
+    case TSP_I_STATS: src = ctx->stats.p; size = ctx->stats.p ? 64 : 0; break;
     case TSP_I_KNN_PATH: src = ctx->last_knn_path; size = ctx->last_knn_path ? 8 : 0; break;
     case TSP_I_VIEW_MEANS: src = ctx->vres0.p; size = vn * 16; break;
     case TSP_I_VIEW_COV: {

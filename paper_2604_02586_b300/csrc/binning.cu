@@ -100,8 +100,10 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
             const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * vs.tw)), ux.y);
             const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * vs.th)), uy.y);
             w.geom0[i] = make_float4(rx, ry, f.x, f.y);
-            const float2 dlt = moment_origin_shift(ux, uy, vs.cam[v].W, vs.cam[v].H);
+            const float2 dlt = moment_origin_shift(ux, uy, rx, ry, p.x0 * vs.tw, p.y0 * vs.th,
+                                                   vs.cam[v].W, vs.cam[v].H);
             w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);
+            w.cull[i] = cull_record(f.x, f.y, f.z, m.w);
             if (mode == 0) {
                 // the pixel holding the moment origin; k_dref reads the track there
                 const int W = vs.cam[v].W, H = vs.cam[v].H;
@@ -150,7 +152,13 @@ __global__ void __launch_bounds__(256) k_dref(const ViewSet vs, Work w, int v0)
     if (g >= vs.vn[v]) return;
     const size_t i = (size_t)vs.vrec[v] + g;
     if (w.touched[i] == 0u) return;
-    w.dref[i] = vs.disp[v][w.oref[i]];
+    const uint32_t pix = w.oref[i];
+    if (w.checked && !pixel_ok(pix, (uint32_t)vs.cam[v].W, (uint32_t)vs.cam[v].H)) {
+        check_failed(w.dstatus, kSiteRefPixel);
+        w.dref[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    w.dref[i] = vs.disp[v][pix];
 }
 
 // Exclusive scan of the NT strided tile counts in three launches: (1) each CTA
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
     const uint32_t base = vs.toff[v];
     const int tx_n = vs.tiles_x[v];
     for (uint32_t it0 = 0; it0 < total; it0 += 32 * kIlp) {
-        uint32_t toff[kIlp], slot[kIlp], k0[kIlp], k1[kIlp];
+        uint32_t toff[kIlp], slot[kIlp], k0[kIlp], k1[kIlp], tt[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const uint32_t item = it0 + (uint32_t)(u * 32 + lane);
@@ -310,8 +318,14 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
             const uint32_t x0 = xy & 0xffffu, y0 = xy >> 16, rw = (zw & 0xffffu) - x0;
             const uint32_t dy = rw ? off / rw : 0u, dx = off - dy * rw;
             const uint32_t t = base + (y0 + dy) * (uint32_t)tx_n + x0 + dx;
+            tt[u] = t;
             // the list's start is fetched while the slot atomic is in flight
             if (item < total) {
+                if (w.checked && !index_ok(t, w.nt)) {
+                    check_failed(w.dstatus, kSiteScatterTile);
+                    tt[u] = 0xffffffffu;
+                    continue;
+                }
                 slot[u] = atomicAdd(&w.tile_fill[(size_t)t * kCounterStride], 1u);
                 toff[u] = w.tile_off[t];
             }
@@ -319,6 +333,13 @@ __global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
 #pragma unroll
         for (int u = 0; u < kIlp; ++u)
             if (it0 + (uint32_t)(u * 32 + lane) < total) {
+                if (w.checked) {
+                    if (tt[u] == 0xffffffffu) continue;
+                    if (!slot_ok(toff[u], slot[u], w.tile_off[tt[u] + 1])) {
+                        check_failed(w.dstatus, kSiteScatterSlot);
+                        continue;
+                    }
+                }
                 const uint64_t pos = (uint64_t)toff[u] + slot[u];
                 if (pos < w.cap) w.pairs[pos] = ((uint64_t)k1[u] << 32) | k0[u];
             }
@@ -469,12 +490,17 @@ __global__ void __launch_bounds__(256) k_tile_sort_warp(const uint32_t* __restri
                                                         uint64_t* __restrict__ pairs, uint32_t cap,
                                                         uint32_t NT, uint32_t* __restrict__ long_list,
                                                         uint32_t* __restrict__ long_count,
-                                                        const uint32_t* __restrict__ enable)
+                                                        const uint32_t* __restrict__ enable,
+                                                        uint32_t* __restrict__ check_status)
 {
     if (enable && !*enable) return;
     const uint32_t t = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= NT) return;
+    if (check_status && !range_ok(off[t], off[t + 1], 0xffffffffu)) {
+        if (lane == 0) check_failed(check_status, kSiteTileRange);
+        return;
+    }
     const uint32_t b = min(off[t], cap), e = min(off[t + 1], cap);
     if (e <= b + 1) return;
     const uint32_t n = e - b;
@@ -604,7 +630,8 @@ cudaError_t launch_segment_sort(const uint32_t* off, uint64_t* keys, uint64_t* t
     if (nseg == 0) return cudaSuccess;
     const cudaError_t e = cudaMemsetAsync(long_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    k_tile_sort_warp<<<(nseg + 7) / 8, 256, 0, st>>>(off, keys, cap, nseg, long_list, long_count, enable);
+    k_tile_sort_warp<<<(nseg + 7) / 8, 256, 0, st>>>(off, keys, cap, nseg, long_list, long_count, enable,
+                                                     nullptr);
     k_tile_sort_warp_long<<<kLongSortCtas, 256, 0, st>>>(off, keys, cap, long_list, long_count, enable);
     k_tile_sort<<<kLongSortCtas, kSortThreads, 0, st>>>(off, keys, tmp, cap, long_list, long_count, enable);
     return cudaGetLastError();
@@ -623,7 +650,7 @@ cudaError_t launch_tile_sort(const Work& w, uint32_t NT, cudaStream_t st)
     if (NT == 0) return cudaSuccess;
     // tile_fill is free once the pairs are scattered: it holds the long-list tiles
     k_tile_sort_warp<<<(NT + 7) / 8, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, NT, w.tile_fill, &w.dstatus[3],
-                                                   nullptr);
+                                                   nullptr, w.checked ? w.dstatus : nullptr);
     k_tile_sort_warp_long<<<kLongSortCtas, 256, 0, st>>>(w.tile_off, w.pairs, w.cap, w.tile_fill, &w.dstatus[3],
                                                          nullptr);
     k_tile_sort<<<kLongSortCtas, kSortThreads, 0, st>>>(w.tile_off, w.pairs, w.pairs_tmp, w.cap, w.tile_fill,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tsplat.h"
+#include "checks.h"
 
 namespace tsp {
 
@@ -74,6 +75,7 @@ struct Work {
     uint32_t* touched;     // [R]
     float4* geom0;         // [R] mu - rect origin (x, y), i11, k  (blend factor form)
     float4* geom1;         // [R] i22, opacity, moment origin - mu (x, y)
+    float4* cull;          // [R] culling constants (cull_record)
     float2* dref;          // [R] reference displacement (track at the moment origin)
     uint32_t* oref;        // [R] pixel index of the moment origin (fit mode)
     float4* color;         // [R] render colour
@@ -88,8 +90,12 @@ struct Work {
     uint64_t* pairs;       // [cap]
     uint64_t* pairs_tmp;   // [cap]
     uint32_t cap;
-    uint32_t* dstatus;     // [4]: 0 flags (bit 0 overflow), 1 K (low 32 bits), 2 K high,
-                           //      3 number of tiles whose lists need the long-list sort
+    uint32_t nt;           // tiles of the call
+    uint32_t checked;      // 1: checked mode (bounds checks into dstatus)
+    uint32_t* dstatus;     // [8]: 0 flags (bit 0 overflow, bit 1 internal, bit 2 check),
+                           //      1 K (low 32 bits), 2 K high, 3 number of tiles whose
+                           //      lists need the long-list sort, 4 first failed check
+                           //      site, 5 failed checks
     unsigned long long* stats;  // [4] raster work counters (collect_stats only)
     unsigned long long* span_sum; // [ceil(NT / 1024)] tile-count scan scratch
     uint32_t* queue;       // [1] work-queue head of the persistent raster
@@ -114,6 +120,15 @@ struct FitParams {
 
 constexpr uint32_t kStatusOverflow = 1u;
 constexpr uint32_t kStatusInternal = 2u;   // a bounded device loop gave up (reported by tsp_sync)
+constexpr uint32_t kStatusChecked = 4u;    // checked mode: an index left its buffer (reported by tsp_sync)
+
+// Checked mode: record a failed bounds check (the caller skips the access).
+__device__ __forceinline__ void check_failed(uint32_t* dstatus, uint32_t site)
+{
+    atomicOr(&dstatus[0], kStatusChecked);
+    atomicCAS(&dstatus[4], 0u, site);
+    atomicAdd(&dstatus[5], 1u);
+}
 
 // --------------------------------------------------------------------------
 // Key path: culling, depth key and tile rectangle in FP32 with a fixed order of
@@ -278,13 +293,17 @@ __device__ __forceinline__ void mean2d_df(const DevCam& c, float4 m, float2& ux,
 // Origin of a (view, Gaussian)'s moment sums: mu_2D clamped to the image
 // rectangle [0, W] x [0, H].  Returns delta = origin - mu_2D.  When the centre
 // lies off-image, only a sliver at the border is visible; sums taken about the
-// far-away centre would lose 2-3 digits to cancellation in FP32.
-__device__ __forceinline__ float2 moment_origin_shift(float2 ux, float2 uy, int W, int H)
+// far-away centre would lose 2-3 digits to cancellation in FP32.  The shift is
+// formed from (rx, ry), the mean relative to the corner pixel (cx, cy) of its
+// tile rectangle -- the value the raster stages -- so that a clamped origin
+// lands on the border to a unit in the last place of the off-image distance,
+// not of |mu_2D|.
+__device__ __forceinline__ float2 moment_origin_shift(float2 ux, float2 uy, float rx, float ry, int cx, int cy,
+                                                      int W, int H)
 {
     const float x = ux.x + ux.y, y = uy.x + uy.y;
-    const float fw = (float)W, fh = (float)H;
-    const float dx = x < 0.f ? -x : (x > fw ? fw - x : 0.f);
-    const float dy = y < 0.f ? -y : (y > fh ? fh - y : 0.f);
+    const float dx = x < 0.f ? __fsub_rn((float)(0 - cx), rx) : (x > (float)W ? __fsub_rn((float)(W - cx), rx) : 0.f);
+    const float dy = y < 0.f ? __fsub_rn((float)(0 - cy), ry) : (y > (float)H ? __fsub_rn((float)(H - cy), ry) : 0.f);
     return make_float2(dx, dy);
 }
 
@@ -473,6 +492,46 @@ __device__ __forceinline__ float render_alpha_g(float4 g0, float4 g1, float xc, 
 // an edge facing the mean: along a vertical edge ex = e it is at ey = k e, along
 // a horizontal edge ey = f at ex = k i22^2 f / (i11^2 + k^2 i22^2), each clamped
 // to the edge.  Returns 0 when the mean is inside.
+// Culling constants of a record, formed once in the projection instead of once
+// per (8x8 block, list entry): the half-extents (hx, hy) of the box holding the
+// alpha >= 1/255 ellipse (footprint_box's), the threshold the block test
+// compares its minimum power with (log2(255 o) with a 0.2 % margin), and
+// k i22^2 / (i11^2 + k^2 i22^2), the slope of the minimizing x along a
+// horizontal edge (block_min_power's).  hx < 0: alpha >= 1/255 nowhere.
+__device__ __forceinline__ float4 cull_record(float i11, float k, float i22, float opacity)
+{
+    const float pm = log2f(255.0f * opacity);
+    if (!(pm > 0.0f)) return make_float4(-1e30f, -1e30f, -1.0f, 0.f);
+    const float sp = sqrtf(pm) * 1.001f;
+    const float ix = 1.0f / i11, iy = 1.0f / i22;
+    const float hx = sp * ix + 1e-3f;
+    const float hy = sp * sqrtf(k * k * ix * ix + iy * iy) + 1e-3f;
+    const float i22s = i22 * i22;
+    return make_float4(hx, hy, pm * 1.002f + 1e-4f, k * i22s / fmaf(i11, i11, k * k * i22s));
+}
+
+// block_min_power with the precomputed slope c1 of cull_record.
+__device__ __forceinline__ float block_min_power_c(float4 g0, float i22, float c1, float bx0, float bx1,
+                                                   float by0, float by1)
+{
+    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
+    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
+    float pv = 3.0e38f, ph = 3.0e38f;
+    if (outx) {
+        const float e = ex0 > 0.f ? ex0 : ex1;
+        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
+        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
+        pv = fmaf(z1, z1, z2 * z2);
+    }
+    if (outy) {
+        const float f = ey0 > 0.f ? ey0 : ey1;
+        const float ex = fminf(fmaxf(c1 * f, ex0), ex1);
+        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
+        ph = fmaf(z1, z1, z2 * z2);
+    }
+    return (outx || outy) ? fminf(pv, ph) : 0.f;
+}
+
 __device__ __forceinline__ float block_min_power(float4 g0, float i22, float bx0, float bx1,
                                                  float by0, float by1)
 {

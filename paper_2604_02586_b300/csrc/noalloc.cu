@@ -54,7 +54,9 @@ __device__ void sort_in_smem(unsigned long long* keys, uint32_t n, unsigned long
 // One CTA per tile.  Lists longer than kCap are sorted in kCap runs and merged
 // pairwise through the static scratch (slice [off[t], off[t+1]) of it, so tiles
 // never share scratch); each key finds its merged slot by binary search in the
-// partner run (keys are unique: depth bits << 32 | Gaussian index).
+// partner run.  A key of the left run counts the partner's keys below it, a key
+// of the right run those not above it, so equal keys in the two runs land on
+// distinct slots (left run first) and every slot is written once.
 __global__ void __launch_bounds__(kThreads) k_sort_tiles_noalloc(unsigned long long* keys,
                                                                  const uint32_t* __restrict__ off,
                                                                  uint32_t num_keys,
@@ -79,10 +81,12 @@ __global__ void __launch_bounds__(kThreads) k_sort_tiles_noalloc(unsigned long l
             const uint64_t ps64 = (uint64_t)partner * L;
             if (ps64 >= n) { dst[i] = key; continue; }
             const uint32_t ps = (uint32_t)ps64, pe = min(ps + L, n);
+            const bool left = run < partner;
             uint32_t lo = ps, hi = pe;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (src[mid] < key) lo = mid + 1; else hi = mid;
+                const unsigned long long m = src[mid];
+                if (left ? (m < key) : (m <= key)) lo = mid + 1; else hi = mid;
             }
             dst[min(run, partner) * L + (i - start) + (lo - ps)] = key;
         }

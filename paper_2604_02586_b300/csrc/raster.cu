@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kBatch = 64;
 constexpr uint32_t kFull = 0xffffffffu;
+constexpr float kLog2_255 = 7.99435329f;   // log2(255): alpha >= 1/255 <=> power - log2 o <= this
 
 // 2^x by the SFU's approximate exponential (flush-to-zero; |rel. error| ~ 2^-22).
 // x <= 0 here, and a result below 2^-126 (alpha < 1/255 by far) flushes to 0.
@@ -224,12 +225,17 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
 // Two-phase accumulate (the default).  Warp w owns the 8x8 block (w & 1, w >> 1)
 // of the tile, lane l the pixels (l & 7, (l >> 3) + 4h), h = 0, 1, and walks the
 // tile's depth-ordered list on its own (no block-wide barrier): 32 entries at a
-// time, lane l loads entry l, tests whether its alpha >= 1/255 ellipse meets the
-// block, and stages the hits in warp-private shared memory.
-//   Phase 1 (blend, pixel-parallel): for each hit, every lane blends its two
-//   pixels and writes the weight w = alpha T (0 where nothing is added) into a
-//   warp-private buffer, one column per pending hit; hits that add no pixel of
-//   the block are dropped.
+// time, lane l loads entry l and tests whether its alpha >= 1/255 ellipse meets
+// the block.  The hits of the step are compacted into warp-private staging in
+// list order (their blend factors) and numbered; each hit's moment origin,
+// reference track and Gaussian index go to a ring indexed by hit number, where
+// they stay until the hit's moments are added.
+//   Phase 1 (blend, pixel-parallel): for each hit in order, every lane blends its
+//   two pixels and writes w = alpha T (0 where nothing is added) into column
+//   `pend` of a warp-private buffer; lane `pend` keeps the ballots of the pixels
+//   the hit added.  The loop has no divergent branch: alpha below 1/255 becomes
+//   alpha' = 0 (T (1 - 0) = T exactly), and the transmittance test both ends a
+//   terminated pixel (T = 0) and zeroes its weight.
 //   Phase 2 (moments, hit-parallel): once 16 hits are pending, lane l sums the
 //   13 weighted moments of hit l & 15 over pixel half l >> 4 (32 pixels) from
 //   the buffer, two horizontally adjacent pixels at a time in packed FP32x2
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
 //   end; two passes, position then displacement moments, so the pairs of sums
 //   fit the 72 registers of 7 CTAs per SM); the halves are joined with one
 //   shuffle per value and lanes 0-15 add the result to global memory with 4
-//   float4 atomics.
+//   float4 atomics (none for a hit that added no pixel).
 // Buffer layout: the weights of hit c at the pixel pair p (pixels 2p, 2p + 1)
 // of half h are the float2 at h * kWHalf + p * kWRow + 2c.  A row stride of 34
 // words makes the phase-1 writes (lane l: pair l >> 1, word l & 1) hit 32
@@ -246,25 +252,31 @@ constexpr int kChunk = 16;
 constexpr int kWRow = 2 * kChunk + 2;
 constexpr int kWHalf = 16 * kWRow;
 constexpr int kWWords = 2 * kWHalf;
+// hits whose moments are pending (< kChunk) plus one walk step's hits (<= 32)
+constexpr int kRing = 48;
 
 // Warp-private shared memory of the two-phase walk.
 struct WarpSmem {
-    float4 g0[32];
-    float4 g1[32];
-    float4 hd[32];                 // (origin x, origin y, reference x, reference y)
-    uint32_t id[32];
+    float4 g0[32];                 // this step's hits: mean (tile-local), i11, k
+    float2 g1[32];                 // this step's hits: i22, log2(opacity)
+    float4 hd[kRing];              // by hit number: (origin x, origin y, reference x, reference y)
+    uint32_t id[kRing];            // by hit number: Gaussian index
+    uint2 mask[kChunk];            // by pending column: the pixels the hit added (rows 0-3, 4-7)
     float W[kWWords];
     float4 D[2][16];               // per half and pixel pair: (d_x, d_x', d_y, d_y')
     float2 S[2][16];               // per half and pixel pair: static flags (0 or 1)
 };
 
 // One warp, one 8x8 block `blk` of tile `tile`: the two-phase walk above.  Work
-// counts (kStats) accumulate in cnt.
+// counts (kStats) accumulate in cnt: [0] (pixel, Gaussian) evaluations, [1]
+// blended contributions, [2] moment additions, [3] block hits (list entries
+// whose ellipse meets the block), [4] hits that add a pixel, [5] phase-2 passes,
+// [6] 32-entry walk steps.
 // TW: tile width, 16 (16 x 16 tiles) or 32 (32 x 8); a compile-time value so the
 // block and pixel coordinates cost no registers.
 template <bool kStats, int TW>
 __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& w, uint32_t tile, int blk,
-                                                 WarpSmem& sm, unsigned long long (&cnt)[3])
+                                                 WarpSmem& sm, unsigned long long (&cnt)[7])
 {
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
     if (beg >= end) return;
@@ -276,26 +288,25 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     const int bxo = (blk % nbx) * 8, byo = (blk / nbx) * 8;
     const int W = vs.cam[v].W, H = vs.cam[v].H;
     const size_t vbase = (size_t)vs.vrec[v];
-    float* const Wb = sm.W;
+    float* const Wb = sm.W + (lane >> 1) * kWRow + (lane & 1);
 
-    // T = 0 marks a pixel that is outside the image or has terminated
-    float T[2];
-    bool vis[2];
+    // the lane's two pixels as pairs: transmittance (0 = outside the image or
+    // terminated) and visibility (1 or 0)
+    float2 T2 = make_float2(0.f, 0.f), vis2 = make_float2(0.f, 0.f);
     uint32_t stat_mask[2];
     const float xc = (float)(bxo + (lane & 7)) + 0.5f;
-    float yc[2];
+    const float yc0 = (float)(byo + (lane >> 3)) + 0.5f;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int ly = byo + (lane >> 3) + 4 * k;
         const int px = tx * TW + bxo + (lane & 7), py = ty * TH + ly;
         const bool inside = px < W && py < H;
-        float ddx = 0.f, ddy = 0.f;
-        vis[k] = false;
+        float ddx = 0.f, ddy = 0.f, vis = 0.f;
         if (inside) {
             const size_t pix = (size_t)py * W + px;
             const float2 d = vs.disp[v][pix];
             ddx = d.x; ddy = d.y;
-            vis[k] = vs.vis[v][pix] != 0;
+            vis = vs.vis[v][pix] != 0 ? 1.f : 0.f;
         }
         // static pixel test |x' - x| < 1 (Sec. 4.5.2), in FP32 as the tracks are FP32
         const bool stat = __fmaf_rn(ddx, ddx, __fmul_rn(ddy, ddy)) < 1.0f;
@@ -304,152 +315,183 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         dp[2 + (lane & 1)] = ddy;
         reinterpret_cast<float*>(&sm.S[k][lane >> 1])[lane & 1] = stat ? 1.f : 0.f;
         stat_mask[k] = __ballot_sync(kFull, stat);
-        yc[k] = (float)ly + 0.5f;
-        T[k] = inside ? 1.0f : 0.0f;
+        if (k == 0) { T2.x = inside ? 1.f : 0.f; vis2.x = vis; }
+        else { T2.y = inside ? 1.f : 0.f; vis2.y = vis; }
     }
     const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
     const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
     if (kStats && blk == 0 && lane == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
-    // pending hit c is held by lane c: moment record, origin and reference, and the
-    // masks of the pixels it added (rows 0-3, 4-7)
-    int pend = 0;
-    uint32_t h_id = 0, h_m0 = 0, h_m1 = 0;
-    float4 h_hd = make_float4(0.f, 0.f, 0.f, 0.f);
+    int pend = 0, q0 = 0, qh = 0;              // pending count, first pending and next hit number (mod kRing)
 
     auto phase2 = [&](int npend) {
+        if (kStats && lane == 0) cnt[5] += 1;
         __syncwarp();
         const int c = lane & 15, half = lane >> 4;
-        const float ox = __shfl_sync(kFull, h_hd.x, c), oy = __shfl_sync(kFull, h_hd.y, c);
-        const float rx = __shfl_sync(kFull, h_hd.z, c), ry = __shfl_sync(kFull, h_hd.w, c);
-        const float x0 = ((float)bxo + 0.5f) - ox;
-        const float y0 = ((float)(byo + 4 * half) + 0.5f) - oy;
+        int slot = q0 + c;
+        slot = slot >= kRing ? slot - kRing : slot;
+        const float4 hd = sm.hd[slot];         // lanes c >= npend read a stale entry and store nothing
+        const float x0 = ((float)bxo + 0.5f) - hd.x;
+        const float y0 = ((float)(byo + 4 * half) + 0.5f) - hd.y;
         // every moment as an (even pixel, odd pixel) pair: a[q] sums moment q
         // over the pixels 2p and 2p + 1 of every pair p; two passes over the
-        // pairs (the position moments, then the displacement moments)
+        // pairs (the position moments, then the displacement moments).  y~ is
+        // constant along a row of 4 pairs, so the moments with a y~ factor are
+        // formed per row from that row's sums: sum w y~ = sum_rows y~ (sum_row w).
         const float2 z = make_float2(0.f, 0.f);
         float2 a0 = z, a1 = z, a2 = z, a3 = z, a4 = z, a5 = z, a6 = z, a7 = z, a8 = z, a9 = z, a10 = z,
                a11 = z, a12 = z;
-        const float* Wh = Wb + half * kWHalf + 2 * c;
+        const float* Wh = sm.W + half * kWHalf + 2 * c;
         const float4* Dh = sm.D[half];
         const float2* Sh = sm.S[half];
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
-            const float2 w2 = *reinterpret_cast<const float2*>(Wh + p * kWRow);
-            const float2 st2 = Sh[p];
-            const int col = 2 * (p & 3);
-            const float2 X = make_float2(x0 + (float)col, x0 + (float)(col + 1));
-            const float yv = y0 + (float)(p >> 2);
-            const float2 Y = make_float2(yv, yv);
-            const float2 wX = __fmul2_rn(w2, X), wY = __fmul2_rn(w2, Y);
-            a0 = __fadd2_rn(a0, w2);
-            a1 = __fadd2_rn(a1, wX);
-            a2 = __fadd2_rn(a2, wY);
-            a3 = __ffma2_rn(wX, X, a3);
-            a4 = __ffma2_rn(wX, Y, a4);
-            a5 = __ffma2_rn(wY, Y, a5);
-            a12 = __ffma2_rn(w2, st2, a12);
-        }
-        const float2 nrx = make_float2(-rx, -rx), nry = make_float2(-ry, -ry);
+        for (int row = 0; row < 4; ++row) {
+            float2 rw = z, rwx = z;
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
-            const float2 w2 = *reinterpret_cast<const float2*>(Wh + p * kWRow);
-            const float4 dd = Dh[p];
-            const int col = 2 * (p & 3);
-            const float2 X = make_float2(x0 + (float)col, x0 + (float)(col + 1));
-            const float yv = y0 + (float)(p >> 2);
+            for (int cp = 0; cp < 4; ++cp) {
+                const int p = 4 * row + cp;
+                const float2 w2 = *reinterpret_cast<const float2*>(Wh + p * kWRow);
+                const float2 st2 = Sh[p];
+                const float2 X = make_float2(x0 + (float)(2 * cp), x0 + (float)(2 * cp + 1));
+                const float2 wX = __fmul2_rn(w2, X);
+                rw = __fadd2_rn(rw, w2);
+                rwx = __fadd2_rn(rwx, wX);
+                a3 = __ffma2_rn(wX, X, a3);
+                a12 = __ffma2_rn(w2, st2, a12);
+            }
+            const float yv = y0 + (float)row;
             const float2 Y = make_float2(yv, yv);
-            const float2 dX = __fadd2_rn(make_float2(dd.x, dd.y), nrx);
-            const float2 dY = __fadd2_rn(make_float2(dd.z, dd.w), nry);
-            const float2 wX = __fmul2_rn(w2, X), wY = __fmul2_rn(w2, Y);
-            a6 = __ffma2_rn(w2, dX, a6);
-            a7 = __ffma2_rn(w2, dY, a7);
-            a8 = __ffma2_rn(wX, dX, a8);
-            a9 = __ffma2_rn(wX, dY, a9);
-            a10 = __ffma2_rn(wY, dX, a10);
-            a11 = __ffma2_rn(wY, dY, a11);
+            const float2 rwy = __fmul2_rn(rw, Y);
+            a0 = __fadd2_rn(a0, rw);
+            a1 = __fadd2_rn(a1, rwx);
+            a2 = __fadd2_rn(a2, rwy);
+            a4 = __ffma2_rn(rwx, Y, a4);
+            a5 = __ffma2_rn(rwy, Y, a5);
         }
-        float s[13] = {a0.x + a0.y, a1.x + a1.y, a2.x + a2.y, a3.x + a3.y, a4.x + a4.y,
-                       a5.x + a5.y, a6.x + a6.y, a7.x + a7.y, a8.x + a8.y, a9.x + a9.y,
-                       a10.x + a10.y, a11.x + a11.y, a12.x + a12.y};
+        const float2 nrx = make_float2(-hd.z, -hd.z), nry = make_float2(-hd.w, -hd.w);
+#pragma unroll
+        for (int row = 0; row < 4; ++row) {
+            float2 rdx = z, rdy = z;
+#pragma unroll
+            for (int cp = 0; cp < 4; ++cp) {
+                const int p = 4 * row + cp;
+                const float2 w2 = *reinterpret_cast<const float2*>(Wh + p * kWRow);
+                const float4 dd = Dh[p];
+                const float2 X = make_float2(x0 + (float)(2 * cp), x0 + (float)(2 * cp + 1));
+                const float2 wdx = __fmul2_rn(w2, __fadd2_rn(make_float2(dd.x, dd.y), nrx));
+                const float2 wdy = __fmul2_rn(w2, __fadd2_rn(make_float2(dd.z, dd.w), nry));
+                rdx = __fadd2_rn(rdx, wdx);
+                rdy = __fadd2_rn(rdy, wdy);
+                a8 = __ffma2_rn(X, wdx, a8);
+                a9 = __ffma2_rn(X, wdy, a9);
+            }
+            const float yv = y0 + (float)row;
+            const float2 Y = make_float2(yv, yv);
+            a6 = __fadd2_rn(a6, rdx);
+            a7 = __fadd2_rn(a7, rdy);
+            a10 = __ffma2_rn(rdx, Y, a10);
+            a11 = __ffma2_rn(rdy, Y, a11);
+        }
+        // the buffer holds -w: negate while joining the pair halves
+        float s[13] = {-a0.x - a0.y, -a1.x - a1.y, -a2.x - a2.y, -a3.x - a3.y, -a4.x - a4.y,
+                       -a5.x - a5.y, -a6.x - a6.y, -a7.x - a7.y, -a8.x - a8.y, -a9.x - a9.y,
+                       -a10.x - a10.y, -a11.x - a11.y, -a12.x - a12.y};
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
-        if (lane < npend) {
-            const float h_np = (float)(__popc(h_m0) + __popc(h_m1));
-            const float h_ns = (float)(__popc(h_m0 & stat_mask[0]) + __popc(h_m1 & stat_mask[1]));
-            float4* dst = &w.moments[(vbase + h_id) * 4];
+        const uint2 hm = sm.mask[c];
+        const int np = __popc(hm.x) + __popc(hm.y);
+        if (lane < npend && np > 0) {
+            const float h_ns = (float)(__popc(hm.x & stat_mask[0]) + __popc(hm.y & stat_mask[1]));
+            float4* dst = &w.moments[(vbase + sm.id[slot]) * 4];
             atomicAdd(dst + 0, make_float4(s[0], s[1], s[2], s[3]));
             atomicAdd(dst + 1, make_float4(s[4], s[5], s[6], s[7]));
             atomicAdd(dst + 2, make_float4(s[8], s[9], s[10], s[11]));
-            atomicAdd(dst + 3, make_float4(s[12], h_np, h_ns, 0.f));
+            atomicAdd(dst + 3, make_float4(s[12], (float)np, h_ns, 0.f));
         }
         __syncwarp();
+        q0 += npend;
+        q0 = q0 >= kRing ? q0 - kRing : q0;
     };
 
     uint32_t g_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
     for (uint32_t b0 = beg; b0 < end; b0 += 32) {
-        if (!__any_sync(kFull, T[0] > 0.f || T[1] > 0.f)) break;
+        if (!__any_sync(kFull, T2.x > 0.f || T2.y > 0.f)) break;
         bool hit = false;
+        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         const uint32_t g = g_next;
         if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
-        if (b0 + lane < end) {
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
-            const float4 g1 = w.geom1[vbase + g];
-            const float4 bb = footprint_box(g0, g1);
-            hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
-            if (hit)
-                hit = block_min_power(g0, g1.x, bx0, bx1, by0, by1) <=
-                      log2f(255.0f * g1.y) * 1.002f + 1e-4f;
-            if (hit) {
-                const float2 rf = w.dref[vbase + g];
-                sm.g0[lane] = g0;
-                sm.g1[lane] = g1;
-                sm.hd[lane] = make_float4(g0.x + g1.z, g0.y + g1.w, rf.x, rf.y);
-                sm.id[lane] = g;
-            }
+        bool live = b0 + lane < end;
+        if (live && w.checked && !index_ok(g, (uint32_t)vs.vn[v])) {
+            check_failed(w.dstatus, kSiteListEntry);
+            live = false;
         }
-        uint32_t m = __ballot_sync(kFull, hit);
+        if (live) {
+            g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
+            g1 = w.geom1[vbase + g];
+            const float4 cr = w.cull[vbase + g];
+            hit = g0.x - cr.x <= bx1 && g0.x + cr.x >= bx0 && g0.y - cr.y <= by1 && g0.y + cr.y >= by0;
+            if (hit) hit = block_min_power_c(g0, g1.x, cr.w, bx0, bx1, by0, by1) <= cr.z;
+        }
+        const uint32_t m = __ballot_sync(kFull, hit);
+        const int nh = __popc(m);
+        if (hit) {
+            // staged in list order: the hit's rank among this step's hits
+            const int r = __popc(m & ((1u << lane) - 1u));
+            int slot = qh + r;
+            slot = slot >= kRing ? slot - kRing : slot;
+            const float2 rf = w.dref[vbase + g];
+            sm.g0[r] = g0;
+            // log2(opacity), so that alpha = 2^(log2 o - power)
+            sm.g1[r] = make_float2(g1.x, log2f(g1.y));
+            sm.hd[slot] = make_float4(g0.x + g1.z, g0.y + g1.w, rf.x, rf.y);
+            sm.id[slot] = g;
+        }
+        if (kStats && lane == 0) { cnt[3] += nh; cnt[6] += 1; }
+        qh += nh;
+        qh = qh >= kRing ? qh - kRing : qh;
         __syncwarp();
-        while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1;
-            const float4 g0 = sm.g0[j];
-            const float4 g1 = sm.g1[j];
-            // both pixels of a lane share the column: ex, z1; the second row is 4 below
-            const float ex = xc - g0.x;
-            const float z1 = ex * g0.z;
-            const float z1s = z1 * z1;
-            float z2[2];
-            z2[0] = fmaf(-g0.w, ex, yc[0] - g0.y) * g1.x;
-            z2[1] = fmaf(4.0f, g1.x, z2[0]);
-            // the lane's two pixels in packed FP32x2 where the operation is shared
-            const float2 z2p = make_float2(z2[0], z2[1]);
-            const float2 pw = __ffma2_rn(z2p, z2p, make_float2(z1s, z1s));
-            const float2 oe = __fmul2_rn(make_float2(g1.y, g1.y), make_float2(sfu_exp2(-pw.x), sfu_exp2(-pw.y)));
-            const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
-            const float2 Tp = make_float2(T[0], T[1]);
-            const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al.x, -al.y)));
-            const float2 wa = __fmul2_rn(al, Tp);
-            bool add[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float alpha = k ? al.y : al.x, tn = k ? Tn.y : Tn.x;
-                const bool pass = alpha >= kAlphaMin;
-                const bool blend = pass && tn >= kTMin;    // T = 0: Tn = 0, never blends
-                add[k] = blend && vis[k];
-                Wb[k * kWHalf + (lane >> 1) * kWRow + 2 * pend + (lane & 1)] = add[k] ? (k ? wa.y : wa.x) : 0.f;
-                if (kStats) { cnt[0] += T[k] > 0.f; cnt[1] += blend; cnt[2] += add[k]; }
-                T[k] = blend ? tn : (pass ? 0.f : T[k]);   // pass without blend: terminated
+        // phase 1 in runs that end where the pending columns fill up
+        for (int i = 0; i < nh;) {
+            const int take = min(nh - i, kChunk - pend);
+            for (int j = 0; j < take; ++j) {
+                const int col = pend + j;
+                const float4 h0 = sm.g0[i + j];
+                const float2 h1 = sm.g1[i + j];
+                // both pixels of a lane share the column: ex, z1; the second row is 4 below
+                const float ex = xc - h0.x;
+                const float z1 = ex * h0.z;
+                const float base = fmaf(z1, z1, -h1.y);          // z1^2 - log2 o
+                const float z20 = fmaf(-h0.w, ex, yc0 - h0.y) * h1.x;
+                const float2 z2 = make_float2(z20, fmaf(4.0f, h1.x, z20));
+                const float2 q = __ffma2_rn(z2, z2, make_float2(base, base));   // power - log2 o
+                // alpha = min(0.99, 2^-q) >= 1/255  <=>  q <= log2 255
+                const bool p0 = q.x <= kLog2_255, p1 = q.y <= kLog2_255;
+                const float e0 = sfu_exp2(-q.x), e1 = sfu_exp2(-q.y);
+                // -alpha' with alpha' = alpha where it passes, else 0 (T is then kept exactly)
+                const float2 nap = make_float2(p0 ? fmaxf(-kAlphaMax, -e0) : 0.f, p1 ? fmaxf(-kAlphaMax, -e1) : 0.f);
+                const float2 Tn = __ffma2_rn(nap, T2, T2);             // T - alpha' T
+                const float2 wv = __fmul2_rn(nap, __fmul2_rn(T2, vis2)); // -alpha' T (0 where not visible)
+                // T (1 - alpha') < 1e-4: terminated (T = 0 stays 0); its weight and
+                // every later one are 0
+                const bool b0k = Tn.x >= kTMin, b1k = Tn.y >= kTMin;
+                if (kStats) {
+                    cnt[0] += (T2.x > 0.f) + (T2.y > 0.f);
+                    cnt[1] += (b0k && p0 && T2.x > 0.f) + (b1k && p1 && T2.y > 0.f);
+                }
+                T2 = make_float2(b0k ? Tn.x : 0.f, b1k ? Tn.y : 0.f);
+                const float w0 = b0k ? wv.x : 0.f, w1 = b1k ? wv.y : 0.f;
+                Wb[2 * col] = w0;                  // the buffer holds -w
+                Wb[kWHalf + 2 * col] = w1;
+                const uint32_t m0 = __ballot_sync(kFull, w0 < 0.f), m1 = __ballot_sync(kFull, w1 < 0.f);
+                if (lane == 0) sm.mask[col] = make_uint2(m0, m1);
+                if (kStats) {
+                    cnt[2] += (w0 < 0.f) + (w1 < 0.f);
+                    if (lane == 0 && (m0 | m1)) cnt[4] += 1;
+                }
             }
-            const uint32_t a0 = __ballot_sync(kFull, add[0]), a1 = __ballot_sync(kFull, add[1]);
-            if ((a0 | a1) == 0u) continue;             // nothing of this block to add
-            if (lane == pend) {
-                h_id = sm.id[j];
-                h_hd = sm.hd[j];
-                h_m0 = a0;
-                h_m1 = a1;
-            }
-            if (++pend == kChunk) {
+            i += take;
+            pend += take;
+            if (pend == kChunk) {
                 phase2(kChunk);
                 pend = 0;
             }
@@ -459,6 +501,18 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     if (pend) phase2(pend);
 }
 
+// Work counts of one warp into the context's counters (stats[3], the list
+// entries, is counted by the walk itself).
+__device__ __forceinline__ void add_stats(const Work& w, const unsigned long long (&cnt)[7])
+{
+    atomicAdd(&w.stats[0], cnt[0]);
+    atomicAdd(&w.stats[1], cnt[1]);
+    atomicAdd(&w.stats[2], cnt[2]);
+#pragma unroll
+    for (int k = 3; k < 7; ++k)
+        if (cnt[k]) atomicAdd(&w.stats[k + 1], cnt[k]);
+}
+
 // Grid form: one CTA per tile, warp w takes block w.
 template <bool kStats, int TW>
 __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet vs, const Work w,
@@ -466,13 +520,9 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p(const ViewSet v
 {
     __shared__ WarpSmem sm[4];
     const int warp = threadIdx.x >> 5;
-    unsigned long long cnt[3] = {0ull, 0ull, 0ull};
+    unsigned long long cnt[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     accumulate_block<kStats, TW>(vs, w, tile_base + blockIdx.x, warp, sm[warp], cnt);
-    if (kStats) {
-        atomicAdd(&w.stats[0], cnt[0]);
-        atomicAdd(&w.stats[1], cnt[1]);
-        atomicAdd(&w.stats[2], cnt[2]);
-    }
+    if (kStats) add_stats(w, cnt);
 }
 
 // Persistent form: a grid sized to the resident CTAs, each warp taking
@@ -487,7 +537,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(cons
 {
     __shared__ WarpSmem sm[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long cnt[3] = {0ull, 0ull, 0ull};
+    unsigned long long cnt[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     const uint32_t items = 4u * ntiles;
     for (;;) {
         uint32_t item = 0u;
@@ -496,11 +546,7 @@ __global__ void __launch_bounds__(128, 7) k_raster_accumulate_2p_persistent(cons
         if (item >= items) break;
         accumulate_block<kStats, TW>(vs, w, tile_base + (item >> 2), (int)(item & 3u), sm[warp], cnt);
     }
-    if (kStats) {
-        atomicAdd(&w.stats[0], cnt[0]);
-        atomicAdd(&w.stats[1], cnt[1]);
-        atomicAdd(&w.stats[2], cnt[2]);
-    }
+    if (kStats) add_stats(w, cnt);
 }
 
 template <bool kStats, int TW>

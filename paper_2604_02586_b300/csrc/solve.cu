@@ -174,7 +174,10 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const FitP
                 float2 mxd, myd;
                 mean2d_df(vs.cam[v], mo[g], mxd, myd);
                 // shift of the centre: mu' - mu = c_o + (I - A) delta
-                const float2 dl = moment_origin_shift(mxd, myd, vs.cam[v].W, vs.cam[v].H);
+                const float rx = __fadd_rn(__fsub_rn(mxd.x, (float)(p.x0 * vs.tw)), mxd.y);
+                const float ry = __fadd_rn(__fsub_rn(myd.x, (float)(p.y0 * vs.th)), myd.y);
+                const float2 dl = moment_origin_shift(mxd, myd, rx, ry, p.x0 * vs.tw, p.y0 * vs.th,
+                                                      vs.cam[v].W, vs.cam[v].H);
                 const float c0 = co0 + dl.x - (A00 * dl.x + A01 * dl.y);
                 const float c1 = co1 + dl.y - (A10 * dl.x + A11 * dl.y);
                 const float ux = mxd.x + (mxd.y + c0), uy = myd.x + (myd.y + c1);

@@ -13,7 +13,13 @@ frame -- and admits waiting requests as slots and device memory free up:
   to make room;
 * each scene owns a CUDA stream, so the work of requests admitted while others
   run overlaps on the device; a scene's frames are serialised on its stream;
-* completion is polled with CUDA events; latency = completion - arrival.
+* completion is polled with CUDA events; latency = completion - arrival;
+* each scene's library context is given the budget's headroom (the budget less
+  what the other resident scenes and the in-flight tracks hold) before every
+  solve, so the library itself refuses a workspace that would overrun it;
+* a request fails alone -- bad arguments, a scene larger than the whole budget,
+  a library refusal or error, a deadline that passed while it waited -- and is
+  listed in ``failed`` with the reason; the others carry on.
 
 ``one_at_a_time`` replays the same arrivals through a single stream, one request
 after the other, as the plain path to compare against.
@@ -50,6 +56,9 @@ class Request:
     done: float = 0.0
     inputs: dict | None = None   # device Gaussians the solve started from (keep_inputs)
     result: dict | None = None   # device outputs
+    deadline: float | None = None  # seconds after arrival by which it must start, or None
+    error: str | None = None     # why the request failed (then result is None)
+    late: bool = False           # finished after arrival + deadline
 
     @property
     def latency(self):
@@ -102,6 +111,7 @@ class MotionServer:
         self.inflight: list[tuple[Request, _Scene, object, tuple]] = []
         self.retries = 0
         self.finished: list[Request] = []
+        self.failed: list[Request] = []
         self.t0 = time.perf_counter()
         self.evictions = 0
         self.peak_bytes = 0
@@ -121,14 +131,22 @@ class MotionServer:
         sc.stream.synchronize()
         return tuple(t.cpu().numpy() for t in sc.dev)
 
-    def _used_bytes(self, extra_views=None):
+    def _used_bytes(self, exclude=None):
         used = 0
         for sc in self.scenes.values():
-            if sc.dev is not None:
+            if sc.dev is not None and sc is not exclude:
                 used += sc.resident_bytes()
         for req, sc, _, _ in self.inflight:
             used += req.track_bytes()
         return used
+
+    def _fail(self, req, sc, why):
+        req.error = why
+        req.result = None
+        req.done = self.now()
+        if sc is not None:
+            sc.busy = False
+        self.failed.append(req)
 
     def _make_resident(self, sc, req):
         torch = self.torch
@@ -162,11 +180,20 @@ class MotionServer:
         keep = collections.deque()
         while self.waiting:
             req = self.waiting.popleft()
-            sc = self.scenes[req.scene]
+            sc = self.scenes.get(req.scene)
+            if sc is None:
+                self._fail(req, None, f"unknown scene {req.scene!r}")
+                continue
+            if req.deadline is not None and self.now() > req.arrival + req.deadline:
+                self._fail(req, None, "deadline passed before the request could start")
+                continue
             if sc.busy or len(self.inflight) >= self.max_inflight:
                 keep.append(req)
                 continue
             need = req.track_bytes() + (0 if sc.dev is not None else sc.resident_bytes(len(req.disp)))
+            if req.track_bytes() + sc.resident_bytes(len(req.disp)) > self.budget:
+                self._fail(req, None, "the scene and its tracks exceed the whole device budget")
+                continue
             used = self._used_bytes()
             if used + need > self.budget:
                 idle = sorted((s for s in self.scenes.values() if s.dev is not None and not s.busy and s is not sc),
@@ -177,17 +204,53 @@ class MotionServer:
                 if used + need > self.budget:
                     keep.append(req)
                     continue
-            self._launch(req, sc)
-            self.peak_bytes = max(self.peak_bytes, self._used_bytes())
+            r = self._launch(req, sc)
+            if r == "wait":
+                keep.append(req)
+            elif r == "ok":
+                self.peak_bytes = max(self.peak_bytes, self._used_bytes())
         self.waiting = keep
 
     def _launch(self, req, sc):
-        torch = self.torch
+        """Start ``req`` on its scene's stream.  Returns "ok", "failed" (the
+        request failed alone and is listed in ``failed``) or "wait" (the library
+        refused a workspace that does not fit while other requests hold memory:
+        the request waits for them)."""
         if sc.dev is None:
             self._make_resident(sc, req)
         sc.busy = True
         sc.views = max(sc.views, len(req.disp))
         req.start = self.now()
+        for attempt in range(2):
+            try:
+                self._fit(req, sc)
+                return "ok"
+            except TspError as e:
+                if e.status != TSP.ERR_BUDGET:
+                    self._fail(req, sc, f"TspError: {e}")
+                    return "failed"
+                idle = [x for x in self.scenes.values() if x.dev is not None and not x.busy and x is not sc]
+                if attempt == 0 and idle:
+                    for x in idle:                 # make room, then try once more
+                        self._evict(x)
+                    continue
+                if any(x.busy and x is not sc for x in self.scenes.values()):
+                    sc.busy = False
+                    return "wait"
+                self._fail(req, sc, f"TspError: {e}")
+                return "failed"
+            except (ValueError, TypeError, IndexError) as e:
+                # nothing of this request was enqueued (argument checks and workspace
+                # refusals come first), and the scene keeps its state
+                self._fail(req, sc, f"{type(e).__name__}: {e}")
+                return "failed"
+        return "failed"
+
+    def _fit(self, req, sc):
+        torch = self.torch
+        # the library may grow this scene's workspace only into the headroom
+        head = self.budget - self._used_bytes(exclude=sc) - req.track_bytes() - 2 * 48 * sc.n
+        sc.ctx.set_budget(max(head, 1))
         with torch.cuda.stream(sc.stream):
             disp = [_to_device(d, self.dev) for d in req.disp]
             vis = [_to_device(v, self.dev) for v in req.vis]
@@ -215,15 +278,17 @@ class MotionServer:
                 try:
                     sc.ctx.sync(sc.stream)
                 except TspError as e:
+                    sc.dev = prev                      # the scene keeps its last good state
                     if e.status != TSP.ERR_OVERFLOW:
-                        raise
+                        self._fail(req, sc, f"TspError: {e}")
+                        continue
                     # the pair buffer was too small for this frame; the library has
                     # grown it, so the frame runs again from the previous state
-                    sc.dev = prev
                     self.retries += 1
                     retry.append(req)
                     continue
                 req.done = self.now()
+                req.late = req.deadline is not None and req.done > req.arrival + req.deadline
                 sc.last_used = req.done
                 done.append(req)
             else:
@@ -246,9 +311,6 @@ class MotionServer:
                 r.arrival *= rate_scale
                 self.submit(r)
             self.poll()
-            if not self.inflight and self.waiting and not pending:
-                # nothing can run: a request larger than the budget
-                raise RuntimeError(f"request {self.waiting[0].rid} does not fit the device budget")
             time.sleep(poll_s)
         return self.finished
 

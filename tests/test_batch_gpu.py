@@ -13,7 +13,7 @@ import pytest
 import oracle
 import synth
 from tests import parity as P
-from tests.test_parity_gpu import check_fitted, POS_TOL, SCALE_TOL
+from tests.test_parity_gpu import caps_for, check_fitted, POS_TOL, SCALE_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -103,14 +103,16 @@ def test_batch_with_wide_tiles_meets_the_oracle(gpu_ready):
         assert np.array_equal(pairs[seg[0]:seg[-1]], ent)
         t0 += nt
         o = oracle.fit_motion(s, opt)
-        check_fitted(s, host(out), o, P.sensitivity(s, o, options=opt))
+        check_fitted(s, host(out), o, P.sensitivity(s, o, options=opt), tag=f"batch32x8:{s.n}",
+                     caps=caps_for(s))
 
 
 def test_batch_frames_meet_the_oracle_bar(batch):
     ss, outs, _, _ = batch
     for s, g in zip(ss, outs):
         o = oracle.fit_motion(s)
-        check_fitted(s, g, o, P.sensitivity(s, o))
+        check_fitted(s, g, o, P.sensitivity(s, o), tag=f"batch:{s.n}",
+                     caps=caps_for(s))
 
 
 def test_batch_frames_equal_frames_alone(batch):

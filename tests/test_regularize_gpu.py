@@ -19,6 +19,7 @@ import pytest
 
 import oracle
 import synth
+from tests import parity as P
 from tests.parity import rot_angle
 
 pytestmark = pytest.mark.gpu
@@ -269,7 +270,6 @@ def test_regularize_edge_cases(ctx):
 def oracle_fit_inputs(s):
     """The oracle's own fit of scene s as regularization inputs: fitted Gaussians
     (float32 [n, 4]), status and per-view moments in the library layout."""
-    from tests.parity import oracle_moments_in_library_layout
     o = oracle.fit_motion(s, per_view=True)
     n = s.n
     mo = np.zeros((n, 4), np.float32)
@@ -278,7 +278,8 @@ def oracle_fit_inputs(s):
     sc = np.zeros((n, 4), np.float32)
     sc[:, :3] = o["out_scale"]
     after = (mo, o["out_quat"].astype(np.float32), sc)
-    mom = oracle_moments_in_library_layout(o["moments"]).astype(np.float32)
+    mom = np.zeros(o["moments"].shape[:2] + (16,), np.float32)
+    mom[..., :15] = P.library_frame(s, o)["mom"]
     return after, o["out_status"].astype(np.uint32), mom
 
 

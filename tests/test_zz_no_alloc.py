@@ -69,6 +69,23 @@ def test_noalloc_sort_matches_fit_motion_lists(gpu_ready, dense):
         assert np.array_equal(got, ref)
 
 
+def test_noalloc_sort_repeated_keys_across_runs(gpu_ready):
+    """Equal keys in both runs of a merge (lists longer than 4096 keys drawn from
+    a few hundred values, so every run boundary splits groups of equal keys):
+    the result is the ascending order of the input, nothing lost or duplicated."""
+    rng = np.random.default_rng(5)
+    sizes = [9000, 1, 0, 4097, 300, 16384 + 17]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    keys = np.concatenate([(rng.integers(0, 257, m).astype(np.uint64) << np.uint64(32)) |
+                           rng.integers(0, 3, m).astype(np.uint64) for m in sizes])
+    want = keys.copy()
+    for t in range(len(sizes)):
+        want[off[t]:off[t + 1]].sort()
+    for _ in range(2):
+        got = sort_noalloc(off, keys)
+        assert np.array_equal(got, want)
+
+
 def test_noalloc_sort_rejects_oversized_input(gpu_ready):
     import paper_2604_02586_b300 as tsp
     too_many = (1 << 20) + 1
