@@ -30,7 +30,7 @@ struct tsp_context {
     std::string err;
     size_t held = 0;
     // per (view, Gaussian)
-    Buf rect, depth, touched, geom0, geom1, cull, dref, oref, color, moments, vres0, vres1, vres2, vres3;
+    Buf rect, depth, touched, rec, oref, color, moments, vres0, vres1, vres2, vres3;
     // per tile
     Buf tiles, tile_off, span_sum, queue;
     Buf gacc;                       // render backward: per (view, Gaussian) 2D gradients
@@ -178,7 +178,7 @@ void release(tsp_context* ctx, Buf& b)
 // Every device buffer of the workspace (not the pinned status words).
 void release_workspace(tsp_context* ctx)
 {
-    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->geom0, &ctx->geom1, &ctx->cull, &ctx->dref, &ctx->oref, &ctx->color,
+    Buf* all[] = {&ctx->rect, &ctx->depth, &ctx->touched, &ctx->rec, &ctx->oref, &ctx->color,
                   &ctx->moments, &ctx->vres0, &ctx->vres1, &ctx->vres2, &ctx->vres3, &ctx->tiles, &ctx->tile_off,
                   &ctx->span_sum, &ctx->queue, &ctx->gacc, &ctx->reg, &ctx->pairs, &ctx->pairs_tmp, &ctx->dstatus,
                   &ctx->stats, &ctx->st_in, &ctx->st_out, &ctx->st_tracks};
@@ -352,10 +352,7 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     if ((s = ensure(ctx, ctx->rect, vn1 * sizeof(short4)))) return s;
     if ((s = ensure(ctx, ctx->depth, vn1 * 4))) return s;
     if ((s = ensure(ctx, ctx->touched, vn1 * 4))) return s;
-    if ((s = ensure(ctx, ctx->geom0, vn1 * 16))) return s;
-    if ((s = ensure(ctx, ctx->geom1, vn1 * 16))) return s;
-    if ((s = ensure(ctx, ctx->cull, vn1 * 16))) return s;
-    if ((s = ensure(ctx, ctx->dref, vn1 * 8))) return s;
+    if ((s = ensure(ctx, ctx->rec, vn1 * 64))) return s;
     if (!render && (s = ensure(ctx, ctx->oref, vn1 * 4))) return s;
     if (render) {
         if ((s = ensure(ctx, ctx->color, vn1 * 16))) return s;
@@ -382,10 +379,7 @@ tsp_status ensure_work(tsp_context* ctx, uint64_t R, uint32_t NT, bool render, W
     w.rect = (short4*)ctx->rect.p;
     w.depth = (uint32_t*)ctx->depth.p;
     w.touched = (uint32_t*)ctx->touched.p;
-    w.geom0 = (float4*)ctx->geom0.p;
-    w.geom1 = (float4*)ctx->geom1.p;
-    w.cull = (float4*)ctx->cull.p;
-    w.dref = (float2*)ctx->dref.p;
+    w.rec = (float4*)ctx->rec.p;
     w.oref = (uint32_t*)ctx->oref.p;
     w.color = (float4*)ctx->color.p;
     w.moments = (float4*)ctx->moments.p;

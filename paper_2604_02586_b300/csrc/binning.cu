@@ -99,11 +99,13 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
             mean2d_df(vs.cam[v], m, ux, uy);
             const float rx = __fadd_rn(__fsub_rn(ux.x, (float)(p.x0 * vs.tw)), ux.y);
             const float ry = __fadd_rn(__fsub_rn(uy.x, (float)(p.y0 * vs.th)), uy.y);
-            w.geom0[i] = make_float4(rx, ry, f.x, f.y);
+            float4* rc = w.rec + 4 * i;
+            rc[kRecGeom0] = make_float4(rx, ry, f.x, f.y);
             const float2 dlt = moment_origin_shift(ux, uy, rx, ry, p.x0 * vs.tw, p.y0 * vs.th,
                                                    vs.cam[v].W, vs.cam[v].H);
-            w.geom1[i] = make_float4(f.z, m.w, dlt.x, dlt.y);
-            w.cull[i] = cull_record(f.x, f.y, f.z, m.w);
+            rc[kRecGeom1] = make_float4(f.z, m.w, dlt.x, dlt.y);
+            rc[kRecCull] = cull_record(f.x, f.y, f.z, m.w);
+            rc[kRecCorner] = make_float4(rec_pack_corner(p.x0, p.y0), 0.f, 0.f, 0.f);
             if (mode == 0) {
                 // the pixel holding the moment origin; k_dref reads the track there
                 const int W = vs.cam[v].W, H = vs.cam[v].H;
@@ -155,10 +157,10 @@ __global__ void __launch_bounds__(256) k_dref(const ViewSet vs, Work w, int v0)
     const uint32_t pix = w.oref[i];
     if (w.checked && !pixel_ok(pix, (uint32_t)vs.cam[v].W, (uint32_t)vs.cam[v].H)) {
         check_failed(w.dstatus, kSiteRefPixel);
-        w.dref[i] = make_float2(0.f, 0.f);
+        reinterpret_cast<float2*>(w.rec + 4 * i + kRecCorner)[1] = make_float2(0.f, 0.f);
         return;
     }
-    w.dref[i] = vs.disp[v][pix];
+    reinterpret_cast<float2*>(w.rec + 4 * i + kRecCorner)[1] = vs.disp[v][pix];
 }
 
 // Exclusive scan of the NT strided tile counts in three launches: (1) each CTA

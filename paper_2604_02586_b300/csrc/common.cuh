@@ -73,10 +73,7 @@ struct Work {
     short4* rect;          // [R] tile rect x0 y0 x1 y1
     uint32_t* depth;       // [R] FP32 depth bits
     uint32_t* touched;     // [R]
-    float4* geom0;         // [R] mu - rect origin (x, y), i11, k  (blend factor form)
-    float4* geom1;         // [R] i22, opacity, moment origin - mu (x, y)
-    float4* cull;          // [R] culling constants (cull_record)
-    float2* dref;          // [R] reference displacement (track at the moment origin)
+    float4* rec;           // [R * 4] blend records (kRec*: one 64-byte block per record)
     uint32_t* oref;        // [R] pixel index of the moment origin (fit mode)
     float4* color;         // [R] render colour
     float4* moments;       // [R*4] 16 floats per (view, Gaussian)
@@ -380,6 +377,30 @@ __device__ __forceinline__ void sh_basis16_grad(float x, float y, float z, float
 
 // Blend record with its mean moved from the Gaussian's rectangle corner to this
 // tile's corner (an exact integer shift, so the staged mean keeps its precision).
+// Blend record of a (view, Gaussian), four float4 in one 64-byte block, so that
+// a tile-list entry costs two 32-byte sectors of one cache line:
+//   [kRecGeom0] mean - rectangle corner pixel (x, y), i11, k (blend factor form)
+//   [kRecGeom1] i22, opacity, moment origin - mean (x, y)
+//   [kRecCull]  culling constants (cull_record)
+//   [kRecCorner] rectangle corner tile (x0, y0) as two 16-bit integers in the
+//               bits of .x, unused .y, reference displacement (.z, .w): the
+//               track at the moment origin (fit mode)
+constexpr int kRecGeom0 = 0, kRecGeom1 = 1, kRecCull = 2, kRecCorner = 3;
+
+__device__ __forceinline__ float rec_pack_corner(int x0, int y0)
+{
+    return __uint_as_float((uint32_t)(uint16_t)x0 | ((uint32_t)(uint16_t)y0 << 16));
+}
+
+// geom0 moved to tile (tx, ty)'s local frame from the packed corner
+__device__ __forceinline__ float4 tile_local_packed(float4 g0, float corner, int tx, int ty, int tw, int th)
+{
+    const uint32_t c = __float_as_uint(corner);
+    g0.x += (float)(((int)(c & 0xffffu) - tx) * tw);
+    g0.y += (float)(((int)(c >> 16) - ty) * th);
+    return g0;
+}
+
 __device__ __forceinline__ float4 tile_local(float4 g0, short4 r, int tx, int ty, int tw, int th)
 {
     g0.x += (float)((r.x - tx) * tw);

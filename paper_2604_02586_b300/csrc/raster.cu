@@ -101,13 +101,15 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
         if (kStats && tid == 0) n_list += nb;
         if (tid < nb) {
             const uint32_t g = (uint32_t)w.pairs[b0 + tid];
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, kTile, kTile);
-            const float4 g1 = w.geom1[vbase + g];
+            const float4* rc = w.rec + 4 * (vbase + g);
+            const float4 c3 = rc[kRecCorner];
+            const float4 g0 = tile_local_packed(rc[kRecGeom0], c3.x, tx, ty, kTile, kTile);
+            const float4 g1 = rc[kRecGeom1];
             s_id[tid] = g;
             s_g0[tid] = g0;
             s_g1[tid] = g1;
             s_box[tid] = footprint_box(g0, g1);
-            s_ref[tid] = w.dref[vbase + g];
+            s_ref[tid] = make_float2(c3.z, c3.w);
         }
         __syncthreads();
         bool alive = false;
@@ -261,7 +263,6 @@ struct WarpSmem {
     float2 g1[32];                 // this step's hits: i22, log2(opacity)
     float4 hd[kRing];              // by hit number: (origin x, origin y, reference x, reference y)
     uint32_t id[kRing];            // by hit number: Gaussian index
-    uint2 mask[kChunk];            // by pending column: the pixels the hit added (rows 0-3, 4-7)
     float W[kWWords];
     float4 D[2][16];               // per half and pixel pair: (d_x, d_x', d_y, d_y')
     float2 S[2][16];               // per half and pixel pair: static flags (0 or 1)
@@ -323,6 +324,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     if (kStats && blk == 0 && lane == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
     int pend = 0, q0 = 0, qh = 0;              // pending count, first pending and next hit number (mod kRing)
+    uint32_t h_m0 = 0, h_m1 = 0;
 
     auto phase2 = [&](int npend) {
         if (kStats && lane == 0) cnt[5] += 1;
@@ -398,7 +400,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
                        -a10.x - a10.y, -a11.x - a11.y, -a12.x - a12.y};
 #pragma unroll
         for (int q = 0; q < 13; ++q) s[q] += __shfl_down_sync(kFull, s[q], 16);
-        const uint2 hm = sm.mask[c];
+        const uint2 hm = make_uint2(h_m0, h_m1);
         const int np = __popc(hm.x) + __popc(hm.y);
         if (lane < npend && np > 0) {
             const float h_ns = (float)(__popc(hm.x & stat_mask[0]) + __popc(hm.y & stat_mask[1]));
@@ -425,10 +427,14 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             check_failed(w.dstatus, kSiteListEntry);
             live = false;
         }
+        float2 rf = make_float2(0.f, 0.f);
         if (live) {
-            g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
-            g1 = w.geom1[vbase + g];
-            const float4 cr = w.cull[vbase + g];
+            const float4* rc = w.rec + 4 * (vbase + g);
+            const float4 c3 = rc[kRecCorner];
+            g0 = tile_local_packed(rc[kRecGeom0], c3.x, tx, ty, TW, TH);
+            g1 = rc[kRecGeom1];
+            rf = make_float2(c3.z, c3.w);
+            const float4 cr = rc[kRecCull];
             hit = g0.x - cr.x <= bx1 && g0.x + cr.x >= bx0 && g0.y - cr.y <= by1 && g0.y + cr.y >= by0;
             if (hit) hit = block_min_power_c(g0, g1.x, cr.w, bx0, bx1, by0, by1) <= cr.z;
         }
@@ -439,7 +445,6 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             const int r = __popc(m & ((1u << lane) - 1u));
             int slot = qh + r;
             slot = slot >= kRing ? slot - kRing : slot;
-            const float2 rf = w.dref[vbase + g];
             sm.g0[r] = g0;
             // log2(opacity), so that alpha = 2^(log2 o - power)
             sm.g1[r] = make_float2(g1.x, log2f(g1.y));
@@ -464,26 +469,31 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
                 const float z20 = fmaf(-h0.w, ex, yc0 - h0.y) * h1.x;
                 const float2 z2 = make_float2(z20, fmaf(4.0f, h1.x, z20));
                 const float2 q = __ffma2_rn(z2, z2, make_float2(base, base));   // power - log2 o
-                // alpha = min(0.99, 2^-q) >= 1/255  <=>  q <= log2 255
-                const bool p0 = q.x <= kLog2_255, p1 = q.y <= kLog2_255;
+                // alpha = min(0.99, 2^-q) >= 1/255  <=>  q <= log2 255.  The tests
+                // yield 1.0 / 0.0 factors, so that the selections run as packed
+                // multiplications on the FMA pipe (the compare-and-select pipe is
+                // the busier one)
+                const float2 pf = make_float2(q.x <= kLog2_255 ? 1.f : 0.f, q.y <= kLog2_255 ? 1.f : 0.f);
                 const float e0 = sfu_exp2(-q.x), e1 = sfu_exp2(-q.y);
                 // -alpha' with alpha' = alpha where it passes, else 0 (T is then kept exactly)
-                const float2 nap = make_float2(p0 ? fmaxf(-kAlphaMax, -e0) : 0.f, p1 ? fmaxf(-kAlphaMax, -e1) : 0.f);
+                const float2 nap = __fmul2_rn(make_float2(fmaxf(-kAlphaMax, -e0), fmaxf(-kAlphaMax, -e1)), pf);
                 const float2 Tn = __ffma2_rn(nap, T2, T2);             // T - alpha' T
                 const float2 wv = __fmul2_rn(nap, __fmul2_rn(T2, vis2)); // -alpha' T (0 where not visible)
                 // T (1 - alpha') < 1e-4: terminated (T = 0 stays 0); its weight and
                 // every later one are 0
-                const bool b0k = Tn.x >= kTMin, b1k = Tn.y >= kTMin;
+                const float2 bf = make_float2(Tn.x >= kTMin ? 1.f : 0.f, Tn.y >= kTMin ? 1.f : 0.f);
                 if (kStats) {
                     cnt[0] += (T2.x > 0.f) + (T2.y > 0.f);
-                    cnt[1] += (b0k && p0 && T2.x > 0.f) + (b1k && p1 && T2.y > 0.f);
+                    cnt[1] += (bf.x > 0.f && pf.x > 0.f && T2.x > 0.f) + (bf.y > 0.f && pf.y > 0.f && T2.y > 0.f);
                 }
-                T2 = make_float2(b0k ? Tn.x : 0.f, b1k ? Tn.y : 0.f);
-                const float w0 = b0k ? wv.x : 0.f, w1 = b1k ? wv.y : 0.f;
+                T2 = __fmul2_rn(Tn, bf);
+                const float2 wb = __fmul2_rn(wv, bf);
+                const float w0 = wb.x, w1 = wb.y;
                 Wb[2 * col] = w0;                  // the buffer holds -w
                 Wb[kWHalf + 2 * col] = w1;
                 const uint32_t m0 = __ballot_sync(kFull, w0 < 0.f), m1 = __ballot_sync(kFull, w1 < 0.f);
-                if (lane == 0) sm.mask[col] = make_uint2(m0, m1);
+                h_m0 = lane == col ? m0 : h_m0;
+                h_m1 = lane == col ? m1 : h_m1;
                 if (kStats) {
                     cnt[2] += (w0 < 0.f) + (w1 < 0.f);
                     if (lane == 0 && (m0 | m1)) cnt[4] += 1;

@@ -56,13 +56,12 @@ __device__ __forceinline__ void render_block(const ViewSet& vs, const Work& w, c
         const uint32_t g = g_next;
         if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
         if (b0 + lane < end) {
-            const float4 g0 = tile_local(w.geom0[vbase + g], w.rect[vbase + g], tx, ty, TW, TH);
-            const float4 g1 = w.geom1[vbase + g];
-            const float4 bb = footprint_box(g0, g1);
-            hit = bb.x <= bx1 && bb.y >= bx0 && bb.z <= by1 && bb.w >= by0;
-            if (hit)
-                hit = block_min_power(g0, g1.x, bx0, bx1, by0, by1) <=
-                      log2f(255.0f * g1.y) * 1.002f + 1e-4f;
+            const float4* rc = w.rec + 4 * (vbase + g);
+            const float4 g0 = tile_local_packed(rc[kRecGeom0], rc[kRecCorner].x, tx, ty, TW, TH);
+            const float4 g1 = rc[kRecGeom1];
+            const float4 cr = rc[kRecCull];
+            hit = g0.x - cr.x <= bx1 && g0.x + cr.x >= bx0 && g0.y - cr.y <= by1 && g0.y + cr.y >= by0;
+            if (hit) hit = block_min_power_c(g0, g1.x, cr.w, bx0, bx1, by0, by1) <= cr.z;
             if (hit) {
                 sm.g0[lane] = g0;
                 sm.g1[lane] = g1;

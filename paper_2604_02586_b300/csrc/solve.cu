@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const FitP
                 const float Y10 = (Sxx * Ry0 - Sxy * Rx0) * idS, Y11 = (Sxx * Ry1 - Sxy * Rx1) * idS;
                 // intercept at the moment origin o = mu + delta; the displacement sums
                 // were taken about the reference r, which only shifts the intercept
-                const float2 rf = w.dref[i];
+                const float4 rc3 = w.rec[4 * i + kRecCorner];
+                const float2 rf = make_float2(rc3.z, rc3.w);
                 const float co0 = (M[6] - M[1] * Y00 - M[2] * Y10) * isw + rf.x;
                 const float co1 = (M[7] - M[1] * Y01 - M[2] * Y11) * isw + rf.y;
                 A00 = 1.0f + Y00; A01 = Y10; A10 = Y01; A11 = 1.0f + Y11;
