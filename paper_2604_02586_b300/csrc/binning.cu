@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const ViewSet vs, const floa
                                                    vs.cam[v].W, vs.cam[v].H);
             rc[kRecGeom1] = make_float4(f.z, m.w, dlt.x, dlt.y);
             rc[kRecCull] = cull_record(f.x, f.y, f.z, m.w);
-            rc[kRecCorner] = make_float4(rec_pack_corner(p.x0, p.y0), 0.f, 0.f, 0.f);
+            rc[kRecCorner] = make_float4(rec_pack_corner(p.x0, p.y0), log2f(m.w), 0.f, 0.f);
             if (mode == 0) {
                 // the pixel holding the moment origin; k_dref reads the track there
                 const int W = vs.cam[v].W, H = vs.cam[v].H;

@@ -383,8 +383,8 @@ __device__ __forceinline__ void sh_basis16_grad(float x, float y, float z, float
 //   [kRecGeom1] i22, opacity, moment origin - mean (x, y)
 //   [kRecCull]  culling constants (cull_record)
 //   [kRecCorner] rectangle corner tile (x0, y0) as two 16-bit integers in the
-//               bits of .x, unused .y, reference displacement (.z, .w): the
-//               track at the moment origin (fit mode)
+//               bits of .x, log2(opacity) in .y, reference displacement
+//               (.z, .w): the track at the moment origin (fit mode)
 constexpr int kRecGeom0 = 0, kRecGeom1 = 1, kRecCull = 2, kRecCorner = 3;
 
 __device__ __forceinline__ float rec_pack_corner(int x0, int y0)

@@ -1,22 +1,22 @@
 // raster.cu -- a5 raster-accumulate (Sec. 4.3.5).
 //
-// One CTA per 16x16 tile.  The tile's depth-sorted list is walked in batches of
-// kBatch Gaussians whose blend parameters are staged in shared memory together
-// with a conservative footprint box.  Each warp owns a block of the tile and
-// skips every Gaussian whose box misses it (no pixel there can reach
-// alpha = 1/255, so nothing changes).  Each
-// pixel blends front to back: alpha = min(0.99, o G(x)), Gaussians with
-// alpha < 1/255 are skipped, the walk stops before a Gaussian that would bring
-// the transmittance below 1e-4, and w = alpha T (Eq. 4's weight).
+// Every pixel blends its tile's depth-sorted list front to back:
+// alpha = min(0.99, o G(x)), Gaussians with alpha < 1/255 are skipped, the walk
+// stops before a Gaussian that would bring the transmittance below 1e-4, and
+// each visible pixel adds w = alpha T (Eq. 4's weight) times its moment terms to
+// the Gaussian's (view, Gaussian) record: 13 sums and two pixel counts.  Sums
+// are taken about a per-(view, Gaussian) origin (mu_2D clamped to the image) and
+// displacement reference (the track at that origin), which keeps FP32 sums free
+// of cancellation; a6 undoes both shifts exactly.
 //
-// Moments: every visible pixel adds 16 values per Gaussian.  The 32 lanes of a
-// warp are folded with a transposing butterfly (16 shuffles for 16 values, each
-// step exchanges half of the values still held), warps are summed through
-// shared memory, and one float4 atomic per 4 values goes to global memory, so a
-// (tile, Gaussian) pair costs 4 vector atomics whatever the number of pixels.
-// Sums are taken about a per-(view, Gaussian) origin (mu_2D clamped to the image)
-// and displacement reference (the track at that origin), which keeps FP32 sums
-// free of cancellation; a6 undoes both shifts exactly.
+// The default kernel, k_raster_accumulate_2p (and its persistent form), runs
+// one warp per 8x8 block of a tile in two phases: a branch-free pixel-parallel
+// blend that writes each pending hit's weights into a warp-private buffer, then
+// a hit-parallel pass that sums 16 hits' moments in packed FP32x2 and adds them
+// with four float4 atomics per hit (see accumulate_block).  The tile-per-CTA
+// warp-shuffle kernels k_raster_accumulate<P> (8x4, 8x8, 8x16 warp blocks) are
+// the autotuner's alternatives: they fold each hit's 16 values across the warp
+// with a transposing butterfly instead of a weight buffer.
 #include <algorithm>
 
 #include "launch.h"
@@ -427,13 +427,12 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             check_failed(w.dstatus, kSiteListEntry);
             live = false;
         }
-        float2 rf = make_float2(0.f, 0.f);
+        float4 c3 = g0;
         if (live) {
             const float4* rc = w.rec + 4 * (vbase + g);
-            const float4 c3 = rc[kRecCorner];
+            c3 = rc[kRecCorner];
             g0 = tile_local_packed(rc[kRecGeom0], c3.x, tx, ty, TW, TH);
             g1 = rc[kRecGeom1];
-            rf = make_float2(c3.z, c3.w);
             const float4 cr = rc[kRecCull];
             hit = g0.x - cr.x <= bx1 && g0.x + cr.x >= bx0 && g0.y - cr.y <= by1 && g0.y + cr.y >= by0;
             if (hit) hit = block_min_power_c(g0, g1.x, cr.w, bx0, bx1, by0, by1) <= cr.z;
@@ -447,8 +446,8 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             slot = slot >= kRing ? slot - kRing : slot;
             sm.g0[r] = g0;
             // log2(opacity), so that alpha = 2^(log2 o - power)
-            sm.g1[r] = make_float2(g1.x, log2f(g1.y));
-            sm.hd[slot] = make_float4(g0.x + g1.z, g0.y + g1.w, rf.x, rf.y);
+            sm.g1[r] = make_float2(g1.x, c3.y);
+            sm.hd[slot] = make_float4(g0.x + g1.z, g0.y + g1.w, c3.z, c3.w);
             sm.id[slot] = g;
         }
         if (kStats && lane == 0) { cnt[3] += nh; cnt[6] += 1; }
