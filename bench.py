@@ -41,13 +41,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve", "train", "reg"],
+    ap.add_argument("--preset", default="capture", choices=["capture", "tiny", "batch", "serve", "train", "reg", "knn"],
                     help="capture: 200k Gaussians x 18 views at 1352x1014 (the metric's workload); "
                          "tiny: 2,000 Gaussians x 4 ring views at 128x128 (launch-bound); "
                          "batch: 8 uneven frame pairs, batched vs one at a time; "
                          "serve: Poisson requests at 40/s, request loop vs one at a time; "
                          "train: render forward + L1 + backward, 300k Gaussians x 16 views; "
-                         "reg: motion regularization after the capture frame's fit")
+                         "reg: motion regularization after the capture frame's fit; "
+                         "knn: the exact 8-nearest-neighbour search on 200k points of four distributions")
     ap.add_argument("--rate", type=float, default=40.0, help="serve: mean requests per second")
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds of arrivals")
     ap.add_argument("--n", type=int, default=None)
@@ -312,6 +313,11 @@ def run_ours(a):
     tbuild.build()
 
     scene = make_scene(a, rank)
+    if job is not None:
+        # the extra records' scenes finish generating before anything is timed,
+        # so that no worker competes with the host side of the measurement
+        import concurrent.futures as cf
+        cf.wait([f for fs in job[1].values() for f in (fs if isinstance(fs, list) else [fs])])
     units = scene.n * scene.num_views
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     mo, q, s = t(scene.means_opacity), t(scene.quats), t(scene.scales)
@@ -833,8 +839,62 @@ def run_reg(a):
     print(json.dumps(line), flush=True)
 
 
+def run_knn(a):
+    """The exact k-nearest-members search (tsp_knn, k = 8, every point a member)
+    on 200k points of four distributions: uniform in a box, sphere surfaces,
+    sphere surfaces with a 5 % far field, and tight blobs.  The skewed sets go to
+    the bounding-volume hierarchy (chosen on the device); the line reports the
+    path and the time of each."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    from paper_2604_02586_b300 import build as tbuild
+    import synth
+    tbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = a.n or 200_000
+    stream = torch.cuda.current_stream()
+    res = {}
+    with tsp.Context(0) as ctx:
+        for kind in ("uniform", "spheres", "spheres_far", "blobs"):
+            rng = np.random.default_rng(17)
+            if kind == "spheres":                            # sphere surfaces, no far field
+                mo = synth.point_set("spheres_far", n, rng)
+                d = rng.normal(size=(n // 20, 3))
+                d /= np.linalg.norm(d, axis=1, keepdims=True)
+                mo[: n // 20, :3] = mo[n // 20: 2 * (n // 20), :3] + 1e-3 * d
+            else:
+                mo = synth.point_set(kind, n, rng)
+            pts = torch.from_numpy(mo).to(dev)
+            mask = torch.ones(n, dtype=torch.uint8, device=dev)
+            for _ in range(a.warmup):
+                ctx.knn(pts, mask, 8)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(a.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.knn(pts, mask, 8)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            ctx.sync()
+            path = int(ctx.inspect(tsp.TSP.I_KNN_PATH)[0])
+            res[kind] = {"ms": float(np.mean(ms)), "p50_ms": float(np.percentile(ms, 50)),
+                         "path": "bvh" if path else "grid"}
+    line = {"metric": "exact 8-nearest-neighbour search (tsp_knn): points/s", "value": n / (res["uniform"]["ms"] / 1e3),
+            "unit": "points/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n} points, k = 8, every point a member; synth.point_set distributions"},
+            "sets": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.preset == "knn":
+        run_knn(a)
+        return
     if a.preset == "train":
         run_train(a)
         return

@@ -457,6 +457,9 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         // phase 1 in runs that end where the pending columns fill up
         for (int i = 0; i < nh;) {
             const int take = min(nh - i, kChunk - pend);
+            // unrolled by 4: a hit's transmittance-free part (power, exponential)
+            // overlaps the previous hit's blend
+#pragma unroll 4
             for (int j = 0; j < take; ++j) {
                 const int col = pend + j;
                 const float4 h0 = sm.g0[i + j];

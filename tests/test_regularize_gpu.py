@@ -44,36 +44,7 @@ def cuda(a):
 
 
 def points(kind, n, rng):
-    mo = np.zeros((n, 4), np.float32)
-    if kind == "uniform":
-        mo[:, :3] = rng.uniform(-2, 2, (n, 3))
-    elif kind == "clustered":
-        c = rng.uniform(-2, 2, (6, 3))
-        mo[:, :3] = c[rng.integers(0, 6, n)] + rng.normal(0, 0.02, (n, 3))
-        mo[: n // 10, :3] = rng.uniform(-20, 20, (n // 10, 3))        # a sparse far field
-    elif kind == "lattice":
-        side = int(np.ceil(n ** (1 / 3))) + 1
-        g = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)
-        mo[:, :3] = g[rng.permutation(len(g))[:n]] * 0.25
-    elif kind == "flat":
-        mo[:, :2] = rng.uniform(-1, 1, (n, 2))
-        mo[:, 2] = 0.5
-    elif kind == "duplicates":
-        base = rng.uniform(-1, 1, (max(1, n // 4), 3))
-        mo[:, :3] = base[rng.integers(0, len(base), n)]
-    elif kind == "offset":                                            # far from the origin
-        mo[:, :3] = 1000.0 + rng.uniform(0, 1, (n, 3))
-    elif kind in ("spheres_far", "blobs"):
-        c = rng.uniform(-2, 2, (20, 3))
-        if kind == "blobs":
-            mo[:, :3] = c[rng.integers(0, 20, n)] + rng.normal(0, 0.02, (n, 3))
-        else:                                                         # surfaces and floaters
-            d = rng.normal(size=(n, 3))
-            d /= np.linalg.norm(d, axis=1, keepdims=True)
-            mo[:, :3] = c[rng.integers(0, 20, n)] + 0.3 * d
-            mo[: n // 20, :3] = rng.uniform(-20, 20, (n // 20, 3))
-    mo[:, 3] = 0.5
-    return mo
+    return synth.point_set(kind, n, rng)
 
 
 def mask_of(kind, n, rng):
