@@ -340,15 +340,14 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         // pairs (the position moments, then the displacement moments).  y~ is
         // constant along a row of 4 pairs, so the moments with a y~ factor are
         // formed per row from that row's sums: sum w y~ = sum_rows y~ (sum_row w).
-        const float2 z = make_float2(0.f, 0.f);
-        float2 a0 = z, a1 = z, a2 = z, a3 = z, a4 = z, a5 = z, a6 = z, a7 = z, a8 = z, a9 = z, a10 = z,
-               a11 = z, a12 = z;
+        // (the first row and pair assign instead of adding to zero)
+        float2 a0, a1, a2, a3, a4, a5, a6, a7, a8, a9, a10, a11, a12;
         const float* Wh = sm.W + half * kWHalf + 2 * c;
         const float4* Dh = sm.D[half];
         const float2* Sh = sm.S[half];
 #pragma unroll
         for (int row = 0; row < 4; ++row) {
-            float2 rw = z, rwx = z;
+            float2 rw, rwx;
 #pragma unroll
             for (int cp = 0; cp < 4; ++cp) {
                 const int p = 4 * row + cp;
@@ -356,24 +355,42 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
                 const float2 st2 = Sh[p];
                 const float2 X = make_float2(x0 + (float)(2 * cp), x0 + (float)(2 * cp + 1));
                 const float2 wX = __fmul2_rn(w2, X);
-                rw = __fadd2_rn(rw, w2);
-                rwx = __fadd2_rn(rwx, wX);
-                a3 = __ffma2_rn(wX, X, a3);
-                a12 = __ffma2_rn(w2, st2, a12);
+                if (cp == 0) {
+                    rw = w2;
+                    rwx = wX;
+                } else {
+                    rw = __fadd2_rn(rw, w2);
+                    rwx = __fadd2_rn(rwx, wX);
+                }
+                if (p == 0) {
+                    a3 = __fmul2_rn(wX, X);
+                    a12 = __fmul2_rn(w2, st2);
+                } else {
+                    a3 = __ffma2_rn(wX, X, a3);
+                    a12 = __ffma2_rn(w2, st2, a12);
+                }
             }
             const float yv = y0 + (float)row;
             const float2 Y = make_float2(yv, yv);
             const float2 rwy = __fmul2_rn(rw, Y);
-            a0 = __fadd2_rn(a0, rw);
-            a1 = __fadd2_rn(a1, rwx);
-            a2 = __fadd2_rn(a2, rwy);
-            a4 = __ffma2_rn(rwx, Y, a4);
-            a5 = __ffma2_rn(rwy, Y, a5);
+            if (row == 0) {
+                a0 = rw;
+                a1 = rwx;
+                a2 = rwy;
+                a4 = __fmul2_rn(rwx, Y);
+                a5 = __fmul2_rn(rwy, Y);
+            } else {
+                a0 = __fadd2_rn(a0, rw);
+                a1 = __fadd2_rn(a1, rwx);
+                a2 = __fadd2_rn(a2, rwy);
+                a4 = __ffma2_rn(rwx, Y, a4);
+                a5 = __ffma2_rn(rwy, Y, a5);
+            }
         }
         const float2 nrx = make_float2(-hd.z, -hd.z), nry = make_float2(-hd.w, -hd.w);
 #pragma unroll
         for (int row = 0; row < 4; ++row) {
-            float2 rdx = z, rdy = z;
+            float2 rdx, rdy;
 #pragma unroll
             for (int cp = 0; cp < 4; ++cp) {
                 const int p = 4 * row + cp;
@@ -382,17 +399,34 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
                 const float2 X = make_float2(x0 + (float)(2 * cp), x0 + (float)(2 * cp + 1));
                 const float2 wdx = __fmul2_rn(w2, __fadd2_rn(make_float2(dd.x, dd.y), nrx));
                 const float2 wdy = __fmul2_rn(w2, __fadd2_rn(make_float2(dd.z, dd.w), nry));
-                rdx = __fadd2_rn(rdx, wdx);
-                rdy = __fadd2_rn(rdy, wdy);
-                a8 = __ffma2_rn(X, wdx, a8);
-                a9 = __ffma2_rn(X, wdy, a9);
+                if (cp == 0) {
+                    rdx = wdx;
+                    rdy = wdy;
+                } else {
+                    rdx = __fadd2_rn(rdx, wdx);
+                    rdy = __fadd2_rn(rdy, wdy);
+                }
+                if (p == 0) {
+                    a8 = __fmul2_rn(X, wdx);
+                    a9 = __fmul2_rn(X, wdy);
+                } else {
+                    a8 = __ffma2_rn(X, wdx, a8);
+                    a9 = __ffma2_rn(X, wdy, a9);
+                }
             }
             const float yv = y0 + (float)row;
             const float2 Y = make_float2(yv, yv);
-            a6 = __fadd2_rn(a6, rdx);
-            a7 = __fadd2_rn(a7, rdy);
-            a10 = __ffma2_rn(rdx, Y, a10);
-            a11 = __ffma2_rn(rdy, Y, a11);
+            if (row == 0) {
+                a6 = rdx;
+                a7 = rdy;
+                a10 = __fmul2_rn(rdx, Y);
+                a11 = __fmul2_rn(rdy, Y);
+            } else {
+                a6 = __fadd2_rn(a6, rdx);
+                a7 = __fadd2_rn(a7, rdy);
+                a10 = __ffma2_rn(rdx, Y, a10);
+                a11 = __ffma2_rn(rdy, Y, a11);
+            }
         }
         // the buffer holds -w: negate while joining the pair halves
         float s[13] = {-a0.x - a0.y, -a1.x - a1.y, -a2.x - a2.y, -a3.x - a3.y, -a4.x - a4.y,
