@@ -97,6 +97,7 @@ def lib():
         _lib.orc_multiview.argtypes = [C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_sh_basis.argtypes = [C.c_double, C.c_double, C.c_double, P]
         _lib.orc_max_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
     return _lib
 
 
@@ -317,6 +318,11 @@ def sh_basis(d):
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads the oracle's parallel regions use from now on (<= 0: the default)."""
+    lib().orc_set_threads(int(n))
 
 
 REG_STATIC, REG_POS_MEDIAN, REG_POS_PROPAGATED, REG_COV_MEDIAN, REG_COV_PROPAGATED = 1, 2, 4, 8, 16

@@ -1522,6 +1522,19 @@ int orc_sh_basis(double x, double y, double z, double* Y)
     return 0;
 }
 
+/* Threads the parallel regions use from now on (timing only: a single-thread
+ * time of the oracle); n <= 0 restores the default. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    static int dflt = 0;
+    if (!dflt) dflt = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : dflt);
+#else
+    (void)n;
+#endif
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP
