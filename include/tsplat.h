@@ -409,6 +409,24 @@ typedef void* (*tsp_alloc_fn)(size_t bytes, int device, void* user);
 typedef void (*tsp_free_fn)(void* ptr, size_t bytes, int device, void* user);
 tsp_status tsp_set_allocator(tsp_context* ctx, tsp_alloc_fn alloc, tsp_free_fn release, void* user);
 
+/* Device-side start gate of the calls that read caller-owned device tracks
+ * (tsp_fit_motion, tsp_fit_motion_batch; not the host-buffer call, which copies
+ * its tracks itself).  With a gate set, such a call projects, bins and sorts as
+ * usual, then waits on the device -- the host is not involved -- until the
+ * 32-bit word at `flag` (device memory of the context's device, 4-byte aligned)
+ * is >= `value`, polling with acquire semantics about once a microsecond: a
+ * producer that writes the tracks on another stream posts the word after them
+ * (with release semantics: a stream-ordered write or a fence before the store).
+ * The wait gives up after `timeout_us` microseconds (the GPU's global timer,
+ * and a poll count as a second bound); the call then computes nothing from the
+ * tracks and writes none of its fitted outputs (means, quats, scales, status,
+ * view_affine, view_flags; a requested view_moments copy holds zeros), and
+ * tsp_sync reports TSP_ERR_TIMEOUT.  The context stays usable.  flag NULL
+ * removes the gate.  The wait counts in the raster stage's time.
+ * Errors: INVALID_ARG (ctx NULL, flag misaligned or not device memory,
+ * timeout_us outside [1, 1e7]). */
+tsp_status tsp_set_track_gate(tsp_context* ctx, const uint32_t* flag, uint32_t value, int64_t timeout_us);
+
 /* Replace the workspace ceiling (options.budget_bytes; 0 = unlimited).  A call
  * whose workspace would grow past it fails with TSP_ERR_BUDGET before any of its
  * work is enqueued (with async_pairs = 0, a pair buffer grown after the count

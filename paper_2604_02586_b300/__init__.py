@@ -115,6 +115,7 @@ def lib():
         L.tsp_stage_times.argtypes = [P, P, I, P]
         L.tsp_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
         L.tsp_set_budget.argtypes = [P, C.c_int64]
+        L.tsp_set_track_gate.argtypes = [P, P, C.c_uint32, C.c_int64]
         L.tsp_sort_tiles_noalloc.argtypes = [P, P, C.c_uint32, C.c_uint32, P]
         L.tsp_sort_tiles_noalloc.restype = I
         L.tsp_status_string.argtypes = [I]
@@ -125,7 +126,7 @@ def lib():
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
                      "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render",
                      "tsp_render_backward", "tsp_sync", "tsp_inspect", "tsp_default_reg_options",
-                     "tsp_regularize", "tsp_knn", "tsp_set_allocator", "tsp_set_budget",
+                     "tsp_regularize", "tsp_knn", "tsp_set_allocator", "tsp_set_budget", "tsp_set_track_gate",
                      "tsp_workspace_bytes", "tsp_stage_times"):
             getattr(L, name).restype = I
         _lib = L
@@ -253,6 +254,20 @@ class Context:
         f = FREE_FN(lambda ptr, nbytes, device, user: free(int(ptr), int(nbytes), int(device)))
         self._check(lib().tsp_set_allocator(self._h, a, f, None), "tsp_set_allocator")
         self._alloc_cb, self._free_cb = a, f          # the library keeps calling these
+
+    def set_track_gate(self, flag=None, value: int = 1, timeout_us: int = 1_000_000):
+        """Make device-track calls wait on the device until the int32 CUDA tensor
+        ``flag`` (one element) reaches ``value``, for at most ``timeout_us``;
+        None removes the gate (tsp_set_track_gate)."""
+        import torch
+        if flag is None:
+            self._gate = None
+            self._check(lib().tsp_set_track_gate(self._h, None, 0, 0), "tsp_set_track_gate")
+            return
+        _need(flag, (1,), torch.int32, None, "flag")
+        self._check(lib().tsp_set_track_gate(self._h, C.c_void_p(flag.data_ptr()), int(value), int(timeout_us)),
+                    "tsp_set_track_gate")
+        self._gate = flag                           # the library keeps the pointer
 
     def set_budget(self, budget_bytes: int):
         """Workspace ceiling in bytes, 0 = unlimited (tsp_set_budget)."""

@@ -41,6 +41,10 @@ struct tsp_context {
     uint64_t want_pairs = 0;
     Buf dstatus, stats;
     uint32_t* h_status = nullptr;   // pinned, 8 words (the device status word's copy)
+    // track gate (tsp_set_track_gate): device word, value it must reach, limit
+    const uint32_t* gate_flag = nullptr;
+    uint32_t gate_value = 0;
+    long long gate_timeout_us = 0;
     // workspace allocator (tsp_set_allocator); nullptr: cudaMalloc / cudaFree
     tsp_alloc_fn alloc_fn = nullptr;
     tsp_free_fn free_fn = nullptr;
@@ -510,7 +514,13 @@ tsp_status fit_device(tsp_context* ctx, const tsp_frame* frames, int F, cudaStre
     const FitParams fp = fit_params(ctx->opt);
     const int V = vs.V;
     ctx->timed = false;
+    // the gate applies to calls on caller-owned device tracks
+    w.gated = (ctx->gate_flag && !ready) ? 1u : 0u;
     if ((s = bin_front(ctx, vs, nullptr, 0, 0, NT, w, st))) return s;
+    if (w.gated) {
+        StageRange r("tsp:track_gate");
+        TSP_CUDA(launch_track_gate(ctx->gate_flag, ctx->gate_value, ctx->gate_timeout_us, w, st));
+    }
     if (group <= 0) group = V;
     {
         StageRange r("tsp:raster");
@@ -781,6 +791,24 @@ tsp_status tsp_set_allocator(tsp_context* ctx, tsp_alloc_fn alloc, tsp_free_fn r
     return TSP_OK;
 }
 
+tsp_status tsp_set_track_gate(tsp_context* ctx, const uint32_t* flag, uint32_t value, int64_t timeout_us)
+{
+    if (!ctx) return TSP_ERR_INVALID_ARG;
+    if (!flag) {
+        ctx->gate_flag = nullptr;
+        return TSP_OK;
+    }
+    if (!aligned(flag, 4) || timeout_us < 1 || timeout_us > 10000000)
+        return fail(ctx, TSP_ERR_INVALID_ARG, "the gate flag must be 4-byte aligned and the limit in [1, 1e7] us");
+    DeviceGuard dg(ctx->device);
+    if (!device_accessible(flag, ctx->device))
+        return fail(ctx, TSP_ERR_INVALID_ARG, "the gate flag is not device memory");
+    ctx->gate_flag = flag;
+    ctx->gate_value = value;
+    ctx->gate_timeout_us = timeout_us;
+    return TSP_OK;
+}
+
 tsp_status tsp_set_budget(tsp_context* ctx, int64_t budget_bytes)
 {
     if (!ctx || budget_bytes < 0) return TSP_ERR_INVALID_ARG;
@@ -1027,6 +1055,12 @@ tsp_status tsp_sync(tsp_context* ctx, void* stream, int timeout_ms)
         return fail(ctx, TSP_ERR_CUDA, std::string("checked mode: an index left its buffer at ") +
                                            check_site_name(site) + " (site " + std::to_string(site) + ", " +
                                            std::to_string(count) + " times); results are invalid");
+    }
+    if (ctx->h_status[0] & kStatusGate) {
+        TSP_CUDA(cudaMemsetAsync(ctx->dstatus.p, 0, 4, st));
+        TSP_CUDA(cudaStreamSynchronize(st));
+        return fail(ctx, TSP_ERR_TIMEOUT, "the track gate's wait ran out: the flag never reached its value; "
+                                          "nothing was computed from the tracks and no fitted output written");
     }
     if (ctx->h_status[0] & kStatusInternal) {
         TSP_CUDA(cudaMemsetAsync(ctx->dstatus.p, 0, 4, st));

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_dref(const ViewSet vs, Work w, int v0)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = v0 + (int)blockIdx.y;
-    if (g >= vs.vn[v]) return;
+    if (g >= vs.vn[v] || gate_closed(w)) return;
     const size_t i = (size_t)vs.vrec[v] + g;
     if (w.touched[i] == 0u) return;
     const uint32_t pix = w.oref[i];
@@ -599,6 +599,40 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float* sh, int sh_degree,
         k_preprocess<1><<<grid, 256, 0, st>>>(vs, sh, sh_degree, w);
         k_colour<<<dim3((vs.nmax + 127) / 128, vs.F), 128, 0, st>>>(vs, sh, sh_degree, w);
     }
+    return cudaGetLastError();
+}
+
+// The track gate: one thread polls the 32-bit word at `flag` until it reaches
+// `value` (acquire at GPU scope, so the tracks written before the producer's
+// release are visible after), sleeping ~1 us between polls.  The wait is bounded
+// twice, by the global timer and by a poll count; when it runs out it sets
+// kStatusGate and returns, and the track readers and output writers of the call
+// return at once (gate_closed).
+__global__ void k_track_gate(const uint32_t* flag, uint32_t value, unsigned long long timeout_ns,
+                             uint32_t max_polls, uint32_t* dstatus)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t polls = 0;; ++polls) {
+        uint32_t cur;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(flag) : "memory");
+        if (cur >= value) return;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (polls >= max_polls || t - t0 >= timeout_ns) {
+            atomicOr(&dstatus[0], kStatusGate);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+cudaError_t launch_track_gate(const uint32_t* flag, uint32_t value, long long timeout_us, const Work& w,
+                              cudaStream_t st)
+{
+    const unsigned long long ns = (unsigned long long)timeout_us * 1000ull;
+    const uint32_t polls = (uint32_t)std::min<long long>(4 * timeout_us + 1000, 0x7fffffffLL);
+    k_track_gate<<<1, 32, 0, st>>>(flag, value, ns, polls, w.dstatus);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ struct Work {
     uint32_t cap;
     uint32_t nt;           // tiles of the call
     uint32_t checked;      // 1: checked mode (bounds checks into dstatus)
+    uint32_t gated;        // 1: a track gate precedes the track readers (tsp_set_track_gate)
     uint32_t* dstatus;     // [8]: 0 flags (bit 0 overflow, bit 1 internal, bit 2 check),
                            //      1 K (low 32 bits), 2 K high, 3 number of tiles whose
                            //      lists need the long-list sort, 4 first failed check
@@ -118,6 +119,14 @@ struct FitParams {
 constexpr uint32_t kStatusOverflow = 1u;
 constexpr uint32_t kStatusInternal = 2u;   // a bounded device loop gave up (reported by tsp_sync)
 constexpr uint32_t kStatusChecked = 4u;    // checked mode: an index left its buffer (reported by tsp_sync)
+constexpr uint32_t kStatusGate = 8u;       // the track gate's wait ran out (reported by tsp_sync)
+
+// A call whose track gate timed out computes nothing from the tracks on: the
+// track readers and the output writers return at once.
+__device__ __forceinline__ bool gate_closed(const Work& w)
+{
+    return w.gated && (w.dstatus[0] & kStatusGate) != 0u;
+}
 
 // Checked mode: record a failed bounds check (the caller skips the access).
 __device__ __forceinline__ void check_failed(uint32_t* dstatus, uint32_t site)

@@ -12,6 +12,8 @@ cudaError_t launch_preprocess(const ViewSet& vs, const float* sh, int sh_degree,
 // a1 (fit mode): reference displacement of views [v0, v1) -- the track at each
 // record's moment origin.  Needs those views' tracks; the other steps of a1-a4 do not.
 cudaError_t launch_dref(const ViewSet& vs, const Work& w, int v0, int v1, cudaStream_t st);
+cudaError_t launch_track_gate(const uint32_t* flag, uint32_t value, long long timeout_us, const Work& w,
+                              cudaStream_t st);
 // a2: exclusive scan of the per-tile counts -> tile offsets and the pair count K.
 cudaError_t launch_scan(const Work& w, uint32_t NT, cudaStream_t st);
 // Exclusive scan of n counts cnt[i * stride] into off[0..n] (off[n] = total);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
 
     const uint32_t tile = tile_base + blockIdx.x;
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
-    if (beg >= end) return;
+    if (beg >= end || gate_closed(w)) return;
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -280,7 +280,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
                                                  WarpSmem& sm, unsigned long long (&cnt)[7])
 {
     const uint32_t beg = min(w.tile_off[tile], w.cap), end = min(w.tile_off[tile + 1], w.cap);
-    if (beg >= end) return;
+    if (beg >= end || gate_closed(w)) return;
     int v, tx, ty;
     view_of_tile(vs, tile, v, tx, ty);
     const int lane = threadIdx.x & 31;

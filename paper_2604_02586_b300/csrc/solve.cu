@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_view_solve(const ViewSet vs, const FitP
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     const int n = vs.vn[v];
-    if (g >= n) return;
+    if (g >= n || gate_closed(w)) return;
     const size_t i = (size_t)vs.vrec[v] + g;
     const int f = vs.vframe[v];
     const float4* __restrict__ mo = vs.fmo[f];
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(128) k_multiview(const ViewSet vs, const FitPa
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int f = blockIdx.y;
-    if (g >= vs.fn[f]) return;
+    if (g >= vs.fn[f] || gate_closed(w)) return;
     const int v0 = vs.fview[f], v1 = vs.fview[f + 1];
     float4* __restrict__ om = fo.means[f];
     float4* __restrict__ oq = fo.quats[f];

@@ -234,3 +234,49 @@ def test_checked_mode_on_valid_inputs(gpu_ready, variant):
     err = np.linalg.norm(a["means"][both, :3] - b["means"][both, :3], axis=1).max() / s.extent
     assert err < POS_TOL, err
     np.testing.assert_allclose(a["view_moments"][..., 13:15], b["view_moments"][..., 13:15], rtol=0, atol=0)
+
+
+def test_track_gate_that_nothing_opens_times_out_and_recovers(gpu_ready):
+    """A device-side wait on a flag that nothing sets (the track gate) gives up
+    after its limit: tsp_sync reports TSP_ERR_TIMEOUT, none of the fitted
+    outputs is written, and the context then fits as a fresh one does."""
+    import time
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s = synth.make_scene("tiny", 35, n=1500)
+    d = P.to_device(s)
+    with tsp.Context(0) as plain:
+        ref = host(fit(plain, s, d))
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with tsp.Context(0, async_pairs=1, pair_capacity=1 << 20) as ctx:
+        ctx.set_track_gate(flag, 1, timeout_us=20_000)
+        out = sentinel_outputs(s.n)
+        t0 = time.perf_counter()
+        fit(ctx, s, d, out=out, sync=False)
+        with pytest.raises(tsp.TspError) as e:
+            ctx.sync()
+        waited = time.perf_counter() - t0
+        assert e.value.status == tsp.TSP.ERR_TIMEOUT
+        assert 0.01 < waited < 5.0
+        assert torch.all(out["means"] == 7.0) and torch.all(out["status"] == -1)
+        ctx.set_track_gate(None)
+        got = host(fit(ctx, s, d))
+    same_fit(got, ref, s.extent)
+
+
+def test_track_gate_already_open_changes_nothing(gpu_ready):
+    """A gate whose flag already holds a value at or above the one it waits for
+    lets the call run as without a gate."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s = synth.make_scene("tiny", 36, n=1500)
+    d = P.to_device(s)
+    with tsp.Context(0) as plain:
+        ref = host(fit(plain, s, d))
+    flag = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    with tsp.Context(0) as ctx:
+        ctx.set_track_gate(flag, 5, timeout_us=1_000_000)
+        got = host(fit(ctx, s, d))
+        with pytest.raises(tsp.TspError):
+            ctx.set_track_gate(flag, 1, timeout_us=0)
+    same_fit(got, ref, s.extent)
