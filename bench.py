@@ -51,6 +51,8 @@ def parse():
                          "knn: the exact 8-nearest-neighbour search on 200k points of four distributions")
     ap.add_argument("--rate", type=float, default=40.0, help="serve: mean requests per second")
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds of arrivals")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="raster kernel (options.raster_variant) of the capture step")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
@@ -339,13 +341,15 @@ def run_ours(a):
     K = int(probe.inspect(tsp.TSP.I_COUNTS)[0])
     probe.close()
     # exact raster work for the ALU roofline (counting variant, untimed)
-    cnt = tsp.Context(local, collect_stats=1, async_pairs=1, pair_capacity=int(K * 1.1) + 1024)
+    cnt = tsp.Context(local, collect_stats=1, async_pairs=1, pair_capacity=int(K * 1.1) + 1024,
+                      raster_variant=a.variant)
     cnt.fit_motion(mo, q, s, cams, disp, vis, out=out, sync=True)
     wstats = [int(x) for x in cnt.inspect(tsp.TSP.I_STATS)]
     n_eval, n_blend, n_add, n_list = wstats[:4]
     cnt.close()
 
-    ctx = tsp.Context(local, async_pairs=1, stage_timing=1, pair_capacity=int(K * 1.1) + 1024)
+    ctx = tsp.Context(local, async_pairs=1, stage_timing=1, pair_capacity=int(K * 1.1) + 1024,
+                      raster_variant=a.variant)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(a.warmup):

@@ -76,7 +76,7 @@ typedef struct tsp_camera {
 } tsp_camera;
 
 typedef struct tsp_gaussians {
-    int32_t n;                  /* number of Gaussians, 0 <= n < 2^31              */
+    int32_t n;                  /* number of Gaussians, 0 <= n < 2^28 (INVALID_ARG) */
     const float* means_opacity; /* [n][4] (x, y, z, opacity); 16-byte aligned      */
     const float* quats;         /* [n][4] (w, x, y, z); 16-byte aligned            */
     const float* scales;        /* [n][4] (sx, sy, sz, unused), linear; 16-byte al. */

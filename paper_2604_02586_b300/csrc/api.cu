@@ -265,7 +265,7 @@ tsp_status make_viewset(tsp_context* ctx, const tsp_frame* frames, int F, ViewSe
         if (V + Vf > TSP_MAX_BATCH_VIEWS)
             return fail(ctx, TSP_ERR_INVALID_ARG, "more than 192 views in one batch");
         if (Vf > 0 && !fr.cams) return fail(ctx, TSP_ERR_INVALID_ARG, "cams is NULL");
-        if (n < 0) return fail(ctx, TSP_ERR_INVALID_ARG, "n < 0");
+        if (n < 0 || n >= (int)kMaxGaussians) return fail(ctx, TSP_ERR_INVALID_ARG, "n must be in [0, 2^28)");
         vs.fview[f] = V;
         vs.fn[f] = n;
         vs.fmo[f] = (const float4*)fr.g.means_opacity;
@@ -312,7 +312,7 @@ tsp_status make_viewset(tsp_context* ctx, const tsp_frame* frames, int F, ViewSe
 tsp_status check_gaussians(tsp_context* ctx, const tsp_gaussians* g, bool device)
 {
     if (!g) return fail(ctx, TSP_ERR_INVALID_ARG, "g is NULL");
-    if (g->n < 0) return fail(ctx, TSP_ERR_INVALID_ARG, "n < 0");
+    if (g->n < 0 || g->n >= (int)kMaxGaussians) return fail(ctx, TSP_ERR_INVALID_ARG, "n must be in [0, 2^28)");
     if (g->n == 0) return TSP_OK;
     const void* ps[3] = {g->means_opacity, g->quats, g->scales};
     for (const void* p : ps) {
@@ -1101,8 +1101,18 @@ tsp_status tsp_inspect(tsp_context* ctx, int which, void* dst, size_t bytes, siz
     case TSP_I_TILES_TOUCHED: src = ctx->touched.p; size = vn * 4; break;
     case TSP_I_TILE_OFFSETS: src = ctx->tile_off.p; size = ((size_t)ctx->last_NT + 1) * 4; break;
     case TSP_I_PAIRS: {
+        // the lists as (depth bits << 32 | Gaussian index): the walks' block masks
+        // are dropped from the stored keys
         const int64_t K = counts[0] < counts[2] ? counts[0] : counts[2];
-        src = ctx->pairs.p; size = (size_t)K * 8; break;
+        size = (size_t)K * 8;
+        if (size_out) *size_out = size;
+        if (!dst) return TSP_OK;
+        const size_t nk = (bytes < size ? bytes : size) / 8;
+        std::vector<uint64_t> keys(nk);
+        if (nk) TSP_CUDA(cudaMemcpy(keys.data(), ctx->pairs.p, nk * 8, cudaMemcpyDeviceToHost));
+        for (uint64_t& k : keys) k = (k & 0xffffffff00000000ull) | ((k & 0xffffffffull) >> 4);
+        std::memcpy(dst, keys.data(), nk * 8);
+        return TSP_OK;
     }
     case TSP_I_MOMENTS: src = ctx->moments.p; size = vn * 64; break;
     case TSP_I_STATS: src = ctx->stats.p; size = ctx->stats.p ? 64 : 0; break;

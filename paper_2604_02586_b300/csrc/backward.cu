@@ -98,8 +98,6 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
     }
     // column 0 of pixel p = lane (+ 32: two quarters further) in the (h, w) buffer
     const int hofs = (lane >> 4) * kBQuarter + (lane & 15) * kBRow;
-    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
     int pend = 0;
 
     auto phase2 = [&](int npend) {
@@ -151,21 +149,16 @@ __device__ __forceinline__ void backward_block(const ViewSet& vs, const Work& w,
 
     for (uint32_t b0 = beg; b0 < end; b0 += 32) {
         if (!__any_sync(kFull, !done[0] || !done[1])) break;
-        bool hit = false;
-        if (b0 + lane < end) {
-            const uint32_t g = (uint32_t)w.pairs[b0 + lane];
+        // list entries carry the block mask: only the hits load their records
+        const uint32_t e = b0 + lane < end ? (uint32_t)w.pairs[b0 + lane] : 0u;
+        const bool hit = b0 + lane < end && ((e >> blk) & 1u);
+        if (hit) {
+            const uint32_t g = entry_gauss(e);
             const float4* rc = w.rec + 4 * (vbase + g);
-            const float4 g0 = tile_local_packed(rc[kRecGeom0], rc[kRecCorner].x, tx, ty, TW, TH);
-            const float4 g1 = rc[kRecGeom1];
-            const float4 cr = rc[kRecCull];
-            hit = g0.x - cr.x <= bx1 && g0.x + cr.x >= bx0 && g0.y - cr.y <= by1 && g0.y + cr.y >= by0;
-            if (hit) hit = block_min_power_c(g0, g1.x, cr.w, bx0, bx1, by0, by1) <= cr.z;
-            if (hit) {
-                sm.g0[lane] = g0;
-                sm.g1[lane] = g1;
-                sm.c[lane] = w.color[vbase + g];
-                sm.id[lane] = g;
-            }
+            sm.g0[lane] = tile_local_packed(rc[kRecGeom0], rc[kRecCorner].x, tx, ty, TW, TH);
+            sm.g1[lane] = rc[kRecGeom1];
+            sm.c[lane] = w.color[vbase + g];
+            sm.id[lane] = g;
         }
         uint32_t m = __ballot_sync(kFull, hit);
         __syncwarp();

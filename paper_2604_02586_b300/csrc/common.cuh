@@ -515,74 +515,84 @@ __device__ __forceinline__ float render_alpha_g(float4 g0, float4 g1, float xc, 
     return fminf(kAlphaMax, __fmul_rn(g1.y, G));
 }
 
-// Smallest value of p = z1^2 + z2^2 (z1 = ex i11, z2 = (ey - k ex) i22) over the
-// pixel-centre rectangle [bx0, bx1] x [by0, by1] of a warp block, for the
-// tile-local mean (g0.x, g0.y) and factor (i11, k, i22) = (g0.z, g0.w, i22).
-// p is convex, so when the mean lies outside the rectangle the minimum sits on
-// an edge facing the mean: along a vertical edge ex = e it is at ey = k e, along
-// a horizontal edge ey = f at ex = k i22^2 f / (i11^2 + k^2 i22^2), each clamped
-// to the edge.  Returns 0 when the mean is inside.
-// Culling constants of a record, formed once in the projection instead of once
-// per (8x8 block, list entry): the half-extents (hx, hy) of the box holding the
-// alpha >= 1/255 ellipse (footprint_box's), the threshold the block test
-// compares its minimum power with (log2(255 o) with a 0.2 % margin), and
-// k i22^2 / (i11^2 + k^2 i22^2), the slope of the minimizing x along a
-// horizontal edge (block_min_power's).  hx < 0: alpha >= 1/255 nowhere.
+// Culling constants of a record, formed once in the projection: the
+// alpha >= 1/255 region of a Gaussian is the ellipse p = z1^2 + z2^2 <= log2(255 o)
+// (z1 = ex i11, z2 = (ey - k ex) i22, (ex, ey) = pixel centre - mean).  Cut at a
+// height ey, it is the interval c1 ey +- w0 sqrt(1 - (ey / hy)^2) with
+//     A = i11^2 + k^2 i22^2,  c1 = k i22^2 / A,  w0 = sqrt(pm / A),
+//     hy = sqrt(pm A) / (i11 i22)  (the half-height),
+// and its rightmost point sits at ey_r = hy tau / sqrt(1 + tau^2), tau = c1 hy / w0
+// (the leftmost at -ey_r).  The record holds (hy, c1, w0, ey_r) for the threshold
+// raised by 0.2 % + 1e-4 and w0, hy widened by 0.1 % + 1e-3 px, so that FP32
+// rounding never drops a pixel the blend keeps.  hy < 0: alpha >= 1/255 nowhere.
 __device__ __forceinline__ float4 cull_record(float i11, float k, float i22, float opacity)
 {
     const float pm = log2f(255.0f * opacity);
-    if (!(pm > 0.0f)) return make_float4(-1e30f, -1e30f, -1.0f, 0.f);
-    const float sp = sqrtf(pm) * 1.001f;
-    const float ix = 1.0f / i11, iy = 1.0f / i22;
-    const float hx = sp * ix + 1e-3f;
-    const float hy = sp * sqrtf(k * k * ix * ix + iy * iy) + 1e-3f;
+    if (!(pm > 0.0f)) return make_float4(-1e30f, 0.f, 0.f, 0.f);
+    const float pw = pm * 1.002f + 1e-4f;
     const float i22s = i22 * i22;
-    return make_float4(hx, hy, pm * 1.002f + 1e-4f, k * i22s / fmaf(i11, i11, k * k * i22s));
+    const float A = fmaf(i11, i11, k * k * i22s);
+    const float c1 = k * i22s / A;
+    const float w0 = sqrtf(pw / A) * 1.001f + 1e-3f;
+    const float hy = sqrtf(pw * A) / (i11 * i22) * 1.001f + 1e-3f;
+    const float tau = c1 * hy / w0;
+    return make_float4(hy, c1, w0, hy * tau / sqrtf(fmaf(tau, tau, 1.0f)));
 }
 
-// block_min_power with the precomputed slope c1 of cull_record.
-__device__ __forceinline__ float block_min_power_c(float4 g0, float i22, float c1, float bx0, float bx1,
-                                                   float by0, float by1)
+// x-interval [xl, xr] (relative to the mean) of the record's ellipse within the
+// horizontal strip [sy0, sy1] (relative to the mean); false if they do not meet.
+// The upper boundary c1 ey + w0 sqrt(1 - (ey/hy)^2) is concave, so its largest
+// value over the strip is at ey_r clamped to the strip (the lower boundary's
+// smallest at -ey_r); 1e-3 px of slack covers the rounding of the evaluation.
+__device__ __forceinline__ bool strip_extent(float4 cr, float sy0, float sy1, float& xl, float& xr)
 {
-    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
-    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
-    float pv = 3.0e38f, ph = 3.0e38f;
-    if (outx) {
-        const float e = ex0 > 0.f ? ex0 : ex1;
-        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
-        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
-        pv = fmaf(z1, z1, z2 * z2);
-    }
-    if (outy) {
-        const float f = ey0 > 0.f ? ey0 : ey1;
-        const float ex = fminf(fmaxf(c1 * f, ex0), ex1);
-        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
-        ph = fmaf(z1, z1, z2 * z2);
-    }
-    return (outx || outy) ? fminf(pv, ph) : 0.f;
+    const float hy = cr.x, c1 = cr.y, w0 = cr.z, eyr = cr.w;
+    if (!(sy0 <= hy && sy1 >= -hy)) return false;
+    const float lo = fmaxf(sy0, -hy), hi = fminf(sy1, hy);
+    const float yr = fminf(fmaxf(eyr, lo), hi), yl = fminf(fmaxf(-eyr, lo), hi);
+    const float ihy = 1.0f / hy;
+    const float tr = yr * ihy, tl = yl * ihy;
+    const float sr = sqrtf(fmaxf(0.f, fmaf(-tr, tr, 1.0f))), sl = sqrtf(fmaxf(0.f, fmaf(-tl, tl, 1.0f)));
+    xr = fmaf(c1, yr, w0 * sr) + 1e-3f;
+    xl = fmaf(c1, yl, -w0 * sl) - 1e-3f;
+    return true;
 }
 
-__device__ __forceinline__ float block_min_power(float4 g0, float i22, float bx0, float bx1,
-                                                 float by0, float by1)
+// Tile-list entry (a 64-bit sort key): FP32 depth bits << 32 | Gaussian index << 4
+// | block mask.  Keys order by (depth, index) -- the mask sits below the index
+// and (depth, index) is unique -- and the low word gives the walks both the
+// Gaussian (index < 2^28) and, in bit b, whether its alpha >= 1/255 ellipse
+// can meet the tile's 8x8 block b (block b at ((b % (tw / 8)) * 8, (b / (tw / 8)) * 8)
+// in the tile: four blocks for 16 x 16 and 32 x 8 tiles).
+constexpr uint32_t kMaxGaussians = 1u << 28;
+__device__ __forceinline__ uint64_t pair_key(uint32_t depth_bits, uint32_t g, uint32_t mask)
 {
-    const float ex0 = bx0 - g0.x, ex1 = bx1 - g0.x, ey0 = by0 - g0.y, ey1 = by1 - g0.y;
-    const bool outx = ex0 > 0.f || ex1 < 0.f, outy = ey0 > 0.f || ey1 < 0.f;
-    float pv = 3.0e38f, ph = 3.0e38f;
-    if (outx) {
-        const float e = ex0 > 0.f ? ex0 : ex1;
-        const float ey = fminf(fmaxf(g0.w * e, ey0), ey1);
-        const float z1 = e * g0.z, z2 = fmaf(-g0.w, e, ey) * i22;
-        pv = fmaf(z1, z1, z2 * z2);
+    return ((uint64_t)depth_bits << 32) | (g << 4) | mask;
+}
+__device__ __forceinline__ uint32_t entry_gauss(uint32_t lo) { return lo >> 4; }
+
+// Block mask of a record in one tile: (mx, my) its mean in the tile's frame, cr
+// its culling constants.  Bit b is set when the ellipse meets block b's pixel
+// centres [bx + 0.5, bx + 7.5] x [by + 0.5, by + 7.5]: per 8-pixel row of blocks,
+// the ellipse's x-interval in that strip against each block's columns.
+__device__ __forceinline__ uint32_t block_hit_mask(float mx, float my, float4 cr, int tw)
+{
+    const int nbx = tw >> 3, nby = 4 / nbx;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r >= nby) break;
+        const float sy0 = ((float)(8 * r) + 0.5f) - my;
+        float xl, xr;
+        if (!strip_extent(cr, sy0, sy0 + 7.0f, xl, xr)) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c >= nbx) break;
+            const float bx0 = ((float)(8 * c) + 0.5f) - mx;
+            if (xl <= bx0 + 7.0f && xr >= bx0) m |= 1u << (r * nbx + c);
+        }
     }
-    if (outy) {
-        const float f = ey0 > 0.f ? ey0 : ey1;
-        const float i22s = i22 * i22;
-        const float a = fmaf(g0.z, g0.z, g0.w * g0.w * i22s);
-        const float ex = fminf(fmaxf(g0.w * i22s * f / a, ex0), ex1);
-        const float z1 = ex * g0.z, z2 = fmaf(-g0.w, ex, f) * i22;
-        ph = fmaf(z1, z1, z2 * z2);
-    }
-    return (outx || outy) ? fminf(pv, ph) : 0.f;
+    return m;
 }
 
 __device__ __forceinline__ float render_transmit(float T, float alpha)

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
         const int nb = (int)min((uint32_t)kBatch, end - b0);
         if (kStats && tid == 0) n_list += nb;
         if (tid < nb) {
-            const uint32_t g = (uint32_t)w.pairs[b0 + tid];
+            const uint32_t g = entry_gauss((uint32_t)w.pairs[b0 + tid]);
             const float4* rc = w.rec + 4 * (vbase + g);
             const float4 c3 = rc[kRecCorner];
             const float4 g0 = tile_local_packed(rc[kRecGeom0], c3.x, tx, ty, kTile, kTile);
@@ -319,8 +319,6 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         if (k == 0) { T2.x = inside ? 1.f : 0.f; vis2.x = vis; }
         else { T2.y = inside ? 1.f : 0.f; vis2.y = vis; }
     }
-    const float bx0 = (float)bxo + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)byo + 0.5f, by1 = by0 + 7.0f;
     if (kStats && blk == 0 && lane == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
     int pend = 0, q0 = 0, qh = 0;              // pending count, first pending and next hit number (mod kRing)
@@ -449,31 +447,28 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         q0 = q0 >= kRing ? q0 - kRing : q0;
     };
 
-    uint32_t g_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
+    // list entries carry the block mask (bit blk: the entry's ellipse may meet
+    // this block); only the hits load their records
+    uint32_t e_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
     for (uint32_t b0 = beg; b0 < end; b0 += 32) {
         if (!__any_sync(kFull, T2.x > 0.f || T2.y > 0.f)) break;
-        bool hit = false;
-        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
-        const uint32_t g = g_next;
-        if (b0 + 32 + lane < end) g_next = (uint32_t)w.pairs[b0 + 32 + lane];
-        bool live = b0 + lane < end;
-        if (live && w.checked && !index_ok(g, (uint32_t)vs.vn[v])) {
+        const uint32_t e = e_next;
+        if (b0 + 32 + lane < end) e_next = (uint32_t)w.pairs[b0 + 32 + lane];
+        const uint32_t g = entry_gauss(e);
+        bool hit = b0 + lane < end && ((e >> blk) & 1u);
+        if (hit && w.checked && !index_ok(g, (uint32_t)vs.vn[v])) {
             check_failed(w.dstatus, kSiteListEntry);
-            live = false;
-        }
-        float4 c3 = g0;
-        if (live) {
-            const float4* rc = w.rec + 4 * (vbase + g);
-            c3 = rc[kRecCorner];
-            g0 = tile_local_packed(rc[kRecGeom0], c3.x, tx, ty, TW, TH);
-            g1 = rc[kRecGeom1];
-            const float4 cr = rc[kRecCull];
-            hit = g0.x - cr.x <= bx1 && g0.x + cr.x >= bx0 && g0.y - cr.y <= by1 && g0.y + cr.y >= by0;
-            if (hit) hit = block_min_power_c(g0, g1.x, cr.w, bx0, bx1, by0, by1) <= cr.z;
+            hit = false;
         }
         const uint32_t m = __ballot_sync(kFull, hit);
+        if (kStats && lane == 0) cnt[6] += 1;
+        if (m == 0u) continue;
         const int nh = __popc(m);
         if (hit) {
+            const float4* rc = w.rec + 4 * (vbase + g);
+            const float4 c3 = rc[kRecCorner];
+            const float4 g0 = tile_local_packed(rc[kRecGeom0], c3.x, tx, ty, TW, TH);
+            const float4 g1 = rc[kRecGeom1];
             // staged in list order: the hit's rank among this step's hits
             const int r = __popc(m & ((1u << lane) - 1u));
             int slot = qh + r;
@@ -484,7 +479,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             sm.hd[slot] = make_float4(g0.x + g1.z, g0.y + g1.w, c3.z, c3.w);
             sm.id[slot] = g;
         }
-        if (kStats && lane == 0) { cnt[3] += nh; cnt[6] += 1; }
+        if (kStats && lane == 0) cnt[3] += nh;
         qh += nh;
         qh = qh >= kRing ? qh - kRing : qh;
         __syncwarp();
