@@ -273,17 +273,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // lane have their slot atomics (and their lists' start offsets) in flight before
 // any result is used.  Lanes stay
 // busy whatever the mix of culled, small and large records.
-__global__ void __launch_bounds__(256, 3) k_scatter(const ViewSet vs, Work w)
+__global__ void __launch_bounds__(256) k_scatter(const ViewSet vs, Work w)
 {
     constexpr int kIlp = 8;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0u, rxy = 0u, rzw = 0u, klo = 0u, khi = 0u;
-    // the record's mean (relative to its rectangle's corner pixel) and culling
-    // constants, for the block mask of each of its tiles
-    float2 rmu = make_float2(0.f, 0.f);
-    float4 rcl = make_float4(-1e30f, 0.f, 0.f, 0.f);
     if (g < vs.vn[v]) {
         const size_t i = (size_t)vs.vrec[v] + g;
         cnt = w.touched[i];
@@ -293,9 +289,6 @@ __global__ void __launch_bounds__(256, 3) k_scatter(const ViewSet vs, Work w)
             rzw = (uint32_t)(uint16_t)r.z | ((uint32_t)(uint16_t)r.w << 16);
             klo = (uint32_t)g;
             khi = w.depth[i];
-            const float4* rc = w.rec + 4 * i;
-            rmu = *reinterpret_cast<const float2*>(rc + kRecGeom0);
-            rcl = rc[kRecCull];
         }
     }
     uint32_t inc = cnt;
@@ -309,7 +302,7 @@ __global__ void __launch_bounds__(256, 3) k_scatter(const ViewSet vs, Work w)
     const uint32_t base = vs.toff[v];
     const int tx_n = vs.tiles_x[v];
     for (uint32_t it0 = 0; it0 < total; it0 += 32 * kIlp) {
-        uint32_t toff[kIlp], slot[kIlp], k0[kIlp], k1[kIlp], tt[kIlp], ow[kIlp];
+        uint32_t toff[kIlp], slot[kIlp], k0[kIlp], k1[kIlp], tt[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const uint32_t item = it0 + (uint32_t)(u * 32 + lane);
@@ -328,8 +321,8 @@ __global__ void __launch_bounds__(256, 3) k_scatter(const ViewSet vs, Work w)
             const uint32_t dy = rw ? off / rw : 0u, dx = off - dy * rw;
             const uint32_t t = base + (y0 + dy) * (uint32_t)tx_n + x0 + dx;
             tt[u] = t;
-            ow[u] = (uint32_t)own | (dx << 8) | (dy << 20);
-            // the list's start is fetched while the slot atomic is in flight
+            // the list's start is fetched, and the entry's block mask formed, while
+            // the slot atomic is in flight
             if (item < total) {
                 if (w.checked && !index_ok(t, w.nt)) {
                     check_failed(w.dstatus, kSiteScatterTile);
@@ -338,21 +331,14 @@ __global__ void __launch_bounds__(256, 3) k_scatter(const ViewSet vs, Work w)
                 }
                 slot[u] = atomicAdd(&w.tile_fill[(size_t)t * kCounterStride], 1u);
                 toff[u] = w.tile_off[t];
+                // the entry's low word: Gaussian << 4 | block mask (pair_key), the mean
+                // moved to the tile's corner by tile_local's exact integer shift
+                const float4* rc = w.rec + 4 * ((size_t)vs.vrec[v] + k0[u]);
+                const float2 mu = *reinterpret_cast<const float2*>(rc + kRecGeom0);
+                const uint32_t mk = block_hit_mask(mu.x + (float)(-(int)dx * vs.tw), mu.y + (float)(-(int)dy * vs.th),
+                                                   rc[kRecCull], vs.tw);
+                k0[u] = (k0[u] << 4) | mk;
             }
-        }
-        // while the atomics are in flight: each item's block mask from its owner's
-        // blend data moved to the item's tile corner (tile_local's exact integer
-        // shift; a rectangle spans fewer than 4096 tiles each way)
-        uint32_t bm[kIlp];
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-            const int own = (int)(ow[u] & 31u);
-            const int dx = (int)((ow[u] >> 8) & 0xfffu), dy = (int)(ow[u] >> 20);
-            const float mx = __shfl_sync(0xffffffffu, rmu.x, own) + (float)(-dx * vs.tw);
-            const float my = __shfl_sync(0xffffffffu, rmu.y, own) + (float)(-dy * vs.th);
-            const float4 cl = make_float4(__shfl_sync(0xffffffffu, rcl.x, own), __shfl_sync(0xffffffffu, rcl.y, own),
-                                          __shfl_sync(0xffffffffu, rcl.z, own), __shfl_sync(0xffffffffu, rcl.w, own));
-            bm[u] = block_hit_mask(mx, my, cl, vs.tw);
         }
 #pragma unroll
         for (int u = 0; u < kIlp; ++u)
@@ -365,7 +351,7 @@ __global__ void __launch_bounds__(256, 3) k_scatter(const ViewSet vs, Work w)
                     }
                 }
                 const uint64_t pos = (uint64_t)toff[u] + slot[u];
-                if (pos < w.cap) w.pairs[pos] = pair_key(k1[u], k0[u], bm[u]);
+                if (pos < w.cap) w.pairs[pos] = ((uint64_t)k1[u] << 32) | k0[u];
             }
     }
 }
