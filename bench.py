@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds of arrivals")
     ap.add_argument("--variant", type=int, default=0,
                     help="raster kernel (options.raster_variant) of the capture step")
+    ap.add_argument("--priority", action="store_true",
+                    help="serve: request streams with CUDA stream priorities by arrival order")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
@@ -292,7 +294,7 @@ def run_extras(a, job):
     ss = [f.result() for f in futs["serve"]]
     ex["serve"] = {"workload": "scenes: " + ", ".join(f"{s.n}x{s.num_views}@{int(s.width[0])}x{int(s.height[0])}"
                                                       for s in ss),
-                   "budget_bytes": 120 << 30, "max_inflight": 8,
+                   "budget_bytes": 120 << 30, "max_inflight": 8, "stream_priorities": False,
                    "at_40_per_s": serve_measure(ss, 40.0, 4.0), "at_150_per_s": serve_measure(ss, 150.0, 3.0)}
     del ss
     torch.cuda.empty_cache()
@@ -604,7 +606,7 @@ def train_scene():
     return synth.make_scene("capture", seed=4, n=300_000, views=16, tracks=False)
 
 
-def serve_measure(scenes, rate, duration, seed=7):
+def serve_measure(scenes, rate, duration, seed=7, priority=False):
     """Poisson arrivals at ``rate`` per second for ``duration`` seconds over a pool
     of scenes, served by the request loop (scene-resident, overlapped,
     HBM-budgeted) and by the plain one-at-a-time path on the same arrival times;
@@ -627,7 +629,7 @@ def serve_measure(scenes, rate, duration, seed=7):
     units = lambda r: int(scenes[int(r.scene[1:])].n) * int(scenes[int(r.scene[1:])].num_views)
 
     def serve():
-        srv = MotionServer(0, budget_bytes=120 << 30, max_inflight=8, chain=False)
+        srv = MotionServer(0, budget_bytes=120 << 30, max_inflight=8, chain=False, priority=priority)
         for k, s in enumerate(scenes):
             srv.add_scene(f"s{k}", s.means_opacity, s.quats, s.scales)
         # one warm-up frame per scene (contexts, workspaces, CUDA modules)
@@ -656,7 +658,7 @@ def run_serve(a):
     tbuild.build()
     torch.cuda.set_device(0)
     scenes = serve_scenes()
-    r = serve_measure(scenes, a.rate, a.duration)
+    r = serve_measure(scenes, a.rate, a.duration, priority=a.priority)
     srv_stats, plain_stats = r["server"], r["one_at_a_time"]
     line = {"metric": f"frame-pair requests: p50/p99 latency and fits/s at {a.rate:g} req/s (Poisson)",
             "value": srv_stats["fits_per_s"], "unit": UNIT, "n_gpus": 1, "steps": r["requests"], "warmup": len(scenes),
@@ -665,7 +667,8 @@ def run_serve(a):
             "config": {"workload": "scenes: " + ", ".join(f"{s.n}x{s.num_views}@{int(s.width[0])}x{int(s.height[0])}"
                                                           for s in scenes),
                        "rate_per_s": a.rate, "duration_s": a.duration, "budget_bytes": 120 << 30,
-                       "max_inflight": 8, "tracks": "pinned host memory, copied inside each request"},
+                       "max_inflight": 8, "stream_priorities": a.priority,
+                       "tracks": "pinned host memory, copied inside each request"},
             "p50_ms": srv_stats["p50_ms"], "p99_ms": srv_stats["p99_ms"], "server": srv_stats,
             "one_at_a_time": plain_stats}
     print(json.dumps(line), flush=True)

@@ -11,8 +11,12 @@ frame -- and admits waiting requests as slots and device memory free up:
   of everything resident plus its tracks stay within ``budget_bytes``; idle
   scenes are evicted (least recently used first, state copied to host memory)
   to make room;
-* each scene owns a CUDA stream, so the work of requests admitted while others
-  run overlaps on the device; a scene's frames are serialised on its stream;
+* requests admitted while others run overlap on the device, each on a stream
+  taken from a pool; a scene's frames are serialised by CUDA events.  With
+  ``priority`` the pool's streams carry CUDA stream priorities and a request
+  gets a lower one than every request already on the device, so that the block
+  scheduler favours the oldest work (B300 offers four levels; on the serving
+  benchmark it did not lower the p99, so it is off by default);
 * completion is polled with CUDA events; latency = completion - arrival;
 * each scene's library context is given the budget's headroom (the budget less
   what the other resident scenes and the in-flight tracks hold) before every
@@ -75,7 +79,8 @@ class _Scene:
         self.host = (mo, q, s)           # host copy while not resident
         self.dev = None                  # (means_opacity, quats, scales) on the device
         self.ctx = None
-        self.stream = None
+        self.stream = None               # the stream of the scene's latest frame
+        self.last_ev = None              # recorded after the scene's latest device work
         self.busy = False
         self.last_used = 0.0
         self.ws_bytes = 0
@@ -95,7 +100,7 @@ class _Scene:
 
 class MotionServer:
     def __init__(self, device=0, budget_bytes=120 << 30, max_inflight=8, keep_inputs=False, chain=True,
-                 **options):
+                 priority=False, **options):
         import torch
         self.torch = torch
         self.device = device
@@ -115,6 +120,11 @@ class MotionServer:
         self.t0 = time.perf_counter()
         self.evictions = 0
         self.peak_bytes = 0
+        # stream pool: level 0 is the highest priority; free streams per level
+        self.priority = priority
+        lo, hi = torch.cuda.Stream.priority_range() if priority else (0, 0)
+        self.levels = list(range(hi, lo + 1)) if hi <= lo else list(range(lo, hi - 1, -1))
+        self.free_streams = {k: [] for k in range(len(self.levels))}
 
     # ---------------------------------------------------------------- scenes
     def add_scene(self, sid, means_opacity, quats, scales):
@@ -128,16 +138,29 @@ class MotionServer:
         sc = self.scenes[sid]
         if sc.dev is None:
             return sc.host
-        sc.stream.synchronize()
+        if sc.last_ev is not None:
+            sc.last_ev.synchronize()
         return tuple(t.cpu().numpy() for t in sc.dev)
+
+    def _take_stream(self):
+        """A free pool stream one level below every request on the device (the
+        lowest level once they reach it).  Returns (level, stream)."""
+        used = [item[4] for item in self.inflight]
+        level = min(max(used) + 1, len(self.levels) - 1) if used else 0
+        pool = self.free_streams[level]
+        st = pool.pop() if pool else self.torch.cuda.Stream(device=self.dev, priority=self.levels[level])
+        return level, st
+
+    def _give_stream(self, level, st):
+        self.free_streams[level].append(st)
 
     def _used_bytes(self, exclude=None):
         used = 0
         for sc in self.scenes.values():
             if sc.dev is not None and sc is not exclude:
                 used += sc.resident_bytes()
-        for req, sc, _, _ in self.inflight:
-            used += req.track_bytes()
+        for item in self.inflight:
+            used += item[0].track_bytes()
         return used
 
     def _fail(self, req, sc, why):
@@ -148,18 +171,18 @@ class MotionServer:
             sc.busy = False
         self.failed.append(req)
 
-    def _make_resident(self, sc, req):
+    def _make_resident(self, sc, stream):
         torch = self.torch
-        if sc.stream is None:
-            sc.stream = torch.cuda.Stream(device=self.dev)
-        with torch.cuda.stream(sc.stream):
+        with torch.cuda.stream(stream):
             sc.dev = tuple(torch.from_numpy(a).pin_memory().to(self.dev, non_blocking=True) for a in sc.host)
+        sc.stream = stream
         sc.host = None
         if sc.ctx is None:
             sc.ctx = Context(self.device, **self.options)
 
     def _evict(self, sc):
-        sc.stream.synchronize()
+        if sc.last_ev is not None:
+            sc.last_ev.synchronize()
         sc.host = tuple(t.cpu().numpy() for t in sc.dev)
         sc.dev = None
         sc.ws_bytes = sc.ctx.workspace_bytes()
@@ -216,24 +239,34 @@ class MotionServer:
         request failed alone and is listed in ``failed``) or "wait" (the library
         refused a workspace that does not fit while other requests hold memory:
         the request waits for them)."""
+        level, st = self._take_stream()
         if sc.dev is None:
-            self._make_resident(sc, req)
+            self._make_resident(sc, st)
+        elif sc.stream is not st:
+            # the frame follows the scene's previous one, which ran on another stream
+            if sc.last_ev is not None:
+                st.wait_event(sc.last_ev)
+            for t in sc.dev:
+                t.record_stream(st)
+            sc.stream = st
         sc.busy = True
         sc.views = max(sc.views, len(req.disp))
         req.start = self.now()
         for attempt in range(2):
             try:
-                self._fit(req, sc)
+                self._fit(req, sc, level)
                 return "ok"
             except TspError as e:
                 if e.status != TSP.ERR_BUDGET:
                     self._fail(req, sc, f"TspError: {e}")
+                    self._give_stream(level, st)
                     return "failed"
                 idle = [x for x in self.scenes.values() if x.dev is not None and not x.busy and x is not sc]
                 if attempt == 0 and idle:
                     for x in idle:                 # make room, then try once more
                         self._evict(x)
                     continue
+                self._give_stream(level, st)
                 if any(x.busy and x is not sc for x in self.scenes.values()):
                     sc.busy = False
                     return "wait"
@@ -243,10 +276,12 @@ class MotionServer:
                 # nothing of this request was enqueued (argument checks and workspace
                 # refusals come first), and the scene keeps its state
                 self._fail(req, sc, f"{type(e).__name__}: {e}")
+                self._give_stream(level, st)
                 return "failed"
+        self._give_stream(level, st)
         return "failed"
 
-    def _fit(self, req, sc):
+    def _fit(self, req, sc, level):
         torch = self.torch
         # the library may grow this scene's workspace only into the headroom
         head = self.budget - self._used_bytes(exclude=sc) - req.track_bytes() - 2 * 48 * sc.n
@@ -262,8 +297,9 @@ class MotionServer:
                 sc.dev = (out["means"], out["quats"], out["scales"])
             ev = torch.cuda.Event()
             ev.record(sc.stream)
+        sc.last_ev = ev
         req.result = out
-        self.inflight.append((req, sc, ev, (disp, vis, (mo, q, s))))
+        self.inflight.append((req, sc, ev, (disp, vis, (mo, q, s)), level, sc.stream))
 
     def poll(self):
         """Retire completed requests; admit waiting ones.  Returns the newly
@@ -272,11 +308,12 @@ class MotionServer:
         still = []
         retry = []
         for item in self.inflight:
-            req, sc, ev, (_, _, prev) = item
+            req, sc, ev, (_, _, prev), level, st = item
             if ev.query():
                 sc.busy = False
+                self._give_stream(level, st)      # idle: nothing is enqueued before _admit
                 try:
-                    sc.ctx.sync(sc.stream)
+                    sc.ctx.sync(st)
                 except TspError as e:
                     sc.dev = prev                      # the scene keeps its last good state
                     if e.status != TSP.ERR_OVERFLOW:
