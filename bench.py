@@ -600,10 +600,11 @@ def serve_scenes(seed=51, count=8):
     return [frame_scene(sp) for sp in serve_specs(seed, count)]
 
 
-def train_scene():
-    """300k Gaussians, SH degree 3, 16 views at 1352x1014 (no tracks)."""
+def train_scene(n=None, views=None):
+    """300k Gaussians, SH degree 3, 16 views at 1352x1014 (no tracks); --n and
+    --views give smaller cases (profiling captures)."""
     import synth
-    return synth.make_scene("capture", seed=4, n=300_000, views=16, tracks=False)
+    return synth.make_scene("capture", seed=4, n=n or 300_000, views=views or 16, tracks=False)
 
 
 def serve_measure(scenes, rate, duration, seed=7, priority=False):
@@ -745,7 +746,7 @@ def run_train(a):
     from paper_2604_02586_b300 import build as tbuild
     tbuild.build()
     torch.cuda.set_device(0)
-    s = train_scene()
+    s = train_scene(a.n, a.views)
     step_ms, fwd_ms, clocks, loss, gnorm = train_measure(s, a.steps, a.warmup)
     units = s.n * s.num_views
     line = {"metric": "gradient-refinement step (render + L1 + backward): Gaussian·view gradients/s",
