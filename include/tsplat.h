@@ -374,8 +374,9 @@ tsp_status tsp_stage_times(tsp_context* ctx, float* ms, int max_n, int* count);
 
 /* Per-tile depth sort without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
- * -- code running while a CUDA graph is being captured, memory-capped tenants
- * of a shared GPU, hosts whose own allocator owns all device memory.
+ * -- memory-capped tenants of a shared GPU whose budget someone else hands out,
+ * hosts whose own allocator owns all device memory, and loops that cannot afford
+ * the device-wide synchronization an allocation or a free may bring.
  * keys: device [num_keys] (depth_bits << 32 | Gaussian), sorted ascending in
  * place within each tile t's slice [offsets[t], offsets[t+1]); keys need not be
  * unique (equal keys are equal values, so their order is immaterial); offsets: device

@@ -1,10 +1,10 @@
 // noalloc.cu -- the per-tile depth sort for callers that cannot allocate device
 // memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured (an allocation would break or serialize the capture), memory-capped
-// tenants of a shared GPU whose budget is handed out by someone else, and hosts
-// that own every byte of device memory through their own allocator.  For them,
+// Some callers cannot call cudaMalloc: memory-capped tenants of a shared GPU
+// whose budget is handed out by someone else, hosts that own every byte of
+// device memory through their own allocator, and latency-bound loops that cannot
+// afford the device-wide synchronization an allocation or a free may bring.  For them,
 // tsp_sort_tiles_noalloc() sorts caller-owned per-tile key lists in place and
 // keeps the merge scratch it needs for long lists in a fixed array compiled into
 // the library (TSP_NOALLOC_SORT_MAX_KEYS keys, 8 MB), which every GPU that loads

@@ -1,6 +1,7 @@
 """tsp_sort_tiles_noalloc: the per-tile depth sort for callers that cannot
-allocate device memory (graph capture in progress, a memory-capped tenant of a
-shared GPU, a host whose own allocator owns the device memory).
+allocate device memory (a memory-capped tenant of a shared GPU, a host whose own
+allocator owns the device memory, a loop that cannot afford an allocation's
+device-wide synchronization).
 
 The entry point is called through the C ABI on shuffled copies of the tile lists
 that tsp_fit_motion produced, twice in a row, and must give back exactly the
