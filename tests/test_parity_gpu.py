@@ -143,6 +143,36 @@ def test_all_list_lengths_bin_bit_exact(gpu_ready, scale):
     assert np.array_equal(g["pairs"], ent)
 
 
+@pytest.mark.parametrize("dup", ["some", "all"])
+def test_equal_depths_bin_bit_exact(gpu_ready, dup):
+    """Copies of Gaussians have bit-equal depths, so their tile lists hold keys of
+    one depth that only the Gaussian index orders (R18): lists of every sort path,
+    with and without such keys, equal the oracle's."""
+    import dataclasses
+    s0 = synth.make_scene("tiny", 3, n=20000, views=2, width=512, height=512, focal=512.0)
+    idx = (np.random.default_rng(5).choice(s0.n, 1500, replace=False) if dup == "some"
+           else np.arange(s0.n))
+    cat = lambda a: np.ascontiguousarray(np.concatenate([a, a[idx]]))
+    s = dataclasses.replace(s0, means_opacity=cat(s0.means_opacity), quats=cat(s0.quats),
+                            scales=cat(s0.scales), sh=cat(s0.sh), labels=cat(s0.labels))
+    g = P.run_gpu(s)
+    off, ent = oracle.bin_lists(s)
+    assert int(g["counts"][0]) == len(ent) and int(g["counts"][3]) == 0
+    assert np.array_equal(g["tile_off"].astype(np.int64), off)
+    assert np.array_equal(g["pairs"], ent)
+    # lists with and without equal depths, among the warp-sorted lengths
+    hi = (ent >> np.uint64(32)).astype(np.int64)
+    same = np.zeros(len(ent), bool)
+    same[1:] = hi[1:] == hi[:-1]
+    same[off[:-1][off[:-1] < len(ent)]] = False          # a list's first key has no predecessor in it
+    tied = np.add.reduceat(same.astype(np.int64), off[:-1].clip(max=len(ent) - 1)) > 0
+    n = np.diff(off)
+    short = (n > 1) & (n <= 512)
+    assert (tied & short).any()
+    if dup == "some":
+        assert (~tied & short).any()
+
+
 def check_moments(s, o, g, tag=None, tile=(16, 16)):
     """All 13 moment sums and both pixel counts of every (view, Gaussian) record
     against the oracle's record restated in the library's frame.
