@@ -216,6 +216,23 @@ tsp_status tsp_fit_motion_batch(tsp_context* ctx, const tsp_frame* frames, int n
 tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats, void* stream,
                         int* chosen, float* fit_ms);
 
+/* The autotuner with a cache file, so that a workload is timed once per machine
+ * and its choice reused by later processes (a tuning choice of the batched launch,
+ * the paper's per-frame parallelism of Sec. 4.6).  The key of a call is (bit length
+ * of the frames' total Gaussian count, total views, largest view's W x H); the
+ * file (cache_path, a host path) holds one text line per tuned key,
+ * "tsp-autotune-v1 <bits> <views> <pixels> <candidate> <median ms>", and the last
+ * line of a key wins.  A key found in the file: its candidate's options are set
+ * and nothing runs on the GPU (*from_cache = 1, fit_ms[candidate] = the stored
+ * median, the other entries -1).  Otherwise tsp_autotune runs as above and a line
+ * is appended (*from_cache = 0).  Lines of another form are skipped.  cache_path
+ * NULL: tsp_autotune alone.  chosen, fit_ms, from_cache are nullable.
+ * Errors: INVALID_ARG (bad frames, or the file cannot be opened for appending:
+ * checked before any tuning), those of tsp_autotune. */
+tsp_status tsp_autotune_cached(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats,
+                               void* stream, const char* cache_path, int* chosen, float* fit_ms,
+                               int* from_cache);
+
 /* Same step for callers that hold everything in host memory: g, tracks and out
  * point to host arrays (pinned memory gives full copy speed and lets the copies
  * overlap the computation).  The Gaussians are copied on `stream` and projected,

@@ -104,6 +104,7 @@ def lib():
         L.tsp_fit_motion_host.argtypes = [P, P, P, I, P, P, P]
         L.tsp_fit_motion_batch.argtypes = [P, P, I, P]
         L.tsp_autotune.argtypes = [P, P, I, I, P, P, P]
+        L.tsp_autotune_cached.argtypes = [P, P, I, I, P, C.c_char_p, P, P, P]
         L.tsp_render.argtypes = [P, P, P, I, P, I, P, P, P]
         L.tsp_render_backward.argtypes = [P, P, P, I, P, I, P, P, P, P]
         L.tsp_default_reg_options.argtypes = [P]
@@ -124,7 +125,7 @@ def lib():
         L.tsp_last_error.restype = C.c_char_p
         L.tsp_version.restype = I
         for name in ("tsp_default_options", "tsp_create", "tsp_destroy", "tsp_fit_motion",
-                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_render",
+                     "tsp_fit_motion_host", "tsp_fit_motion_batch", "tsp_autotune", "tsp_autotune_cached", "tsp_render",
                      "tsp_render_backward", "tsp_sync", "tsp_inspect", "tsp_default_reg_options",
                      "tsp_regularize", "tsp_knn", "tsp_set_allocator", "tsp_set_budget", "tsp_set_track_gate",
                      "tsp_workspace_bytes", "tsp_stage_times"):
@@ -357,17 +358,21 @@ class Context:
     # (tile_w, tile_h, raster_variant), in the order of tsp_autotune's candidates
     TUNE_CANDIDATES = ((16, 16, 0), (16, 16, 5), (16, 16, 2), (16, 16, 1), (16, 16, 4), (32, 8, 0), (32, 8, 5))
 
-    def autotune(self, frames, repeats=3, stream=None):
-        """Time each candidate (tile shape, raster kernel) on ``frames``
-        (fit_motion_batch arguments) by the whole fit and keep the fastest.
-        Returns (candidate, {candidate: median ms}), candidates as in
-        TUNE_CANDIDATES."""
+    def _tune_frames(self, frames):
         keys = ("means_opacity", "quats", "scales", "cams", "disp", "vis")
         prep = [self._frame(*[f[k] for k in keys], f.get("out")) for f in frames]
         arr = (Frame * max(len(prep), 1))()
         for k, (g, carr, V, tr, r, _) in enumerate(prep):
             arr[k].g, arr[k].cams, arr[k].num_views = g, C.cast(carr, C.c_void_p), V
             arr[k].tracks, arr[k].out = C.cast(tr, C.c_void_p), r
+        return prep, arr
+
+    def autotune(self, frames, repeats=3, stream=None):
+        """Time each candidate (tile shape, raster kernel) on ``frames``
+        (fit_motion_batch arguments) by the whole fit and keep the fastest.
+        Returns (candidate, {candidate: median ms}), candidates as in
+        TUNE_CANDIDATES."""
+        prep, arr = self._tune_frames(frames)
         chosen = C.c_int(0)
         ms = (C.c_float * len(self.TUNE_CANDIDATES))()
         self._check(lib().tsp_autotune(self._h, arr, len(prep), int(repeats), _stream_handle(stream),
@@ -375,6 +380,20 @@ class Context:
         best = self.TUNE_CANDIDATES[chosen.value]
         self.opt.tile_w, self.opt.tile_h, self.opt.raster_variant = best
         return best, dict(zip(self.TUNE_CANDIDATES, [float(x) for x in ms]))
+
+    def autotune_cached(self, frames, cache_path, repeats=3, stream=None):
+        """tsp_autotune_cached: the choice for this workload's key from the cache
+        file if it holds one, else tuned as ``autotune`` and appended.  Returns
+        (candidate, {candidate: median ms, -1 where not timed}, from_cache)."""
+        prep, arr = self._tune_frames(frames)
+        chosen, hit = C.c_int(0), C.c_int(0)
+        ms = (C.c_float * len(self.TUNE_CANDIDATES))()
+        self._check(lib().tsp_autotune_cached(self._h, arr, len(prep), int(repeats), _stream_handle(stream),
+                                              os.fsencode(cache_path), C.byref(chosen), ms, C.byref(hit)),
+                    "tsp_autotune_cached")
+        best = self.TUNE_CANDIDATES[chosen.value]
+        self.opt.tile_w, self.opt.tile_h, self.opt.raster_variant = best
+        return best, dict(zip(self.TUNE_CANDIDATES, [float(x) for x in ms])), bool(hit.value)
 
     def fit_motion_host(self, means_opacity, quats, scales, cams, disp, vis, out=None, stream=None):
         """Host path: numpy inputs and outputs; copies happen inside the library."""

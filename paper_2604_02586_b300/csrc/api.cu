@@ -1205,6 +1205,82 @@ tsp_status tsp_autotune(tsp_context* ctx, const tsp_frame* frames, int num_frame
     return TSP_OK;
 }
 
+// Cache key of a tuning call: bit length of the total Gaussian count, total
+// views, the largest view's pixel count.
+struct TuneKey {
+    long long bits, views, pixels;
+};
+
+tsp_status tune_key(const tsp_frame* frames, int num_frames, TuneKey& k)
+{
+    if (!frames || num_frames < 1 || num_frames > TSP_MAX_FRAMES) return TSP_ERR_INVALID_ARG;
+    long long n = 0;
+    k = TuneKey{0, 0, 0};
+    for (int f = 0; f < num_frames; ++f) {
+        const tsp_frame& fr = frames[f];
+        if (fr.g.n < 0 || fr.num_views < 0 || fr.num_views > TSP_MAX_VIEWS || (fr.num_views > 0 && !fr.cams))
+            return TSP_ERR_INVALID_ARG;
+        n += fr.g.n;
+        k.views += fr.num_views;
+        for (int v = 0; v < fr.num_views; ++v)
+            k.pixels = std::max(k.pixels, (long long)fr.cams[v].width * (long long)fr.cams[v].height);
+    }
+    while (n > 0) { ++k.bits; n >>= 1; }
+    return TSP_OK;
+}
+
+tsp_status tsp_autotune_cached(tsp_context* ctx, const tsp_frame* frames, int num_frames, int repeats,
+                               void* stream, const char* cache_path, int* chosen, float* fit_ms,
+                               int* from_cache)
+{
+    if (from_cache) *from_cache = 0;
+    if (!cache_path) return tsp_autotune(ctx, frames, num_frames, repeats, stream, chosen, fit_ms);
+    if (!ctx || repeats < 1 || repeats > 100) return TSP_ERR_INVALID_ARG;
+    TuneKey key;
+    if (tune_key(frames, num_frames, key) != TSP_OK) return fail(ctx, TSP_ERR_INVALID_ARG, "autotune: bad frames");
+    // the last line of this key in the file, if any
+    int hit = -1;
+    float hit_ms = -1.f;
+    if (FILE* f = std::fopen(cache_path, "r")) {
+        char line[256];
+        while (std::fgets(line, sizeof line, f)) {
+            long long b, v, p;
+            int c;
+            float ms;
+            char tag[32];
+            if (std::sscanf(line, "%31s %lld %lld %lld %d %f", tag, &b, &v, &p, &c, &ms) == 6 &&
+                std::strcmp(tag, "tsp-autotune-v1") == 0 && b == key.bits && v == key.views && p == key.pixels &&
+                c >= 0 && c < kTuneCandidates) {
+                hit = c;
+                hit_ms = ms;
+            }
+        }
+        std::fclose(f);
+    }
+    if (hit >= 0) {
+        ctx->opt.tile_w = kTuneTable[hit][0];
+        ctx->opt.tile_h = kTuneTable[hit][1];
+        ctx->opt.raster_variant = kTuneTable[hit][2];
+        if (chosen) *chosen = hit;
+        if (fit_ms)
+            for (int c = 0; c < kTuneCandidates; ++c) fit_ms[c] = c == hit ? hit_ms : -1.f;
+        if (from_cache) *from_cache = 1;
+        return TSP_OK;
+    }
+    FILE* out = std::fopen(cache_path, "a");
+    if (!out) return fail(ctx, TSP_ERR_INVALID_ARG, std::string("autotune: cannot append to ") + cache_path);
+    int c = -1;
+    float ms[kTuneCandidates];
+    const tsp_status s = tsp_autotune(ctx, frames, num_frames, repeats, stream, &c, ms);
+    if (s == TSP_OK && c >= 0)
+        std::fprintf(out, "tsp-autotune-v1 %lld %lld %lld %d %.4f\n", key.bits, key.views, key.pixels, c, ms[c]);
+    std::fclose(out);
+    if (s != TSP_OK) return s;
+    if (chosen) *chosen = c;
+    if (fit_ms) std::memcpy(fit_ms, ms, sizeof ms);
+    return TSP_OK;
+}
+
 tsp_status tsp_default_reg_options(tsp_reg_options* o)
 {
     if (!o) return TSP_ERR_INVALID_ARG;

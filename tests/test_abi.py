@@ -68,6 +68,14 @@ def test_null_context_is_rejected(L):
     assert L.tsp_destroy(None) == tsp.TSP.OK
 
 
+def test_cached_autotune_rejects_null_context_before_touching_the_cache(L, tmp_path):
+    path = tmp_path / "tune.txt"
+    assert L.tsp_autotune_cached(None, None, 1, 3, None, os.fsencode(str(path)), None, None, None) == \
+        tsp.TSP.ERR_INVALID_ARG
+    assert L.tsp_autotune_cached(None, None, 1, 3, None, None, None, None, None) == tsp.TSP.ERR_INVALID_ARG
+    assert not path.exists()
+
+
 def test_create_without_gpu_fails_cleanly(L):
     import torch
     if torch.cuda.is_available():

@@ -199,6 +199,33 @@ def test_batch_replays_from_a_cuda_graph(gpu_ready):
                 d.mul_(2.0)
 
 
+def test_autotune_cache_times_once_and_reuses_the_choice(gpu_ready, tmp_path):
+    """The first call tunes and appends one line for the workload's key; the next
+    call, and a fresh context, take that choice from the file without timing;
+    lines of another form or another key do not match."""
+    import paper_2604_02586_b300 as tsp
+    ss = scenes()
+    args = [frame_args(s) for s in ss]
+    path = tmp_path / "tune.txt"
+    path.write_text("not a tuning line\ntsp-autotune-v1 1 1 1 3 0.5\n")
+    with tsp.Context(0) as ctx:
+        chosen, times, hit = ctx.autotune_cached(args, str(path), repeats=1)
+        assert not hit and chosen in tsp.Context.TUNE_CANDIDATES
+        assert times[chosen] == min(times.values()) > 0
+        lines = path.read_text().splitlines()
+        assert len(lines) == 3 and lines[-1].startswith("tsp-autotune-v1 ")
+        chosen2, times2, hit2 = ctx.autotune_cached(args, str(path), repeats=1)
+        assert hit2 and chosen2 == chosen
+        assert times2[chosen] == pytest.approx(times[chosen], rel=1e-3)
+        assert all(v == -1.0 for c, v in times2.items() if c != chosen)
+    with tsp.Context(0) as ctx:
+        chosen3, _, hit3 = ctx.autotune_cached(args, str(path), repeats=1)
+        assert hit3 and chosen3 == chosen
+        o = ctx.opt
+        assert (o.tile_w, o.tile_h, o.raster_variant) == chosen
+    assert len(path.read_text().splitlines()) == 3
+
+
 def test_autotune_picks_a_candidate_and_results_hold(gpu_ready):
     import paper_2604_02586_b300 as tsp
     ss = scenes()
