@@ -199,6 +199,46 @@ def test_batch_replays_from_a_cuda_graph(gpu_ready):
                 d.mul_(2.0)
 
 
+def test_single_fit_replays_from_a_cuda_graph(gpu_ready):
+    """tsp_fit_motion on one frame, captured once in a CUDA graph (the bench times
+    its steps this way) and replayed after the tracks change in place, gives what a
+    direct call on the changed tracks gives; the tile lists are the same keys."""
+    import torch
+    import paper_2604_02586_b300 as tsp
+    s = scenes()[1]
+    a = frame_args(s)
+    with tsp.Context(0) as probe:
+        probe.fit_motion(a["means_opacity"], a["quats"], a["scales"], s, a["disp"], a["vis"], sync=True)
+        K = int(probe.inspect(tsp.TSP.I_COUNTS)[0])
+    with tsp.Context(0, async_pairs=1, pair_capacity=2 * K) as ctx:
+        out = ctx.fit_motion(a["means_opacity"], a["quats"], a["scales"], s, a["disp"], a["vis"], sync=True)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            ctx.fit_motion(a["means_opacity"], a["quats"], a["scales"], s, a["disp"], a["vis"], out=out)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            ctx.fit_motion(a["means_opacity"], a["quats"], a["scales"], s, a["disp"], a["vis"], out=out)
+        for d in a["disp"]:
+            d.mul_(0.5)
+        graph.replay()
+        torch.cuda.synchronize()
+        got = host(out)
+        pairs_graph = ctx.inspect(tsp.TSP.I_PAIRS)
+        ctx.sync()
+    with tsp.Context(0) as ref:
+        direct = host(ref.fit_motion(a["means_opacity"], a["quats"], a["scales"], s, a["disp"], a["vis"], sync=True))
+        pairs_direct = ref.inspect(tsp.TSP.I_PAIRS)
+    assert np.array_equal(pairs_graph, pairs_direct)
+    assert (got["status"] == direct["status"]).mean() > 0.999
+    both = ((got["status"] & 1) > 0) & ((direct["status"] & 1) > 0)
+    assert both.mean() > 0.3
+    dp = np.linalg.norm(got["means"][both, :3] - direct["means"][both, :3], axis=1) / s.extent
+    assert dp.max() < POS_TOL
+
+
 def test_autotune_cache_times_once_and_reuses_the_choice(gpu_ready, tmp_path):
     """The first call tunes and appends one line for the workload's key; the next
     call, and a fresh context, take that choice from the file without timing;
