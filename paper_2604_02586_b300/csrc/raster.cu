@@ -266,6 +266,7 @@ struct WarpSmem {
     float W[kWWords];
     float4 D[2][16];               // per half and pixel pair: (d_x, d_x', d_y, d_y')
     float2 S[2][16];               // per half and pixel pair: static flags (0 or 1)
+    uint32_t enext[32];            // per lane: the next walk step's list entry (low word)
 };
 
 // One warp, one 8x8 block `blk` of tile `tile`: the two-phase walk above.  Work
@@ -448,12 +449,19 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     };
 
     // list entries carry the block mask (bit blk: the entry's ellipse may meet
-    // this block); only the hits load their records
-    uint32_t e_next = beg + lane < end ? (uint32_t)w.pairs[beg + lane] : 0u;
+    // this block); only the hits load their records.  Each lane's entry of the
+    // next walk step is copied into its shared slot (cp.async) while this step
+    // runs, so that no register holds it through the step's moment passes.
+    const uint32_t e_slot = (uint32_t)__cvta_generic_to_shared(&sm.enext[lane]);
+    if (beg + lane < end)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(e_slot), "l"(&w.pairs[beg + lane]) : "memory");
     for (uint32_t b0 = beg; b0 < end; b0 += 32) {
         if (!__any_sync(kFull, T2.x > 0.f || T2.y > 0.f)) break;
-        const uint32_t e = e_next;
-        if (b0 + 32 + lane < end) e_next = (uint32_t)w.pairs[b0 + 32 + lane];
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        const uint32_t e = sm.enext[lane];        // the low word: Gaussian << 4 | block mask
+        if (b0 + 32 + lane < end)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(e_slot), "l"(&w.pairs[b0 + 32 + lane])
+                         : "memory");
         const uint32_t g = entry_gauss(e);
         bool hit = b0 + lane < end && ((e >> blk) & 1u);
         if (hit && w.checked && !index_ok(g, (uint32_t)vs.vn[v])) {
@@ -540,6 +548,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
         __syncwarp();                                  // staging is rewritten next
     }
     if (pend) phase2(pend);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");   // a copy still in flight after an early end
 }
 
 // Work counts of one warp into the context's counters (stats[3], the list
