@@ -322,7 +322,7 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
     }
     if (kStats && blk == 0 && lane == 0) atomicAdd(&w.stats[3], (unsigned long long)(end - beg));
 
-    int pend = 0, q0 = 0, qh = 0;              // pending count, first pending and next hit number (mod kRing)
+    int pend = 0, q0 = 0;                      // pending count and first pending hit number (mod kRing)
     uint32_t h_m0 = 0, h_m1 = 0;
 
     auto phase2 = [&](int npend) {
@@ -479,7 +479,8 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             const float4 g1 = rc[kRecGeom1];
             // staged in list order: the hit's rank among this step's hits
             const int r = __popc(m & ((1u << lane) - 1u));
-            int slot = qh + r;
+            // hits are numbered on from the pending ones: q0 + pend + r < 2 kRing
+            int slot = q0 + pend + r;
             slot = slot >= kRing ? slot - kRing : slot;
             sm.g0[r] = g0;
             // log2(opacity), so that alpha = 2^(log2 o - power)
@@ -488,8 +489,6 @@ __device__ __forceinline__ void accumulate_block(const ViewSet& vs, const Work& 
             sm.id[slot] = g;
         }
         if (kStats && lane == 0) cnt[3] += nh;
-        qh += nh;
-        qh = qh >= kRing ? qh - kRing : qh;
         __syncwarp();
         // phase 1 in runs that end where the pending columns fill up
         for (int i = 0; i < nh;) {
