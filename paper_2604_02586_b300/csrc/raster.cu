@@ -227,9 +227,11 @@ __global__ void __launch_bounds__(kTilePx / P) k_raster_accumulate(const ViewSet
 // Two-phase accumulate (the default).  Warp w owns the 8x8 block (w & 1, w >> 1)
 // of the tile, lane l the pixels (l & 7, (l >> 3) + 4h), h = 0, 1, and walks the
 // tile's depth-ordered list on its own (no block-wide barrier): 32 entries at a
-// time, lane l loads entry l and tests whether its alpha >= 1/255 ellipse meets
-// the block.  The hits of the step are compacted into warp-private staging in
-// list order (their blend factors) and numbered; each hit's moment origin,
+// time, lane l takes entry l (copied into its shared slot by cp.async during the
+// step before) and tests the entry's bit for the block (whether its alpha >= 1/255
+// ellipse meets the block).  The hits of the step are compacted into warp-private
+// staging in list order (their blend factors) and numbered on from the pending
+// ones; each hit's moment origin,
 // reference track and Gaussian index go to a ring indexed by hit number, where
 // they stay until the hit's moments are added.
 //   Phase 1 (blend, pixel-parallel): for each hit in order, every lane blends its
