@@ -6,6 +6,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -28,3 +30,30 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     c = d["config"]
     assert c["n_gaussians"] == 3000 and c["views"] == 2 and "workload" in c
+
+
+@pytest.mark.gpu
+def test_our_arm_prints_one_contract_line():
+    """bench.py on the tiny frame pair: the keys of the contract, the roofline of the
+    raster kernel, sampled clocks, the kernel count, the launch-loop record beside
+    the graph-replayed steps, and the CPU baseline with its single-thread time."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--preset", "tiny", "--steps", "5", "--warmup", "3",
+           "--no-extras"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "p50_ms", "p99_ms", "roofline", "hbm_step", "stage_ms",
+              "launch_loop", "gpu_launches", "clocks", "e2e", "cpu_baseline"):
+        assert k in d, k
+    assert d["n_gpus"] == 1 and d["steps"] == 5 and d["value"] > 0 and d["gpu_launches"] > 0
+    assert "CUDA-graph replay" in d["config"]["launch"]
+    rf = d["roofline"]
+    assert rf["bound"] == "alu" and rf["unit"] == "TFLOP/s" and 0 < rf["frac"] == pytest.approx(rf["achieved"] / rf["peak"])
+    assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and "single_thread" in d["cpu_baseline"]
+    assert d["launch_loop"]["ms_per_step"] > 0
