@@ -1,6 +1,6 @@
-"""The JSON line of bench.py's reference arm (the FP64 oracle on the host cores),
-run on a small frame pair: one line with the keys the measurement contract names,
-the reference's e2e block moving no bytes, and the workload named in its config."""
+"""The JSON lines of bench.py's two arms against the measurement contract: the
+reference arm (the FP64 oracle on the host cores) on a small frame pair, on the
+CPU, and this library's arm on the tiny frame pair, on the GPU."""
 import json
 import os
 import subprocess
